@@ -1,0 +1,293 @@
+"""Benchmark: MLUPS and fraction of the HBM roofline of the two-component
+Shan-Chen D3Q19 update on one GB300.
+
+Workload: random packed spheres 256^3 (overlapping spheres r = 12 to porosity
+0.40, seed 3), 1 % minority component as droplets r = 4, viscosity ratio 100
+(nu_1 = 0.17, nu_2 = 0.0017), G = -2.2, rho^s = 0, body force 1e-6 along x,
+FP32 arithmetic, storage selected by --precision (default 16-bit shifted).
+A step is one update of the whole domain.  f (>= 1.27 GB) is larger than L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16s|bf16s]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 256
+PARAMS = dict(tau=(0.17 * 3 + 0.5, 0.0017 * 3 + 0.5), G=-2.2, rho_s=0.0, g=(1e-6, 0.0, 0.0))
+F_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
+# DRAM traffic per fluid-cell update of the dominant kernel from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum per launch / cells), keyed by
+# kernel strategy and precision, with the hash of the kernel sources they were
+# taken on; any change of the sources voids them.
+NCU_TRAFFIC = {}
+KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cu", "lbm_fused.cu"]
+
+
+def sources_hash() -> str:
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES:
+        p = os.path.join(ROOT, "paper_1711_03254_gb300", "csrc", s)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def workload(n=N):
+    from paper_1711_03254_gb300 import workloads as W
+    cache = f"/tmp/lbm_spheres_{n}.npz"
+    if os.path.exists(cache):
+        z = np.load(cache)
+        return z["t"], z["r1"], z["r2"], z["u"]
+    t, r1, r2, u = W.packed_spheres(n=n, r=12.0, porosity=0.40, seed=3, droplet_r=4.0, minority=0.01)
+    try:
+        np.savez(cache, t=t, r1=r1, r2=r2, u=u)
+    except OSError:
+        pass
+    return t, r1, r2, u
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.path = f"/tmp/lbm_clocks_{os.getpid()}.csv"
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(t, r1, r2, u, target_s=15.0, crop=64):
+    """Time the FP64 oracle, as it stands, on host cores over a bounded sample:
+    a crop^3 corner of the same geometry for as many updates as fit ~target_s."""
+    import oracle
+    oracle.build()
+    c = (slice(0, crop),) * 3
+    tc, a, b, v = t[c].copy(), r1[c].copy(), r2[c].copy(), u[c].copy()
+    sim = oracle.OracleSim(crop, crop, crop, [PARAMS])
+    sim.set_geometry(tc[None])
+    sim.set_fields(a[None], b[None], v[None])
+    sim.step(1)
+    t0 = time.perf_counter()
+    sim.step(2)
+    per = (time.perf_counter() - t0) / 2
+    steps = max(1, int(target_s / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    fluid = int((tc != 1).sum())
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": fluid * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{crop}^3 corner of the 256^3 packed-sphere workload, {steps} updates, FP64"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    t, r1, r2, u = workload()
+    res = []
+    for _ in range(args.warmup):
+        pass
+    for _ in range(max(1, args.steps)):
+        res.append(cpu_baseline(t, r1, r2, u, target_s=min(20.0, 120.0 / max(1, args.steps)))["value"])
+    cb = cpu_baseline(t, r1, r2, u, target_s=2.0)
+    v = statistics.median(res)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": "MLUPS (fluid-cell updates per second, 2-comp D3Q19)", "value": v,
+            "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "packed spheres 256^3 (sampled as 64^3 corner on host cores)",
+                       "precision": "fp64"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", default="fp16s", choices=["fp32", "fp16s", "bf16s", "fp64"])
+    ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=N)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_1711_03254_gb300 import build, lbm
+    build.build()
+    lbm.use_torch_allocator()
+    n = args.size
+    t, r1, r2, u = workload(n)
+    fluid = int((t != 1).sum())
+    stream = torch.cuda.current_stream()
+
+    sim = lbm.Sim(n, n, n, [PARAMS], precision=args.precision, kernel=args.kernel)
+    lbm.lbm_set_stream(sim.ctx, stream.cuda_stream)
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    red0 = sim.reduce(allow_diverged=True)
+
+    clk = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    l0 = sim.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.stop()
+    launches = sim.launches - l0
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, ws)
+    red1 = sim.reduce(allow_diverged=True)
+    mass_drift = float(np.max(np.abs(red1[0, :2] - red0[0, :2]) / red0[0, :2]))
+
+    mlups = fluid * args.steps * ws / (ms_max / 1e3) / 1e6
+    hbm, peak_kind = peaks()
+    sb = F_BYTES[args.precision]
+    alg_per_cell = 2 * 38 * sb + 1
+    kernels_per_step = launches / max(1, args.steps)
+    # every launch of the step; the bytes the method must move per update
+    achieved = alg_per_cell * fluid / ((ms / args.steps) / 1e3) / 1e9
+    key = f"{args.kernel}/{args.precision}"
+    tr = NCU_TRAFFIC.get(key)
+    traffic = None
+    if tr and tr.get("src") == sources_hash():
+        traffic = tr["bytes_per_cell"] * fluid
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_cell": alg_per_cell, "kernels_per_step": kernels_per_step}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if ws == 1:
+        ke = max(1, min(args.steps, 100))
+        sim2 = lbm.Sim(n, n, n, [PARAMS], precision=args.precision, kernel=args.kernel)
+        lbm.lbm_set_stream(sim2.ctx, stream.cuda_stream)
+        r1b, r2b, ub = np.empty_like(r1[None]), np.empty_like(r2[None]), np.empty_like(u[None])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2.set_geometry(t[None])
+        sim2.set_fields(r1[None], r2[None], u[None])
+        sim2.step(ke)
+        lbm.lbm_get_fields(sim2.ctx, r1b, r2b, ub)
+        dt = time.perf_counter() - t0
+        h2d = t.size * 1 + r1.size * 8 * 2 + u.size * 8
+        d2h = r1.size * 8 * 2 + u.size * 8
+        e2e = {"value": round(fluid * ke / dt / 1e6, 1), "unit": "MLUPS", "steps": ke,
+               "h2d_bytes_per_step": h2d // ke, "d2h_bytes_per_step": d2h // ke}
+        sim2.close()
+
+    cb = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(t, r1, r2, u)
+
+    if rank == 0:
+        line = {"metric": "MLUPS (fluid-cell updates per second, 2-comp D3Q19)", "value": round(mlups, 1),
+                "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"packed spheres {n}^3, r=12, porosity 0.40, 1% minority r=4, "
+                                       f"nu ratio 100, G=-2.2, g=1e-6",
+                           "storage": args.precision, "kernel": args.kernel, "fluid_cells": fluid,
+                           "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
+                "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "mass_drift": mass_drift}
+        print(json.dumps(line))
+    sim.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * lbm.h - C ABI of the GB300 two-component Shan-Chen D3Q19 lattice Boltzmann
+ * library (Otomo et al., "Multi-component lattice Boltzmann models for
+ * accurate simulation of flows with wide viscosity variation",
+ * arXiv:1711.03254).
+ *
+ * One update (lbm_step) is, per cell and per component alpha in {1, 2}:
+ *   S1 pull streaming f_i(x) = f*_i(x - c_i), halfway bounce-back
+ *      f_i(x) = f*_{-i}(x) when x - c_i is SOLID            (Eq. 1, Eq. 9, Sec. 2 walls)
+ *   S2 rho_alpha = sum_i f_i, j = sum_alpha sum_i c_i f_i     (Eq. 4)
+ *   S3 psi_beta = rho_beta in fluid, rho^s_beta in SOLID      (Eq. 7, Eq. 11)
+ *   S4 F^alpha = G rho_alpha sum_i ws_i c_i psi_beta(x + c_i) (beta != alpha), the
+ *      SOLID terms balanced between components (wall model 0) + rho_alpha g
+ *                                                             (Eq. 7, Eq. 11)
+ *   S5 u_F = (j + F/2) / rho, nu_mix = p nu_1 + (1-p) nu_2 with p = rho_1/rho in
+ *      [0, 1], tau = nu_mix / T0 + 1/2                        (Eq. 5, 6, 8)
+ *   S6 feq (Eq. 3), Pi^neq, f' = Phi : Pi (2nd-order Hermite, Eq. 10), forcing
+ *   S7 f* = feq + (1 - 1/tau) f' + F_i                        (Eq. 9)
+ * with D3Q19 weights w_i (1/3, 1/18, 1/36), T0 = 1/3, force-stencil weights
+ * ws_i = 2 w_i, and F_i = w_i c_i.F/(2 T0) + (1 - 1/(2 tau)) w_i/(2 T0^2)
+ * (c_i c_i - T0 I):(u_F F + F u_F).
+ *
+ * Conventions
+ *  - Lattice units, Delta t = 1.  Grids are periodic in x, y and z; walls come
+ *    from SOLID cells of the geometry.
+ *  - Host arrays are C order [batch][nz][ny][nx] (x fastest); velocities have a
+ *    trailing axis of 3: [batch][nz][ny][nx][3].
+ *  - Cell types: 0 FLUID, 1 SOLID, 2 INLET (holds feq(rho_in, u_in)),
+ *    3 OUTLET (takes the streamed distributions of its -x neighbour).
+ *  - Ownership: the caller owns every host buffer it passes; the library owns
+ *    all device memory, allocated through the allocator hook (default
+ *    cudaMalloc) and released by lbm_destroy.
+ *  - Errors: every call returns an lbm_status; nothing is thrown across the
+ *    ABI.  lbm_last_error gives the message of the context's last failure.
+ *    After LBM_ERR_DIVERGED the context stays valid for lbm_get_*,
+ *    lbm_set_state and lbm_destroy.
+ *  - Work is queued on the context's stream (lbm_set_stream; default: the
+ *    legacy default stream).  Calls that return host data synchronise that
+ *    stream; lbm_step does not.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* invalid argument (sizes, tau <= 1/2, bad cell type, ...) */
+    LBM_ERR_CUDA = 2,     /* a CUDA runtime call failed (message in lbm_last_error) */
+    LBM_ERR_OOM = 3,      /* device allocation failed */
+    LBM_ERR_DIVERGED = 4, /* non-finite value, or |u_F| above the sound speed 1/sqrt(3), found by lbm_reduce */
+    LBM_ERR_TIMEOUT = 5,  /* reserved for bounded device-side waits */
+    LBM_ERR_STATE = 6     /* call out of order (e.g. step before set_fields) */
+} lbm_status;
+
+/* Storage of the distributions.  Arithmetic is FP64 in LBM_FP64 and FP32 in
+ * the other modes.  The 16-bit modes store f_i - w_i rho0_alpha (the deviation
+ * from the rest equilibrium of density rho0_alpha) rounded to nearest even. */
+typedef enum {
+    LBM_FP64 = 0,
+    LBM_FP32 = 1,
+    LBM_FP32_F16S = 2,
+    LBM_FP32_BF16S = 3
+} lbm_precision;
+
+/* Kernel strategy for lbm_step. */
+typedef enum {
+    LBM_KERNEL_AUTO = 0,     /* fused when the grid allows it, else two-pass */
+    LBM_KERNEL_TWO_PASS = 1, /* density pre-pass, then stream+collide */
+    LBM_KERNEL_FUSED = 2,    /* single read of f: z-marching tiles with a recomputed density halo */
+    LBM_KERNEL_CLUSTER = 3   /* persistent: one thread-block cluster per instance, n updates per launch */
+} lbm_kernel;
+
+typedef struct {
+    int nx, ny, nz;          /* cells per axis, each >= 1 */
+    int batch;               /* independent instances, >= 1 */
+    lbm_precision precision;
+    int eq_order;            /* 0: Eq. 3 as printed (no quadratic terms); 1: with them */
+    int wall_model;          /* 0: wall forces balanced between components; 1: plain rho^s */
+    double rho0_shift[2];    /* 16-bit storage shift rho0_alpha (use 1.0 when unsure) */
+} lbm_config;
+
+typedef struct {
+    double tau[2];   /* relaxation time of each pure component, > 1/2; nu_k = (tau_k - 1/2)/3 */
+    double G;        /* inter-component coupling of Eq. 7 (negative: repulsive) */
+    double rho_s;    /* single wettability parameter: rho^s_1 = max(-rho_s, 0), rho^s_2 = max(rho_s, 0) */
+    double g[3];     /* body acceleration applied to both components */
+    double rho_in[2];/* INLET densities */
+    double u_in[3];  /* INLET velocity */
+} lbm_instance_params;
+
+/* Create a context for cfg->batch instances with per-instance parameters
+ * per_instance[batch] (host array, copied).  Allocates the device buffers.
+ * Errors: LBM_ERR_ARG (null pointers, a dimension < 1, batch < 1,
+ * tau <= 1/2, eq_order or wall_model out of range), LBM_ERR_OOM, LBM_ERR_CUDA.
+ * On failure *out is NULL. */
+lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_instance, lbm_ctx **out);
+
+/* Upload the cell types, host uint8 [batch][nz][ny][nx] with values 0..3.
+ * Errors: LBM_ERR_ARG (null, value > 3, an instance without any FLUID cell). */
+lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *cell_type);
+
+/* Initialise every non-solid cell to f = feq(rho_alpha, u) (Eq. 3, no force
+ * correction); INLET cells take feq(rho_in, u_in).  Host FP64 arrays
+ * rho1, rho2 [batch][nz][ny][nx] and u [batch][nz][ny][nx][3].  Resets the
+ * residual snapshot.  Errors: LBM_ERR_ARG (null), LBM_ERR_STATE (no geometry). */
+lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho1, const double *rho2, const double *u);
+
+/* Advance every instance by n >= 0 updates (asynchronous on the context's
+ * stream).  The densities and velocity u_F of the last update are kept for
+ * lbm_get_fields / lbm_reduce.  Errors: LBM_ERR_ARG (n < 0),
+ * LBM_ERR_STATE (no fields), LBM_ERR_CUDA (launch failure). */
+lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Copy the macroscopic fields of the last update (or of lbm_set_fields) to
+ * host FP64 arrays rho1, rho2 [batch][nz][ny][nx], u [batch][nz][ny][nx][3]
+ * (u is u_F of Eq. 8; zero in SOLID cells).  Any pointer may be NULL to skip
+ * that field.  Synchronises the stream. */
+lbm_status lbm_get_fields(lbm_ctx *ctx, double *rho1, double *rho2, double *u);
+
+/* FP64 reductions per instance over non-solid cells, written to the host
+ * array out[batch][7] = {M1, M2, Px, Py, Pz, residual, max|u_F|} with
+ * P = sum rho u_F and residual = |u - u_prev|_2 / (k |u|_2 + 1e-30), where
+ * u_prev and k are the velocity at and the updates since the previous
+ * lbm_reduce (0 when k = 0).  The sums use a fixed-order tree, so repeated
+ * runs give identical bits.  Returns LBM_ERR_DIVERGED (after filling out) when a
+ * value is not finite or max|u_F| > 1/sqrt(3).  Synchronises the stream. */
+lbm_status lbm_reduce(lbm_ctx *ctx, double *out);
+
+/* Post-collision distributions of the current state as FP64 (16-bit storage
+ * modes are expanded back to f = stored + w_i rho0_alpha), host array
+ * f[batch][2][19][nz][ny][nx] with the direction order 0 rest, then pairs
+ * +x,-x, +y,-y, +z,-z, (1,1,0),(-1,-1,0), (1,-1,0),(-1,1,0), (1,0,1),(-1,0,-1),
+ * (1,0,-1),(-1,0,1), (0,1,1),(0,-1,-1), (0,1,-1),(0,-1,1).  Values in SOLID
+ * cells are unspecified.  lbm_set_distributions uploads such an array (rounded
+ * to the storage format) as the new state; the fields of the last update are
+ * kept.  Errors: LBM_ERR_ARG (null), LBM_ERR_STATE (no fields yet). */
+lbm_status lbm_get_distributions(lbm_ctx *ctx, double *f);
+lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *f);
+
+/* Checkpoint: with buf == NULL, *bytes receives the size needed; otherwise
+ * the distributions, cell types, fields and counters are written to buf
+ * (host, *bytes large enough).  lbm_set_state restores a buffer written by a
+ * context of the same configuration; the continuation is bitwise identical.
+ * Errors: LBM_ERR_ARG (size or configuration mismatch). */
+lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t *bytes);
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes);
+
+/* Use the given cudaStream_t (cast to void*) for all later work; NULL selects
+ * the legacy default stream.  The caller keeps ownership of the stream. */
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
+/* Choose the kernel strategy (default LBM_KERNEL_AUTO).  LBM_ERR_ARG if the
+ * strategy cannot run this configuration (e.g. CLUSTER on a large grid). */
+lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel);
+
+/* Tiling of the fused kernel: tile 0 = 32x8, 1 = 32x4, 2 = 64x4, 3 = 32x16
+ * cells per thread block, each marching zchunk planes; -1 selects the
+ * built-in choice.  Errors: LBM_ERR_ARG (out of range). */
+lbm_status lbm_set_tiling(lbm_ctx *ctx, int tile, int zchunk);
+
+/* Number of CUDA kernel launches the context has issued so far. */
+long long lbm_launch_count(const lbm_ctx *ctx);
+
+/* Process-wide device allocator hook used by contexts created afterwards:
+ * alloc(bytes, stream) returns device memory or NULL; release(ptr, stream)
+ * frees it.  Passing NULLs restores cudaMalloc / cudaFree. */
+lbm_status lbm_set_allocator(void *(*alloc)(size_t bytes, void *stream),
+                             void (*release)(void *ptr, void *stream));
+
+/* Message of the context's last error ("" when none); ctx may be NULL for the
+ * last lbm_create / lbm_set_allocator failure.  Valid until the next call. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Release the context and its device memory (synchronises its stream). */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,304 @@
+// Device building blocks of the two-component Shan-Chen D3Q19 update
+// (Otomo et al., arXiv:1711.03254, Sec. 2).  Everything here is inlined into
+// the kernels of lbm_kernels.cu; nothing is shared with the CPU oracle.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "lbm_types.h"
+
+namespace lbm {
+
+constexpr int kQ = 19;
+
+// D3Q19 velocities: 0 rest, then opposite pairs (2k-1, 2k):
+// +-x, +-y, +-z, (+x+y,-x-y), (+x-y,-x+y), (+x+z,-x-z), (+x-z,-x+z),
+// (+y+z,-y-z), (+y-z,-y+z).
+__host__ __device__ constexpr int cx(int i) {
+    constexpr int v[kQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return v[i];
+}
+__host__ __device__ constexpr int cy(int i) {
+    constexpr int v[kQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return v[i];
+}
+__host__ __device__ constexpr int cz(int i) {
+    constexpr int v[kQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return v[i];
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// lattice weights (1/3, 1/18, 1/36) as exact rationals num/36
+__host__ __device__ constexpr int w36(int i) { return i == 0 ? 12 : (i <= 6 ? 2 : 1); }
+
+template <class T> __device__ __forceinline__ constexpr T wgt(int i) { return T(w36(i)) / T(36); }
+
+// Cell-type encoding of the per-cell geometry word: bits 0..18 flag the
+// directions i whose neighbour x + c_i is SOLID, bits 24..25 hold the type.
+constexpr uint32_t kFluid = 0, kSolid = 1, kInlet = 2, kOutlet = 3;
+__device__ __forceinline__ uint32_t cell_type(uint32_t word) { return (word >> 24) & 3u; }
+
+// -------------------------------------------------------------- storage
+// How one distribution value is held in HBM.  The 16-bit formats store the
+// deviation from the rest equilibrium w_i rho0_alpha.
+template <class S> struct Storage;
+template <> struct Storage<double> {
+    using T = double;
+    static constexpr bool shifted = false;
+    __device__ static __forceinline__ double load(const double *p, double) { return __ldg(p); }
+    __device__ static __forceinline__ void store(double *p, double v, double) { *p = v; }
+};
+template <> struct Storage<float> {
+    using T = float;
+    static constexpr bool shifted = false;
+    __device__ static __forceinline__ float load(const float *p, float) { return __ldg(p); }
+    __device__ static __forceinline__ void store(float *p, float v, float) { *p = v; }
+};
+template <> struct Storage<__half> {
+    using T = float;
+    static constexpr bool shifted = true;
+    __device__ static __forceinline__ float load(const __half *p, float sh) {
+        return __half2float(__ldg(p)) + sh;
+    }
+    __device__ static __forceinline__ void store(__half *p, float v, float sh) { *p = __float2half_rn(v - sh); }
+};
+template <> struct Storage<__nv_bfloat16> {
+    using T = float;
+    static constexpr bool shifted = true;
+    __device__ static __forceinline__ float load(const __nv_bfloat16 *p, float sh) {
+        return __bfloat162float(__ldg(p)) + sh;
+    }
+    __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v, float sh) {
+        *p = __float2bfloat16_rn(v - sh);
+    }
+};
+
+// -------------------------------------------------------------- neighbours
+// Wrapped coordinates x-1, x, x+1 (and y, z scaled to linear offsets).
+struct Nbr {
+    int X[3], Y[3], Z[3];
+    __device__ __forceinline__ void init(int x, int y, int z, const Grid &g) {
+        X[0] = x == 0 ? g.nx - 1 : x - 1;
+        X[1] = x;
+        X[2] = x == g.nx - 1 ? 0 : x + 1;
+        Y[0] = (y == 0 ? g.ny - 1 : y - 1) * g.nx;
+        Y[1] = y * g.nx;
+        Y[2] = (y == g.ny - 1 ? 0 : y + 1) * g.nx;
+        Z[0] = (z == 0 ? g.nz - 1 : z - 1) * g.nxy;
+        Z[1] = z * g.nxy;
+        Z[2] = (z == g.nz - 1 ? 0 : z + 1) * g.nxy;
+    }
+    // linear index of x - c_i (pull source)
+    __device__ __forceinline__ int src(int i) const { return X[1 - cx(i)] + Y[1 - cy(i)] + Z[1 - cz(i)]; }
+    // linear index of x + c_i
+    __device__ __forceinline__ int dst(int i) const { return X[1 + cx(i)] + Y[1 + cy(i)] + Z[1 + cz(i)]; }
+};
+
+// Moments of the streamed distributions of one component (S1-S2):
+// density, momentum and the raw second moment sum_i c_i c_i f_i.
+template <class T> struct Moments {
+    T rho, jx, jy, jz;
+    T pxx, pyy, pzz, pxy, pxz, pyz;
+};
+
+// Pull the 19 streamed values of component `comp` into cell `self` (linear
+// index) whose neighbours are `nb` and whose solid-neighbour bits are `links`
+// (bit k: x + c_k is SOLID, so the value travelling in direction i comes back
+// from the cell itself when bit opp(i) is set), and reduce them to moments.
+template <class S>
+__device__ __forceinline__ Moments<typename Storage<S>::T>
+pull_moments(const S *__restrict__ fcomp, long long n, int self, const Nbr &nb, uint32_t links,
+             typename Storage<S>::T rho0) {
+    using T = typename Storage<S>::T;
+    T v[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const bool bb = (links >> opp(i)) & 1u;
+        const long long idx = bb ? (long long)opp(i) * n + self : (long long)i * n + nb.src(i);
+        v[i] = Storage<S>::load(fcomp + idx, Storage<S>::shifted ? wgt<T>(i) * rho0 : T(0));
+    }
+    Moments<T> m;
+    T r = v[0];
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) r += v[i];
+    m.rho = r;
+    m.jx = (v[1] - v[2]) + (v[7] - v[8]) + (v[9] - v[10]) + (v[11] - v[12]) + (v[13] - v[14]);
+    m.jy = (v[3] - v[4]) + (v[7] - v[8]) + (v[10] - v[9]) + (v[15] - v[16]) + (v[17] - v[18]);
+    m.jz = (v[5] - v[6]) + (v[11] - v[12]) + (v[14] - v[13]) + (v[15] - v[16]) + (v[18] - v[17]);
+    const T e_xy = (v[7] + v[8]) + (v[9] + v[10]);
+    const T e_xz = (v[11] + v[12]) + (v[13] + v[14]);
+    const T e_yz = (v[15] + v[16]) + (v[17] + v[18]);
+    m.pxx = (v[1] + v[2]) + e_xy + e_xz;
+    m.pyy = (v[3] + v[4]) + e_xy + e_yz;
+    m.pzz = (v[5] + v[6]) + e_xz + e_yz;
+    m.pxy = (v[7] + v[8]) - (v[9] + v[10]);
+    m.pxz = (v[11] + v[12]) - (v[13] + v[14]);
+    m.pyz = (v[15] + v[16]) - (v[17] + v[18]);
+    return m;
+}
+
+// Density only (for the pseudo-potential pass), same summation order.
+template <class S>
+__device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restrict__ fcomp, long long n, int self,
+                                                              const Nbr &nb, uint32_t links,
+                                                              typename Storage<S>::T rho0) {
+    using T = typename Storage<S>::T;
+    T v[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const bool bb = (links >> opp(i)) & 1u;
+        const long long idx = bb ? (long long)opp(i) * n + self : (long long)i * n + nb.src(i);
+        v[i] = Storage<S>::load(fcomp + idx, Storage<S>::shifted ? wgt<T>(i) * rho0 : T(0));
+    }
+    T r = v[0];
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) r += v[i];
+    return r;
+}
+
+// Equilibrium of Eq. 3 for direction i (EQ = 1 adds the quadratic terms).
+template <class T, int EQ>
+__device__ __forceinline__ T feq_dir(int i, T rho, T ux, T uy, T uz, T uu) {
+    const T cu = T(cx(i)) * ux + T(cy(i)) * uy + T(cz(i)) * uz;
+    // 1/T0 = 3, 1/(6 T0^3) = 1/(2 T0^2) = 9/2
+    T e = T(1) + cu * (T(3) + T(4.5) * cu * cu - T(4.5) * uu);
+    if (EQ == 1) e += T(4.5) * cu * cu - T(1.5) * uu;
+    return rho * wgt<T>(i) * e;
+}
+
+// S6-S7 for one component: writes f*_i = feq_i + w_i/(2 T0^2) H_i : A + w_i c_i.F/(2 T0)
+// with A = (1 - 1/tau) Pi^neq + (1 - 1/(2 tau)) (u_F F + F u_F).
+template <class S, int EQ>
+__device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n, int self,
+                                              const Moments<typename Storage<S>::T> &m,
+                                              typename Storage<S>::T ux, typename Storage<S>::T uy,
+                                              typename Storage<S>::T uz, typename Storage<S>::T Fx,
+                                              typename Storage<S>::T Fy, typename Storage<S>::T Fz,
+                                              typename Storage<S>::T omega, typename Storage<S>::T fcoef,
+                                              typename Storage<S>::T rho0) {
+    using T = typename Storage<S>::T;
+    const T T0 = T(1) / T(3);
+    const T uu = ux * ux + uy * uy + uz * uz;
+    // Pi^neq = Pi - Pi^eq with Pi^eq = rho T0 I (+ rho u u for EQ = 1)
+    T nxx = m.pxx - m.rho * T0, nyy = m.pyy - m.rho * T0, nzz = m.pzz - m.rho * T0;
+    T nxy = m.pxy, nxz = m.pxz, nyz = m.pyz;
+    if (EQ == 1) {
+        nxx -= m.rho * ux * ux; nyy -= m.rho * uy * uy; nzz -= m.rho * uz * uz;
+        nxy -= m.rho * ux * uy; nxz -= m.rho * ux * uz; nyz -= m.rho * uy * uz;
+    }
+    const T axx = omega * nxx + fcoef * (T(2) * ux * Fx);
+    const T ayy = omega * nyy + fcoef * (T(2) * uy * Fy);
+    const T azz = omega * nzz + fcoef * (T(2) * uz * Fz);
+    const T axy = omega * nxy + fcoef * (ux * Fy + uy * Fx);
+    const T axz = omega * nxz + fcoef * (ux * Fz + uz * Fx);
+    const T ayz = omega * nyz + fcoef * (uy * Fz + uz * Fy);
+    const T ktr = -T(1.5) * (axx + ayy + azz);  // -(T0/(2 T0^2)) tr A
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const T c0 = T(cx(i)), c1 = T(cy(i)), c2 = T(cz(i));
+        const T cAc = c0 * c0 * axx + c1 * c1 * ayy + c2 * c2 * azz +
+                      T(2) * (c0 * c1 * axy + c0 * c2 * axz + c1 * c2 * ayz);
+        const T cF = c0 * Fx + c1 * Fy + c2 * Fz;
+        const T fe = feq_dir<T, EQ>(i, m.rho, ux, uy, uz, uu);
+        const T v = fe + wgt<T>(i) * (T(4.5) * cAc + ktr + T(1.5) * cF);
+        Storage<S>::store(fout + (long long)i * n + self, v, Storage<S>::shifted ? wgt<T>(i) * rho0 : T(0));
+    }
+}
+
+template <class S, int EQ>
+__device__ __forceinline__ void store_equilibrium(S *__restrict__ fout, long long n, int self,
+                                                  typename Storage<S>::T rho, typename Storage<S>::T ux,
+                                                  typename Storage<S>::T uy, typename Storage<S>::T uz,
+                                                  typename Storage<S>::T rho0) {
+    using T = typename Storage<S>::T;
+    const T uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i)
+        Storage<S>::store(fout + (long long)i * n + self, feq_dir<T, EQ>(i, rho, ux, uy, uz, uu),
+                          Storage<S>::shifted ? wgt<T>(i) * rho0 : T(0));
+}
+
+// S4: forces on both components from the pseudo-potential of the 18
+// neighbours (psi_nb[beta] read through `psi_at`), the SOLID-neighbour bits
+// and the body force.  Force-stencil weights are 2 w_i.
+template <class T> struct Forces {
+    T F[2][3];
+};
+
+template <class T, class PsiAt>
+__device__ __forceinline__ Forces<T> sc_forces(const PsiAt &psi_at, uint32_t links, T rho0, T rho1,
+                                               const InstParam<T> &p, int wall_model) {
+    T s[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};  // bulk sums for psi_1, psi_2
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        const bool solid = (links >> i) & 1u;
+        T p0, p1;
+        psi_at(i, p0, p1);
+        p0 = solid ? T(0) : p0;
+        p1 = solid ? T(0) : p1;
+        const T ws = T(2) * wgt<T>(i);
+        if (cx(i)) { s[0][0] += T(cx(i)) * ws * p0; s[1][0] += T(cx(i)) * ws * p1; }
+        if (cy(i)) { s[0][1] += T(cy(i)) * ws * p0; s[1][1] += T(cy(i)) * ws * p1; }
+        if (cz(i)) { s[0][2] += T(cz(i)) * ws * p0; s[1][2] += T(cz(i)) * ws * p1; }
+    }
+    Forces<T> out;
+    const T r[2] = {rho0, rho1};
+    // bulk part: F^alpha = G rho_alpha sum ws c psi_beta, beta != alpha
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out.F[0][a] = p.G * r[0] * s[1][a];
+        out.F[1][a] = p.G * r[1] * s[0][a];
+    }
+    const uint32_t wl = links & 0x7FFFEu;
+    if (wl) {
+        // wall part (Eq. 11): psi_beta(SOLID) = rho^s_beta
+        T d[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+            if ((links >> i) & 1u) {
+                const T ws = T(2) * wgt<T>(i);
+                d[0] += T(cx(i)) * ws;
+                d[1] += T(cy(i)) * ws;
+                d[2] += T(cz(i)) * ws;
+            }
+        }
+        T fw[2][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            fw[0][a] = p.G * r[0] * (p.rs[1] * d[a]);
+            fw[1][a] = p.G * r[1] * (p.rs[0] * d[a]);
+        }
+        if (wall_model == 0) {
+            const T rho = r[0] + r[1];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T net = fw[0][a] + fw[1][a];
+                fw[0][a] -= r[0] / rho * net;
+                fw[1][a] -= r[1] / rho * net;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            out.F[0][a] += fw[0][a];
+            out.F[1][a] += fw[1][a];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out.F[0][a] += r[0] * p.g[a];
+        out.F[1][a] += r[1] * p.g[a];
+    }
+    return out;
+}
+
+// S5: tau_mix from the density-weighted viscosity, p = rho_1 / rho in [0, 1].
+template <class T> __device__ __forceinline__ T tau_mix(T rho0, T rho1, const InstParam<T> &p) {
+    T q = rho0 / (rho0 + rho1);
+    q = q < T(0) ? T(0) : (q > T(1) ? T(1) : q);
+    const T nu = q * p.nu[0] + (T(1) - q) * p.nu[1];
+    return nu / (T(1) / T(3)) + T(0.5);
+}
+
+}  // namespace lbm

@@ -1,0 +1,69 @@
+// Internal interfaces between the host runtime (lbm_api.cu) and the kernel
+// launchers.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "lbm_types.h"
+
+namespace lbm {
+
+struct StepArgs {
+    lbm_precision precision;
+    int eq_order, wall_model, write_macro;
+    int batch;
+    Grid g;
+    const void *f_in;
+    void *f_out;
+    const uint32_t *link;
+    void *psi;
+    void *macro;
+    const void *par;   // InstParam<T>[batch] on the device
+    double rho0[2];
+    cudaStream_t stream;
+};
+
+struct InitArgs {
+    lbm_precision precision;
+    int eq_order;
+    int batch;
+    Grid g;
+    const double *r1, *r2, *u;  // device FP64 fields (u interleaved)
+    const uint32_t *link;
+    void *f_out, *macro, *usnap;
+    const void *par;
+    double rho0[2];
+    cudaStream_t stream;
+};
+
+struct ReduceArgs {
+    bool fp64;
+    int batch;
+    Grid g;
+    const void *macro;
+    void *usnap;
+    const uint32_t *link;
+    double *partial;   // [batch][nblk][9]
+    int nblk;
+    double *out;       // [batch][9]: M1 M2 Px Py Pz |du|^2 |u|^2 max|u| non-finite count
+    long long k;       // updates since the snapshot
+    cudaStream_t stream;
+};
+
+cudaError_t launch_two_pass(const StepArgs &a);
+// tile: 0 = 32x8, 1 = 32x4, 2 = 64x4, 3 = 32x16 cells per CTA; zchunk planes per CTA
+cudaError_t launch_fused(const StepArgs &a, int tile, int zchunk);
+int fused_tile_count();
+cudaError_t launch_init(const InitArgs &a);
+cudaError_t launch_links(const uint8_t *type, uint32_t *link, const Grid &g, int batch, cudaStream_t s);
+cudaError_t launch_macro_to_f64(const void *macro, bool fp64, double *r1, double *r2, double *u, const Grid &g,
+                                int batch, cudaStream_t s);
+cudaError_t launch_reduce(const ReduceArgs &a, int *launches);
+// out != NULL: expand f to FP64 into out; otherwise store `in` (FP64) into fo.
+cudaError_t launch_f_convert(lbm_precision prec, const void *f, double *out, const double *in, void *fo,
+                             const Grid &g, int batch, const double *rho0, cudaStream_t s);
+int reduce_blocks(long long n);
+
+}  // namespace lbm

@@ -1,0 +1,337 @@
+// Two-pass update kernels, initialisation and geometry preprocessing.
+//
+//   k_psi      S1-S3: pull the 19 streamed values of each component, sum them
+//              to rho_alpha and store the pseudo-potential psi (rho in fluid,
+//              rho^s at SOLID cells, rho_in at INLET cells).
+//   k_collide  S1-S7: pull again, reduce to moments, read psi of the 18
+//              neighbours, forces, u_F, tau_mix, regularised collision, store.
+//
+// Layout in HBM (per instance b): f[b][alpha][i][cell], cell = x + nx (y + ny z);
+// psi[b][alpha][cell]; macro[b][{rho1, rho2, ux, uy, uz}][cell]; geometry word
+// link[b][cell] (bits 0..18 SOLID neighbours, bits 24..25 cell type).
+#include "lbm_internal.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ void cell_coords(long long k, const Grid &g, int &x, int &y, int &z) {
+    const int kk = (int)k;
+    const int t = kk / g.nx;
+    x = kk - t * g.nx;
+    z = t / g.ny;
+    y = t - z * g.ny;
+}
+
+// OUTLET cells stream the values of their upstream (-x) neighbour unless that
+// neighbour is SOLID or OUTLET itself.
+__device__ __forceinline__ void source_cell(const uint32_t *__restrict__ link_b, uint32_t word, int &x, int y, int z,
+                                            const Grid &g, uint32_t &src_word) {
+    src_word = word;
+    if (cell_type(word) == kOutlet) {
+        const int xu = x == 0 ? g.nx - 1 : x - 1;
+        const uint32_t wu = __ldg(link_b + xu + y * g.nx + (long long)z * g.nxy);
+        const uint32_t tu = cell_type(wu);
+        if (tu != kSolid && tu != kOutlet) {
+            x = xu;
+            src_word = wu;
+        }
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_psi(const S *__restrict__ f, const uint32_t *__restrict__ link,
+                                             typename Storage<S>::T *__restrict__ psi, Grid g,
+                                             const InstParam<typename Storage<S>::T> *__restrict__ par,
+                                             typename Storage<S>::T rho0_0, typename Storage<S>::T rho0_1) {
+    using T = typename Storage<S>::T;
+    const int b = blockIdx.y;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const uint32_t *link_b = link + (long long)b * g.n;
+    const uint32_t word = __ldg(link_b + k);
+    const uint32_t t = cell_type(word);
+    const InstParam<T> &p = par[b];
+    T p0, p1;
+    if (t == kSolid) {
+        p0 = p.rs[0];
+        p1 = p.rs[1];
+    } else if (t == kInlet) {
+        p0 = p.rho_in[0];
+        p1 = p.rho_in[1];
+    } else {
+        int x, y, z;
+        cell_coords(k, g, x, y, z);
+        uint32_t sw;
+        source_cell(link_b, word, x, y, z, g, sw);
+        Nbr nb;
+        nb.init(x, y, z, g);
+        const int self = x + y * g.nx + z * g.nxy;
+        const S *fb = f + (long long)b * 2 * kQ * g.n;
+        p0 = pull_density<S>(fb, g.n, self, nb, sw, rho0_0);
+        p1 = pull_density<S>(fb + kQ * g.n, g.n, self, nb, sw, rho0_1);
+    }
+    psi[((long long)b * 2 + 0) * g.n + k] = p0;
+    psi[((long long)b * 2 + 1) * g.n + k] = p1;
+}
+
+template <class S, int EQ>
+__global__ void __launch_bounds__(256) k_collide(const S *__restrict__ f, S *__restrict__ fo,
+                                                 const uint32_t *__restrict__ link,
+                                                 const typename Storage<S>::T *__restrict__ psi,
+                                                 typename Storage<S>::T *__restrict__ macro, Grid g,
+                                                 const InstParam<typename Storage<S>::T> *__restrict__ par,
+                                                 typename Storage<S>::T rho0_0, typename Storage<S>::T rho0_1,
+                                                 int wall_model, int write_macro) {
+    using T = typename Storage<S>::T;
+    const int b = blockIdx.y;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const uint32_t *link_b = link + (long long)b * g.n;
+    const uint32_t word = __ldg(link_b + k);
+    const uint32_t t = cell_type(word);
+    const InstParam<T> &p = par[b];
+    const long long fofs = (long long)b * 2 * kQ * g.n;
+    T *mac = macro + (long long)b * 5 * g.n;
+    if (t == kSolid) {
+        if (write_macro)
+            for (int c = 0; c < 5; ++c) mac[c * g.n + k] = T(0);
+        return;
+    }
+    if (t == kInlet) {
+        store_equilibrium<S, EQ>(fo + fofs, g.n, (int)k, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], rho0_0);
+        store_equilibrium<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2],
+                                 rho0_1);
+        if (write_macro) {
+            mac[k] = p.rho_in[0];
+            mac[g.n + k] = p.rho_in[1];
+            mac[2 * g.n + k] = p.u_in[0];
+            mac[3 * g.n + k] = p.u_in[1];
+            mac[4 * g.n + k] = p.u_in[2];
+        }
+        return;
+    }
+    int x, y, z;
+    cell_coords(k, g, x, y, z);
+    Nbr own;
+    own.init(x, y, z, g);
+    int sx = x;
+    uint32_t sw;
+    source_cell(link_b, word, sx, y, z, g, sw);
+    Moments<T> m0, m1;
+    if (sx == x) {
+        m0 = pull_moments<S>(f + fofs, g.n, (int)k, own, sw, rho0_0);
+        m1 = pull_moments<S>(f + fofs + kQ * g.n, g.n, (int)k, own, sw, rho0_1);
+    } else {
+        Nbr up;
+        up.init(sx, y, z, g);
+        const int self = sx + y * g.nx + z * g.nxy;
+        m0 = pull_moments<S>(f + fofs, g.n, self, up, sw, rho0_0);
+        m1 = pull_moments<S>(f + fofs + kQ * g.n, g.n, self, up, sw, rho0_1);
+    }
+    const T *psi0 = psi + (long long)b * 2 * g.n;
+    const T *psi1 = psi0 + g.n;
+    auto psi_at = [&](int i, T &a, T &c) {
+        const int j = own.dst(i);
+        a = __ldg(psi0 + j);
+        c = __ldg(psi1 + j);
+    };
+    const Forces<T> F = sc_forces<T>(psi_at, word, m0.rho, m1.rho, p, wall_model);
+    const T rho = m0.rho + m1.rho;
+    const T Fx = F.F[0][0] + F.F[1][0], Fy = F.F[0][1] + F.F[1][1], Fz = F.F[0][2] + F.F[1][2];
+    // Eq. 8: u_F = u + g/2 with u = j/rho and g = F_tot/rho
+    const T ux = (m0.jx + m1.jx) / rho + T(0.5) * (Fx / rho);
+    const T uy = (m0.jy + m1.jy) / rho + T(0.5) * (Fy / rho);
+    const T uz = (m0.jz + m1.jz) / rho + T(0.5) * (Fz / rho);
+    const T tau = tau_mix<T>(m0.rho, m1.rho, p);
+    const T omega = T(1) - T(1) / tau;
+    const T fcoef = T(1) - T(1) / (T(2) * tau);
+    collide_store<S, EQ>(fo + fofs, g.n, (int)k, m0, ux, uy, uz, F.F[0][0], F.F[0][1], F.F[0][2], omega, fcoef,
+                         rho0_0);
+    collide_store<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, m1, ux, uy, uz, F.F[1][0], F.F[1][1], F.F[1][2], omega,
+                         fcoef, rho0_1);
+    if (write_macro) {
+        mac[k] = m0.rho;
+        mac[g.n + k] = m1.rho;
+        mac[2 * g.n + k] = ux;
+        mac[3 * g.n + k] = uy;
+        mac[4 * g.n + k] = uz;
+    }
+}
+
+// f := feq(rho_alpha, u) from FP64 fields (u interleaved [b][cell][3]).
+template <class S, int EQ>
+__global__ void k_init(const double *__restrict__ r1, const double *__restrict__ r2, const double *__restrict__ u,
+                       const uint32_t *__restrict__ link, S *__restrict__ fo, typename Storage<S>::T *__restrict__ macro,
+                       typename Storage<S>::T *__restrict__ usnap, Grid g,
+                       const InstParam<typename Storage<S>::T> *__restrict__ par, typename Storage<S>::T rho0_0,
+                       typename Storage<S>::T rho0_1) {
+    using T = typename Storage<S>::T;
+    const int b = blockIdx.y;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const long long gk = (long long)b * g.n + k;
+    const uint32_t t = cell_type(link[gk]);
+    const InstParam<T> &p = par[b];
+    T a0, a1, ux, uy, uz;
+    if (t == kSolid) {
+        a0 = a1 = ux = uy = uz = T(0);
+    } else if (t == kInlet) {
+        a0 = p.rho_in[0]; a1 = p.rho_in[1];
+        ux = p.u_in[0]; uy = p.u_in[1]; uz = p.u_in[2];
+    } else {
+        a0 = (T)r1[gk]; a1 = (T)r2[gk];
+        ux = (T)u[3 * gk]; uy = (T)u[3 * gk + 1]; uz = (T)u[3 * gk + 2];
+    }
+    const long long fofs = (long long)b * 2 * kQ * g.n;
+    store_equilibrium<S, EQ>(fo + fofs, g.n, (int)k, a0, ux, uy, uz, rho0_0);
+    store_equilibrium<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, a1, ux, uy, uz, rho0_1);
+    T *mac = macro + (long long)b * 5 * g.n;
+    mac[k] = a0; mac[g.n + k] = a1;
+    mac[2 * g.n + k] = ux; mac[3 * g.n + k] = uy; mac[4 * g.n + k] = uz;
+    T *us = usnap + (long long)b * 3 * g.n;
+    us[k] = ux; us[g.n + k] = uy; us[2 * g.n + k] = uz;
+}
+
+__global__ void k_links(const uint8_t *__restrict__ type, uint32_t *__restrict__ link, Grid g) {
+    const int b = blockIdx.y;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    int x, y, z;
+    cell_coords(k, g, x, y, z);
+    Nbr nb;
+    nb.init(x, y, z, g);
+    const uint8_t *tb = type + (long long)b * g.n;
+    uint32_t w = (uint32_t)tb[k] << 24;
+#pragma unroll
+    for (int i = 1; i < kQ; ++i)
+        if (tb[nb.dst(i)] == kSolid) w |= 1u << i;
+    link[(long long)b * g.n + k] = w;
+}
+
+// Macro fields (T) -> FP64 host layout (u interleaved).
+template <class T>
+__global__ void k_macro_to_f64(const T *__restrict__ macro, double *__restrict__ r1, double *__restrict__ r2,
+                               double *__restrict__ u, Grid g) {
+    const int b = blockIdx.y;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const T *mac = macro + (long long)b * 5 * g.n;
+    const long long gk = (long long)b * g.n + k;
+    r1[gk] = (double)mac[k];
+    r2[gk] = (double)mac[g.n + k];
+    u[3 * gk] = (double)mac[2 * g.n + k];
+    u[3 * gk + 1] = (double)mac[3 * g.n + k];
+    u[3 * gk + 2] = (double)mac[4 * g.n + k];
+}
+
+// Distributions <-> FP64 (plane p = (b*2 + alpha)*19 + i holds direction i).
+template <class S>
+__global__ void k_f_convert(const S *__restrict__ f, double *__restrict__ out, const double *__restrict__ in,
+                            S *__restrict__ fo, long long n, int planes, double rho0_0, double rho0_1) {
+    using T = typename Storage<S>::T;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (k >= n || p >= planes) return;
+    const int i = p % kQ;
+    const int alpha = (p / kQ) & 1;
+    const T sh = Storage<S>::shifted ? wgt<T>(i) * (T)(alpha ? rho0_1 : rho0_0) : T(0);
+    const long long idx = (long long)p * n + k;
+    if (out)
+        out[idx] = (double)Storage<S>::load(f + idx, sh);
+    else
+        Storage<S>::store(fo + idx, (T)in[idx], sh);
+}
+
+// ------------------------------------------------------------------ launchers
+
+static dim3 cell_grid(const Grid &g, int batch, int threads) {
+    return dim3((unsigned)((g.n + threads - 1) / threads), (unsigned)batch, 1);
+}
+
+template <class S>
+static cudaError_t launch_two_pass_t(const StepArgs &a) {
+    using T = typename Storage<S>::T;
+    const dim3 grid = cell_grid(a.g, a.batch, 256);
+    const T r00 = (T)a.rho0[0], r01 = (T)a.rho0[1];
+    k_psi<S><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, a.link, (T *)a.psi, a.g, (const InstParam<T> *)a.par, r00,
+                                         r01);
+    if (a.eq_order == 0)
+        k_collide<S, 0><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.link, (const T *)a.psi,
+                                                    (T *)a.macro, a.g, (const InstParam<T> *)a.par, r00, r01,
+                                                    a.wall_model, a.write_macro);
+    else
+        k_collide<S, 1><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.link, (const T *)a.psi,
+                                                    (T *)a.macro, a.g, (const InstParam<T> *)a.par, r00, r01,
+                                                    a.wall_model, a.write_macro);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_two_pass(const StepArgs &a) {
+    switch (a.precision) {
+    case LBM_FP64: return launch_two_pass_t<double>(a);
+    case LBM_FP32: return launch_two_pass_t<float>(a);
+    case LBM_FP32_F16S: return launch_two_pass_t<__half>(a);
+    case LBM_FP32_BF16S: return launch_two_pass_t<__nv_bfloat16>(a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S>
+static cudaError_t launch_init_t(const InitArgs &a) {
+    using T = typename Storage<S>::T;
+    const dim3 grid = cell_grid(a.g, a.batch, 256);
+    const T r00 = (T)a.rho0[0], r01 = (T)a.rho0[1];
+    if (a.eq_order == 0)
+        k_init<S, 0><<<grid, 256, 0, a.stream>>>(a.r1, a.r2, a.u, a.link, (S *)a.f_out, (T *)a.macro, (T *)a.usnap,
+                                                 a.g, (const InstParam<T> *)a.par, r00, r01);
+    else
+        k_init<S, 1><<<grid, 256, 0, a.stream>>>(a.r1, a.r2, a.u, a.link, (S *)a.f_out, (T *)a.macro, (T *)a.usnap,
+                                                 a.g, (const InstParam<T> *)a.par, r00, r01);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const InitArgs &a) {
+    switch (a.precision) {
+    case LBM_FP64: return launch_init_t<double>(a);
+    case LBM_FP32: return launch_init_t<float>(a);
+    case LBM_FP32_F16S: return launch_init_t<__half>(a);
+    case LBM_FP32_BF16S: return launch_init_t<__nv_bfloat16>(a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S>
+static cudaError_t launch_f_convert_t(const void *f, double *out, const double *in, void *fo, const Grid &g, int batch,
+                                      const double *rho0, cudaStream_t s) {
+    const int planes = batch * 2 * kQ;
+    const dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)planes, 1);
+    k_f_convert<S><<<grid, 256, 0, s>>>((const S *)f, out, in, (S *)fo, g.n, planes, rho0[0], rho0[1]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f_convert(lbm_precision prec, const void *f, double *out, const double *in, void *fo,
+                             const Grid &g, int batch, const double *rho0, cudaStream_t s) {
+    switch (prec) {
+    case LBM_FP64: return launch_f_convert_t<double>(f, out, in, fo, g, batch, rho0, s);
+    case LBM_FP32: return launch_f_convert_t<float>(f, out, in, fo, g, batch, rho0, s);
+    case LBM_FP32_F16S: return launch_f_convert_t<__half>(f, out, in, fo, g, batch, rho0, s);
+    case LBM_FP32_BF16S: return launch_f_convert_t<__nv_bfloat16>(f, out, in, fo, g, batch, rho0, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_links(const uint8_t *type, uint32_t *link, const Grid &g, int batch, cudaStream_t s) {
+    k_links<<<cell_grid(g, batch, 256), 256, 0, s>>>(type, link, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_to_f64(const void *macro, bool fp64, double *r1, double *r2, double *u, const Grid &g,
+                                int batch, cudaStream_t s) {
+    if (fp64)
+        k_macro_to_f64<double><<<cell_grid(g, batch, 256), 256, 0, s>>>((const double *)macro, r1, r2, u, g);
+    else
+        k_macro_to_f64<float><<<cell_grid(g, batch, 256), 256, 0, s>>>((const float *)macro, r1, r2, u, g);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,72 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/lbm.h, the binding carries the same names, and argument
+errors are reported before any device work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_1711_03254_gb300 import build
+    build.build()
+    from paper_1711_03254_gb300 import lbm as mod
+    mod.library()
+    return mod
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("lbm_create", "lbm_set_geometry", "lbm_set_fields", "lbm_step", "lbm_get_fields",
+                     "lbm_reduce", "lbm_destroy", "lbm_last_error", "lbm_set_stream", "lbm_set_allocator",
+                     "lbm_get_state", "lbm_set_state"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lbm):
+    lib = lbm.library()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_has_same_names(lbm):
+    for name in _declared():
+        assert callable(getattr(lbm, name, None)), name
+
+
+def test_create_rejects_bad_arguments(lbm):
+    good = dict(tau=(1.0, 1.0), G=-2.2)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_config(0, 4, 4), lbm.make_params([good]))
+    assert e.value.status == 1
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_config(4, 4, 4), lbm.make_params([dict(tau=(0.5, 1.0))]))
+    assert e.value.status == 1
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_config(4, 4, 4, eq_order=2), lbm.make_params([good]))
+    assert e.value.status == 1
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_config(4, 4, 4), lbm.make_params([dict(tau=(1.0, 1.0), G=float("nan"))]))
+    assert e.value.status == 1
+
+
+def test_allocator_hook_needs_both(lbm):
+    lib = lbm.library()
+    assert lib.lbm_set_allocator(lbm._ALLOC_T(lambda n, s: 0), lbm._FREE_T()) == 1
+    assert lib.lbm_set_allocator(lbm._ALLOC_T(), lbm._FREE_T()) == 0
+
+
+def test_structs_match_header(lbm):
+    import ctypes
+    assert ctypes.sizeof(lbm.lbm_config) == 7 * 4 + 4 + 16  # 7 ints, padding, 2 doubles
+    assert ctypes.sizeof(lbm.lbm_instance_params) == 12 * 8

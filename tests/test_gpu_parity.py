@@ -1,0 +1,258 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Tolerances (relative to the field's scale, max over cells):
+  FP64 storage + FP64 arithmetic   1e-11  (after the whole run)
+  FP32                              1e-5
+  FP16 / BF16 shifted storage       1e-3 / 4e-3 (rounding of the stored deviation)
+"""
+import numpy as np
+import pytest
+
+from paper_1711_03254_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_03254_gb300 import build
+    build.build()
+    from paper_1711_03254_gb300 import lbm as mod
+    return mod
+
+
+def _rel(a, b):
+    scale = max(np.abs(b).max(), 1e-30)
+    return float(np.abs(a - b).max() / scale)
+
+
+def _pair(lbm, oracle_mod, shape, params, t, r1, r2, u, steps, precision="fp64", eq_order=0, wall_model=0,
+          kernel="auto", rho0_shift=(1.0, 1.0)):
+    nx, ny, nz = shape
+    B = len(params)
+    sim = lbm.Sim(nx, ny, nz, params, precision=precision, eq_order=eq_order, wall_model=wall_model,
+                  kernel=kernel, rho0_shift=rho0_shift)
+    sim.set_geometry(t.reshape((B, nz, ny, nx)))
+    sim.set_fields(r1, r2, u)
+    sim.step(steps)
+    g = sim.get_fields()
+    ref = oracle_mod.OracleSim(nx, ny, nz, params, eq_order=eq_order, wall_model=wall_model)
+    ref.set_geometry(t.reshape((B, nz, ny, nx)))
+    ref.set_fields(r1.reshape((B, nz, ny, nx)), r2.reshape((B, nz, ny, nx)), u.reshape((B, nz, ny, nx, 3)))
+    ref.step(steps)
+    o = ref.get_fields()
+    return sim, ref, g, o
+
+
+def _errs(g, o):
+    return _rel(g[0], o[0]), _rel(g[1], o[1]), _rel(g[2], o[2])
+
+
+KERNELS = ["two_pass", "fused"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp64_droplet_32cubed(lbm, oracle_mod, kernel):
+    """32^3 periodic droplet, R = 8, G = -2.2, tau = 1, 1000 updates, FP64."""
+    t, r1, r2, u = W.droplet(32, 32, 32, 8.0)
+    p = [dict(tau=(1.0, 1.0), G=-2.2)]
+    sim, ref, g, o = _pair(lbm, oracle_mod, (32, 32, 32), p, t, r1, r2, u, 1000, kernel=kernel)
+    e = _errs(g, o)
+    assert max(e) < 1e-11, e
+    red = sim.reduce()[0]
+    rref = ref.reduce()[0]
+    assert abs(red[0] - rref[0]) / rref[0] < 1e-12 and abs(red[1] - rref[1]) / rref[1] < 1e-12
+
+
+def _random_geometry(shape, frac, seed, inlet_outlet=False, lo=0.05, hi=1.0):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    t = np.where(rng.random((nz, ny, nx)) < frac, W.SOLID, W.FLUID).astype(np.uint8)
+    if inlet_outlet:
+        t[:, :, 0] = np.where(t[:, :, 0] == W.SOLID, W.SOLID, W.INLET)
+        t[:, :, nx - 1] = np.where(t[:, :, nx - 1] == W.SOLID, W.SOLID, W.OUTLET)
+    r1 = np.where(t == W.SOLID, 0.0, rng.uniform(lo, hi, t.shape))
+    r2 = np.where(t == W.SOLID, 0.0, rng.uniform(lo, hi, t.shape))
+    u = rng.uniform(-0.02, 0.02, t.shape + (3,))
+    u[t == W.SOLID] = 0
+    return t, r1, r2, u
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(6, 5, 7), (13, 7, 9), (33, 3, 2), (70, 19, 23)])
+@pytest.mark.parametrize("eq_order,wall_model", [(0, 0), (1, 1), (0, 1)])
+def test_fp64_odd_grids_with_walls(lbm, oracle_mod, shape, eq_order, wall_model, kernel):
+    """Odd grids (ragged tiles), random SOLID cells, wetting walls, extreme tau:
+    cell by cell."""
+    t, r1, r2, u = _random_geometry(shape, 0.2, 5 + sum(shape), lo=0.3, hi=0.7)
+    p = [dict(tau=(0.5051, 5.6), G=-1.2, rho_s=0.3, g=(1e-4, -2e-5, 3e-5))]
+    _, _, g, o = _pair(lbm, oracle_mod, shape, p, t[None], r1[None], r2[None], u[None], 20, eq_order=eq_order,
+                       wall_model=wall_model, kernel=kernel)
+    e = _errs(g, o)
+    assert max(e) < 1e-12, e
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp64_inlet_outlet(lbm, oracle_mod, kernel):
+    shape = (12, 6, 5)
+    t, r1, r2, u = _random_geometry(shape, 0.1, 9, inlet_outlet=True, lo=0.4, hi=0.6)
+    p = [dict(tau=(0.6, 2.0), G=-1.0, rho_s=-0.2, rho_in=(0.1, 0.9), u_in=(0.01, 0.0, 0.0))]
+    _, _, g, o = _pair(lbm, oracle_mod, shape, p, t[None], r1[None], r2[None], u[None], 30, kernel=kernel)
+    e = _errs(g, o)
+    assert max(e) < 1e-12, e
+
+
+@pytest.mark.parametrize("tile,zchunk", [(0, 8), (1, 5), (2, 16), (3, 3)])
+def test_fp64_fused_tilings(lbm, oracle_mod, tile, zchunk):
+    """Every fused tiling, several z chunks and ragged edges, against the oracle."""
+    shape = (45, 21, 19)
+    t, r1, r2, u = _random_geometry(shape, 0.15, 77, lo=0.3, hi=0.7)
+    p = [dict(tau=(0.7, 1.9), G=-1.4, rho_s=0.2, g=(2e-5, 0, 1e-5))]
+    nx, ny, nz = shape
+    sim = lbm.Sim(nx, ny, nz, p, kernel="fused")
+    lbm.lbm_set_tiling(sim.ctx, tile, zchunk)
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    sim.step(12)
+    ref = oracle_mod.OracleSim(nx, ny, nz, p)
+    ref.set_geometry(t[None])
+    ref.set_fields(r1[None], r2[None], u[None])
+    ref.step(12)
+    e = _errs(sim.get_fields(), ref.get_fields())
+    assert max(e) < 1e-12, e
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp64_batched_instances(lbm, oracle_mod, kernel):
+    """Three instances with different parameters in one context."""
+    shape = (8, 10, 6)
+    geo = [_random_geometry(shape, 0.15, 20 + k, lo=0.3, hi=0.7) for k in range(3)]
+    t = np.stack([x[0] for x in geo])
+    r1 = np.stack([x[1] for x in geo])
+    r2 = np.stack([x[2] for x in geo])
+    u = np.stack([x[3] for x in geo])
+    p = [dict(tau=(1.0, 1.0), G=-2.2), dict(tau=(0.52, 3.0), G=-1.7, rho_s=0.4, g=(0, 1e-4, 0)),
+         dict(tau=(2.0, 0.6), G=-2.4, rho_s=-0.3, g=(1e-5, 0, 2e-5))]
+    _, _, g, o = _pair(lbm, oracle_mod, shape, p, t, r1, r2, u, 25, kernel=kernel)
+    assert max(_errs(g, o)) < 1e-12
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 1e-3), ("bf16s", 4e-3)])
+def test_reduced_precision_droplet(lbm, oracle_mod, precision, tol, kernel):
+    """32^3 droplet, 1000 updates: FP32 arithmetic with FP32 / 16-bit storage."""
+    t, r1, r2, u = W.droplet(32, 32, 32, 8.0)
+    p = [dict(tau=(1.0, 1.0), G=-2.2)]
+    _, _, g, o = _pair(lbm, oracle_mod, (32, 32, 32), p, t, r1, r2, u, 1000, precision=precision, kernel=kernel)
+    e = _errs(g, o)
+    assert _rel(g[0], o[0]) < tol and _rel(g[1], o[1]) < tol, e
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 2e-3), ("bf16s", 1e-2)])
+def test_reduced_precision_walls(lbm, oracle_mod, precision, tol):
+    shape = (13, 7, 9)
+    t, r1, r2, u = _random_geometry(shape, 0.2, 31, lo=0.3, hi=0.7)
+    p = [dict(tau=(0.7, 1.5), G=-1.8, rho_s=0.3, g=(1e-4, 0, 0))]
+    _, _, g, o = _pair(lbm, oracle_mod, shape, p, t[None], r1[None], r2[None], u[None], 20, precision=precision)
+    e = _errs(g, o)
+    assert _rel(g[0], o[0]) < tol and _rel(g[1], o[1]) < tol, e
+
+
+def test_reductions_match_oracle(lbm, oracle_mod):
+    shape = (16, 12, 10)
+    t, r1, r2, u = _random_geometry(shape, 0.1, 41, lo=0.3, hi=0.7)
+    p = [dict(tau=(0.8, 1.2), G=-2.0, g=(1e-4, 0, 0))]
+    sim, ref, _, _ = _pair(lbm, oracle_mod, shape, p, t[None], r1[None], r2[None], u[None], 15)
+    a = sim.reduce()[0]
+    b = ref.reduce()[0]
+    assert np.allclose(a[:2], b[:2], rtol=1e-13)
+    assert np.allclose(a[2:5], b[2:5], rtol=1e-10, atol=1e-14)
+    assert abs(a[5] - b[5]) <= 1e-10 * abs(b[5]) and abs(a[6] - b[6]) <= 1e-12
+    sim.step(5)
+    ref.step(5)
+    a = sim.reduce()[0]
+    b = ref.reduce()[0]
+    assert abs(a[5] - b[5]) <= 1e-9 * abs(b[5])
+
+
+def test_reductions_are_deterministic(lbm):
+    t, r1, r2, u = W.droplet(24, 24, 24, 6.0)
+    outs = []
+    for _ in range(2):
+        sim = lbm.Sim(24, 24, 24, [dict(tau=(1.0, 0.7), G=-2.2)], precision="fp32")
+        sim.set_geometry(t[None])
+        sim.set_fields(r1[None], r2[None], u[None])
+        sim.step(50)
+        outs.append(sim.reduce())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_checkpoint_roundtrip_bitwise(lbm):
+    t, r1, r2, u = _random_geometry((10, 9, 8), 0.1, 51, lo=0.3, hi=0.7)
+    p = [dict(tau=(0.9, 1.4), G=-2.0, rho_s=0.1, g=(1e-5, 0, 0))]
+    for prec in ("fp64", "fp16s"):
+        a = lbm.Sim(10, 9, 8, p, precision=prec)
+        a.set_geometry(t[None])
+        a.set_fields(r1[None], r2[None], u[None])
+        a.step(10)
+        st = a.get_state()
+        a.step(10)
+        fa = a.get_fields()
+        b = lbm.Sim(10, 9, 8, p, precision=prec)
+        b.set_state(st)
+        b.step(10)
+        fb = b.get_fields()
+        for x, y in zip(fa, fb):
+            assert np.array_equal(x, y)
+
+
+def test_errors_reported(lbm):
+    sim = lbm.Sim(4, 4, 4, [dict(tau=(1.0, 1.0))])
+    with pytest.raises(lbm.LbmError) as e:
+        sim.step(1)
+    assert e.value.status == 6
+    with pytest.raises(lbm.LbmError) as e:
+        sim.set_geometry(np.full((1, 4, 4, 4), 7, np.uint8))
+    assert e.value.status == 1
+    with pytest.raises(lbm.LbmError) as e:
+        sim.set_geometry(np.full((1, 4, 4, 4), 1, np.uint8))
+    assert e.value.status == 1
+
+
+def test_divergence_is_flagged(lbm):
+    """A blow-up (tau -> 1/2 with a huge body force) is reported as
+    LBM_ERR_DIVERGED by the reduction, and the context stays usable."""
+    t, r1, r2, u = W.droplet(8, 8, 8, 2.0)
+    sim = lbm.Sim(8, 8, 8, [dict(tau=(0.5001, 0.5001), G=-2.2, g=(0.5, 0.3, 0.0))], precision="fp32")
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    sim.step(200)
+    with pytest.raises(lbm.LbmError) as e:
+        sim.reduce()
+    assert e.value.status == 4
+    sim.get_fields()
+
+
+def test_distributions_roundtrip(lbm, oracle_mod):
+    """FP64 distributions exported by the library step identically in the oracle."""
+    shape = (9, 8, 7)
+    t, r1, r2, u = _random_geometry(shape, 0.1, 61, lo=0.3, hi=0.7)
+    p = [dict(tau=(0.8, 1.1), G=-2.0, rho_s=0.2)]
+    sim = lbm.Sim(*shape, p)
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    sim.step(7)
+    f = sim.get_f()
+    ref = oracle_mod.OracleSim(*shape, p)
+    ref.set_geometry(t[None])
+    ref.set_fields(r1[None], r2[None], u[None])
+    ref.set_f(f)
+    ref.step(1)
+    sim.step(1)
+    assert max(_errs(sim.get_fields(), ref.get_fields())) < 1e-13
+    sim.set_f(f)
+    sim.step(1)
+    assert max(_errs(sim.get_fields(), ref.get_fields())) < 1e-13
