@@ -9,8 +9,8 @@
  *      f_i(x) = f*_{-i}(x) when x - c_i is SOLID            (Eq. 1, Eq. 9, Sec. 2 walls)
  *   S2 rho_alpha = sum_i f_i, j = sum_alpha sum_i c_i f_i     (Eq. 4)
  *   S3 psi_beta = rho_beta in fluid, rho^s_beta in SOLID      (Eq. 7, Eq. 11)
- *   S4 F^alpha = G rho_alpha sum_i ws_i c_i psi_beta(x + c_i) (beta != alpha), the
- *      SOLID terms balanced between components (wall model 0) + rho_alpha g
+ *   S4 F^alpha = G rho_alpha sum_i ws_i c_i psi_beta(x + c_i) (beta != alpha), with
+ *      psi_beta of a SOLID neighbour set by the wall model, + rho_alpha g
  *                                                             (Eq. 7, Eq. 11)
  *   S5 u_F = (j + F/2) / rho, nu_mix = p nu_1 + (1-p) nu_2 with p = rho_1/rho in
  *      [0, 1], tau = nu_mix / T0 + 1/2                        (Eq. 5, 6, 8)
@@ -61,8 +61,10 @@ typedef enum {
 } lbm_status;
 
 /* Storage of the distributions.  Arithmetic is FP64 in LBM_FP64 and FP32 in
- * the other modes.  The 16-bit modes store f_i - w_i rho0_alpha (the deviation
- * from the rest equilibrium of density rho0_alpha) rounded to nearest even. */
+ * the other modes.  LBM_FP32 and the 16-bit modes store each value as its
+ * deviation f_i - w_i R from a rest equilibrium, rounded to nearest even,
+ * where R is the density (rounded to FP16, kept per cell and component) that
+ * the cell the value streams into had at its last update. */
 typedef enum {
     LBM_FP64 = 0,
     LBM_FP32 = 1,
@@ -83,8 +85,9 @@ typedef struct {
     int batch;               /* independent instances, >= 1 */
     lbm_precision precision;
     int eq_order;            /* 0: Eq. 3 as printed (no quadratic terms); 1: with them */
-    int wall_model;          /* 0: wall forces balanced between components; 1: plain rho^s */
-    double rho0_shift[2];    /* 16-bit storage shift rho0_alpha (use 1.0 when unsure) */
+    int wall_model;          /* psi of a SOLID neighbour: 0 rho^s_beta with the wall forces balanced
+                                between components, 1 plain rho^s_beta, 2 the cell's own
+                                rho_beta + rho^s_beta (neutral wall at rho^s = 0; recommended) */
 } lbm_config;
 
 typedef struct {
@@ -134,8 +137,8 @@ lbm_status lbm_get_fields(lbm_ctx *ctx, double *rho1, double *rho2, double *u);
  * value is not finite or max|u_F| > 1/sqrt(3).  Synchronises the stream. */
 lbm_status lbm_reduce(lbm_ctx *ctx, double *out);
 
-/* Post-collision distributions of the current state as FP64 (16-bit storage
- * modes are expanded back to f = stored + w_i rho0_alpha), host array
+/* Post-collision distributions of the current state as FP64 (the shifted
+ * storage modes are expanded back to f = stored + w_i R), host array
  * f[batch][2][19][nz][ny][nx] with the direction order 0 rest, then pairs
  * +x,-x, +y,-y, +z,-z, (1,1,0),(-1,-1,0), (1,-1,0),(-1,1,0), (1,0,1),(-1,0,-1),
  * (1,0,-1),(-1,0,1), (0,1,1),(0,-1,-1), (0,1,-1),(0,-1,1).  Values in SOLID
@@ -165,6 +168,25 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel);
  * cells per thread block, each marching zchunk planes; -1 selects the
  * built-in choice.  Errors: LBM_ERR_ARG (out of range). */
 lbm_status lbm_set_tiling(lbm_ctx *ctx, int tile, int zchunk);
+
+/* Autotuner: time every kernel strategy and fused tiling on the current state
+ * (steps_per_trial updates each, CUDA events on the context's stream), keep the
+ * fastest for later lbm_step calls, and restore the state, so the next update
+ * is the one that would have followed without tuning.  With cache_path non-NULL
+ * the choice is looked up in / appended to that file (one JSON object per line,
+ * keyed by grid, batch, precision, equilibrium order and device name); a hit
+ * skips the timing.  *chosen (may be NULL) receives the strategy, tile and
+ * zchunk.  Errors: LBM_ERR_STATE (no fields), LBM_ERR_ARG (steps_per_trial < 1). */
+lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_path, int chosen[3]);
+
+/* Advance until every instance's residual (as in lbm_reduce) is <= tol,
+ * checking every check_every updates, for at most max_steps updates.  The
+ * check_every updates and the reduction are captured once as a CUDA graph and
+ * replayed.  *steps_done and residual[batch] (may be NULL) receive the update
+ * count and the last residuals.  Returns LBM_ERR_DIVERGED if a reduction sees a
+ * non-finite value.  Errors: LBM_ERR_ARG (check_every < 1, max_steps < 0). */
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_steps, int *steps_done,
+                             double *residual);
 
 /* Number of CUDA kernel launches the context has issued so far. */
 long long lbm_launch_count(const lbm_ctx *ctx);

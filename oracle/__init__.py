@@ -159,7 +159,7 @@ class OracleSim:
     [batch, nz, ny, nx] (u: [batch, nz, ny, nx, 3]).
     """
 
-    def __init__(self, nx, ny, nz, params, eq_order=0, wall_model=0):
+    def __init__(self, nx, ny, nz, params, eq_order=0, wall_model=2):
         self.shape = (len(params), nz, ny, nx)
         cfg = _Config(nx, ny, nz, len(params), eq_order, wall_model)
         arr = (_Params * len(params))()

@@ -42,10 +42,13 @@
  *     Sec. 3.2 are missed by tens of percent.
  *   - Regularisation: f'_i = w_i/(2 T0^2) (c_i c_i - T0 I) : Pi^neq with
  *     Pi^neq = sum_i c_i c_i (f_i - feq_i).
- *   - Wall model 1 ("B", plain): psi_beta(solid) = rho^s_beta.  Wall model 0
- *     ("A", balanced): B, then the wall part of the force is projected so that
- *     F_w^1 + F_w^2 = 0 in every cell (forces along walls balanced between
- *     components, local momentum conserved).
+ *   - rho'_beta of a solid neighbour (Eq. 11).  Wall model 2 (recommended):
+ *     rho_beta of the cell itself plus rho^s_beta, so the transition into the
+ *     wall is smooth and a uniform fluid next to a wall feels no interaction
+ *     force (local momentum conserved).  Wall model 1 ("B", plain):
+ *     psi_beta(solid) = rho^s_beta.  Wall model 0 ("A", balanced): B, then the
+ *     wall part of the force is projected so that F_w^1 + F_w^2 = 0 in every
+ *     cell (forces along walls balanced between components).
  *   - rho^s_1 = -rho^s * Theta(-rho^s), rho^s_2 = rho^s * Theta(rho^s).
  *   - INLET cells hold feq(rho_in, u_in) after every step; an OUTLET cell
  *     takes the streamed distributions of its upstream (-x) neighbour.
@@ -114,7 +117,7 @@ static double force_weight(int i) { return 2.0 * W[i]; }
 typedef struct {
     int nx, ny, nz, batch;
     int eq_order;   /* 0 = Eq. 3 as printed, 1 = with quadratic terms */
-    int wall_model; /* 0 = balanced (A), 1 = plain (B) */
+    int wall_model; /* 0 = balanced (A), 1 = plain (B), 2 = own density + rho^s */
 } oracle_config;
 
 typedef struct {
@@ -455,6 +458,9 @@ static void step_instance(oracle_ctx *ctx, int b)
                         size_t nb = cell_index(cfg, wrap(x + C[i][0], nx), wrap(y + C[i][1], ny),
                                                wrap(z + C[i][2], nz));
                         double ps = ctx->psi[(size_t)be * n + nb];
+                        /* wall model 2: the solid neighbour carries the fluid
+                         * density of this cell plus the wall potential */
+                        if (type[nb] == CELL_SOLID && cfg->wall_model == 2) ps = rho_a[be] + rs[be];
                         for (int a = 0; a < 3; ++a) {
                             if (type[nb] == CELL_SOLID)
                                 sw[a] += force_weight(i) * C[i][a] * ps;

@@ -20,6 +20,9 @@ thread_local std::string g_last_error;
 
 // |u_F| beyond the lattice speed of sound sqrt(T0) is outside the scheme's range
 constexpr double kMaxSpeed = 0.57735026918962576;
+// the persistent cluster kernel loops each thread over cells of its instance
+constexpr long long kClusterMaxCells = 65536;
+constexpr long long kClusterAutoCells = 32768;
 
 size_t storage_bytes(lbm_precision p) {
     switch (p) {
@@ -41,6 +44,7 @@ struct lbm_ctx {
     void (*release)(void *, void *) = nullptr;
     std::vector<void *> owned;
     void *f[2] = {nullptr, nullptr};
+    Ref *ref[2] = {nullptr, nullptr};  // reference densities, swapped with f (not used in FP64)
     int cur = 0;
     uint32_t *link = nullptr;
     void *psi = nullptr, *macro = nullptr, *usnap = nullptr, *dpar = nullptr;
@@ -57,6 +61,7 @@ struct lbm_ctx {
     size_t tbytes() const { return fp64() ? 8 : 4; }
     size_t cells() const { return (size_t)cfg.batch * (size_t)g.n; }
     size_t f_bytes() const { return cells() * 2 * 19 * storage_bytes(cfg.precision); }
+    size_t ref_bytes() const { return fp64() ? 0 : cells() * 2 * sizeof(Ref); }
 
     lbm_status fail(lbm_status s, const std::string &m) {
         err = m;
@@ -136,6 +141,15 @@ lbm_status upload_params(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
+// Strategy for an n-update call.  AUTO: the persistent cluster kernel for
+// small instances advanced by several updates at once (launch overhead
+// dominates there), the fused kernel otherwise.
+lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
+    if (ctx->kernel != LBM_KERNEL_AUTO) return ctx->kernel;
+    if (ctx->g.n <= kClusterAutoCells && n > 1) return LBM_KERNEL_CLUSTER;
+    return LBM_KERNEL_FUSED;
+}
+
 // Fused-kernel tiling when none was set: 32x8 columns (32x4 in FP64, whose
 // ring buffers are twice as large), z chunks sized for about eight CTAs per SM.
 void default_tiling(const lbm_ctx *ctx, int &tile, int &zchunk) {
@@ -169,8 +183,8 @@ StepArgs step_args(lbm_ctx *ctx, int write_macro) {
     a.psi = ctx->psi;
     a.macro = ctx->macro;
     a.par = ctx->dpar;
-    a.rho0[0] = ctx->cfg.rho0_shift[0];
-    a.rho0[1] = ctx->cfg.rho0_shift[1];
+    a.ref_in = ctx->ref[ctx->cur];
+    a.ref_out = ctx->ref[ctx->cur ^ 1];
     a.stream = ctx->stream;
     return a;
 }
@@ -205,7 +219,7 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
         return LBM_ERR_ARG;
     }
     if (cfg->precision < LBM_FP64 || cfg->precision > LBM_FP32_BF16S || cfg->eq_order < 0 || cfg->eq_order > 1 ||
-        cfg->wall_model < 0 || cfg->wall_model > 1) {
+        cfg->wall_model < 0 || cfg->wall_model > 2) {
         g_last_error = "lbm_create: precision, eq_order or wall_model out of range";
         return LBM_ERR_ARG;
     }
@@ -245,6 +259,10 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
     ctx->nblk = reduce_blocks(ctx->g.n);
     ctx->f[0] = ctx->dalloc(ctx->f_bytes());
     ctx->f[1] = ctx->dalloc(ctx->f_bytes());
+    if (!ctx->fp64()) {
+        ctx->ref[0] = (Ref *)ctx->dalloc(ctx->ref_bytes());
+        ctx->ref[1] = (Ref *)ctx->dalloc(ctx->ref_bytes());
+    }
     ctx->link = (uint32_t *)ctx->dalloc(cells * 4);
     ctx->psi = ctx->dalloc(cells * 2 * ctx->tbytes());
     ctx->macro = ctx->dalloc(cells * 5 * ctx->tbytes());
@@ -252,7 +270,7 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
     ctx->dpar = ctx->dalloc((size_t)cfg->batch * sizeof(InstParam<double>));
     ctx->partial = (double *)ctx->dalloc((size_t)cfg->batch * ctx->nblk * 9 * sizeof(double));
     ctx->red_out = (double *)ctx->dalloc((size_t)cfg->batch * 9 * sizeof(double));
-    if (!ctx->f[0] || !ctx->f[1] || !ctx->link || !ctx->psi || !ctx->macro || !ctx->usnap || !ctx->dpar ||
+    if (!ctx->f[0] || !ctx->f[1] || (!ctx->fp64() && (!ctx->ref[0] || !ctx->ref[1])) || !ctx->link || !ctx->psi || !ctx->macro || !ctx->usnap || !ctx->dpar ||
         !ctx->partial || !ctx->red_out) {
         g_last_error = "lbm_create: device allocation failed";
         lbm_destroy(ctx);
@@ -283,8 +301,10 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
 
 lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
     if (!ctx) return LBM_ERR_ARG;
-    if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_TWO_PASS && kernel != LBM_KERNEL_FUSED)
-        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: strategy not available for this configuration");
+    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_CLUSTER)
+        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: unknown strategy");
+    if (kernel == LBM_KERNEL_CLUSTER && ctx->g.n > kClusterMaxCells)
+        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: CLUSTER needs at most 65536 cells per instance");
     ctx->kernel = kernel;
     return LBM_OK;
 }
@@ -347,11 +367,10 @@ lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho1, const double *rho2, 
         a.u = d + 2 * cells;
         a.link = ctx->link;
         a.f_out = ctx->f[ctx->cur];
+        a.ref_out = ctx->ref[ctx->cur];
         a.macro = ctx->macro;
         a.usnap = ctx->usnap;
         a.par = ctx->dpar;
-        a.rho0[0] = ctx->cfg.rho0_shift[0];
-        a.rho0[1] = ctx->cfg.rho0_shift[1];
         a.stream = ctx->stream;
         e = launch_init(a);
     }
@@ -369,7 +388,20 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     if (n < 0) return ctx->fail(LBM_ERR_ARG, "lbm_step: negative step count");
     if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_step: call lbm_set_fields first");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
-    const bool fused = ctx->kernel != LBM_KERNEL_TWO_PASS;
+    const lbm_kernel k = resolve_kernel(ctx, n);
+    if (k == LBM_KERNEL_CLUSTER) {
+        if (n > 0) {
+            StepArgs a = step_args(ctx, 1);
+            cudaError_t e = launch_cluster(a, n);
+            if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_step cluster launch");
+            ctx->launches += 1;
+            ctx->cur ^= (n & 1);
+        }
+        ctx->step += n;
+        ctx->since_snap += n;
+        return LBM_OK;
+    }
+    const bool fused = k == LBM_KERNEL_FUSED;
     int tile = ctx->tile, zchunk = ctx->zchunk;
     if (fused) default_tiling(ctx, tile, zchunk);
     for (int s = 0; s < n; ++s) {
@@ -448,8 +480,8 @@ lbm_status lbm_get_distributions(lbm_ctx *ctx, double *f) {
     const size_t vals = ctx->cells() * 2 * 19;
     double *d = (double *)ctx->dalloc(vals * 8);
     if (!d) return ctx->fail(LBM_ERR_OOM, "lbm_get_distributions: device allocation failed");
-    cudaError_t e = launch_f_convert(ctx->cfg.precision, ctx->f[ctx->cur], d, nullptr, nullptr, ctx->g,
-                                     ctx->cfg.batch, ctx->cfg.rho0_shift, ctx->stream);
+    cudaError_t e = launch_f_convert(ctx->cfg.precision, ctx->f[ctx->cur], d, nullptr, nullptr, ctx->ref[ctx->cur],
+                                     ctx->link, ctx->g, ctx->cfg.batch, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, vals * 8, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     ctx->dfree(d);
@@ -467,8 +499,8 @@ lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *f) {
     if (!d) return ctx->fail(LBM_ERR_OOM, "lbm_set_distributions: device allocation failed");
     cudaError_t e = cudaMemcpyAsync(d, f, vals * 8, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
-        e = launch_f_convert(ctx->cfg.precision, nullptr, nullptr, d, ctx->f[ctx->cur], ctx->g, ctx->cfg.batch,
-                             ctx->cfg.rho0_shift, ctx->stream);
+        e = launch_f_convert(ctx->cfg.precision, nullptr, nullptr, d, ctx->f[ctx->cur], ctx->ref[ctx->cur],
+                             ctx->link, ctx->g, ctx->cfg.batch, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     ctx->dfree(d);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_set_distributions");
@@ -483,7 +515,7 @@ struct StateHeader {
     uint32_t pad;
     lbm_config cfg;
     long long step, since_snap;
-    uint64_t f_bytes, link_bytes, macro_bytes, usnap_bytes;
+    uint64_t f_bytes, ref_bytes, link_bytes, macro_bytes, usnap_bytes;
 };
 }  // namespace
 
@@ -492,15 +524,16 @@ lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t *bytes) {
     const size_t cells = ctx->cells();
     StateHeader h{};
     std::memcpy(h.magic, "LBMSTATE", 8);
-    h.version = 1;
+    h.version = 2;
     h.cfg = ctx->cfg;
     h.step = ctx->step;
     h.since_snap = ctx->since_snap;
     h.f_bytes = ctx->f_bytes();
+    h.ref_bytes = ctx->ref_bytes();
     h.link_bytes = cells * 4;
     h.macro_bytes = cells * 5 * ctx->tbytes();
     h.usnap_bytes = cells * 3 * ctx->tbytes();
-    const size_t need = sizeof(h) + h.f_bytes + h.link_bytes + h.macro_bytes + h.usnap_bytes;
+    const size_t need = sizeof(h) + h.f_bytes + h.ref_bytes + h.link_bytes + h.macro_bytes + h.usnap_bytes;
     if (!buf) {
         *bytes = need;
         return LBM_OK;
@@ -513,6 +546,10 @@ lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t *bytes) {
     p += sizeof(h);
     LBM_CUDA(cudaMemcpyAsync(p, ctx->f[ctx->cur], h.f_bytes, cudaMemcpyDeviceToHost, ctx->stream), "get_state f");
     p += h.f_bytes;
+    if (h.ref_bytes)
+        LBM_CUDA(cudaMemcpyAsync(p, ctx->ref[ctx->cur], h.ref_bytes, cudaMemcpyDeviceToHost, ctx->stream),
+                 "get_state ref");
+    p += h.ref_bytes;
     LBM_CUDA(cudaMemcpyAsync(p, ctx->link, h.link_bytes, cudaMemcpyDeviceToHost, ctx->stream), "get_state link");
     p += h.link_bytes;
     LBM_CUDA(cudaMemcpyAsync(p, ctx->macro, h.macro_bytes, cudaMemcpyDeviceToHost, ctx->stream), "get_state macro");
@@ -529,20 +566,23 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes) {
     if (bytes < sizeof(h)) return ctx->fail(LBM_ERR_ARG, "lbm_set_state: buffer too small");
     std::memcpy(&h, buf, sizeof(h));
     const lbm_config &c = ctx->cfg;
-    if (std::memcmp(h.magic, "LBMSTATE", 8) != 0 || h.version != 1 || h.cfg.nx != c.nx || h.cfg.ny != c.ny ||
+    if (std::memcmp(h.magic, "LBMSTATE", 8) != 0 || h.version != 2 || h.cfg.nx != c.nx || h.cfg.ny != c.ny ||
         h.cfg.nz != c.nz || h.cfg.batch != c.batch || h.cfg.precision != c.precision ||
-        h.cfg.eq_order != c.eq_order || h.cfg.wall_model != c.wall_model ||
-        h.cfg.rho0_shift[0] != c.rho0_shift[0] || h.cfg.rho0_shift[1] != c.rho0_shift[1])
+        h.cfg.eq_order != c.eq_order || h.cfg.wall_model != c.wall_model)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_state: configuration mismatch");
     const size_t cells = ctx->cells();
-    if (h.f_bytes != ctx->f_bytes() || h.link_bytes != cells * 4 || h.macro_bytes != cells * 5 * ctx->tbytes() ||
-        h.usnap_bytes != cells * 3 * ctx->tbytes() ||
-        bytes < sizeof(h) + h.f_bytes + h.link_bytes + h.macro_bytes + h.usnap_bytes)
+    if (h.f_bytes != ctx->f_bytes() || h.ref_bytes != ctx->ref_bytes() || h.link_bytes != cells * 4 ||
+        h.macro_bytes != cells * 5 * ctx->tbytes() || h.usnap_bytes != cells * 3 * ctx->tbytes() ||
+        bytes < sizeof(h) + h.f_bytes + h.ref_bytes + h.link_bytes + h.macro_bytes + h.usnap_bytes)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_state: size mismatch");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
     const char *p = (const char *)buf + sizeof(h);
     LBM_CUDA(cudaMemcpyAsync(ctx->f[ctx->cur], p, h.f_bytes, cudaMemcpyHostToDevice, ctx->stream), "set_state f");
     p += h.f_bytes;
+    if (h.ref_bytes)
+        LBM_CUDA(cudaMemcpyAsync(ctx->ref[ctx->cur], p, h.ref_bytes, cudaMemcpyHostToDevice, ctx->stream),
+                 "set_state ref");
+    p += h.ref_bytes;
     LBM_CUDA(cudaMemcpyAsync(ctx->link, p, h.link_bytes, cudaMemcpyHostToDevice, ctx->stream), "set_state link");
     p += h.link_bytes;
     LBM_CUDA(cudaMemcpyAsync(ctx->macro, p, h.macro_bytes, cudaMemcpyHostToDevice, ctx->stream), "set_state macro");
@@ -552,6 +592,235 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes) {
     ctx->step = h.step;
     ctx->since_snap = h.since_snap;
     ctx->has_geometry = ctx->has_fields = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_path, int chosen[3]) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (steps_per_trial < 1) return ctx->fail(LBM_ERR_ARG, "lbm_autotune: steps_per_trial < 1");
+    if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_autotune: call lbm_set_fields first");
+    LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    cudaDeviceProp prop;
+    LBM_CUDA(cudaGetDeviceProperties(&prop, ctx->dev), "cudaGetDeviceProperties");
+    char key[512];
+    std::snprintf(key, sizeof key, "%dx%dx%d b%d p%d e%d w%d %s", ctx->cfg.nx, ctx->cfg.ny, ctx->cfg.nz,
+                  ctx->cfg.batch, (int)ctx->cfg.precision, ctx->cfg.eq_order, ctx->cfg.wall_model, prop.name);
+    for (char *c = key; *c; ++c)
+        if (*c == '"' || *c == '\\') *c = '_';
+    auto apply = [&](int k, int t, int z) {
+        ctx->kernel = (lbm_kernel)k;
+        ctx->tile = t;
+        ctx->zchunk = z;
+        if (chosen) {
+            chosen[0] = k;
+            chosen[1] = t;
+            chosen[2] = z;
+        }
+    };
+    if (cache_path) {
+        if (FILE *fp = std::fopen(cache_path, "r")) {
+            char line[1024];
+            int hit = 0, k = 0, t = 0, z = 0;
+            while (std::fgets(line, sizeof line, fp)) {
+                char kbuf[512];
+                int kk, tt, zz;
+                double ms;
+                if (std::sscanf(line, "{\"key\": \"%511[^\"]\", \"kernel\": %d, \"tile\": %d, \"zchunk\": %d, \"ms\": %lf",
+                                kbuf, &kk, &tt, &zz, &ms) == 5 &&
+                    std::strcmp(kbuf, key) == 0) {
+                    hit = 1;
+                    k = kk;
+                    t = tt;
+                    z = zz;
+                }
+            }
+            std::fclose(fp);
+            if (hit) {
+                apply(k, t, z);
+                return LBM_OK;
+            }
+        }
+    }
+    // save the state: both f and reference buffers of the current side, fields
+    const size_t fb = ctx->f_bytes(), rb = ctx->ref_bytes(), mb = ctx->cells() * 5 * ctx->tbytes();
+    void *sf = ctx->dalloc(fb);
+    void *sr = rb ? ctx->dalloc(rb) : nullptr;
+    void *smac = ctx->dalloc(mb);
+    if (!sf || (rb && !sr) || !smac) {
+        ctx->dfree(sf);
+        ctx->dfree(sr);
+        ctx->dfree(smac);
+        return ctx->fail(LBM_ERR_OOM, "lbm_autotune: no room to save the state");
+    }
+    const int cur0 = ctx->cur;
+    const long long step0 = ctx->step, snap0 = ctx->since_snap, launches0 = ctx->launches;
+    const lbm_kernel k_save = ctx->kernel;
+    const int t_save = ctx->tile, z_save = ctx->zchunk;
+    cudaError_t e = cudaMemcpyAsync(sf, ctx->f[cur0], fb, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess && rb) e = cudaMemcpyAsync(sr, ctx->ref[cur0], rb, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(smac, ctx->macro, mb, cudaMemcpyDeviceToDevice, ctx->stream);
+    struct Cand {
+        int k, t, z;
+    };
+    std::vector<Cand> cands;
+    cands.push_back({LBM_KERNEL_TWO_PASS, -1, -1});
+    if (ctx->g.n <= kClusterMaxCells) cands.push_back({LBM_KERNEL_CLUSTER, -1, -1});
+    for (int t = 0; t < fused_tile_count(); ++t) {
+        cands.push_back({LBM_KERNEL_FUSED, t, -1});
+        for (int z : {8, 16, 32, 64})
+            if (z < ctx->g.nz) cands.push_back({LBM_KERNEL_FUSED, t, z});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    Cand pick = {LBM_KERNEL_FUSED, -1, -1};
+    lbm_status st = LBM_OK;
+    for (const Cand &c : cands) {
+        if (e != cudaSuccess) break;
+        ctx->kernel = (lbm_kernel)c.k;
+        ctx->tile = c.t;
+        ctx->zchunk = c.z;
+        st = lbm_step(ctx, steps_per_trial);  // warm-up (also compiles nothing: all code is ahead-of-time)
+        if (st != LBM_OK) break;
+        e = cudaEventRecord(e0, ctx->stream);
+        if (e != cudaSuccess) break;
+        st = lbm_step(ctx, steps_per_trial);
+        if (st != LBM_OK) break;
+        e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            pick = c;
+        }
+        // restore the saved state for the next candidate
+        ctx->cur = cur0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->f[cur0], sf, fb, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess && rb)
+            e = cudaMemcpyAsync(ctx->ref[cur0], sr, rb, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->macro, smac, mb, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ctx->dfree(sf);
+    ctx->dfree(sr);
+    ctx->dfree(smac);
+    ctx->cur = cur0;
+    ctx->step = step0;
+    ctx->since_snap = snap0;
+    (void)launches0;
+    if (st != LBM_OK || e != cudaSuccess) {
+        ctx->kernel = k_save;
+        ctx->tile = t_save;
+        ctx->zchunk = z_save;
+        return st != LBM_OK ? st : ctx->cuda_fail(e, "lbm_autotune");
+    }
+    if (pick.k == LBM_KERNEL_FUSED) default_tiling(ctx, pick.t, pick.z);
+    apply(pick.k, pick.t, pick.z);
+    if (cache_path) {
+        if (FILE *fp = std::fopen(cache_path, "a")) {
+            std::fprintf(fp, "{\"key\": \"%s\", \"kernel\": %d, \"tile\": %d, \"zchunk\": %d, \"ms\": %.6f}\n", key,
+                         pick.k, pick.t, pick.z, best / steps_per_trial);
+            std::fclose(fp);
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_steps, int *steps_done,
+                             double *residual) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (check_every < 1 || max_steps < 0) return ctx->fail(LBM_ERR_ARG, "lbm_run_to_steady: bad counts");
+    if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_run_to_steady: call lbm_set_fields first");
+    LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    const int B = ctx->cfg.batch;
+    // capture on a private stream ordered after the context's stream
+    cudaStream_t cs = nullptr;
+    LBM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream");
+    double *hres = nullptr;
+    cudaError_t e = cudaMallocHost(&hres, (size_t)B * 9 * sizeof(double));
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaStream_t user = ctx->stream;
+    const int cur0 = ctx->cur;
+    auto capture = [&](int parity) -> cudaError_t {
+        // record check_every updates + reduction + read-back starting from side `parity`
+        cudaGraph_t gph = nullptr;
+        const long long st0 = ctx->step, sn0 = ctx->since_snap, la0 = ctx->launches;
+        ctx->stream = cs;
+        ctx->cur = parity;
+        cudaError_t ee = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ee != cudaSuccess) return ee;
+        lbm_status s1 = lbm_step(ctx, check_every);
+        ReduceArgs a{};
+        a.fp64 = ctx->fp64();
+        a.batch = B;
+        a.g = ctx->g;
+        a.macro = ctx->macro;
+        a.usnap = ctx->usnap;
+        a.link = ctx->link;
+        a.partial = ctx->partial;
+        a.nblk = ctx->nblk;
+        a.out = ctx->red_out;
+        a.stream = cs;
+        int nl = 0;
+        cudaError_t e2 = s1 == LBM_OK ? launch_reduce(a, &nl) : cudaErrorUnknown;
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpyAsync(hres, ctx->red_out, (size_t)B * 9 * sizeof(double), cudaMemcpyDeviceToHost, cs);
+        ee = cudaStreamEndCapture(cs, &gph);
+        if (ee == cudaSuccess) ee = e2;
+        if (ee == cudaSuccess) ee = cudaGraphInstantiate(&exec[parity], gph, 0);
+        if (gph) cudaGraphDestroy(gph);
+        ctx->stream = user;
+        ctx->cur = cur0;
+        ctx->step = st0;
+        ctx->since_snap = sn0;
+        ctx->launches = la0;
+        return ee;
+    };
+    if (e == cudaSuccess) e = capture(cur0);
+    if (e == cudaSuccess && (check_every & 1)) e = capture(cur0 ^ 1);
+    // order the private stream after work already queued on the user stream
+    cudaEvent_t ev = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    int done = 0;
+    bool diverged = false;
+    const lbm_kernel kres = resolve_kernel(ctx, check_every);
+    const long long launches_per_replay =
+        (kres == LBM_KERNEL_CLUSTER ? 1 : (kres == LBM_KERNEL_FUSED ? check_every : 2LL * check_every)) + 2;
+    ctx->since_snap = 0;  // the first replay measures against the current snapshot
+    while (e == cudaSuccess && done + check_every <= max_steps) {
+        e = cudaGraphLaunch(exec[ctx->cur], cs);  // graphs are indexed by the side holding the state
+        if (e != cudaSuccess) break;
+        e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) break;
+        done += check_every;
+        ctx->cur ^= (check_every & 1);
+        ctx->step += check_every;
+        ctx->launches += launches_per_replay;
+        bool conv = true;
+        for (int b = 0; b < B; ++b) {
+            const double *r = hres + (size_t)b * 9;
+            const double res = std::sqrt(r[5]) / ((double)check_every * std::sqrt(r[6]) + 1e-30);
+            if (residual) residual[b] = res;
+            if (r[8] > 0 || !std::isfinite(res)) diverged = true;
+            if (!(res <= tol)) conv = false;
+        }
+        if (diverged || conv) break;
+    }
+    ctx->since_snap = 0;
+    if (steps_done) *steps_done = done;
+    if (ev) cudaEventDestroy(ev);
+    for (auto &x : exec)
+        if (x) cudaGraphExecDestroy(x);
+    if (hres) cudaFreeHost(hres);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_run_to_steady");
+    if (diverged) return ctx->fail(LBM_ERR_DIVERGED, "lbm_run_to_steady: non-finite value");
     return LBM_OK;
 }
 

@@ -41,20 +41,29 @@ constexpr uint32_t kFluid = 0, kSolid = 1, kInlet = 2, kOutlet = 3;
 __device__ __forceinline__ uint32_t cell_type(uint32_t word) { return (word >> 24) & 3u; }
 
 // -------------------------------------------------------------- storage
-// How one distribution value is held in HBM.  The 16-bit formats store the
-// deviation from the rest equilibrium w_i rho0_alpha.
+// How one distribution value is held in HBM.  FP32 and the 16-bit formats
+// store the deviation from a rest equilibrium w_i R, where R is the density
+// (rounded to FP16) that the cell the value streams into had at its last
+// update: R is the same for all 19 values a cell pulls, so the reader adds
+// w_i R(self) back.  A constant reference density would leave the minority
+// phase (f ~ 0) stored as -w_i rho0, whose rounding error repeats every update
+// and drifts the minority mass.
 template <class S> struct Storage;
+__device__ __forceinline__ float ref_value(float r) { return __half2float(__float2half_rn(r)); }
+__device__ __forceinline__ double ref_value(double r) { return r; }
 template <> struct Storage<double> {
     using T = double;
     static constexpr bool shifted = false;
     __device__ static __forceinline__ double load(const double *p, double) { return __ldg(p); }
+    __device__ static __forceinline__ double load_rw(const double *p, double) { return __ldcg(p); }
     __device__ static __forceinline__ void store(double *p, double v, double) { *p = v; }
 };
 template <> struct Storage<float> {
     using T = float;
-    static constexpr bool shifted = false;
-    __device__ static __forceinline__ float load(const float *p, float) { return __ldg(p); }
-    __device__ static __forceinline__ void store(float *p, float v, float) { *p = v; }
+    static constexpr bool shifted = true;
+    __device__ static __forceinline__ float load(const float *p, float sh) { return __ldg(p) + sh; }
+    __device__ static __forceinline__ float load_rw(const float *p, float sh) { return __ldcg(p) + sh; }
+    __device__ static __forceinline__ void store(float *p, float v, float sh) { *p = v - sh; }
 };
 template <> struct Storage<__half> {
     using T = float;
@@ -62,6 +71,7 @@ template <> struct Storage<__half> {
     __device__ static __forceinline__ float load(const __half *p, float sh) {
         return __half2float(__ldg(p)) + sh;
     }
+    __device__ static __forceinline__ float load_rw(const __half *p, float sh) { return __half2float(__ldcg(p)) + sh; }
     __device__ static __forceinline__ void store(__half *p, float v, float sh) { *p = __float2half_rn(v - sh); }
 };
 template <> struct Storage<__nv_bfloat16> {
@@ -69,6 +79,9 @@ template <> struct Storage<__nv_bfloat16> {
     static constexpr bool shifted = true;
     __device__ static __forceinline__ float load(const __nv_bfloat16 *p, float sh) {
         return __bfloat162float(__ldg(p)) + sh;
+    }
+    __device__ static __forceinline__ float load_rw(const __nv_bfloat16 *p, float sh) {
+        return __bfloat162float(__ldcg(p)) + sh;
     }
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v, float sh) {
         *p = __float2bfloat16_rn(v - sh);
@@ -107,17 +120,21 @@ template <class T> struct Moments {
 // index) whose neighbours are `nb` and whose solid-neighbour bits are `links`
 // (bit k: x + c_k is SOLID, so the value travelling in direction i comes back
 // from the cell itself when bit opp(i) is set), and reduce them to moments.
-template <class S>
+// `rref` is the reference density R of the pulling cell (see Storage).
+// RO = true reads through the read-only data path (buffers not written by the
+// same launch); RO = false uses coherent loads (persistent kernels).
+template <class S, bool RO = true>
 __device__ __forceinline__ Moments<typename Storage<S>::T>
 pull_moments(const S *__restrict__ fcomp, long long n, int self, const Nbr &nb, uint32_t links,
-             typename Storage<S>::T rho0) {
+             typename Storage<S>::T rref) {
     using T = typename Storage<S>::T;
     T v[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const bool bb = (links >> opp(i)) & 1u;
         const long long idx = bb ? (long long)opp(i) * n + self : (long long)i * n + nb.src(i);
-        v[i] = Storage<S>::load(fcomp + idx, Storage<S>::shifted ? wgt<T>(i) * rho0 : T(0));
+        const T sh = Storage<S>::shifted ? wgt<T>(i) * rref : T(0);
+        v[i] = RO ? Storage<S>::load(fcomp + idx, sh) : Storage<S>::load_rw(fcomp + idx, sh);
     }
     Moments<T> m;
     T r = v[0];
@@ -140,17 +157,18 @@ pull_moments(const S *__restrict__ fcomp, long long n, int self, const Nbr &nb, 
 }
 
 // Density only (for the pseudo-potential pass), same summation order.
-template <class S>
+template <class S, bool RO = true>
 __device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restrict__ fcomp, long long n, int self,
                                                               const Nbr &nb, uint32_t links,
-                                                              typename Storage<S>::T rho0) {
+                                                              typename Storage<S>::T rref) {
     using T = typename Storage<S>::T;
     T v[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const bool bb = (links >> opp(i)) & 1u;
         const long long idx = bb ? (long long)opp(i) * n + self : (long long)i * n + nb.src(i);
-        v[i] = Storage<S>::load(fcomp + idx, Storage<S>::shifted ? wgt<T>(i) * rho0 : T(0));
+        const T sh = Storage<S>::shifted ? wgt<T>(i) * rref : T(0);
+        v[i] = RO ? Storage<S>::load(fcomp + idx, sh) : Storage<S>::load_rw(fcomp + idx, sh);
     }
     T r = v[0];
 #pragma unroll
@@ -170,14 +188,15 @@ __device__ __forceinline__ T feq_dir(int i, T rho, T ux, T uy, T uz, T uu) {
 
 // S6-S7 for one component: writes f*_i = feq_i + w_i/(2 T0^2) H_i : A + w_i c_i.F/(2 T0)
 // with A = (1 - 1/tau) Pi^neq + (1 - 1/(2 tau)) (u_F F + F u_F).
-template <class S, int EQ>
+// sig(i) is the reference density of the cell value i streams into.
+template <class S, int EQ, class Sig>
 __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n, int self,
                                               const Moments<typename Storage<S>::T> &m,
                                               typename Storage<S>::T ux, typename Storage<S>::T uy,
                                               typename Storage<S>::T uz, typename Storage<S>::T Fx,
                                               typename Storage<S>::T Fy, typename Storage<S>::T Fz,
                                               typename Storage<S>::T omega, typename Storage<S>::T fcoef,
-                                              typename Storage<S>::T rho0) {
+                                              const Sig &sig) {
     using T = typename Storage<S>::T;
     const T T0 = T(1) / T(3);
     const T uu = ux * ux + uy * uy + uz * uz;
@@ -203,21 +222,21 @@ __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n,
         const T cF = c0 * Fx + c1 * Fy + c2 * Fz;
         const T fe = feq_dir<T, EQ>(i, m.rho, ux, uy, uz, uu);
         const T v = fe + wgt<T>(i) * (T(4.5) * cAc + ktr + T(1.5) * cF);
-        Storage<S>::store(fout + (long long)i * n + self, v, Storage<S>::shifted ? wgt<T>(i) * rho0 : T(0));
+        Storage<S>::store(fout + (long long)i * n + self, v, Storage<S>::shifted ? wgt<T>(i) * sig(i) : T(0));
     }
 }
 
-template <class S, int EQ>
+template <class S, int EQ, class Sig>
 __device__ __forceinline__ void store_equilibrium(S *__restrict__ fout, long long n, int self,
                                                   typename Storage<S>::T rho, typename Storage<S>::T ux,
                                                   typename Storage<S>::T uy, typename Storage<S>::T uz,
-                                                  typename Storage<S>::T rho0) {
+                                                  const Sig &sig) {
     using T = typename Storage<S>::T;
     const T uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < kQ; ++i)
         Storage<S>::store(fout + (long long)i * n + self, feq_dir<T, EQ>(i, rho, ux, uy, uz, uu),
-                          Storage<S>::shifted ? wgt<T>(i) * rho0 : T(0));
+                          Storage<S>::shifted ? wgt<T>(i) * sig(i) : T(0));
 }
 
 // S4: forces on both components from the pseudo-potential of the 18
@@ -253,7 +272,8 @@ __device__ __forceinline__ Forces<T> sc_forces(const PsiAt &psi_at, uint32_t lin
     }
     const uint32_t wl = links & 0x7FFFEu;
     if (wl) {
-        // wall part (Eq. 11): psi_beta(SOLID) = rho^s_beta
+        // wall part (Eq. 11): psi_beta(SOLID) = rho^s_beta (models 0, 1), or the
+        // cell's own rho_beta plus rho^s_beta (model 2)
         T d[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
@@ -267,8 +287,10 @@ __device__ __forceinline__ Forces<T> sc_forces(const PsiAt &psi_at, uint32_t lin
         T fw[2][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            fw[0][a] = p.G * r[0] * (p.rs[1] * d[a]);
-            fw[1][a] = p.G * r[1] * (p.rs[0] * d[a]);
+            const T w1 = wall_model == 2 ? r[1] + p.rs[1] : p.rs[1];
+            const T w0 = wall_model == 2 ? r[0] + p.rs[0] : p.rs[0];
+            fw[0][a] = p.G * r[0] * (w1 * d[a]);
+            fw[1][a] = p.G * r[1] * (w0 * d[a]);
         }
         if (wall_model == 0) {
             const T rho = r[0] + r[1];

@@ -1,15 +1,20 @@
 // Fused single-read update: each CTA owns a TX x TY column of cells and
 // marches it through a chunk of z planes.  For every plane it pulls the
 // streamed distributions once, keeps the 10 moments per component of its own
-// cells in registers, and writes the pseudo-potential of the plane plus a
+// cells in shared memory, and writes the pseudo-potential of the plane plus a
 // one-cell ring around it into a 3-plane ring buffer in shared memory (the
-// ring cells are recomputed from their streamed values rather than read
-// back from a separate density pass).  One plane behind, it evaluates the
+// ring cells are recomputed from their streamed values rather than read back
+// from a separate density pass).  One plane behind, it evaluates the
 // interaction forces from shared memory and collides (S4-S7).
 //
+// Work is compacted per plane: the cells that need a pull (non-SOLID,
+// non-INLET cells of the extended tile) and the cells that collide are packed
+// into order-preserving lists, so warps run full in porous geometries where
+// most cells of a tile may be SOLID.
+//
 // HBM traffic per fluid cell is the algorithmic minimum (f in, f out, one
-// geometry word) plus the halo re-reads, which hit L2 because neighbouring
-// columns march in step.
+// geometry word, the reference densities) plus halo re-reads, which mostly
+// hit L2 because neighbouring columns march in step.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -17,8 +22,10 @@ namespace lbm {
 
 template <int TX, int TY> struct Tile {
     static constexpr int EX = TX + 2, EY = TY + 2;
-    static constexpr int NT = TX * TY;
-    static constexpr int HALO = 2 * EX + 2 * TY;  // ring cells of the extended tile
+    static constexpr int NT = TX * TY;            // threads = interior cells per plane
+    static constexpr int NE = EX * EY;            // extended cells per plane
+    static constexpr int K = (NE + NT - 1) / NT;  // extended cells classified per thread
+    static constexpr int NW = NT / 32;
 };
 
 // ring-buffer slot of the plane at z offset cz(i) from the colliding plane
@@ -26,29 +33,17 @@ __device__ __forceinline__ int cz_slot(int i, int sl, int sm, int su) {
     return cz(i) < 0 ? sl : (cz(i) > 0 ? su : sm);
 }
 
-// Pull one cell (x, y, z) -> density (and moments when `want_moments`);
-// returns the pseudo-potential pair via psi0/psi1.
+// Pull one component of one cell (x, y, z): returns its density and, when
+// `mom` is non-null, stores its 10 moments at mom[q * stride].  Components are
+// pulled one after the other so that only 19 loads are in flight per thread.
 template <class S>
-__device__ __forceinline__ void cell_pull(const S *__restrict__ fb, const uint32_t *__restrict__ link_b,
-                                          const Grid &g, const InstParam<typename Storage<S>::T> &p, int x, int y,
-                                          int z, uint32_t word, bool want_moments,
-                                          Moments<typename Storage<S>::T> &m0, Moments<typename Storage<S>::T> &m1,
-                                          typename Storage<S>::T &psi0, typename Storage<S>::T &psi1,
-                                          typename Storage<S>::T r00, typename Storage<S>::T r01) {
+__device__ __forceinline__ typename Storage<S>::T cell_pull(const S *__restrict__ fb, const uint32_t *__restrict__ link_b,
+                                                           const Grid &g, int x, int y, int z, uint32_t word, int comp,
+                                                           typename Storage<S>::T *mom, int stride,
+                                                           const Ref *__restrict__ rin_b) {
     using T = typename Storage<S>::T;
-    const uint32_t t = cell_type(word);
-    if (t == kSolid) {
-        psi0 = p.rs[0];
-        psi1 = p.rs[1];
-        return;
-    }
-    if (t == kInlet) {
-        psi0 = p.rho_in[0];
-        psi1 = p.rho_in[1];
-        return;
-    }
     uint32_t sw = word;
-    if (t == kOutlet) {
+    if (cell_type(word) == kOutlet) {
         const int xu = x == 0 ? g.nx - 1 : x - 1;
         const uint32_t wu = __ldg(link_b + xu + y * g.nx + (long long)z * g.nxy);
         const uint32_t tu = cell_type(wu);
@@ -60,39 +55,44 @@ __device__ __forceinline__ void cell_pull(const S *__restrict__ fb, const uint32
     Nbr nb;
     nb.init(x, y, z, g);
     const int self = x + y * g.nx + z * g.nxy;
-    if (want_moments) {
-        m0 = pull_moments<S>(fb, g.n, self, nb, sw, r00);
-        m1 = pull_moments<S>(fb + kQ * g.n, g.n, self, nb, sw, r01);
-        psi0 = m0.rho;
-        psi1 = m1.rho;
-    } else {
-        psi0 = pull_density<S>(fb, g.n, self, nb, sw, r00);
-        psi1 = pull_density<S>(fb + kQ * g.n, g.n, self, nb, sw, r01);
+    T rr = T(0);
+    if constexpr (Storage<S>::shifted) rr = (T)__half2float(rin_b[comp * g.n + self]);
+    const S *fc = fb + (long long)comp * kQ * g.n;
+    if (mom) {
+        const Moments<T> m = pull_moments<S>(fc, g.n, self, nb, sw, rr);
+        mom[0] = m.rho; mom[stride] = m.jx; mom[2 * stride] = m.jy; mom[3 * stride] = m.jz;
+        mom[4 * stride] = m.pxx; mom[5 * stride] = m.pyy; mom[6 * stride] = m.pzz;
+        mom[7 * stride] = m.pxy; mom[8 * stride] = m.pxz; mom[9 * stride] = m.pyz;
+        return m.rho;
     }
+    return pull_density<S>(fc, g.n, self, nb, sw, rr);
 }
 
-template <class T, int TX, int TY> __host__ __device__ constexpr int fused_psi_bytes() {
-    return (int)(((3 * 2 * (TX + 2) * (TY + 2) * sizeof(T)) + 15) / 16 * 16);
-}
-template <class T, int TX, int TY> __host__ __device__ constexpr int fused_smem_bytes() {
-    return fused_psi_bytes<T, TX, TY>() + (int)(2 * 20 * TX * TY * sizeof(T));
-}
+// Shared-memory layout of the fused kernel.
+template <class T, int TX, int TY> struct FusedSmem {
+    using TL = Tile<TX, TY>;
+    T sp[3][2][TL::EY][TL::EX];   // pseudo-potential ring of three planes
+    T mom[2][20][TL::NT];         // moments of the interior cells, by plane parity
+    uint32_t word[2][TL::NT];     // geometry words of the interior cells, by plane parity
+    uint16_t work[TL::NE];        // pull items of the current plane: extended index | 0x8000 if moments
+    uint16_t coll[2][TL::NT];     // colliding interior slots, by plane parity
+    int ncoll[2];
+    int nwork;
+    int wsum[TL::NW + 1];
+};
 
 template <class S, int EQ, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_fused(const S *__restrict__ f, S *__restrict__ fo,
+__global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1)) k_fused(const S *__restrict__ f, S *__restrict__ fo,
+                                                  const Ref *__restrict__ rin, Ref *__restrict__ rout,
                                                   const uint32_t *__restrict__ link,
                                                   typename Storage<S>::T *__restrict__ macro, Grid g,
                                                   const InstParam<typename Storage<S>::T> *__restrict__ par,
-                                                  typename Storage<S>::T r00, typename Storage<S>::T r01,
                                                   int wall_model, int write_macro, int tiles_x, int tiles_y,
                                                   int zchunk, int nchunks) {
     using T = typename Storage<S>::T;
     using TL = Tile<TX, TY>;
-    // dynamic shared memory: pseudo-potential ring of 3 planes [3][2][EY][EX],
-    // then the moments of the own cells of the last two planes [2][20][NT]
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*sp)[2][TL::EY][TL::EX] = reinterpret_cast<T(*)[2][TL::EY][TL::EX]>(smem_raw);
-    T(*sm_mom)[20][TL::NT] = reinterpret_cast<T(*)[20][TL::NT]>(smem_raw + fused_psi_bytes<T, TX, TY>());
+    FusedSmem<T, TX, TY> &sm = *reinterpret_cast<FusedSmem<T, TX, TY> *>(smem_raw);
 
     // block -> (tile x, tile y, z chunk, instance)
     int bid = blockIdx.x;
@@ -104,110 +104,154 @@ __global__ void __launch_bounds__(TX *TY) k_fused(const S *__restrict__ f, S *__
     const int b = bid / nchunks;
     const int z0 = zc * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
-
-    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
-    const int x = tx0 + lx, y = ty0 + ly;
-    const bool mine = x < g.nx && y < g.ny;
-    const int xw = x % g.nx, yw = y % g.ny;  // wrapped (only for ragged tiles)
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
 
     const uint32_t *link_b = link + (long long)b * g.n;
     const S *fb = f + (long long)b * 2 * kQ * g.n;
     S *fob = fo + (long long)b * 2 * kQ * g.n;
     T *mac = macro + (long long)b * 5 * g.n;
     const InstParam<T> &p = par[b];
+    const Ref *rin_b = rin + (long long)b * 2 * g.n;
+    Ref *rout_b = rout + (long long)b * 2 * g.n;
 
-    // halo cell assigned to this thread (ring of the extended tile)
-    const int h = threadIdx.x;
-    int hex = -1, hey = -1;
-    if (h < TL::HALO) {
-        if (h < TL::EX) {
-            hex = h; hey = 0;
-        } else if (h < 2 * TL::EX) {
-            hex = h - TL::EX; hey = TL::EY - 1;
-        } else if (h < 2 * TL::EX + TY) {
-            hex = 0; hey = 1 + (h - 2 * TL::EX);
-        } else {
-            hex = TL::EX - 1; hey = 1 + (h - 2 * TL::EX - TY);
-        }
-    }
-    int hx = 0, hy = 0;
-    if (hex >= 0) {
-        hx = tx0 - 1 + hex;
-        hy = ty0 - 1 + hey;
-        hx = ((hx % g.nx) + g.nx) % g.nx;
-        hy = ((hy % g.ny) + g.ny) % g.ny;
-    }
-
-    uint32_t word_prev = 0, word_cur = 0;
+    auto ext_xy = [&](int e, int &x, int &y) {
+        const int ey = e / TL::EX, ex = e - ey * TL::EX;
+        x = tx0 - 1 + ex;
+        y = ty0 - 1 + ey;
+        x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+        y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+        x = x % g.nx;  // grids narrower than a tile wrap more than once
+        y = y % g.ny;
+    };
 
     for (int pz = z0 - 1; pz <= z1; ++pz) {
         const int zz = pz < 0 ? pz + g.nz : (pz >= g.nz ? pz - g.nz : pz);
         const int slot = (pz + 3) % 3;
+        const int par2 = pz & 1;
         const bool inner = pz >= z0 && pz < z1;
-        // own cell of this plane
-        {
-            const uint32_t w = __ldg(link_b + xw + yw * g.nx + (long long)zz * g.nxy);
-            T q0, q1;
-            Moments<T> c0, c1;
-            const bool want = inner && mine;
-            cell_pull<S>(fb, link_b, g, p, xw, yw, zz, w, want, c0, c1, q0, q1, r00, r01);
-            sp[slot][0][ly + 1][lx + 1] = q0;
-            sp[slot][1][ly + 1][lx + 1] = q1;
-            if (want && cell_type(w) != kSolid && cell_type(w) != kInlet) {
-                T *ms = &sm_mom[pz & 1][0][threadIdx.x];
-                const T v[20] = {c0.rho, c0.jx, c0.jy, c0.jz, c0.pxx, c0.pyy, c0.pzz, c0.pxy, c0.pxz, c0.pyz,
-                                 c1.rho, c1.jx, c1.jy, c1.jz, c1.pxx, c1.pyy, c1.pzz, c1.pxy, c1.pxz, c1.pyz};
+
+        // ---- classify the extended plane and build the compacted lists
+        uint32_t w_e[TL::K];
+        int npull = 0, ncol = 0;
 #pragma unroll
-                for (int q = 0; q < 20; ++q) ms[q * TL::NT] = v[q];
+        for (int k = 0; k < TL::K; ++k) {
+            const int e = tid * TL::K + k;
+            w_e[k] = 0;
+            if (e < TL::NE) {
+                int x, y;
+                ext_xy(e, x, y);
+                const uint32_t w = __ldg(link_b + x + y * g.nx + (long long)zz * g.nxy);
+                w_e[k] = w;
+                const uint32_t t = cell_type(w);
+                const int ey = e / TL::EX, ex = e - ey * TL::EX;
+                const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
+                const bool mine = interior && tx0 + ex - 1 < g.nx && ty0 + ey - 1 < g.ny;
+                if (t == kSolid) {
+                    sm.sp[slot][0][ey][ex] = p.rs[0];
+                    sm.sp[slot][1][ey][ex] = p.rs[1];
+                } else if (t == kInlet) {
+                    sm.sp[slot][0][ey][ex] = p.rho_in[0];
+                    sm.sp[slot][1][ey][ex] = p.rho_in[1];
+                } else {
+                    ++npull;
+                    if (inner && mine) ++ncol;
+                }
+                if (interior) sm.word[par2][(ey - 1) * TX + (ex - 1)] = mine && inner ? w : (1u << 30);
             }
-            word_cur = w;
         }
-        if (hex >= 0) {
-            const uint32_t w = __ldg(link_b + hx + hy * g.nx + (long long)zz * g.nxy);
-            T q0, q1;
-            Moments<T> d0, d1;
-            cell_pull<S>(fb, link_b, g, p, hx, hy, zz, w, false, d0, d1, q0, q1, r00, r01);
-            sp[slot][0][hey][hex] = q0;
-            sp[slot][1][hey][hex] = q1;
+        // exclusive scan of (npull, ncol) over the block, in thread order
+        int packed = npull | (ncol << 16);
+        int incl = packed;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) sm.wsum[warp] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int k = 0; k < TL::NW; ++k) {
+                const int c = sm.wsum[k];
+                sm.wsum[k] = acc;
+                acc += c;
+            }
+            sm.nwork = acc & 0xffff;
+            sm.ncoll[par2] = acc >> 16;
         }
         __syncthreads();
-        // collide the previous plane
+        {
+            int base = sm.wsum[warp] + incl - packed;
+            int wp = base & 0xffff, wc = base >> 16;
+#pragma unroll
+            for (int k = 0; k < TL::K; ++k) {
+                const int e = tid * TL::K + k;
+                if (e < TL::NE) {
+                    const uint32_t t = cell_type(w_e[k]);
+                    if (t != kSolid && t != kInlet) {
+                        const int ey = e / TL::EX, ex = e - ey * TL::EX;
+                        const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
+                        const bool mine = interior && tx0 + ex - 1 < g.nx && ty0 + ey - 1 < g.ny;
+                        const bool col = inner && mine;
+                        sm.work[wp++] = (uint16_t)(e | (col ? 0x8000 : 0));
+                        if (col) sm.coll[par2][wc++] = (uint16_t)((ey - 1) * TX + (ex - 1));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- pulls: pseudo-potential of the extended plane, moments of own cells
+        const int nwork = sm.nwork;
+        for (int j = tid; j < nwork; j += TL::NT) {
+            const int item = sm.work[j];
+            const int e = item & 0x7fff;
+            const bool want = (item & 0x8000) != 0;
+            int x, y;
+            ext_xy(e, x, y);
+            const int ey = e / TL::EX, ex = e - ey * TL::EX;
+            const uint32_t w = __ldg(link_b + x + y * g.nx + (long long)zz * g.nxy);
+            const int s = want ? (ey - 1) * TX + (ex - 1) : 0;
+#pragma unroll 1
+            for (int comp = 0; comp < 2; ++comp) {
+                T *mom = want ? &sm.mom[par2][comp * 10][s] : nullptr;
+                sm.sp[slot][comp][ey][ex] = cell_pull<S>(fb, link_b, g, x, y, zz, w, comp, mom, TL::NT, rin_b);
+            }
+        }
+        __syncthreads();
+
+        // ---- collide the previous plane
         const int cz = pz - 1;
-        if (cz >= z0 && cz < z1 && mine) {
-            const uint32_t word = word_prev;
-            const uint32_t t = cell_type(word);
-            const long long k = (long long)x + (long long)y * g.nx + (long long)cz * g.nxy;
-            if (t == kInlet) {
-                store_equilibrium<S, EQ>(fob, g.n, (int)k, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], r00);
-                store_equilibrium<S, EQ>(fob + kQ * g.n, g.n, (int)k, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2],
-                                         r01);
-                if (write_macro) {
-                    mac[k] = p.rho_in[0];
-                    mac[g.n + k] = p.rho_in[1];
-                    mac[2 * g.n + k] = p.u_in[0];
-                    mac[3 * g.n + k] = p.u_in[1];
-                    mac[4 * g.n + k] = p.u_in[2];
-                }
-            } else if (t == kSolid) {
-                if (write_macro)
-                    for (int c = 0; c < 5; ++c) mac[c * g.n + k] = T(0);
-            } else {
+        if (cz >= z0 && cz < z1) {
+            const int cpar = cz & 1;
+            const int sm_ = (cz + 3) % 3, sl = (cz + 2) % 3, su = (cz + 4) % 3;  // planes cz, cz-1, cz+1
+            const int ncl = sm.ncoll[cpar];
+            for (int j = tid; j < ncl; j += TL::NT) {
+                const int s = sm.coll[cpar][j];
+                const int lx = s % TX, ly = s / TX;
+                const long long k = (long long)(tx0 + lx) + (long long)(ty0 + ly) * g.nx + (long long)cz * g.nxy;
+                const uint32_t word = sm.word[cpar][s];
                 Moments<T> a0, a1;
-                {
-                    const T *ms = &sm_mom[cz & 1][0][threadIdx.x];
-                    a0.rho = ms[0]; a0.jx = ms[1 * TL::NT]; a0.jy = ms[2 * TL::NT]; a0.jz = ms[3 * TL::NT];
-                    a0.pxx = ms[4 * TL::NT]; a0.pyy = ms[5 * TL::NT]; a0.pzz = ms[6 * TL::NT];
-                    a0.pxy = ms[7 * TL::NT]; a0.pxz = ms[8 * TL::NT]; a0.pyz = ms[9 * TL::NT];
-                    a1.rho = ms[10 * TL::NT]; a1.jx = ms[11 * TL::NT]; a1.jy = ms[12 * TL::NT];
-                    a1.jz = ms[13 * TL::NT]; a1.pxx = ms[14 * TL::NT]; a1.pyy = ms[15 * TL::NT];
-                    a1.pzz = ms[16 * TL::NT]; a1.pxy = ms[17 * TL::NT]; a1.pxz = ms[18 * TL::NT];
-                    a1.pyz = ms[19 * TL::NT];
-                }
-                const int sm = (cz + 3) % 3, sl = (cz + 2) % 3, su = (cz + 4) % 3;  // planes cz, cz-1, cz+1
+                a0.rho = sm.mom[cpar][0][s]; a0.jx = sm.mom[cpar][1][s]; a0.jy = sm.mom[cpar][2][s];
+                a0.jz = sm.mom[cpar][3][s]; a0.pxx = sm.mom[cpar][4][s]; a0.pyy = sm.mom[cpar][5][s];
+                a0.pzz = sm.mom[cpar][6][s]; a0.pxy = sm.mom[cpar][7][s]; a0.pxz = sm.mom[cpar][8][s];
+                a0.pyz = sm.mom[cpar][9][s];
+                a1.rho = sm.mom[cpar][10][s]; a1.jx = sm.mom[cpar][11][s]; a1.jy = sm.mom[cpar][12][s];
+                a1.jz = sm.mom[cpar][13][s]; a1.pxx = sm.mom[cpar][14][s]; a1.pyy = sm.mom[cpar][15][s];
+                a1.pzz = sm.mom[cpar][16][s]; a1.pxy = sm.mom[cpar][17][s]; a1.pxz = sm.mom[cpar][18][s];
+                a1.pyz = sm.mom[cpar][19][s];
                 auto psi_at = [&](int i, T &v0, T &v1) {
-                    const int s = cz_slot(i, sl, sm, su);
-                    v0 = sp[s][0][ly + 1 + cy(i)][lx + 1 + cx(i)];
-                    v1 = sp[s][1][ly + 1 + cy(i)][lx + 1 + cx(i)];
+                    const int sl_ = cz_slot(i, sl, sm_, su);
+                    v0 = sm.sp[sl_][0][ly + 1 + cy(i)][lx + 1 + cx(i)];
+                    v1 = sm.sp[sl_][1][ly + 1 + cy(i)][lx + 1 + cx(i)];
+                };
+                auto sig_for = [&](int comp, T own_rho) {
+                    return [&, comp, own_rho](int i) -> T {
+                        return ref_value(((word >> i) & 1u)
+                                             ? own_rho
+                                             : sm.sp[cz_slot(i, sl, sm_, su)][comp][ly + 1 + cy(i)][lx + 1 + cx(i)]);
+                    };
                 };
                 const Forces<T> F = sc_forces<T>(psi_at, word, a0.rho, a1.rho, p, wall_model);
                 const T rho = a0.rho + a1.rho;
@@ -219,9 +263,13 @@ __global__ void __launch_bounds__(TX *TY) k_fused(const S *__restrict__ f, S *__
                 const T omega = T(1) - T(1) / tau;
                 const T fcoef = T(1) - T(1) / (T(2) * tau);
                 collide_store<S, EQ>(fob, g.n, (int)k, a0, ux, uy, uz, F.F[0][0], F.F[0][1], F.F[0][2], omega, fcoef,
-                                     r00);
+                                     sig_for(0, a0.rho));
                 collide_store<S, EQ>(fob + kQ * g.n, g.n, (int)k, a1, ux, uy, uz, F.F[1][0], F.F[1][1], F.F[1][2],
-                                     omega, fcoef, r01);
+                                     omega, fcoef, sig_for(1, a1.rho));
+                if constexpr (Storage<S>::shifted) {
+                    rout_b[k] = __float2half_rn((float)a0.rho);
+                    rout_b[g.n + k] = __float2half_rn((float)a1.rho);
+                }
                 if (write_macro) {
                     mac[k] = a0.rho;
                     mac[g.n + k] = a1.rho;
@@ -230,10 +278,50 @@ __global__ void __launch_bounds__(TX *TY) k_fused(const S *__restrict__ f, S *__
                     mac[4 * g.n + k] = uz;
                 }
             }
+            // INLET cells and, on the last update, the fields of SOLID cells
+            {
+                const int s = tid;
+                const uint32_t word = sm.word[cpar][s];
+                const int lx = s % TX, ly = s / TX;
+                const long long k = (long long)(tx0 + lx) + (long long)(ty0 + ly) * g.nx + (long long)cz * g.nxy;
+                if (!(word & (1u << 30))) {
+                    const uint32_t t = cell_type(word);
+                    if (t == kInlet) {
+                        auto sig_in = [&](int comp, T own_rho) {
+                            return [&, comp, own_rho](int i) -> T {
+                                return ref_value(
+                                    ((word >> i) & 1u)
+                                        ? own_rho
+                                        : sm.sp[cz_slot(i, sl, sm_, su)][comp][ly + 1 + cy(i)][lx + 1 + cx(i)]);
+                            };
+                        };
+                        store_equilibrium<S, EQ>(fob, g.n, (int)k, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2],
+                                                 sig_in(0, p.rho_in[0]));
+                        store_equilibrium<S, EQ>(fob + kQ * g.n, g.n, (int)k, p.rho_in[1], p.u_in[0], p.u_in[1],
+                                                 p.u_in[2], sig_in(1, p.rho_in[1]));
+                        if constexpr (Storage<S>::shifted) {
+                            rout_b[k] = __float2half_rn((float)p.rho_in[0]);
+                            rout_b[g.n + k] = __float2half_rn((float)p.rho_in[1]);
+                        }
+                        if (write_macro) {
+                            mac[k] = p.rho_in[0];
+                            mac[g.n + k] = p.rho_in[1];
+                            mac[2 * g.n + k] = p.u_in[0];
+                            mac[3 * g.n + k] = p.u_in[1];
+                            mac[4 * g.n + k] = p.u_in[2];
+                        }
+                    } else if (t == kSolid && write_macro) {
+                        for (int c = 0; c < 5; ++c) mac[c * g.n + k] = T(0);
+                    }
+                }
+            }
         }
-        word_prev = word_cur;
         __syncthreads();
     }
+}
+
+template <class T, int TX, int TY> constexpr int fused_smem_bytes() {
+    return (int)((sizeof(FusedSmem<T, TX, TY>) + 15) / 16 * 16);
 }
 
 template <class S, int EQ, int TX, int TY>
@@ -253,8 +341,8 @@ static cudaError_t launch_fused_tile(const StepArgs &a, int zchunk) {
         attr_set = true;
     }
     k_fused<S, EQ, TX, TY><<<(unsigned)blocks, TX * TY, smem, a.stream>>>(
-        (const S *)a.f_in, (S *)a.f_out, a.link, (T *)a.macro, a.g, (const InstParam<T> *)a.par, (T)a.rho0[0],
-        (T)a.rho0[1], a.wall_model, a.write_macro, tiles_x, tiles_y, zchunk, nchunks);
+        (const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link, (T *)a.macro, a.g,
+        (const InstParam<T> *)a.par, a.wall_model, a.write_macro, tiles_x, tiles_y, zchunk, nchunks);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,8 @@ struct StepArgs {
     void *psi;
     void *macro;
     const void *par;   // InstParam<T>[batch] on the device
-    double rho0[2];
+    const Ref *ref_in; // reference densities of the current state (unused in FP64)
+    Ref *ref_out;      // reference densities written with f_out
     cudaStream_t stream;
 };
 
@@ -33,8 +34,8 @@ struct InitArgs {
     const double *r1, *r2, *u;  // device FP64 fields (u interleaved)
     const uint32_t *link;
     void *f_out, *macro, *usnap;
+    Ref *ref_out;
     const void *par;
-    double rho0[2];
     cudaStream_t stream;
 };
 
@@ -56,6 +57,9 @@ cudaError_t launch_two_pass(const StepArgs &a);
 // tile: 0 = 32x8, 1 = 32x4, 2 = 64x4, 3 = 32x16 cells per CTA; zchunk planes per CTA
 cudaError_t launch_fused(const StepArgs &a, int tile, int zchunk);
 int fused_tile_count();
+// nsteps updates in one persistent launch, one thread-block cluster per instance
+cudaError_t launch_cluster(const StepArgs &a, int nsteps);
+int cluster_size_for(long long n);
 cudaError_t launch_init(const InitArgs &a);
 cudaError_t launch_links(const uint8_t *type, uint32_t *link, const Grid &g, int batch, cudaStream_t s);
 cudaError_t launch_macro_to_f64(const void *macro, bool fp64, double *r1, double *r2, double *u, const Grid &g,
@@ -63,7 +67,7 @@ cudaError_t launch_macro_to_f64(const void *macro, bool fp64, double *r1, double
 cudaError_t launch_reduce(const ReduceArgs &a, int *launches);
 // out != NULL: expand f to FP64 into out; otherwise store `in` (FP64) into fo.
 cudaError_t launch_f_convert(lbm_precision prec, const void *f, double *out, const double *in, void *fo,
-                             const Grid &g, int batch, const double *rho0, cudaStream_t s);
+                             const Ref *ref, const uint32_t *link, const Grid &g, int batch, cudaStream_t s);
 int reduce_blocks(long long n);
 
 }  // namespace lbm

@@ -7,7 +7,8 @@
 //              neighbours, forces, u_F, tau_mix, regularised collision, store.
 //
 // Layout in HBM (per instance b): f[b][alpha][i][cell], cell = x + nx (y + ny z);
-// psi[b][alpha][cell]; macro[b][{rho1, rho2, ux, uy, uz}][cell]; geometry word
+// psi[b][alpha][cell]; macro[b][{rho1, rho2, ux, uy, uz}][cell]; reference
+// densities ref[b][alpha][cell] (FP16, double-buffered with f); geometry word
 // link[b][cell] (bits 0..18 SOLID neighbours, bits 24..25 cell type).
 #include "lbm_internal.h"
 #include "lbm_device.cuh"
@@ -39,10 +40,17 @@ __device__ __forceinline__ void source_cell(const uint32_t *__restrict__ link_b,
 }
 
 template <class S>
-__global__ void __launch_bounds__(256) k_psi(const S *__restrict__ f, const uint32_t *__restrict__ link,
-                                             typename Storage<S>::T *__restrict__ psi, Grid g,
-                                             const InstParam<typename Storage<S>::T> *__restrict__ par,
-                                             typename Storage<S>::T rho0_0, typename Storage<S>::T rho0_1) {
+__device__ __forceinline__ typename Storage<S>::T ref_at(const Ref *__restrict__ r, long long idx) {
+    if constexpr (Storage<S>::shifted)
+        return (typename Storage<S>::T)__half2float(r[idx]);
+    else
+        return typename Storage<S>::T(0);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_psi(const S *__restrict__ f, const Ref *__restrict__ rin,
+                                             const uint32_t *__restrict__ link, typename Storage<S>::T *__restrict__ psi,
+                                             Grid g, const InstParam<typename Storage<S>::T> *__restrict__ par) {
     using T = typename Storage<S>::T;
     const int b = blockIdx.y;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -67,8 +75,9 @@ __global__ void __launch_bounds__(256) k_psi(const S *__restrict__ f, const uint
         nb.init(x, y, z, g);
         const int self = x + y * g.nx + z * g.nxy;
         const S *fb = f + (long long)b * 2 * kQ * g.n;
-        p0 = pull_density<S>(fb, g.n, self, nb, sw, rho0_0);
-        p1 = pull_density<S>(fb + kQ * g.n, g.n, self, nb, sw, rho0_1);
+        const long long rb = (long long)b * 2 * g.n;
+        p0 = pull_density<S>(fb, g.n, self, nb, sw, ref_at<S>(rin, rb + self));
+        p1 = pull_density<S>(fb + kQ * g.n, g.n, self, nb, sw, ref_at<S>(rin, rb + g.n + self));
     }
     psi[((long long)b * 2 + 0) * g.n + k] = p0;
     psi[((long long)b * 2 + 1) * g.n + k] = p1;
@@ -76,11 +85,11 @@ __global__ void __launch_bounds__(256) k_psi(const S *__restrict__ f, const uint
 
 template <class S, int EQ>
 __global__ void __launch_bounds__(256) k_collide(const S *__restrict__ f, S *__restrict__ fo,
+                                                 const Ref *__restrict__ rin, Ref *__restrict__ rout,
                                                  const uint32_t *__restrict__ link,
                                                  const typename Storage<S>::T *__restrict__ psi,
                                                  typename Storage<S>::T *__restrict__ macro, Grid g,
                                                  const InstParam<typename Storage<S>::T> *__restrict__ par,
-                                                 typename Storage<S>::T rho0_0, typename Storage<S>::T rho0_1,
                                                  int wall_model, int write_macro) {
     using T = typename Storage<S>::T;
     const int b = blockIdx.y;
@@ -91,16 +100,35 @@ __global__ void __launch_bounds__(256) k_collide(const S *__restrict__ f, S *__r
     const uint32_t t = cell_type(word);
     const InstParam<T> &p = par[b];
     const long long fofs = (long long)b * 2 * kQ * g.n;
+    const long long rb = (long long)b * 2 * g.n;
     T *mac = macro + (long long)b * 5 * g.n;
     if (t == kSolid) {
         if (write_macro)
             for (int c = 0; c < 5; ++c) mac[c * g.n + k] = T(0);
         return;
     }
+    int x, y, z;
+    cell_coords(k, g, x, y, z);
+    Nbr own;
+    own.init(x, y, z, g);
+    const T *psi0 = psi + (long long)b * 2 * g.n;
+    const T *psi1 = psi0 + g.n;
+    // reference density of the cell each value streams into (own cell when the
+    // neighbour is SOLID and the value bounces back)
+    auto sig_for = [&](const T *ps, T own_rho) {
+        return [=, &own](int i) -> T {
+            return ref_value(((word >> i) & 1u) ? own_rho : __ldg(ps + own.dst(i)));
+        };
+    };
     if (t == kInlet) {
-        store_equilibrium<S, EQ>(fo + fofs, g.n, (int)k, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], rho0_0);
+        store_equilibrium<S, EQ>(fo + fofs, g.n, (int)k, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2],
+                                 sig_for(psi0, p.rho_in[0]));
         store_equilibrium<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2],
-                                 rho0_1);
+                                 sig_for(psi1, p.rho_in[1]));
+        if constexpr (Storage<S>::shifted) {
+            rout[rb + k] = __float2half_rn((float)p.rho_in[0]);
+            rout[rb + g.n + k] = __float2half_rn((float)p.rho_in[1]);
+        }
         if (write_macro) {
             mac[k] = p.rho_in[0];
             mac[g.n + k] = p.rho_in[1];
@@ -110,26 +138,20 @@ __global__ void __launch_bounds__(256) k_collide(const S *__restrict__ f, S *__r
         }
         return;
     }
-    int x, y, z;
-    cell_coords(k, g, x, y, z);
-    Nbr own;
-    own.init(x, y, z, g);
     int sx = x;
     uint32_t sw;
     source_cell(link_b, word, sx, y, z, g, sw);
     Moments<T> m0, m1;
     if (sx == x) {
-        m0 = pull_moments<S>(f + fofs, g.n, (int)k, own, sw, rho0_0);
-        m1 = pull_moments<S>(f + fofs + kQ * g.n, g.n, (int)k, own, sw, rho0_1);
+        m0 = pull_moments<S>(f + fofs, g.n, (int)k, own, sw, ref_at<S>(rin, rb + k));
+        m1 = pull_moments<S>(f + fofs + kQ * g.n, g.n, (int)k, own, sw, ref_at<S>(rin, rb + g.n + k));
     } else {
         Nbr up;
         up.init(sx, y, z, g);
         const int self = sx + y * g.nx + z * g.nxy;
-        m0 = pull_moments<S>(f + fofs, g.n, self, up, sw, rho0_0);
-        m1 = pull_moments<S>(f + fofs + kQ * g.n, g.n, self, up, sw, rho0_1);
+        m0 = pull_moments<S>(f + fofs, g.n, self, up, sw, ref_at<S>(rin, rb + self));
+        m1 = pull_moments<S>(f + fofs + kQ * g.n, g.n, self, up, sw, ref_at<S>(rin, rb + g.n + self));
     }
-    const T *psi0 = psi + (long long)b * 2 * g.n;
-    const T *psi1 = psi0 + g.n;
     auto psi_at = [&](int i, T &a, T &c) {
         const int j = own.dst(i);
         a = __ldg(psi0 + j);
@@ -146,9 +168,13 @@ __global__ void __launch_bounds__(256) k_collide(const S *__restrict__ f, S *__r
     const T omega = T(1) - T(1) / tau;
     const T fcoef = T(1) - T(1) / (T(2) * tau);
     collide_store<S, EQ>(fo + fofs, g.n, (int)k, m0, ux, uy, uz, F.F[0][0], F.F[0][1], F.F[0][2], omega, fcoef,
-                         rho0_0);
+                         sig_for(psi0, m0.rho));
     collide_store<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, m1, ux, uy, uz, F.F[1][0], F.F[1][1], F.F[1][2], omega,
-                         fcoef, rho0_1);
+                         fcoef, sig_for(psi1, m1.rho));
+    if constexpr (Storage<S>::shifted) {
+        rout[rb + k] = __float2half_rn((float)m0.rho);
+        rout[rb + g.n + k] = __float2half_rn((float)m1.rho);
+    }
     if (write_macro) {
         mac[k] = m0.rho;
         mac[g.n + k] = m1.rho;
@@ -158,20 +184,28 @@ __global__ void __launch_bounds__(256) k_collide(const S *__restrict__ f, S *__r
     }
 }
 
-// f := feq(rho_alpha, u) from FP64 fields (u interleaved [b][cell][3]).
+// f := feq(rho_alpha, u) from FP64 fields (u interleaved [b][cell][3]); the
+// reference densities are the initial densities.
 template <class S, int EQ>
 __global__ void k_init(const double *__restrict__ r1, const double *__restrict__ r2, const double *__restrict__ u,
-                       const uint32_t *__restrict__ link, S *__restrict__ fo, typename Storage<S>::T *__restrict__ macro,
-                       typename Storage<S>::T *__restrict__ usnap, Grid g,
-                       const InstParam<typename Storage<S>::T> *__restrict__ par, typename Storage<S>::T rho0_0,
-                       typename Storage<S>::T rho0_1) {
+                       const uint32_t *__restrict__ link, S *__restrict__ fo, Ref *__restrict__ rout,
+                       typename Storage<S>::T *__restrict__ macro, typename Storage<S>::T *__restrict__ usnap, Grid g,
+                       const InstParam<typename Storage<S>::T> *__restrict__ par) {
     using T = typename Storage<S>::T;
     const int b = blockIdx.y;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
     const long long gk = (long long)b * g.n + k;
-    const uint32_t t = cell_type(link[gk]);
+    const uint32_t word = link[gk];
+    const uint32_t t = cell_type(word);
     const InstParam<T> &p = par[b];
+    // initial density of a cell as its neighbours see it
+    auto init_rho = [&](long long cell, int comp) -> T {
+        const uint32_t tc = cell_type(link[(long long)b * g.n + cell]);
+        if (tc == kSolid) return T(0);
+        if (tc == kInlet) return p.rho_in[comp];
+        return (T)(comp == 0 ? r1 : r2)[(long long)b * g.n + cell];
+    };
     T a0, a1, ux, uy, uz;
     if (t == kSolid) {
         a0 = a1 = ux = uy = uz = T(0);
@@ -182,9 +216,19 @@ __global__ void k_init(const double *__restrict__ r1, const double *__restrict__
         a0 = (T)r1[gk]; a1 = (T)r2[gk];
         ux = (T)u[3 * gk]; uy = (T)u[3 * gk + 1]; uz = (T)u[3 * gk + 2];
     }
+    int x, y, z;
+    cell_coords(k, g, x, y, z);
+    Nbr nb;
+    nb.init(x, y, z, g);
     const long long fofs = (long long)b * 2 * kQ * g.n;
-    store_equilibrium<S, EQ>(fo + fofs, g.n, (int)k, a0, ux, uy, uz, rho0_0);
-    store_equilibrium<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, a1, ux, uy, uz, rho0_1);
+    store_equilibrium<S, EQ>(fo + fofs, g.n, (int)k, a0, ux, uy, uz,
+                             [&](int i) -> T { return ref_value(((word >> i) & 1u) ? a0 : init_rho(nb.dst(i), 0)); });
+    store_equilibrium<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, a1, ux, uy, uz,
+                             [&](int i) -> T { return ref_value(((word >> i) & 1u) ? a1 : init_rho(nb.dst(i), 1)); });
+    if constexpr (Storage<S>::shifted) {
+        rout[(long long)b * 2 * g.n + k] = __float2half_rn((float)a0);
+        rout[(long long)b * 2 * g.n + g.n + k] = __float2half_rn((float)a1);
+    }
     T *mac = macro + (long long)b * 5 * g.n;
     mac[k] = a0; mac[g.n + k] = a1;
     mac[2 * g.n + k] = ux; mac[3 * g.n + k] = uy; mac[4 * g.n + k] = uz;
@@ -224,22 +268,37 @@ __global__ void k_macro_to_f64(const T *__restrict__ macro, double *__restrict__
     u[3 * gk + 2] = (double)mac[4 * g.n + k];
 }
 
-// Distributions <-> FP64 (plane p = (b*2 + alpha)*19 + i holds direction i).
+// Distributions <-> FP64, one thread per cell and component: value i of cell x
+// is stored relative to the reference density of x + c_i (or of x itself when
+// x + c_i is SOLID).
 template <class S>
 __global__ void k_f_convert(const S *__restrict__ f, double *__restrict__ out, const double *__restrict__ in,
-                            S *__restrict__ fo, long long n, int planes, double rho0_0, double rho0_1) {
+                            S *__restrict__ fo, const Ref *__restrict__ ref, const uint32_t *__restrict__ link,
+                            Grid g) {
     using T = typename Storage<S>::T;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = blockIdx.y;
-    if (k >= n || p >= planes) return;
-    const int i = p % kQ;
-    const int alpha = (p / kQ) & 1;
-    const T sh = Storage<S>::shifted ? wgt<T>(i) * (T)(alpha ? rho0_1 : rho0_0) : T(0);
-    const long long idx = (long long)p * n + k;
-    if (out)
-        out[idx] = (double)Storage<S>::load(f + idx, sh);
-    else
-        Storage<S>::store(fo + idx, (T)in[idx], sh);
+    const int bc = blockIdx.y;  // b * 2 + alpha
+    if (k >= g.n) return;
+    const int b = bc >> 1;
+    const uint32_t word = link[(long long)b * g.n + k];
+    int x, y, z;
+    cell_coords(k, g, x, y, z);
+    Nbr nb;
+    nb.init(x, y, z, g);
+    const long long rb = (long long)bc * g.n;
+#pragma unroll 1
+    for (int i = 0; i < kQ; ++i) {
+        T sh = T(0);
+        if constexpr (Storage<S>::shifted) {
+            const long long src = ((word >> i) & 1u) ? k : nb.dst(i);
+            sh = wgt<T>(i) * (T)__half2float(ref[rb + src]);
+        }
+        const long long idx = ((long long)bc * kQ + i) * g.n + k;
+        if (out)
+            out[idx] = (double)Storage<S>::load(f + idx, sh);
+        else
+            Storage<S>::store(fo + idx, (T)in[idx], sh);
+    }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -252,16 +311,15 @@ template <class S>
 static cudaError_t launch_two_pass_t(const StepArgs &a) {
     using T = typename Storage<S>::T;
     const dim3 grid = cell_grid(a.g, a.batch, 256);
-    const T r00 = (T)a.rho0[0], r01 = (T)a.rho0[1];
-    k_psi<S><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, a.link, (T *)a.psi, a.g, (const InstParam<T> *)a.par, r00,
-                                         r01);
+    k_psi<S><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, a.ref_in, a.link, (T *)a.psi, a.g,
+                                         (const InstParam<T> *)a.par);
     if (a.eq_order == 0)
-        k_collide<S, 0><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.link, (const T *)a.psi,
-                                                    (T *)a.macro, a.g, (const InstParam<T> *)a.par, r00, r01,
+        k_collide<S, 0><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
+                                                    (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
                                                     a.wall_model, a.write_macro);
     else
-        k_collide<S, 1><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.link, (const T *)a.psi,
-                                                    (T *)a.macro, a.g, (const InstParam<T> *)a.par, r00, r01,
+        k_collide<S, 1><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
+                                                    (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
                                                     a.wall_model, a.write_macro);
     return cudaGetLastError();
 }
@@ -280,13 +338,12 @@ template <class S>
 static cudaError_t launch_init_t(const InitArgs &a) {
     using T = typename Storage<S>::T;
     const dim3 grid = cell_grid(a.g, a.batch, 256);
-    const T r00 = (T)a.rho0[0], r01 = (T)a.rho0[1];
     if (a.eq_order == 0)
-        k_init<S, 0><<<grid, 256, 0, a.stream>>>(a.r1, a.r2, a.u, a.link, (S *)a.f_out, (T *)a.macro, (T *)a.usnap,
-                                                 a.g, (const InstParam<T> *)a.par, r00, r01);
+        k_init<S, 0><<<grid, 256, 0, a.stream>>>(a.r1, a.r2, a.u, a.link, (S *)a.f_out, a.ref_out, (T *)a.macro,
+                                                 (T *)a.usnap, a.g, (const InstParam<T> *)a.par);
     else
-        k_init<S, 1><<<grid, 256, 0, a.stream>>>(a.r1, a.r2, a.u, a.link, (S *)a.f_out, (T *)a.macro, (T *)a.usnap,
-                                                 a.g, (const InstParam<T> *)a.par, r00, r01);
+        k_init<S, 1><<<grid, 256, 0, a.stream>>>(a.r1, a.r2, a.u, a.link, (S *)a.f_out, a.ref_out, (T *)a.macro,
+                                                 (T *)a.usnap, a.g, (const InstParam<T> *)a.par);
     return cudaGetLastError();
 }
 
@@ -301,21 +358,20 @@ cudaError_t launch_init(const InitArgs &a) {
 }
 
 template <class S>
-static cudaError_t launch_f_convert_t(const void *f, double *out, const double *in, void *fo, const Grid &g, int batch,
-                                      const double *rho0, cudaStream_t s) {
-    const int planes = batch * 2 * kQ;
-    const dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)planes, 1);
-    k_f_convert<S><<<grid, 256, 0, s>>>((const S *)f, out, in, (S *)fo, g.n, planes, rho0[0], rho0[1]);
+static cudaError_t launch_f_convert_t(const void *f, double *out, const double *in, void *fo, const Ref *ref,
+                                      const uint32_t *link, const Grid &g, int batch, cudaStream_t s) {
+    const dim3 grid((unsigned)((g.n + 255) / 256), (unsigned)(batch * 2), 1);
+    k_f_convert<S><<<grid, 256, 0, s>>>((const S *)f, out, in, (S *)fo, ref, link, g);
     return cudaGetLastError();
 }
 
 cudaError_t launch_f_convert(lbm_precision prec, const void *f, double *out, const double *in, void *fo,
-                             const Grid &g, int batch, const double *rho0, cudaStream_t s) {
+                             const Ref *ref, const uint32_t *link, const Grid &g, int batch, cudaStream_t s) {
     switch (prec) {
-    case LBM_FP64: return launch_f_convert_t<double>(f, out, in, fo, g, batch, rho0, s);
-    case LBM_FP32: return launch_f_convert_t<float>(f, out, in, fo, g, batch, rho0, s);
-    case LBM_FP32_F16S: return launch_f_convert_t<__half>(f, out, in, fo, g, batch, rho0, s);
-    case LBM_FP32_BF16S: return launch_f_convert_t<__nv_bfloat16>(f, out, in, fo, g, batch, rho0, s);
+    case LBM_FP64: return launch_f_convert_t<double>(f, out, in, fo, ref, link, g, batch, s);
+    case LBM_FP32: return launch_f_convert_t<float>(f, out, in, fo, ref, link, g, batch, s);
+    case LBM_FP32_F16S: return launch_f_convert_t<__half>(f, out, in, fo, ref, link, g, batch, s);
+    case LBM_FP32_BF16S: return launch_f_convert_t<__nv_bfloat16>(f, out, in, fo, ref, link, g, batch, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -2,8 +2,12 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 
 namespace lbm {
+
+// storage type of the per-cell reference density of the shifted formats
+using Ref = __half;
 
 // Per-instance parameters in the arithmetic type T (double or float).
 template <class T> struct InstParam {

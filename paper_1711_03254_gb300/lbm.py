@@ -33,8 +33,7 @@ class LbmError(RuntimeError):
 
 class lbm_config(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("batch", ctypes.c_int),
-                ("precision", ctypes.c_int), ("eq_order", ctypes.c_int), ("wall_model", ctypes.c_int),
-                ("rho0_shift", ctypes.c_double * 2)]
+                ("precision", ctypes.c_int), ("eq_order", ctypes.c_int), ("wall_model", ctypes.c_int)]
 
 
 class lbm_instance_params(ctypes.Structure):
@@ -70,6 +69,9 @@ def library() -> ctypes.CDLL:
         L.lbm_set_stream.argtypes = [vp, vp]
         L.lbm_set_kernel.argtypes = [vp, ctypes.c_int]
         L.lbm_set_tiling.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.lbm_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]
+        L.lbm_run_to_steady.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), dp]
         L.lbm_launch_count.argtypes = [vp]
         L.lbm_launch_count.restype = ctypes.c_longlong
         L.lbm_set_allocator.argtypes = [_ALLOC_T, _FREE_T]
@@ -78,7 +80,7 @@ def library() -> ctypes.CDLL:
         L.lbm_destroy.argtypes = [vp]
         L.lbm_destroy.restype = None
         for name in ("lbm_create", "lbm_set_geometry", "lbm_set_fields", "lbm_step", "lbm_get_fields",
-                     "lbm_reduce", "lbm_get_distributions", "lbm_set_distributions", "lbm_get_state", "lbm_set_state", "lbm_set_stream", "lbm_set_kernel", "lbm_set_tiling",
+                     "lbm_reduce", "lbm_get_distributions", "lbm_set_distributions", "lbm_get_state", "lbm_set_state", "lbm_set_stream", "lbm_set_kernel", "lbm_set_tiling", "lbm_autotune", "lbm_run_to_steady",
                      "lbm_set_allocator"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -122,12 +124,11 @@ def use_torch_allocator():
     lbm_set_allocator(alloc, release)
 
 
-def make_config(nx, ny, nz, batch=1, precision="fp64", eq_order=0, wall_model=0, rho0_shift=(1.0, 1.0)):
+def make_config(nx, ny, nz, batch=1, precision="fp64", eq_order=0, wall_model=2):
     c = lbm_config()
     c.nx, c.ny, c.nz, c.batch = int(nx), int(ny), int(nz), int(batch)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     c.eq_order, c.wall_model = int(eq_order), int(wall_model)
-    c.rho0_shift[:] = [float(rho0_shift[0]), float(rho0_shift[1])]
     return c
 
 
@@ -223,10 +224,9 @@ def lbm_destroy(ctx):
 class Sim:
     """Small convenience wrapper holding one context (same calls, same order)."""
 
-    def __init__(self, nx, ny, nz, params, precision="fp64", eq_order=0, wall_model=0, rho0_shift=(1.0, 1.0),
-                 kernel="auto"):
+    def __init__(self, nx, ny, nz, params, precision="fp64", eq_order=0, wall_model=2, kernel="auto"):
         self.shape = (len(params), nz, ny, nx)
-        self.cfg = make_config(nx, ny, nz, len(params), precision, eq_order, wall_model, rho0_shift)
+        self.cfg = make_config(nx, ny, nz, len(params), precision, eq_order, wall_model)
         self._params = make_params(params)
         self.ctx = lbm_create(self.cfg, self._params)
         if kernel != "auto":
@@ -286,3 +286,20 @@ class Sim:
 
 def lbm_last_error(ctx=None) -> str:
     return library().lbm_last_error(ctx).decode()
+
+
+def lbm_autotune(ctx, steps_per_trial: int = 5, cache_path: str | None = None):
+    """Time the kernel strategies and tilings; returns (strategy, tile, zchunk)."""
+    out = (ctypes.c_int * 3)()
+    cp = cache_path.encode() if cache_path else None
+    _check(library().lbm_autotune(ctx, int(steps_per_trial), cp, out), ctx)
+    return tuple(out)
+
+
+def lbm_run_to_steady(ctx, check_every: int, tol: float, max_steps: int, batch: int):
+    """Advance until every residual <= tol; returns (updates done, residuals)."""
+    done = ctypes.c_int(0)
+    res = np.zeros(batch)
+    rc = library().lbm_run_to_steady(ctx, int(check_every), float(tol), int(max_steps), ctypes.byref(done), _dp(res))
+    _check(rc, ctx)
+    return done.value, res

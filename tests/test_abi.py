@@ -68,5 +68,5 @@ def test_allocator_hook_needs_both(lbm):
 
 def test_structs_match_header(lbm):
     import ctypes
-    assert ctypes.sizeof(lbm.lbm_config) == 7 * 4 + 4 + 16  # 7 ints, padding, 2 doubles
+    assert ctypes.sizeof(lbm.lbm_config) == 7 * 4  # 7 ints
     assert ctypes.sizeof(lbm.lbm_instance_params) == 12 * 8

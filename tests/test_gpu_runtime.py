@@ -1,0 +1,93 @@
+"""Runtime features through the C ABI on the GPU: autotuner, graph-replayed
+run to steady state, CUDA stream hand-off and the torch allocator hook."""
+import numpy as np
+import pytest
+
+from paper_1711_03254_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_03254_gb300 import build
+    build.build()
+    from paper_1711_03254_gb300 import lbm as mod
+    return mod
+
+
+def _sim(lbm, n=24, precision="fp64", **kw):
+    t, r1, r2, u = W.droplet(n, n, n, n / 4)
+    t[:, 0, :] = W.SOLID
+    r1[t == W.SOLID] = 0
+    r2[t == W.SOLID] = 0
+    s = lbm.Sim(n, n, n, [dict(tau=(0.8, 1.2), G=-1.8, rho_s=0.1, g=(1e-5, 0, 0))], precision=precision, **kw)
+    s.set_geometry(t[None])
+    s.set_fields(r1[None], r2[None], u[None])
+    return s
+
+
+def test_autotune_keeps_state_and_results(lbm, tmp_path):
+    """Tuning leaves the state untouched: the next updates match a run that
+    never tuned, and a second tune hits the cache file."""
+    a = _sim(lbm)
+    b = _sim(lbm, kernel="two_pass")
+    a.step(3)
+    b.step(3)
+    cache = str(tmp_path / "tune.jsonl")
+    k, t, z = lbm.lbm_autotune(a.ctx, 2, cache)
+    assert k in (1, 2, 3)
+    a.step(10)
+    b.step(10)
+    for x, y in zip(a.get_fields(), b.get_fields()):
+        assert np.allclose(x, y, rtol=0, atol=1e-13)
+    c = _sim(lbm)
+    assert lbm.lbm_autotune(c.ctx, 2, cache) == (k, t, z)
+    assert len(open(cache).read().strip().splitlines()) == 1
+
+
+@pytest.mark.parametrize("check_every", [50, 25])
+def test_run_to_steady_matches_plain_steps(lbm, check_every):
+    """The graph-replayed loop stops once the residual is below tol and leaves
+    the same state as plain updates of the same count."""
+    a = _sim(lbm, precision="fp32")
+    done, res = lbm.lbm_run_to_steady(a.ctx, check_every, 1e-4, 4000, 1)
+    assert done % check_every == 0 and 0 < done <= 4000
+    assert res[0] <= 1e-4 or done == 4000
+    b = _sim(lbm, precision="fp32")
+    for _ in range(done // check_every):
+        b.step(check_every)
+        b.reduce()
+    for x, y in zip(a.get_fields(), b.get_fields()):
+        assert np.array_equal(x, y)
+
+
+def test_stream_and_torch_allocator(lbm):
+    import torch
+    lbm.use_torch_allocator()
+    try:
+        s = torch.cuda.Stream()
+        a = _sim(lbm, precision="fp32")
+        lbm.lbm_set_stream(a.ctx, s.cuda_stream)
+        a.step(20)
+        ref = _sim(lbm, precision="fp32")
+        ref.step(20)
+        for x, y in zip(a.get_fields(), ref.get_fields()):
+            assert np.array_equal(x, y)
+        a.close()
+    finally:
+        lbm.lbm_set_allocator()
+
+
+def test_launch_counts(lbm):
+    a = _sim(lbm, precision="fp32", kernel="fused")
+    l0 = a.launches
+    a.step(7)
+    assert a.launches - l0 == 7
+    b = _sim(lbm, precision="fp32", kernel="cluster")
+    l0 = b.launches
+    b.step(7)
+    assert b.launches - l0 == 1

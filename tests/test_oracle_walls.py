@@ -1,0 +1,91 @@
+"""Pins of the oracle's wall model 2 (Eq. 11 with rho'_beta of a solid
+neighbour = the cell's own rho_beta + rho^s_beta).
+
+Closed forms: the interaction stencil sums to zero over all 18 neighbours
+(sum_i ws_i c_i = 0), so next to any wall
+  * a uniform fluid feels no interaction force when rho^s = 0, and
+  * with rho^s != 0 the force is exactly G rho_alpha rho^s_beta D, where
+    D = sum over SOLID neighbours of ws_i c_i (ws_i = 2 w_i).
+"""
+import numpy as np
+
+from paper_1711_03254_gb300 import workloads as W
+
+
+def _geometry(n=8):
+    t = np.zeros((n, n, n), np.uint8)
+    t[:, 0, :] = W.SOLID
+    t[2, 4, 5] = W.SOLID
+    t[5, 2:4, 1] = W.SOLID
+    return t
+
+
+def _one_step_force(oracle_mod, t, rho1, rho2, rho_s, G=-2.0):
+    n = t.shape[0]
+    r1 = np.where(t == W.SOLID, 0.0, rho1)
+    r2 = np.where(t == W.SOLID, 0.0, rho2)
+    sim = oracle_mod.OracleSim(n, n, n, [dict(tau=(1.0, 1.0), G=G, rho_s=rho_s)], wall_model=2)
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], np.zeros((1, n, n, n, 3)))
+    sim.step(1)
+    a, b, _ = sim.get_fields()
+    return sim.get_force()[0], a[0], b[0]
+
+
+def test_neutral_wall_exerts_no_force(oracle_mod):
+    """Uniform mixture at rest next to walls, rho^s = 0: every cell's
+    interaction force vanishes (the streamed fields stay uniform)."""
+    t = _geometry()
+    F, a, b = _one_step_force(oracle_mod, t, 0.4, 0.6, 0.0)
+    assert np.allclose(a[t != W.SOLID], 0.4, atol=1e-15)
+    assert np.abs(F).max() < 1e-15
+
+
+def test_wall_potential_force_closed_form(oracle_mod):
+    """Uniform mixture, rho^s = 0.3 (acts on component 1 through rho^s_2):
+    F^1 = G rho_1 rho^s_2 D and F^2 = 0 in every fluid cell."""
+    c, w, _ = oracle_mod.lattice()
+    t = _geometry()
+    n = t.shape[0]
+    G, rs = -2.0, 0.3
+    F, a, b = _one_step_force(oracle_mod, t, 0.4, 0.6, rs, G)
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                if t[z, y, x] == W.SOLID:
+                    continue
+                D = np.zeros(3)
+                for i in range(1, 19):
+                    zz, yy, xx = (z + c[i, 2]) % n, (y + c[i, 1]) % n, (x + c[i, 0]) % n
+                    if t[zz, yy, xx] == W.SOLID:
+                        D += 2 * w[i] * c[i]
+                assert np.allclose(F[0, z, y, x], G * 0.4 * rs * D, atol=1e-15)
+                assert np.allclose(F[1, z, y, x], 0.0, atol=1e-15)
+
+
+def test_wall_model2_mass_and_symmetry(oracle_mod):
+    """Walls of model 2 keep each component's mass, and exchanging the
+    components together with rho^s -> -rho^s mirrors the evolution."""
+    n = 10
+    t, r1, r2, u = W.layered_channel(n, n, n, layout="12")
+    t[:, 4, 4] = W.SOLID
+    r1[t == W.SOLID] = 0
+    r2[t == W.SOLID] = 0
+    outs = []
+    for swap in (False, True):
+        p = dict(tau=(0.7, 1.9), G=-2.0, rho_s=0.25, g=(2e-5, 0, 0))
+        a, b = r1, r2
+        if swap:
+            p = dict(tau=(1.9, 0.7), G=-2.0, rho_s=-0.25, g=(2e-5, 0, 0))
+            a, b = r2, r1
+        sim = oracle_mod.OracleSim(n, n, n, [p], wall_model=2)
+        sim.set_geometry(t[None])
+        sim.set_fields(a[None], b[None], u[None])
+        m0 = sim.reduce()[0]
+        sim.step(60)
+        m = sim.reduce()[0]
+        assert abs(m[0] - m0[0]) / m0[0] < 1e-13 and abs(m[1] - m0[1]) / m0[1] < 1e-13
+        outs.append(sim.get_fields())
+    (a1, b1, u1), (a2, b2, u2) = outs
+    assert np.allclose(a1, b2, atol=1e-13) and np.allclose(b1, a2, atol=1e-13)
+    assert np.allclose(u1, u2, atol=1e-13)
