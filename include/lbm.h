@@ -188,6 +188,25 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
 lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_steps, int *steps_done,
                              double *residual);
 
+/* Allocation-free FP64 field sums (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory when they need the check, e.g.
+ * code inside a fixed-size memory pool, a real-time loop that must not call
+ * cudaMalloc because it synchronises the device, or a host application that
+ * owns all GPU memory).  Same sums as lbm_reduce, computed from caller-owned
+ * device arrays: rho1, rho2 [batch][ncells] and u [batch][ncells][3] (FP64),
+ * cell_type [batch][ncells] (uint8, SOLID cells skipped); writes the device
+ * array out[batch][6] = {M1, M2, Px, Py, Pz, max|u|} (max|u| is NaN if a value
+ * is not finite).  Work is queued on `stream` (a cudaStream_t, NULL = legacy
+ * default) and not synchronised.  The per-block partial sums live in a fixed
+ * 1 MiB device array inside the library (held by every GPU that loads it until
+ * exit), so no call allocates; every call overwrites the part it uses, and two
+ * calls that overlap on the GPU race on that array.  The first call on a
+ * device looks up the array's device address; make that first call before any
+ * stream capture.  Errors: LBM_ERR_ARG (null pointer, ncells < 1, batch < 1 or
+ * batch > 64), LBM_ERR_CUDA (no device, lookup or launch failure). */
+lbm_status lbm_field_sums_static(const double *rho1, const double *rho2, const double *u,
+                                 const uint8_t *cell_type, long long ncells, int batch, double *out, void *stream);
+
 /* Number of CUDA kernel launches the context has issued so far. */
 long long lbm_launch_count(const lbm_ctx *ctx);
 

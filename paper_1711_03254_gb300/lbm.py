@@ -303,3 +303,17 @@ def lbm_run_to_steady(ctx, check_every: int, tol: float, max_steps: int, batch: 
     rc = library().lbm_run_to_steady(ctx, int(check_every), float(tol), int(max_steps), ctypes.byref(done), _dp(res))
     _check(rc, ctx)
     return done.value, res
+
+
+def lbm_field_sums_static(rho1_ptr: int, rho2_ptr: int, u_ptr: int, type_ptr: int, ncells: int, batch: int,
+                          out_ptr: int, stream: int = 0):
+    """Mass and momentum sums of caller-owned device fields without any device
+    allocation (raw device addresses, e.g. torch tensors' data_ptr()); writes
+    out[batch][6] on the device.  For callers that must not allocate at this
+    point: a fixed memory pool, a loop that cannot afford cudaMalloc's device
+    synchronisation, or a host that owns all GPU memory."""
+    L = library()
+    f = L.lbm_field_sums_static
+    f.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    return _check(f(rho1_ptr, rho2_ptr, u_ptr, type_ptr, int(ncells), int(batch), out_ptr, stream or None))
