@@ -28,7 +28,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N = 256
-PARAMS = dict(tau=(0.17 * 3 + 0.5, 0.0017 * 3 + 0.5), G=-2.2, rho_s=0.0, g=(1e-6, 0.0, 0.0))
+NU = (1.0, 0.01)  # majority / minority kinematic viscosity (ratio 100)
+G = -2.2
+
+
+def params(nu=NU, G=G):
+    return dict(tau=(nu[0] * 3 + 0.5, nu[1] * 3 + 0.5), G=G, rho_s=0.0, g=(1e-6, 0.0, 0.0))
+
+
+PARAMS = params()
 F_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
 # DRAM traffic per fluid-cell update of the dominant kernel from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum per launch / cells), keyed by
@@ -280,7 +288,7 @@ def main():
                 "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"packed spheres {n}^3, r=12, porosity 0.40, 1% minority r=4, "
-                                       f"nu ratio 100, G=-2.2, g=1e-6",
+                                       f"nu {NU[0]}/{NU[1]} (ratio 100), G={G}, g=1e-6, wall model 2",
                            "storage": args.precision, "kernel": args.kernel, "fluid_cells": fluid,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),

@@ -1,0 +1,83 @@
+/*
+ * ws.h - C ABI of the warm-start surrogate kernels (BF16 tensor-core 3-D
+ * convolutions with FP32 accumulation, and the elementwise pieces of a 3-D
+ * U-Net).  The surrogate maps (geometry mask, wall potential, viscosity ratio,
+ * inclination, body force) to initial fields for the lattice Boltzmann solver;
+ * the paper has no counterpart (it is a systems layer on top of the method).
+ *
+ * Conventions
+ *  - All pointers are DEVICE pointers owned by the caller; nothing allocates.
+ *  - Activations are channels-last BF16: element (n, z, y, x, c) of a tensor
+ *    with row stride ld (>= channels) is at ((((n*D + z)*H + y)*W + x)*ld + c);
+ *    a channel offset is applied by passing a pointer into the row.  Channel
+ *    counts are multiples of 16; ld is a multiple of 8 and the base 16-byte
+ *    aligned for BF16 tensors read by the convolutions.
+ *  - Convolution weights are BF16 [Co][k][k][k][Ci] (k = 1 or 3, "same" zero
+ *    padding, stride 1); biases and weight gradients are FP32.
+ *  - Work is queued on `stream` (cudaStream_t, NULL = legacy default) without
+ *    synchronisation.  Return value: 0 ok, 1 invalid argument (nothing
+ *    launched), 2 CUDA launch error.
+ */
+#ifndef WS_H
+#define WS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* y = act(conv(x, w) + bias); y is BF16 (y_f32 = 0) or FP32 (y_f32 = 1) with
+ * row stride ldy; relu != 0 applies max(., 0); bias may be NULL. */
+int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void *y, int ldy, int y_f32, int N,
+                  int D, int H, int W, int Ci, int Co, int k, int relu, void *stream);
+
+/* wf[ci][t][co] = w[co][k^3-1-t][ci]: weights for the data gradient, which is
+ * then ws_conv3d_fwd(dy, wf) with Ci and Co exchanged. */
+int ws_conv3d_flip_weights(const void *w, void *wf, int Co, int Ci, int k, void *stream);
+
+/* dw[co][t][ci] += sum_p dy[p][co] x[p + t - k/2][ci] and db[co] += sum_p dy[p][co]
+ * (db may be NULL).  Accumulates: clear dw and db first. */
+int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float *dw, float *db, int N, int D, int H,
+                         int W, int Ci, int Co, int k, void *stream);
+
+/* 2x2x2 average pooling (D, H, W even) and its adjoint; nearest-neighbour 2x
+ * upsampling and its adjoint (sum of the 8 children).  BF16 in and out.  The
+ * adjoints of pool/upsample accumulate into dx when accumulate != 0.  D, H, W
+ * are the sizes of the finer tensor for the pooling calls and of the coarser
+ * one for the upsampling calls. */
+int ws_avgpool2(const void *x, int ldx, void *y, int ldy, int N, int D, int H, int W, int C, void *stream);
+int ws_avgpool2_bwd(const void *dy, int ldy, void *dx, int ldx, int N, int D, int H, int W, int C, int accumulate,
+                    void *stream);
+int ws_upsample2(const void *x, int ldx, void *y, int ldy, int N, int D, int H, int W, int C, void *stream);
+int ws_upsample2_bwd(const void *dy, int ldy, void *dx, int ldx, int N, int D, int H, int W, int C, int accumulate,
+                     void *stream);
+
+/* ReLU adjoint in place: dy[p][c] = 0 where y[p][c] <= 0 (y is the BF16
+ * activation the forward pass produced). */
+int ws_relu_bwd(const void *y, int ldy, void *dy, int lddy, long long P, int C, void *stream);
+
+/* Masked mean-squared error between prediction pred (FP32, [P][ldp], first C
+ * channels) and target (FP32 [P][C]) over cells with mask[p] != 0, weighted per
+ * channel by wch[C]; writes the BF16 gradient d(loss)/d(pred) into dpred
+ * ([P][lddp], channels beyond C zeroed) and adds the loss to *loss (FP32,
+ * device). */
+int ws_mse_loss(const float *pred, int ldp, const float *target, const uint8_t *mask, const float *wch, void *dpred,
+                int lddp, float *loss, long long P, int C, void *stream);
+
+/* Adam with FP32 master weights w, moments m and v, gradient g (n values);
+ * writes the BF16 copy wb used by the convolutions (wb may be NULL) and
+ * clears g for the next accumulation.  lr_t is the bias-corrected step size
+ * of this iteration. */
+int ws_adam(float *w, float *m, float *v, float *g, void *wb, long long n, float lr_t, float beta1, float beta2,
+            float eps, float weight_decay, void *stream);
+
+/* FP32 -> BF16 copy into a channel slice: y[p][c] = x[p*ldx + c], c < C. */
+int ws_to_bf16(const float *x, int ldx, void *y, int ldy, long long P, int C, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WS_H */

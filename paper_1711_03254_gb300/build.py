@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
-SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_reduce.cu", "lbm_fused.cu", "lbm_cluster.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_reduce.cu", "lbm_fused.cu", "lbm_cluster.cu", "lbm_noalloc.cu",
+           "ws_conv.cu", "ws_ops.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
@@ -33,6 +34,7 @@ def _stale(obj: str, src: str) -> bool:
         return True
     deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(HERE, "..", "include", "lbm.h"))
+    deps.append(os.path.join(HERE, "..", "include", "ws.h"))
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

@@ -109,10 +109,13 @@ struct Nbr {
     __device__ __forceinline__ int dst(int i) const { return X[1 + cx(i)] + Y[1 + cy(i)] + Z[1 + cz(i)]; }
 };
 
-// Moments of the streamed distributions of one component (S1-S2):
-// density, momentum and the raw second moment sum_i c_i c_i f_i.
+// Moments of the streamed distributions of one component (S1-S2).  In the
+// shifted storage formats they are summed over the stored deviations
+// d_i = f_i - w_i R (no cancellation against the rest equilibrium):
+//   rho = R + sum d,  rd = sum d,  j = sum c d,  p = sum c c d,
+// so that Pi - rho T0 I = p - rd T0 I.  Unshifted: rd = rho, p = sum c c f.
 template <class T> struct Moments {
-    T rho, jx, jy, jz;
+    T rho, rd, jx, jy, jz;
     T pxx, pyy, pzz, pxy, pxz, pyz;
 };
 
@@ -128,19 +131,19 @@ __device__ __forceinline__ Moments<typename Storage<S>::T>
 pull_moments(const S *__restrict__ fcomp, long long n, int self, const Nbr &nb, uint32_t links,
              typename Storage<S>::T rref) {
     using T = typename Storage<S>::T;
-    T v[kQ];
+    T v[kQ];  // stored values: deviations d_i in the shifted formats, f_i otherwise
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const bool bb = (links >> opp(i)) & 1u;
         const long long idx = bb ? (long long)opp(i) * n + self : (long long)i * n + nb.src(i);
-        const T sh = Storage<S>::shifted ? wgt<T>(i) * rref : T(0);
-        v[i] = RO ? Storage<S>::load(fcomp + idx, sh) : Storage<S>::load_rw(fcomp + idx, sh);
+        v[i] = RO ? Storage<S>::load(fcomp + idx, T(0)) : Storage<S>::load_rw(fcomp + idx, T(0));
     }
     Moments<T> m;
     T r = v[0];
 #pragma unroll
     for (int i = 1; i < kQ; ++i) r += v[i];
-    m.rho = r;
+    m.rd = r;
+    m.rho = Storage<S>::shifted ? rref + r : r;
     m.jx = (v[1] - v[2]) + (v[7] - v[8]) + (v[9] - v[10]) + (v[11] - v[12]) + (v[13] - v[14]);
     m.jy = (v[3] - v[4]) + (v[7] - v[8]) + (v[10] - v[9]) + (v[15] - v[16]) + (v[17] - v[18]);
     m.jz = (v[5] - v[6]) + (v[11] - v[12]) + (v[14] - v[13]) + (v[15] - v[16]) + (v[18] - v[17]);
@@ -167,13 +170,12 @@ __device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restri
     for (int i = 0; i < kQ; ++i) {
         const bool bb = (links >> opp(i)) & 1u;
         const long long idx = bb ? (long long)opp(i) * n + self : (long long)i * n + nb.src(i);
-        const T sh = Storage<S>::shifted ? wgt<T>(i) * rref : T(0);
-        v[i] = RO ? Storage<S>::load(fcomp + idx, sh) : Storage<S>::load_rw(fcomp + idx, sh);
+        v[i] = RO ? Storage<S>::load(fcomp + idx, T(0)) : Storage<S>::load_rw(fcomp + idx, T(0));
     }
     T r = v[0];
 #pragma unroll
     for (int i = 1; i < kQ; ++i) r += v[i];
-    return r;
+    return Storage<S>::shifted ? rref + r : r;
 }
 
 // Equilibrium of Eq. 3 for direction i (EQ = 1 adds the quadratic terms).
@@ -201,7 +203,7 @@ __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n,
     const T T0 = T(1) / T(3);
     const T uu = ux * ux + uy * uy + uz * uz;
     // Pi^neq = Pi - Pi^eq with Pi^eq = rho T0 I (+ rho u u for EQ = 1)
-    T nxx = m.pxx - m.rho * T0, nyy = m.pyy - m.rho * T0, nzz = m.pzz - m.rho * T0;
+    T nxx = m.pxx - m.rd * T0, nyy = m.pyy - m.rd * T0, nzz = m.pzz - m.rd * T0;
     T nxy = m.pxy, nxz = m.pxz, nyz = m.pyz;
     if (EQ == 1) {
         nxx -= m.rho * ux * ux; nyy -= m.rho * uy * uy; nzz -= m.rho * uz * uz;

@@ -1,20 +1,16 @@
 // Fused single-read update: each CTA owns a TX x TY column of cells and
 // marches it through a chunk of z planes.  For every plane it pulls the
-// streamed distributions once, keeps the 10 moments per component of its own
-// cells in shared memory, and writes the pseudo-potential of the plane plus a
-// one-cell ring around it into a 3-plane ring buffer in shared memory (the
-// ring cells are recomputed from their streamed values rather than read back
-// from a separate density pass).  One plane behind, it evaluates the
-// interaction forces from shared memory and collides (S4-S7).
-//
-// Work is compacted per plane: the cells that need a pull (non-SOLID,
-// non-INLET cells of the extended tile) and the cells that collide are packed
-// into order-preserving lists, so warps run full in porous geometries where
-// most cells of a tile may be SOLID.
+// streamed distributions once, keeps the moments of its own cells in shared
+// memory, and writes the pseudo-potential of the plane plus a one-cell ring
+// around it into a 3-plane ring buffer in shared memory (the ring cells are
+// recomputed from their streamed values rather than read back from a separate
+// density pass).  One plane behind, it evaluates the interaction forces from
+// shared memory and collides (S4-S7).
 //
 // HBM traffic per fluid cell is the algorithmic minimum (f in, f out, one
-// geometry word, the reference densities) plus halo re-reads, which mostly
-// hit L2 because neighbouring columns march in step.
+// geometry word, the reference densities) plus halo re-reads, which mostly hit
+// L2 because neighbouring columns march in step, and the unused parts of
+// 32-byte sectors shared with SOLID cells.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -22,11 +18,11 @@ namespace lbm {
 
 template <int TX, int TY> struct Tile {
     static constexpr int EX = TX + 2, EY = TY + 2;
-    static constexpr int NT = TX * TY;            // threads = interior cells per plane
-    static constexpr int NE = EX * EY;            // extended cells per plane
-    static constexpr int K = (NE + NT - 1) / NT;  // extended cells classified per thread
-    static constexpr int NW = NT / 32;
+    static constexpr int NT = TX * TY;  // threads = interior cells per plane
+    static constexpr int NE = EX * EY;  // extended cells per plane
 };
+
+constexpr int kMom = 11;  // moments kept per component (see Moments)
 
 // ring-buffer slot of the plane at z offset cz(i) from the colliding plane
 __device__ __forceinline__ int cz_slot(int i, int sl, int sm, int su) {
@@ -34,7 +30,7 @@ __device__ __forceinline__ int cz_slot(int i, int sl, int sm, int su) {
 }
 
 // Pull one component of one cell (x, y, z): returns its density and, when
-// `mom` is non-null, stores its 10 moments at mom[q * stride].  Components are
+// `mom` is non-null, stores its moments at mom[q * stride].  Components are
 // pulled one after the other so that only 19 loads are in flight per thread.
 template <class S>
 __device__ __forceinline__ typename Storage<S>::T cell_pull(const S *__restrict__ fb, const uint32_t *__restrict__ link_b,
@@ -60,35 +56,39 @@ __device__ __forceinline__ typename Storage<S>::T cell_pull(const S *__restrict_
     const S *fc = fb + (long long)comp * kQ * g.n;
     if (mom) {
         const Moments<T> m = pull_moments<S>(fc, g.n, self, nb, sw, rr);
-        mom[0] = m.rho; mom[stride] = m.jx; mom[2 * stride] = m.jy; mom[3 * stride] = m.jz;
-        mom[4 * stride] = m.pxx; mom[5 * stride] = m.pyy; mom[6 * stride] = m.pzz;
-        mom[7 * stride] = m.pxy; mom[8 * stride] = m.pxz; mom[9 * stride] = m.pyz;
+        mom[0] = m.rho; mom[stride] = m.rd; mom[2 * stride] = m.jx; mom[3 * stride] = m.jy;
+        mom[4 * stride] = m.jz; mom[5 * stride] = m.pxx; mom[6 * stride] = m.pyy; mom[7 * stride] = m.pzz;
+        mom[8 * stride] = m.pxy; mom[9 * stride] = m.pxz; mom[10 * stride] = m.pyz;
         return m.rho;
     }
     return pull_density<S>(fc, g.n, self, nb, sw, rr);
 }
 
+template <class T>
+__device__ __forceinline__ Moments<T> read_moments(const T *mom, int stride) {
+    Moments<T> m;
+    m.rho = mom[0]; m.rd = mom[stride]; m.jx = mom[2 * stride]; m.jy = mom[3 * stride]; m.jz = mom[4 * stride];
+    m.pxx = mom[5 * stride]; m.pyy = mom[6 * stride]; m.pzz = mom[7 * stride];
+    m.pxy = mom[8 * stride]; m.pxz = mom[9 * stride]; m.pyz = mom[10 * stride];
+    return m;
+}
+
 // Shared-memory layout of the fused kernel.
 template <class T, int TX, int TY> struct FusedSmem {
     using TL = Tile<TX, TY>;
-    T sp[3][2][TL::EY][TL::EX];   // pseudo-potential ring of three planes
-    T mom[2][20][TL::NT];         // moments of the interior cells, by plane parity
-    uint32_t word[2][TL::NT];     // geometry words of the interior cells, by plane parity
-    uint16_t work[TL::NE];        // pull items of the current plane: extended index | 0x8000 if moments
-    uint16_t coll[2][TL::NT];     // colliding interior slots, by plane parity
-    int ncoll[2];
-    int nwork;
-    int wsum[TL::NW + 1];
+    T sp[3][2][TL::EY][TL::EX];        // pseudo-potential ring of three planes
+    T mom[2][2 * kMom][TL::NT];        // moments of the interior cells, by plane parity
+    uint32_t word[2][TL::NT];          // geometry words of the interior cells, by plane parity
 };
 
+constexpr uint32_t kNoCollide = 1u << 30;  // interior slot outside the domain or on a halo plane
+
 template <class S, int EQ, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1)) k_fused(const S *__restrict__ f, S *__restrict__ fo,
-                                                  const Ref *__restrict__ rin, Ref *__restrict__ rout,
-                                                  const uint32_t *__restrict__ link,
-                                                  typename Storage<S>::T *__restrict__ macro, Grid g,
-                                                  const InstParam<typename Storage<S>::T> *__restrict__ par,
-                                                  int wall_model, int write_macro, int tiles_x, int tiles_y,
-                                                  int zchunk, int nchunks) {
+__global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1))
+    k_fused(const S *__restrict__ f, S *__restrict__ fo, const Ref *__restrict__ rin, Ref *__restrict__ rout,
+            const uint32_t *__restrict__ link, typename Storage<S>::T *__restrict__ macro, Grid g,
+            const InstParam<typename Storage<S>::T> *__restrict__ par, int wall_model, int write_macro, int tiles_x,
+            int tiles_y, int zchunk, int nchunks) {
     using T = typename Storage<S>::T;
     using TL = Tile<TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -105,7 +105,6 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1)) k_fused(cons
     const int z0 = zc * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
 
     const uint32_t *link_b = link + (long long)b * g.n;
     const S *fb = f + (long long)b * 2 * kQ * g.n;
@@ -115,108 +114,38 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1)) k_fused(cons
     const Ref *rin_b = rin + (long long)b * 2 * g.n;
     Ref *rout_b = rout + (long long)b * 2 * g.n;
 
-    auto ext_xy = [&](int e, int &x, int &y) {
-        const int ey = e / TL::EX, ex = e - ey * TL::EX;
-        x = tx0 - 1 + ex;
-        y = ty0 - 1 + ey;
-        x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
-        y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
-        x = x % g.nx;  // grids narrower than a tile wrap more than once
-        y = y % g.ny;
-    };
-
     for (int pz = z0 - 1; pz <= z1; ++pz) {
         const int zz = pz < 0 ? pz + g.nz : (pz >= g.nz ? pz - g.nz : pz);
         const int slot = (pz + 3) % 3;
         const int par2 = pz & 1;
         const bool inner = pz >= z0 && pz < z1;
 
-        // ---- classify the extended plane and build the compacted lists
-        uint32_t w_e[TL::K];
-        int npull = 0, ncol = 0;
-#pragma unroll
-        for (int k = 0; k < TL::K; ++k) {
-            const int e = tid * TL::K + k;
-            w_e[k] = 0;
-            if (e < TL::NE) {
-                int x, y;
-                ext_xy(e, x, y);
-                const uint32_t w = __ldg(link_b + x + y * g.nx + (long long)zz * g.nxy);
-                w_e[k] = w;
-                const uint32_t t = cell_type(w);
-                const int ey = e / TL::EX, ex = e - ey * TL::EX;
-                const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
-                const bool mine = interior && tx0 + ex - 1 < g.nx && ty0 + ey - 1 < g.ny;
-                if (t == kSolid) {
-                    sm.sp[slot][0][ey][ex] = p.rs[0];
-                    sm.sp[slot][1][ey][ex] = p.rs[1];
-                } else if (t == kInlet) {
-                    sm.sp[slot][0][ey][ex] = p.rho_in[0];
-                    sm.sp[slot][1][ey][ex] = p.rho_in[1];
-                } else {
-                    ++npull;
-                    if (inner && mine) ++ncol;
-                }
-                if (interior) sm.word[par2][(ey - 1) * TX + (ex - 1)] = mine && inner ? w : (1u << 30);
-            }
-        }
-        // exclusive scan of (npull, ncol) over the block, in thread order
-        int packed = npull | (ncol << 16);
-        int incl = packed;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane == 31) sm.wsum[warp] = incl;
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int k = 0; k < TL::NW; ++k) {
-                const int c = sm.wsum[k];
-                sm.wsum[k] = acc;
-                acc += c;
-            }
-            sm.nwork = acc & 0xffff;
-            sm.ncoll[par2] = acc >> 16;
-        }
-        __syncthreads();
-        {
-            int base = sm.wsum[warp] + incl - packed;
-            int wp = base & 0xffff, wc = base >> 16;
-#pragma unroll
-            for (int k = 0; k < TL::K; ++k) {
-                const int e = tid * TL::K + k;
-                if (e < TL::NE) {
-                    const uint32_t t = cell_type(w_e[k]);
-                    if (t != kSolid && t != kInlet) {
-                        const int ey = e / TL::EX, ex = e - ey * TL::EX;
-                        const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
-                        const bool mine = interior && tx0 + ex - 1 < g.nx && ty0 + ey - 1 < g.ny;
-                        const bool col = inner && mine;
-                        sm.work[wp++] = (uint16_t)(e | (col ? 0x8000 : 0));
-                        if (col) sm.coll[par2][wc++] = (uint16_t)((ey - 1) * TX + (ex - 1));
-                    }
-                }
-            }
-        }
-        __syncthreads();
-
-        // ---- pulls: pseudo-potential of the extended plane, moments of own cells
-        const int nwork = sm.nwork;
-        for (int j = tid; j < nwork; j += TL::NT) {
-            const int item = sm.work[j];
-            const int e = item & 0x7fff;
-            const bool want = (item & 0x8000) != 0;
-            int x, y;
-            ext_xy(e, x, y);
+        // ---- extended plane: pseudo-potential of every cell, moments of own cells
+        for (int e = tid; e < TL::NE; e += TL::NT) {
             const int ey = e / TL::EX, ex = e - ey * TL::EX;
+            int x = tx0 - 1 + ex, y = ty0 - 1 + ey;
+            x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+            y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+            x %= g.nx;  // grids narrower than a tile wrap more than once
+            y %= g.ny;
             const uint32_t w = __ldg(link_b + x + y * g.nx + (long long)zz * g.nxy);
-            const int s = want ? (ey - 1) * TX + (ex - 1) : 0;
+            const uint32_t t = cell_type(w);
+            const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
+            const bool mine = interior && inner && tx0 + ex - 1 < g.nx && ty0 + ey - 1 < g.ny;
+            const int s = interior ? (ey - 1) * TX + (ex - 1) : 0;
+            if (interior) sm.word[par2][s] = mine ? w : kNoCollide;
+            if (t == kSolid) {
+                sm.sp[slot][0][ey][ex] = p.rs[0];
+                sm.sp[slot][1][ey][ex] = p.rs[1];
+            } else if (t == kInlet) {
+                sm.sp[slot][0][ey][ex] = p.rho_in[0];
+                sm.sp[slot][1][ey][ex] = p.rho_in[1];
+            } else {
 #pragma unroll 1
-            for (int comp = 0; comp < 2; ++comp) {
-                T *mom = want ? &sm.mom[par2][comp * 10][s] : nullptr;
-                sm.sp[slot][comp][ey][ex] = cell_pull<S>(fb, link_b, g, x, y, zz, w, comp, mom, TL::NT, rin_b);
+                for (int comp = 0; comp < 2; ++comp) {
+                    T *mom = mine ? &sm.mom[par2][comp * kMom][s] : nullptr;
+                    sm.sp[slot][comp][ey][ex] = cell_pull<S>(fb, link_b, g, x, y, zz, w, comp, mom, TL::NT, rin_b);
+                }
             }
         }
         __syncthreads();
@@ -226,32 +155,27 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1)) k_fused(cons
         if (cz >= z0 && cz < z1) {
             const int cpar = cz & 1;
             const int sm_ = (cz + 3) % 3, sl = (cz + 2) % 3, su = (cz + 4) % 3;  // planes cz, cz-1, cz+1
-            const int ncl = sm.ncoll[cpar];
-            for (int j = tid; j < ncl; j += TL::NT) {
-                const int s = sm.coll[cpar][j];
-                const int lx = s % TX, ly = s / TX;
-                const long long k = (long long)(tx0 + lx) + (long long)(ty0 + ly) * g.nx + (long long)cz * g.nxy;
-                const uint32_t word = sm.word[cpar][s];
-                Moments<T> a0, a1;
-                a0.rho = sm.mom[cpar][0][s]; a0.jx = sm.mom[cpar][1][s]; a0.jy = sm.mom[cpar][2][s];
-                a0.jz = sm.mom[cpar][3][s]; a0.pxx = sm.mom[cpar][4][s]; a0.pyy = sm.mom[cpar][5][s];
-                a0.pzz = sm.mom[cpar][6][s]; a0.pxy = sm.mom[cpar][7][s]; a0.pxz = sm.mom[cpar][8][s];
-                a0.pyz = sm.mom[cpar][9][s];
-                a1.rho = sm.mom[cpar][10][s]; a1.jx = sm.mom[cpar][11][s]; a1.jy = sm.mom[cpar][12][s];
-                a1.jz = sm.mom[cpar][13][s]; a1.pxx = sm.mom[cpar][14][s]; a1.pyy = sm.mom[cpar][15][s];
-                a1.pzz = sm.mom[cpar][16][s]; a1.pxy = sm.mom[cpar][17][s]; a1.pxz = sm.mom[cpar][18][s];
-                a1.pyz = sm.mom[cpar][19][s];
+            const int s = tid;
+            const uint32_t word = sm.word[cpar][s];
+            const int lx = s % TX, ly = s / TX;
+            const long long k = (long long)(tx0 + lx) + (long long)(ty0 + ly) * g.nx + (long long)cz * g.nxy;
+            const uint32_t t = cell_type(word);
+            auto sig_for = [&](int comp, T own_rho) {
+                return [&, comp, own_rho](int i) -> T {
+                    return ref_value(((word >> i) & 1u)
+                                         ? own_rho
+                                         : sm.sp[cz_slot(i, sl, sm_, su)][comp][ly + 1 + cy(i)][lx + 1 + cx(i)]);
+                };
+            };
+            if (word & kNoCollide) {
+                // outside the domain: nothing to do
+            } else if (t == kFluid || t == kOutlet) {
+                const Moments<T> a0 = read_moments<T>(&sm.mom[cpar][0][s], TL::NT);
+                const Moments<T> a1 = read_moments<T>(&sm.mom[cpar][kMom][s], TL::NT);
                 auto psi_at = [&](int i, T &v0, T &v1) {
                     const int sl_ = cz_slot(i, sl, sm_, su);
                     v0 = sm.sp[sl_][0][ly + 1 + cy(i)][lx + 1 + cx(i)];
                     v1 = sm.sp[sl_][1][ly + 1 + cy(i)][lx + 1 + cx(i)];
-                };
-                auto sig_for = [&](int comp, T own_rho) {
-                    return [&, comp, own_rho](int i) -> T {
-                        return ref_value(((word >> i) & 1u)
-                                             ? own_rho
-                                             : sm.sp[cz_slot(i, sl, sm_, su)][comp][ly + 1 + cy(i)][lx + 1 + cx(i)]);
-                    };
                 };
                 const Forces<T> F = sc_forces<T>(psi_at, word, a0.rho, a1.rho, p, wall_model);
                 const T rho = a0.rho + a1.rho;
@@ -277,43 +201,24 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1)) k_fused(cons
                     mac[3 * g.n + k] = uy;
                     mac[4 * g.n + k] = uz;
                 }
-            }
-            // INLET cells and, on the last update, the fields of SOLID cells
-            {
-                const int s = tid;
-                const uint32_t word = sm.word[cpar][s];
-                const int lx = s % TX, ly = s / TX;
-                const long long k = (long long)(tx0 + lx) + (long long)(ty0 + ly) * g.nx + (long long)cz * g.nxy;
-                if (!(word & (1u << 30))) {
-                    const uint32_t t = cell_type(word);
-                    if (t == kInlet) {
-                        auto sig_in = [&](int comp, T own_rho) {
-                            return [&, comp, own_rho](int i) -> T {
-                                return ref_value(
-                                    ((word >> i) & 1u)
-                                        ? own_rho
-                                        : sm.sp[cz_slot(i, sl, sm_, su)][comp][ly + 1 + cy(i)][lx + 1 + cx(i)]);
-                            };
-                        };
-                        store_equilibrium<S, EQ>(fob, g.n, (int)k, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2],
-                                                 sig_in(0, p.rho_in[0]));
-                        store_equilibrium<S, EQ>(fob + kQ * g.n, g.n, (int)k, p.rho_in[1], p.u_in[0], p.u_in[1],
-                                                 p.u_in[2], sig_in(1, p.rho_in[1]));
-                        if constexpr (Storage<S>::shifted) {
-                            rout_b[k] = __float2half_rn((float)p.rho_in[0]);
-                            rout_b[g.n + k] = __float2half_rn((float)p.rho_in[1]);
-                        }
-                        if (write_macro) {
-                            mac[k] = p.rho_in[0];
-                            mac[g.n + k] = p.rho_in[1];
-                            mac[2 * g.n + k] = p.u_in[0];
-                            mac[3 * g.n + k] = p.u_in[1];
-                            mac[4 * g.n + k] = p.u_in[2];
-                        }
-                    } else if (t == kSolid && write_macro) {
-                        for (int c = 0; c < 5; ++c) mac[c * g.n + k] = T(0);
-                    }
+            } else if (t == kInlet) {
+                store_equilibrium<S, EQ>(fob, g.n, (int)k, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2],
+                                         sig_for(0, p.rho_in[0]));
+                store_equilibrium<S, EQ>(fob + kQ * g.n, g.n, (int)k, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2],
+                                         sig_for(1, p.rho_in[1]));
+                if constexpr (Storage<S>::shifted) {
+                    rout_b[k] = __float2half_rn((float)p.rho_in[0]);
+                    rout_b[g.n + k] = __float2half_rn((float)p.rho_in[1]);
                 }
+                if (write_macro) {
+                    mac[k] = p.rho_in[0];
+                    mac[g.n + k] = p.rho_in[1];
+                    mac[2 * g.n + k] = p.u_in[0];
+                    mac[3 * g.n + k] = p.u_in[1];
+                    mac[4 * g.n + k] = p.u_in[2];
+                }
+            } else if (write_macro) {  // SOLID
+                for (int c = 0; c < 5; ++c) mac[c * g.n + k] = T(0);
             }
         }
         __syncthreads();

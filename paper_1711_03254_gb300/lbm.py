@@ -44,7 +44,7 @@ class lbm_instance_params(ctypes.Structure):
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 _lib = None
-_hooks = None
+_hooks = []  # installed allocator hooks (kept alive, see lbm_set_allocator)
 
 
 def library() -> ctypes.CDLL:
@@ -101,13 +101,13 @@ def _dp(a: np.ndarray):
 def lbm_set_allocator(alloc=None, release=None):
     """Install a device allocator (python callables alloc(bytes, stream) -> int,
     release(ptr, stream)); with no arguments restore cudaMalloc."""
-    global _hooks
     if alloc is None:
-        _hooks = None
         return _check(library().lbm_set_allocator(_ALLOC_T(), _FREE_T()))
     a = _ALLOC_T(lambda n, s: alloc(n, s))
     f = _FREE_T(lambda p, s: release(p, s))
-    _hooks = (a, f)
+    # contexts created while a hook is installed keep calling it until they are
+    # destroyed, so every hook stays alive for the life of the process
+    _hooks.append((a, f))
     return _check(library().lbm_set_allocator(a, f))
 
 

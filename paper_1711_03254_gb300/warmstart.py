@@ -1,0 +1,201 @@
+"""Learned warm start of the two-component solver (data generation with the
+solver, training of the U-Net, and the steps-to-steady comparison).
+
+Problem family: a droplet of component 2 on an inclined flat wall (the
+inclined-channel geometry of Sec. 3.4), parameters drawn from a seeded
+generator:
+  * wettability rho^s ~ U[-0.4, 0.4] (taken directly: the contact-angle
+    calibration of Sec. 3.3 is not part of this library),
+  * inclination ~ U[0 deg, 45 deg],
+  * viscosity ratio ~ logU[1, 100] with nu_high = 1.0 (nu_low >= 0.01), the
+    droplet taking the low or the high viscosity at random,
+  * G = -1.8, no body force (the steady state is static).
+
+The solver's state after `steps` updates from the plain initial state (sharp
+droplet, fluid at rest) is the training target.  The warm start runs the
+network at 64^3 (inputs sampled every second cell for 128^3 problems) and
+upsamples its output by nearest neighbours; the solver then runs from those
+fields to the same residual as from the plain state.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import lbm, surrogate, workloads as W
+
+G_WS = -1.8
+NU_HIGH = 1.0
+
+
+def sample_cases(n: int, seed: int):
+    rng = np.random.default_rng(seed)
+    cases = []
+    for _ in range(n):
+        ratio = 10 ** rng.uniform(0.0, 2.0)
+        low = NU_HIGH / ratio
+        drop_low = bool(rng.random() < 0.5)
+        nu1, nu2 = (NU_HIGH, low) if drop_low else (low, NU_HIGH)
+        cases.append(dict(rho_s=float(rng.uniform(-0.4, 0.4)), incline=float(rng.uniform(0.0, 45.0)),
+                          nu=(nu1, nu2), ratio=float(ratio)))
+    return cases
+
+
+def case_params(c):
+    return dict(tau=(c["nu"][0] * 3 + 0.5, c["nu"][1] * 3 + 0.5), G=G_WS, rho_s=c["rho_s"], g=(0.0, 0.0, 0.0))
+
+
+def case_geometry(c, S: int):
+    return W.inclined_droplet(S, c["incline"], R=S / 8.0)
+
+
+def case_inputs(c, S: int):
+    t, r1, r2, u = case_geometry(c, S)
+    return surrogate.encode_inputs(t, c["rho_s"], c["ratio"], c["incline"], 0.0, r2), t, r1, r2, u
+
+
+def generate(cases, S: int = 64, steps: int = 3000, batch: int = 32, precision: str = "fp32"):
+    """Run the solver on every case; returns (inputs, targets, masks) arrays."""
+    X, Y, M = [], [], []
+    for k0 in range(0, len(cases), batch):
+        cs = cases[k0:k0 + batch]
+        geo = [case_geometry(c, S) for c in cs]
+        t = np.stack([g[0] for g in geo])
+        sim = lbm.Sim(S, S, S, [case_params(c) for c in cs], precision=precision)
+        sim.set_geometry(t)
+        sim.set_fields(np.stack([g[1] for g in geo]), np.stack([g[2] for g in geo]), np.stack([g[3] for g in geo]))
+        sim.step(steps)
+        r1, r2, u = sim.get_fields()
+        sim.close()
+        for j, c in enumerate(cs):
+            X.append(surrogate.encode_inputs(geo[j][0], c["rho_s"], c["ratio"], c["incline"], 0.0, geo[j][2]))
+            Y.append(surrogate.encode_targets(r1[j], r2[j], u[j]))
+            M.append((geo[j][0] != W.SOLID).astype(np.uint8))
+    return np.stack(X), np.stack(Y), np.stack(M)
+
+
+def train(net, X, Y, M, iters: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50):
+    """Adam on random mini-batches of net.N samples; returns the loss history."""
+    import torch
+    rng = np.random.default_rng(seed)
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    Md = torch.from_numpy(M).to(dev)
+    wch = torch.tensor([1.0, 10.0, 1.0, 1.0, 1.0], dtype=torch.float32, device=dev)
+    hist = []
+    for it in range(iters):
+        idx = torch.from_numpy(rng.choice(len(X), size=net.N, replace=False)).to(dev)
+        x = Xd.index_select(0, idx).contiguous()
+        y = Yd.index_select(0, idx).contiguous()
+        m = Md.index_select(0, idx).contiguous()
+        net.forward(x)
+        loss = net.loss_and_grad(y, m, wch)
+        net.backward()
+        a = lr * 0.5 * (1 + math.cos(math.pi * it / max(1, iters)))
+        net.adam_step(lr=a)
+        if it % log_every == 0 or it == iters - 1:
+            hist.append((it, float(loss.item())))
+    return hist
+
+
+def predict(net, x64):
+    """Network output for one 64^3 input (FP32 numpy [64,64,64,CIN])."""
+    import torch
+    x = torch.zeros((net.N,) + x64.shape, dtype=torch.float32, device="cuda")
+    x[0] = torch.from_numpy(x64).cuda()
+    out = net.forward(x)
+    return out[0].float().cpu().numpy()
+
+
+def warm_fields(net, c, S: int):
+    """Initial fields for an S^3 case (S = 64 or 128) from the network."""
+    x, t, r1, r2, u = case_inputs(c, S)
+    if S == 64:
+        out = predict(net, x)
+    else:
+        f = S // 64
+        xs = np.ascontiguousarray(x[::f, ::f, ::f])
+        o = predict(net, xs)
+        out = o.repeat(f, 0).repeat(f, 1).repeat(f, 2)
+    return t, surrogate.decode_fields(out, t)
+
+
+def steps_to_steady(c, S, init, tol, check_every=100, max_steps=20000, precision="fp32"):
+    """(updates, wall seconds, fields) to reach residual <= tol from `init`."""
+    t, (r1, r2, u) = init
+    sim = lbm.Sim(S, S, S, [case_params(c)], precision=precision)
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done, res = lbm.lbm_run_to_steady(sim.ctx, check_every, tol, max_steps, 1)
+    dt = time.perf_counter() - t0
+    fields = sim.get_fields()
+    sim.close()
+    return done, dt, float(res[0]), fields
+
+
+def experiment(n_train=512, n_test=8, S_train=64, S_test=128, gen_steps=3000, iters=1500, batch=4, lr=1e-3,
+               tol=1e-5, check_every=100, max_steps=20000, seed_train=5, seed_test=6, log=print):
+    """Generate, train, and compare steps / wall time to steady state from the
+    plain and the learned initial fields.  Returns a summary dict."""
+    import torch
+    t0 = time.perf_counter()
+    X, Y, M = generate(sample_cases(n_train, seed_train), S=S_train, steps=gen_steps)
+    t_gen = time.perf_counter() - t0
+    log(f"generated {len(X)} steady states at {S_train}^3 in {t_gen:.1f} s")
+    net = surrogate.UNet3D(batch, S_train, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = train(net, X, Y, M, iters, lr=lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    flops = 3.0 * net.flops_per_sample() * batch * iters
+    log(f"trained {iters} iterations in {t_train:.1f} s ({flops / t_train / 1e12:.1f} TFLOP/s), "
+        f"loss {hist[0][1]:.4g} -> {hist[-1][1]:.4g}")
+    rows = []
+    for c in sample_cases(n_test, seed_test):
+        x, t, r1, r2, u = case_inputs(c, S_test)
+        plain = steps_to_steady(c, S_test, (t, (r1, r2, u)), tol, check_every, max_steps)
+        tw0 = time.perf_counter()
+        init = warm_fields(net, c, S_test)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - tw0
+        warm = steps_to_steady(c, S_test, init, tol, check_every, max_steps)
+        fluid = t != W.SOLID
+        diff = max(float(np.abs(plain[3][k][0][fluid] - warm[3][k][0][fluid]).max()) for k in (0, 1))
+        rows.append(dict(case=c, plain_steps=plain[0], plain_s=plain[1], plain_res=plain[2], warm_steps=warm[0],
+                         warm_s=warm[1] + t_inf, warm_res=warm[2], infer_s=t_inf, max_density_diff=diff))
+        log(f"case {len(rows)}: plain {plain[0]} updates {plain[1]:.2f} s | warm {warm[0]} updates "
+            f"{warm[1] + t_inf:.2f} s (inference {t_inf:.3f} s) | max |d rho| {diff:.2e}")
+    return dict(train=dict(n=n_train, size=S_train, gen_steps=gen_steps, gen_s=t_gen, iters=iters, batch=batch,
+                           train_s=t_train, tflops=flops / t_train / 1e12, loss=hist),
+                test=dict(n=n_test, size=S_test, tol=tol, check_every=check_every, max_steps=max_steps, rows=rows))
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="learned warm start: generate, train, compare steps to steady")
+    ap.add_argument("--n-train", type=int, default=512)
+    ap.add_argument("--n-test", type=int, default=8)
+    ap.add_argument("--size-train", type=int, default=64)
+    ap.add_argument("--size-test", type=int, default=128)
+    ap.add_argument("--gen-steps", type=int, default=3000)
+    ap.add_argument("--iters", type=int, default=1500)
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--max-steps", type=int, default=20000)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    res = experiment(a.n_train, a.n_test, a.size_train, a.size_test, a.gen_steps, a.iters, tol=a.tol,
+                     max_steps=a.max_steps)
+    js = json.dumps(res, default=float)
+    if a.out:
+        open(a.out, "w").write(js)
+    print(js)

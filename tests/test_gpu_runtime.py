@@ -78,6 +78,7 @@ def test_stream_and_torch_allocator(lbm):
         for x, y in zip(a.get_fields(), ref.get_fields()):
             assert np.array_equal(x, y)
         a.close()
+        ref.close()
     finally:
         lbm.lbm_set_allocator()
 
