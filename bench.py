@@ -55,8 +55,13 @@ def sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def workload(n=N):
+def workload(n=N, kind="spheres"):
+    """The packed-sphere benchmark geometry, or (kind="droplet") an all-fluid
+    periodic box with one droplet of radius n/8, used to see the kernel without
+    SOLID cells."""
     from paper_1711_03254_gb300 import workloads as W
+    if kind == "droplet":
+        return W.droplet(n, n, n, n / 8.0)
     cache = f"/tmp/lbm_spheres_{n}.npz"
     if os.path.exists(cache):
         z = np.load(cache)
@@ -202,6 +207,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=N)
+    ap.add_argument("--workload", default="spheres", choices=["spheres", "droplet"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -213,7 +219,7 @@ def main():
     build.build()
     lbm.use_torch_allocator()
     n = args.size
-    t, r1, r2, u = workload(n)
+    t, r1, r2, u = workload(n, args.workload)
     fluid = int((t != 1).sum())
     stream = torch.cuda.current_stream()
 
@@ -287,8 +293,10 @@ def main():
                 "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"packed spheres {n}^3, r=12, porosity 0.40, 1% minority r=4, "
-                                       f"nu {NU[0]}/{NU[1]} (ratio 100), G={G}, g=1e-6, wall model 2",
+                "config": {"workload": (f"packed spheres {n}^3, r=12, porosity 0.40, 1% minority r=4, "
+                                        f"nu {NU[0]}/{NU[1]} (ratio 100), G={G}, g=1e-6, wall model 2"
+                                        if args.workload == "spheres" else
+                                        f"periodic droplet {n}^3, R={n // 8}, no walls"),
                            "storage": args.precision, "kernel": args.kernel, "fluid_cells": fluid,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),

@@ -47,6 +47,9 @@ struct lbm_ctx {
     Ref *ref[2] = {nullptr, nullptr};  // reference densities, swapped with f (not used in FP64)
     int cur = 0;
     uint32_t *link = nullptr;
+    uint32_t *list = nullptr;  // non-solid cells of each instance, in cell order [batch][n]
+    int *list_count = nullptr; // entries per instance
+    long long list_max = 0;
     void *psi = nullptr, *macro = nullptr, *usnap = nullptr, *dpar = nullptr;
     double *partial = nullptr, *red_out = nullptr;
     int nblk = 0;
@@ -169,6 +172,33 @@ void default_tiling(const lbm_ctx *ctx, int &tile, int &zchunk) {
     }
 }
 
+// Lists of the non-solid cells of every instance (in cell order) for the
+// two-pass kernels, and the static pseudo-potential of the SOLID cells.
+// type_of(global cell index) gives the cell type.
+template <class F> lbm_status build_cell_lists(lbm_ctx *ctx, F type_of) {
+    const long long n = ctx->g.n;
+    std::vector<uint32_t> lst((size_t)ctx->cfg.batch * n);
+    std::vector<int> cnt(ctx->cfg.batch);
+    long long mx = 0;
+    for (int b = 0; b < ctx->cfg.batch; ++b) {
+        int c = 0;
+        for (long long k = 0; k < n; ++k)
+            if (type_of((size_t)b * n + k) != 1u) lst[(size_t)b * n + c++] = (uint32_t)k;
+        cnt[b] = c;
+        if (c > mx) mx = c;
+    }
+    LBM_CUDA(cudaMemcpyAsync(ctx->list, lst.data(), lst.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "cell list");
+    LBM_CUDA(cudaMemcpyAsync(ctx->list_count, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             ctx->stream),
+             "cell list");
+    LBM_CUDA(launch_psi_solid(ctx->link, ctx->psi, ctx->fp64(), ctx->g, ctx->cfg.batch, ctx->dpar, ctx->stream),
+             "solid psi");
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "cell list");
+    ctx->launches += 1;
+    ctx->list_max = mx;
+    return LBM_OK;
+}
+
 StepArgs step_args(lbm_ctx *ctx, int write_macro) {
     StepArgs a{};
     a.precision = ctx->cfg.precision;
@@ -185,6 +215,9 @@ StepArgs step_args(lbm_ctx *ctx, int write_macro) {
     a.par = ctx->dpar;
     a.ref_in = ctx->ref[ctx->cur];
     a.ref_out = ctx->ref[ctx->cur ^ 1];
+    a.list = ctx->list;
+    a.list_count = ctx->list_count;
+    a.list_max = ctx->list_max;
     a.stream = ctx->stream;
     return a;
 }
@@ -214,8 +247,9 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
         g_last_error = "lbm_create: every dimension and the batch must be >= 1";
         return LBM_ERR_ARG;
     }
-    if ((long long)cfg->nx * cfg->ny * cfg->nz >= (1LL << 31)) {
-        g_last_error = "lbm_create: more than 2^31 cells per instance";
+    // kernels index one component's 19 planes with 32-bit offsets
+    if (19LL * cfg->nx * cfg->ny * cfg->nz >= (1LL << 32)) {
+        g_last_error = "lbm_create: more than 226 million cells per instance";
         return LBM_ERR_ARG;
     }
     if (cfg->precision < LBM_FP64 || cfg->precision > LBM_FP32_BF16S || cfg->eq_order < 0 || cfg->eq_order > 1 ||
@@ -264,6 +298,13 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
         ctx->ref[1] = (Ref *)ctx->dalloc(ctx->ref_bytes());
     }
     ctx->link = (uint32_t *)ctx->dalloc(cells * 4);
+    ctx->list = (uint32_t *)ctx->dalloc(cells * 4);
+    ctx->list_count = (int *)ctx->dalloc((size_t)cfg->batch * sizeof(int));
+    if (!ctx->list || !ctx->list_count) {
+        g_last_error = "lbm_create: device allocation failed";
+        lbm_destroy(ctx);
+        return LBM_ERR_OOM;
+    }
     ctx->psi = ctx->dalloc(cells * 2 * ctx->tbytes());
     ctx->macro = ctx->dalloc(cells * 5 * ctx->tbytes());
     ctx->usnap = ctx->dalloc(cells * 3 * ctx->tbytes());
@@ -341,6 +382,8 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *cell_type) {
     ctx->dfree(dt);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_set_geometry");
     ctx->launches += 1;
+    lbm_status s = build_cell_lists(ctx, [&](size_t gk) { return (uint32_t)cell_type[gk]; });
+    if (s != LBM_OK) return s;
     ctx->has_geometry = true;
     ctx->has_fields = false;
     return LBM_OK;
@@ -589,6 +632,16 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes) {
     p += h.macro_bytes;
     LBM_CUDA(cudaMemcpyAsync(ctx->usnap, p, h.usnap_bytes, cudaMemcpyHostToDevice, ctx->stream), "set_state usnap");
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_state sync");
+    {
+        const uint32_t *words = reinterpret_cast<const uint32_t *>((const char *)buf + sizeof(h) + h.f_bytes +
+                                                                   h.ref_bytes);
+        lbm_status s = build_cell_lists(ctx, [&](size_t gk) {
+            uint32_t w;
+            std::memcpy(&w, words + gk, 4);
+            return (w >> 24) & 3u;
+        });
+        if (s != LBM_OK) return s;
+    }
     ctx->step = h.step;
     ctx->since_snap = h.since_snap;
     ctx->has_geometry = ctx->has_fields = true;

@@ -135,7 +135,9 @@ pull_moments(const S *__restrict__ fcomp, long long n, int self, const Nbr &nb, 
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const bool bb = (links >> opp(i)) & 1u;
-        const long long idx = bb ? (long long)opp(i) * n + self : (long long)i * n + nb.src(i);
+        // 32-bit offsets within one component's planes (19 n < 2^32 is checked at creation)
+        const uint32_t idx = bb ? (uint32_t)opp(i) * (uint32_t)n + (uint32_t)self
+                                : (uint32_t)i * (uint32_t)n + (uint32_t)nb.src(i);
         v[i] = RO ? Storage<S>::load(fcomp + idx, T(0)) : Storage<S>::load_rw(fcomp + idx, T(0));
     }
     Moments<T> m;
@@ -169,7 +171,9 @@ __device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restri
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const bool bb = (links >> opp(i)) & 1u;
-        const long long idx = bb ? (long long)opp(i) * n + self : (long long)i * n + nb.src(i);
+        // 32-bit offsets within one component's planes (19 n < 2^32 is checked at creation)
+        const uint32_t idx = bb ? (uint32_t)opp(i) * (uint32_t)n + (uint32_t)self
+                                : (uint32_t)i * (uint32_t)n + (uint32_t)nb.src(i);
         v[i] = RO ? Storage<S>::load(fcomp + idx, T(0)) : Storage<S>::load_rw(fcomp + idx, T(0));
     }
     T r = v[0];
@@ -224,7 +228,8 @@ __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n,
         const T cF = c0 * Fx + c1 * Fy + c2 * Fz;
         const T fe = feq_dir<T, EQ>(i, m.rho, ux, uy, uz, uu);
         const T v = fe + wgt<T>(i) * (T(4.5) * cAc + ktr + T(1.5) * cF);
-        Storage<S>::store(fout + (long long)i * n + self, v, Storage<S>::shifted ? wgt<T>(i) * sig(i) : T(0));
+        Storage<S>::store(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)self), v,
+                          Storage<S>::shifted ? wgt<T>(i) * sig(i) : T(0));
     }
 }
 
@@ -237,7 +242,7 @@ __device__ __forceinline__ void store_equilibrium(S *__restrict__ fout, long lon
     const T uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < kQ; ++i)
-        Storage<S>::store(fout + (long long)i * n + self, feq_dir<T, EQ>(i, rho, ux, uy, uz, uu),
+        Storage<S>::store(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)self), feq_dir<T, EQ>(i, rho, ux, uy, uz, uu),
                           Storage<S>::shifted ? wgt<T>(i) * sig(i) : T(0));
 }
 

@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1))
             int x = tx0 - 1 + ex, y = ty0 - 1 + ey;
             x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
             y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
-            x %= g.nx;  // grids narrower than a tile wrap more than once
-            y %= g.ny;
+            if (g.nx < TL::EX) x %= g.nx;  // grids narrower than a tile wrap more than once
+            if (g.ny < TL::EY) y %= g.ny;
             const uint32_t w = __ldg(link_b + x + y * g.nx + (long long)zz * g.nxy);
             const uint32_t t = cell_type(w);
             const bool interior = ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;

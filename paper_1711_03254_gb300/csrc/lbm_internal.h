@@ -23,6 +23,9 @@ struct StepArgs {
     const void *par;   // InstParam<T>[batch] on the device
     const Ref *ref_in; // reference densities of the current state (unused in FP64)
     Ref *ref_out;      // reference densities written with f_out
+    const uint32_t *list = nullptr;  // non-solid cells per instance [batch][n] (two-pass), or NULL
+    const int *list_count = nullptr; // entries per instance (device)
+    long long list_max = 0;          // largest entry count
     cudaStream_t stream;
 };
 
@@ -54,6 +57,8 @@ struct ReduceArgs {
 };
 
 cudaError_t launch_two_pass(const StepArgs &a);
+cudaError_t launch_psi_solid(const uint32_t *link, void *psi, bool fp64, const Grid &g, int batch, const void *par,
+                             cudaStream_t s);
 // tile: 0 = 32x8, 1 = 32x4, 2 = 64x4, 3 = 32x16 cells per CTA; zchunk planes per CTA
 cudaError_t launch_fused(const StepArgs &a, int tile, int zchunk);
 int fused_tile_count();

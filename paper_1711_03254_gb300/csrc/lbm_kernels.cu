@@ -47,14 +47,30 @@ __device__ __forceinline__ typename Storage<S>::T ref_at(const Ref *__restrict__
         return typename Storage<S>::T(0);
 }
 
+// Cell handled by this thread: the thread index itself, or (with a list) the
+// j-th non-solid cell of the instance, so that warps only carry cells that
+// do work.  Returns false when the thread has no cell.
+__device__ __forceinline__ bool my_cell(const uint32_t *__restrict__ list, const int *__restrict__ count, int b,
+                                        const Grid &g, long long &k) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (list) {
+        if (j >= count[b]) return false;
+        k = __ldg(list + (long long)b * g.n + j);
+        return true;
+    }
+    k = j;
+    return j < g.n;
+}
+
 template <class S>
 __global__ void __launch_bounds__(256) k_psi(const S *__restrict__ f, const Ref *__restrict__ rin,
                                              const uint32_t *__restrict__ link, typename Storage<S>::T *__restrict__ psi,
-                                             Grid g, const InstParam<typename Storage<S>::T> *__restrict__ par) {
+                                             Grid g, const InstParam<typename Storage<S>::T> *__restrict__ par,
+                                             const uint32_t *__restrict__ list, const int *__restrict__ count) {
     using T = typename Storage<S>::T;
     const int b = blockIdx.y;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.n) return;
+    long long k;
+    if (!my_cell(list, count, b, g, k)) return;
     const uint32_t *link_b = link + (long long)b * g.n;
     const uint32_t word = __ldg(link_b + k);
     const uint32_t t = cell_type(word);
@@ -84,17 +100,18 @@ __global__ void __launch_bounds__(256) k_psi(const S *__restrict__ f, const Ref 
 }
 
 template <class S, int EQ>
-__global__ void __launch_bounds__(256) k_collide(const S *__restrict__ f, S *__restrict__ fo,
+__global__ void __launch_bounds__(256, 2) k_collide(const S *__restrict__ f, S *__restrict__ fo,
                                                  const Ref *__restrict__ rin, Ref *__restrict__ rout,
                                                  const uint32_t *__restrict__ link,
                                                  const typename Storage<S>::T *__restrict__ psi,
                                                  typename Storage<S>::T *__restrict__ macro, Grid g,
                                                  const InstParam<typename Storage<S>::T> *__restrict__ par,
-                                                 int wall_model, int write_macro) {
+                                                 int wall_model, int write_macro, const uint32_t *__restrict__ list,
+                                                 const int *__restrict__ count) {
     using T = typename Storage<S>::T;
     const int b = blockIdx.y;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.n) return;
+    long long k;
+    if (!my_cell(list, count, b, g, k)) return;
     const uint32_t *link_b = link + (long long)b * g.n;
     const uint32_t word = __ldg(link_b + k);
     const uint32_t t = cell_type(word);
@@ -310,17 +327,42 @@ static dim3 cell_grid(const Grid &g, int batch, int threads) {
 template <class S>
 static cudaError_t launch_two_pass_t(const StepArgs &a) {
     using T = typename Storage<S>::T;
-    const dim3 grid = cell_grid(a.g, a.batch, 256);
+    // with cell lists only the non-solid cells get threads (ψ of SOLID cells is static)
+    const long long span = a.list ? (a.list_max > 0 ? a.list_max : 1) : a.g.n;
+    const dim3 grid((unsigned)((span + 255) / 256), (unsigned)a.batch, 1);
     k_psi<S><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, a.ref_in, a.link, (T *)a.psi, a.g,
-                                         (const InstParam<T> *)a.par);
+                                         (const InstParam<T> *)a.par, a.list, a.list_count);
     if (a.eq_order == 0)
         k_collide<S, 0><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
                                                     (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
-                                                    a.wall_model, a.write_macro);
+                                                    a.wall_model, a.write_macro, a.list, a.list_count);
     else
         k_collide<S, 1><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
                                                     (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
-                                                    a.wall_model, a.write_macro);
+                                                    a.wall_model, a.write_macro, a.list, a.list_count);
+    return cudaGetLastError();
+}
+
+// ψ of every SOLID cell (constant in time; the list kernels never visit them).
+template <class T>
+__global__ void k_psi_solid(const uint32_t *__restrict__ link, T *__restrict__ psi, Grid g,
+                            const InstParam<T> *__restrict__ par) {
+    const int b = blockIdx.y;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    if (cell_type(link[(long long)b * g.n + k]) != kSolid) return;
+    psi[((long long)b * 2 + 0) * g.n + k] = par[b].rs[0];
+    psi[((long long)b * 2 + 1) * g.n + k] = par[b].rs[1];
+}
+
+cudaError_t launch_psi_solid(const uint32_t *link, void *psi, bool fp64, const Grid &g, int batch, const void *par,
+                             cudaStream_t s) {
+    if (fp64)
+        k_psi_solid<double><<<cell_grid(g, batch, 256), 256, 0, s>>>(link, (double *)psi, g,
+                                                                     (const InstParam<double> *)par);
+    else
+        k_psi_solid<float><<<cell_grid(g, batch, 256), 256, 0, s>>>(link, (float *)psi, g,
+                                                                    (const InstParam<float> *)par);
     return cudaGetLastError();
 }
 
