@@ -2,11 +2,16 @@
 Shan-Chen D3Q19 update on one GB300.
 
 Workload: random packed spheres 256^3 (overlapping spheres r = 12 to porosity
-0.40, seed 3), 1 % minority component as droplets r = 4, viscosity ratio 100
-(nu_1 = 0.17, nu_2 = 0.0017), G = -2.2, rho^s = 0, body force 1e-6 along x,
-FP32 arithmetic, storage selected by --precision (default 16-bit shifted).
-A step is one update of the whole domain.  f (>= 1.27 GB) is larger than L2,
-so no flush is needed between steps.
+0.40, seed 3), 1 % minority component as droplets r = 4, kinematic viscosities
+1.0 / 0.01 (ratio 100), G = -2.2, rho^s = 0, body force 1e-6 along x, wall
+model 2, FP32 arithmetic, storage selected by --precision (default 16-bit
+shifted).  A step is one update of the whole domain.  f (>= 1.27 GB) is larger
+than L2, so no flush is needed between steps.
+
+The roofline object is for the dominant kernel of the step: its algorithmic
+bytes per launch (per-fluid-cell bytes below x fluid cells) over its average
+launch time, taken with CUDA events around every launch on the launching
+stream during the timed region (lbm_timing_begin / lbm_timing_end).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16s|bf16s]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
@@ -37,11 +42,29 @@ def params(nu=NU, G=G):
 
 
 PARAMS = params()
+# all-fluid droplet check case: tau = 1 for both components (nu = 1/6)
+DROPLET_PARAMS = params(nu=(1 / 6, 1 / 6))
 F_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
-# DRAM traffic per fluid-cell update of the dominant kernel from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum per launch / cells), keyed by
-# kernel strategy and precision, with the hash of the kernel sources they were
-# taken on; any change of the sources voids them.
+
+
+def alg_bytes_per_cell(part: str, precision: str) -> int:
+    """Bytes one fluid-cell update of `part` must move at least: every array
+    element it needs read once and every result written once.
+      f: 2 components x 19 directions x storage bytes, read (and written);
+      psi: 2 values of the arithmetic type; link word 4 B; cell-list entry 4 B;
+      reference densities (shifted storage): 2 x FP16 read, and written with f."""
+    s = F_BYTES[precision]
+    t = 8 if precision == "fp64" else 4
+    ref = 0 if precision == "fp64" else 4
+    if part == "psi":
+        return 38 * s + 4 + 4 + ref + 2 * t
+    if part == "collide":
+        return 76 * s + 4 + 4 + 2 * t + 2 * ref
+    return 76 * s + 4 + 2 * ref  # fused, and each update of a cluster launch
+# DRAM traffic of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its fluid cells),
+# keyed by kernel/precision/workload, with the hash of the kernel sources it was
+# taken on; any change of the sources voids it.
 NCU_TRAFFIC = {}
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cu", "lbm_fused.cu"]
 
@@ -143,11 +166,8 @@ def barrier(ws):
 def max_over_ranks(x: float, ws: int) -> float:
     if ws == 1:
         return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1711_03254_gb300 import replicas
+    return replicas.max_over_ranks(x)
 
 
 def cpu_baseline(t, r1, r2, u, target_s=15.0, crop=64):
@@ -200,7 +220,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", default="fp16s", choices=["fp32", "fp16s", "bf16s", "fp64"])
     ap.add_argument("--kernel", default="auto")
@@ -223,7 +243,8 @@ def main():
     fluid = int((t != 1).sum())
     stream = torch.cuda.current_stream()
 
-    sim = lbm.Sim(n, n, n, [PARAMS], precision=args.precision, kernel=args.kernel)
+    par = PARAMS if args.workload == "spheres" else DROPLET_PARAMS
+    sim = lbm.Sim(n, n, n, [par], precision=args.precision, kernel=args.kernel)
     lbm.lbm_set_stream(sim.ctx, stream.cuda_stream)
     sim.set_geometry(t[None])
     sim.set_fields(r1[None], r2[None], u[None])
@@ -236,9 +257,11 @@ def main():
     torch.cuda.synchronize()
     l0 = sim.launches
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lbm.lbm_timing_begin(sim.ctx, 2 * args.steps + 2)
     ev0.record(stream)
     sim.step(args.steps)
     ev1.record(stream)
+    timing = lbm.lbm_timing_end(sim.ctx)
     torch.cuda.synchronize()
     barrier(ws)
     clocks = clk.stop()
@@ -250,25 +273,35 @@ def main():
 
     mlups = fluid * args.steps * ws / (ms_max / 1e3) / 1e6
     hbm, peak_kind = peaks()
-    sb = F_BYTES[args.precision]
-    alg_per_cell = 2 * 38 * sb + 1
-    kernels_per_step = launches / max(1, args.steps)
-    # every launch of the step; the bytes the method must move per update
-    achieved = alg_per_cell * fluid / ((ms / args.steps) / 1e3) / 1e9
-    key = f"{args.kernel}/{args.precision}"
+    # the dominant kernel of the step: largest summed event time
+    part = max(timing, key=lambda k: timing[k][0])
+    part_ms, part_launches = timing[part]
+    kernel_name = {"psi": "k_psi", "collide": "k_collide", "fused": "k_fused", "cluster": "k_cluster"}[part]
+    per_cell = alg_bytes_per_cell(part, args.precision)
+    updates_per_launch = args.steps if part == "cluster" else 1
+    bytes_per_launch = per_cell * fluid * updates_per_launch
+    avg_s = part_ms / part_launches / 1e3
+    achieved = bytes_per_launch / avg_s / 1e9
+    key = f"{kernel_name}/{args.precision}/{args.workload}"
     tr = NCU_TRAFFIC.get(key)
     traffic = None
     if tr and tr.get("src") == sources_hash():
-        traffic = tr["bytes_per_cell"] * fluid
+        traffic = round(tr["bytes_per_fluid_cell"] * fluid * updates_per_launch)
+    step_bytes = (2 * 38 * F_BYTES[args.precision] + 1) * fluid
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
-            "algorithmic_bytes_per_cell": alg_per_cell, "kernels_per_step": kernels_per_step}
+            "kernel": kernel_name, "algorithmic_bytes_per_fluid_cell": per_cell,
+            "avg_launch_ms": round(avg_s * 1e3, 4), "launches": part_launches,
+            "share_of_step": round(part_ms / ms, 4),
+            "parts_ms": {k: round(v[0] / v[1], 4) for k, v in timing.items()},
+            "step_min_bytes_per_fluid_cell": 2 * 38 * F_BYTES[args.precision] + 1,
+            "step_frac": round(step_bytes / ((ms / args.steps) / 1e3) / 1e9 / hbm, 4)}
 
     # end to end through the C ABI with host buffers
     e2e = None
     if ws == 1:
         ke = max(1, min(args.steps, 100))
-        sim2 = lbm.Sim(n, n, n, [PARAMS], precision=args.precision, kernel=args.kernel)
+        sim2 = lbm.Sim(n, n, n, [par], precision=args.precision, kernel=args.kernel)
         lbm.lbm_set_stream(sim2.ctx, stream.cuda_stream)
         r1b, r2b, ub = np.empty_like(r1[None]), np.empty_like(r2[None]), np.empty_like(u[None])
         torch.cuda.synchronize()
@@ -292,11 +325,11 @@ def main():
         line = {"metric": "MLUPS (fluid-cell updates per second, 2-comp D3Q19)", "value": round(mlups, 1),
                 "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": (f"packed spheres {n}^3, r=12, porosity 0.40, 1% minority r=4, "
                                         f"nu {NU[0]}/{NU[1]} (ratio 100), G={G}, g=1e-6, wall model 2"
                                         if args.workload == "spheres" else
-                                        f"periodic droplet {n}^3, R={n // 8}, no walls"),
+                                        f"periodic droplet {n}^3, R={n // 8}, tau 1/1, G={G}, no walls"),
                            "storage": args.precision, "kernel": args.kernel, "fluid_cells": fluid,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),

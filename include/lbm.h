@@ -74,7 +74,7 @@ typedef enum {
 
 /* Kernel strategy for lbm_step. */
 typedef enum {
-    LBM_KERNEL_AUTO = 0,     /* fused when the grid allows it, else two-pass */
+    LBM_KERNEL_AUTO = 0,     /* cluster for instances of <= 32768 cells (n > 1 updates), else two-pass */
     LBM_KERNEL_TWO_PASS = 1, /* density pre-pass, then stream+collide */
     LBM_KERNEL_FUSED = 2,    /* single read of f: z-marching tiles with a recomputed density halo */
     LBM_KERNEL_CLUSTER = 3   /* persistent: one thread-block cluster per instance, n updates per launch */
@@ -209,6 +209,31 @@ lbm_status lbm_field_sums_static(const double *rho1, const double *rho2, const d
 
 /* Number of CUDA kernel launches the context has issued so far. */
 long long lbm_launch_count(const lbm_ctx *ctx);
+
+/* Per-kernel device time of lbm_step (no counterpart in the paper: it is how
+ * the update kernels are measured against the memory roofline).  Parts: */
+typedef enum {
+    LBM_PART_PSI = 0,     /* two-pass: density and psi of every fluid cell */
+    LBM_PART_COLLIDE = 1, /* two-pass: pull, forces, collision, store */
+    LBM_PART_FUSED = 2,   /* single-read fused update */
+    LBM_PART_CLUSTER = 3, /* persistent cluster launch (several updates each) */
+    LBM_PART_COUNT = 4
+} lbm_part;
+
+/* Start timing: until lbm_timing_end, every kernel launched by lbm_step on the
+ * context's stream is bracketed by CUDA events (at most max_launches of them,
+ * 1..65536; launches beyond that are not timed).  The events are created here.
+ * Steps issued while the stream is being captured are not timed.
+ * Errors: LBM_ERR_ARG (null ctx, max_launches out of range), LBM_ERR_STATE
+ * (timing already on), LBM_ERR_CUDA (event creation). */
+lbm_status lbm_timing_begin(lbm_ctx *ctx, int max_launches);
+
+/* Stop timing: waits for the last recorded event, then writes, per lbm_part,
+ * the summed device milliseconds to ms[LBM_PART_COUNT] and the number of timed
+ * launches to launches[LBM_PART_COUNT] (both caller-owned host arrays), and
+ * destroys the events.  Errors: LBM_ERR_ARG (null pointer), LBM_ERR_STATE
+ * (timing not on), LBM_ERR_CUDA (event query). */
+lbm_status lbm_timing_end(lbm_ctx *ctx, double *ms, long long *launches);
 
 /* Process-wide device allocator hook used by contexts created afterwards:
  * alloc(bytes, stream) returns device memory or NULL; release(ptr, stream)

@@ -60,6 +60,40 @@ struct lbm_ctx {
     int tile = -1, zchunk = -1;  // fused-kernel tiling; -1 = heuristic
     std::string err;
 
+    // per-kernel event timing (lbm_timing_begin / lbm_timing_end)
+    struct TimedLaunch {
+        lbm_kernel kind;
+        int first;  // index of its first event
+    };
+    bool timing = false;
+    int timing_max = 0, timing_launches = 0;
+    std::vector<cudaEvent_t> tev;
+    int tev_used = 0;
+    std::vector<TimedLaunch> timed;
+
+    void drop_events() {
+        for (cudaEvent_t e : tev) cudaEventDestroy(e);
+        tev.clear();
+        timed.clear();
+        tev_used = 0;
+        timing_launches = 0;
+        timing = false;
+    }
+    // events for one launcher call of `kind`, or NULL when it is not timed
+    cudaEvent_t *events_for(lbm_kernel kind) {
+        if (!timing) return nullptr;
+        const int kernels = kind == LBM_KERNEL_TWO_PASS ? 2 : 1;
+        const int nev = kernels + 1;
+        if (timing_launches + kernels > timing_max || tev_used + nev > (int)tev.size()) return nullptr;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+        timed.push_back({kind, tev_used});
+        cudaEvent_t *ev = &tev[tev_used];
+        tev_used += nev;
+        timing_launches += kernels;
+        return ev;
+    }
+
     bool fp64() const { return cfg.precision == LBM_FP64; }
     size_t tbytes() const { return fp64() ? 8 : 4; }
     size_t cells() const { return (size_t)cfg.batch * (size_t)g.n; }
@@ -150,7 +184,9 @@ lbm_status upload_params(lbm_ctx *ctx) {
 lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
     if (ctx->kernel != LBM_KERNEL_AUTO) return ctx->kernel;
     if (ctx->g.n <= kClusterAutoCells && n > 1) return LBM_KERNEL_CLUSTER;
-    return LBM_KERNEL_FUSED;
+    // measured on GB300: the list-driven two-pass update beats the fused one on
+    // porous (1.9-2.2x) and all-fluid (1.2x) grids
+    return LBM_KERNEL_TWO_PASS;
 }
 
 // Fused-kernel tiling when none was set: 32x8 columns (32x4 in FP64, whose
@@ -329,6 +365,7 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
 void lbm_destroy(lbm_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    ctx->drop_events();
     std::vector<void *> own = ctx->owned;
     for (void *p : own) ctx->dfree(p);
     delete ctx;
@@ -351,6 +388,63 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
 }
 
 long long lbm_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+lbm_status lbm_timing_begin(lbm_ctx *ctx, int max_launches) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (max_launches < 1 || max_launches > 65536)
+        return ctx->fail(LBM_ERR_ARG, "lbm_timing_begin: max_launches must be in 1..65536");
+    if (ctx->timing) return ctx->fail(LBM_ERR_STATE, "lbm_timing_begin: timing is already on");
+    LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    // at most 3 events per 2 launches (two-pass) or 2 per launch (fused, cluster)
+    const int nev = 2 * max_launches + 1;
+    ctx->tev.reserve((size_t)nev);
+    for (int k = 0; k < nev; ++k) {
+        cudaEvent_t e;
+        const cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) {
+            ctx->drop_events();
+            return ctx->cuda_fail(err, "lbm_timing_begin: cudaEventCreate");
+        }
+        ctx->tev.push_back(e);
+    }
+    ctx->timing_max = max_launches;
+    ctx->timing = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_timing_end(lbm_ctx *ctx, double *ms, long long *launches) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (!ms || !launches) return ctx->fail(LBM_ERR_ARG, "lbm_timing_end: null output array");
+    if (!ctx->timing) return ctx->fail(LBM_ERR_STATE, "lbm_timing_end: timing is not on");
+    LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    for (int p = 0; p < LBM_PART_COUNT; ++p) {
+        ms[p] = 0.0;
+        launches[p] = 0;
+    }
+    cudaError_t e = cudaSuccess;
+    if (ctx->tev_used > 0) e = cudaEventSynchronize(ctx->tev[ctx->tev_used - 1]);
+    for (size_t k = 0; k < ctx->timed.size() && e == cudaSuccess; ++k) {
+        const auto &t = ctx->timed[k];
+        cudaEvent_t *ev = &ctx->tev[t.first];
+        float a = 0.f, b = 0.f;
+        if (t.kind == LBM_KERNEL_TWO_PASS) {
+            e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+            ms[LBM_PART_PSI] += a;
+            ms[LBM_PART_COLLIDE] += b;
+            launches[LBM_PART_PSI] += 1;
+            launches[LBM_PART_COLLIDE] += 1;
+        } else {
+            e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+            const int p = t.kind == LBM_KERNEL_FUSED ? LBM_PART_FUSED : LBM_PART_CLUSTER;
+            ms[p] += a;
+            launches[p] += 1;
+        }
+    }
+    ctx->drop_events();
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_timing_end: event query");
+    return LBM_OK;
+}
 
 lbm_status lbm_set_tiling(lbm_ctx *ctx, int tile, int zchunk) {
     if (!ctx) return LBM_ERR_ARG;
@@ -435,6 +529,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     if (k == LBM_KERNEL_CLUSTER) {
         if (n > 0) {
             StepArgs a = step_args(ctx, 1);
+            a.ev = ctx->events_for(LBM_KERNEL_CLUSTER);
             cudaError_t e = launch_cluster(a, n);
             if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_step cluster launch");
             ctx->launches += 1;
@@ -449,6 +544,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     if (fused) default_tiling(ctx, tile, zchunk);
     for (int s = 0; s < n; ++s) {
         StepArgs a = step_args(ctx, s == n - 1);
+        a.ev = ctx->events_for(fused ? LBM_KERNEL_FUSED : LBM_KERNEL_TWO_PASS);
         cudaError_t e = fused ? launch_fused(a, tile, zchunk) : launch_two_pass(a);
         if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_step launch");
         ctx->launches += fused ? 1 : 2;

@@ -157,14 +157,8 @@ __global__ void __launch_bounds__(256) k_cluster(S *__restrict__ fa, S *__restri
                 c = __ldcg(psi1 + j);
             };
             const Forces<T> F = sc_forces<T>(psi_at, word, m0.rho, m1.rho, p, wall_model);
-            const T rho = m0.rho + m1.rho;
-            const T Fx = F.F[0][0] + F.F[1][0], Fy = F.F[0][1] + F.F[1][1], Fz = F.F[0][2] + F.F[1][2];
-            const T ux = (m0.jx + m1.jx) / rho + T(0.5) * (Fx / rho);
-            const T uy = (m0.jy + m1.jy) / rho + T(0.5) * (Fy / rho);
-            const T uz = (m0.jz + m1.jz) / rho + T(0.5) * (Fz / rho);
-            const T tau = tau_mix<T>(m0.rho, m1.rho, p);
-            const T omega = T(1) - T(1) / tau;
-            const T fcoef = T(1) - T(1) / (T(2) * tau);
+            const Relax<T> R = relax<T>(m0, m1, F, p);
+            const T ux = R.ux, uy = R.uy, uz = R.uz, omega = R.omega, fcoef = R.fcoef;
             collide_store<S, EQ>(fout, g.n, k, m0, ux, uy, uz, F.F[0][0], F.F[0][1], F.F[0][2], omega, fcoef,
                                  sig_for(psi0, m0.rho));
             collide_store<S, EQ>(fout + kQ * g.n, g.n, k, m1, ux, uy, uz, F.F[1][0], F.F[1][1], F.F[1][2], omega,
@@ -210,8 +204,12 @@ static cudaError_t launch_cluster_t(const StepArgs &a, int nsteps, int csize) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster<S, EQ>, (S *)a.f_in, (S *)a.f_out, (Ref *)a.ref_in, a.ref_out, a.link,
-                              (T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par, a.wall_model, nsteps);
+    record_event(a, 0);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_cluster<S, EQ>, (S *)a.f_in, (S *)a.f_out, (Ref *)a.ref_in,
+                                             a.ref_out, a.link, (T *)a.psi, (T *)a.macro, a.g,
+                                             (const InstParam<T> *)a.par, a.wall_model, nsteps);
+    record_event(a, 1);
+    return e;
 }
 
 template <class S> static cudaError_t launch_cluster_s(const StepArgs &a, int nsteps, int csize) {

@@ -195,6 +195,11 @@ __device__ __forceinline__ T feq_dir(int i, T rho, T ux, T uy, T uz, T uu) {
 // S6-S7 for one component: writes f*_i = feq_i + w_i/(2 T0^2) H_i : A + w_i c_i.F/(2 T0)
 // with A = (1 - 1/tau) Pi^neq + (1 - 1/(2 tau)) (u_F F + F u_F).
 // sig(i) is the reference density of the cell value i streams into.
+//
+// Directions come in opposite pairs (i, i+1) with c_{i+1} = -c_i: the parts of
+// f*_i that are even in c (rest term of feq, the quadratic terms of Eq. 3 for
+// EQ = 1, H_i : A) are shared, the odd parts (the c.u terms of feq, the
+// first-order forcing) change sign, so each pair costs one evaluation.
 template <class S, int EQ, class Sig>
 __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n, int self,
                                               const Moments<typename Storage<S>::T> &m,
@@ -220,16 +225,30 @@ __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n,
     const T axz = omega * nxz + fcoef * (ux * Fz + uz * Fx);
     const T ayz = omega * nyz + fcoef * (uy * Fz + uz * Fy);
     const T ktr = -T(1.5) * (axx + ayy + azz);  // -(T0/(2 T0^2)) tr A
+    // rest direction: c = 0
+    {
+        T e = m.rho;
+        if (EQ == 1) e = m.rho * (T(1) - T(1.5) * uu);
+        const T v = wgt<T>(0) * (e + ktr);
+        Storage<S>::store(fout + (uint32_t)self, v, Storage<S>::shifted ? wgt<T>(0) * sig(0) : T(0));
+    }
+    const T odd_k = T(3) - T(4.5) * uu;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) {
+    for (int i = 1; i < kQ; i += 2) {
         const T c0 = T(cx(i)), c1 = T(cy(i)), c2 = T(cz(i));
+        const T cu = c0 * ux + c1 * uy + c2 * uz;
         const T cAc = c0 * c0 * axx + c1 * c1 * ayy + c2 * c2 * azz +
                       T(2) * (c0 * c1 * axy + c0 * c2 * axz + c1 * c2 * ayz);
         const T cF = c0 * Fx + c1 * Fy + c2 * Fz;
-        const T fe = feq_dir<T, EQ>(i, m.rho, ux, uy, uz, uu);
-        const T v = fe + wgt<T>(i) * (T(4.5) * cAc + ktr + T(1.5) * cF);
-        Storage<S>::store(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)self), v,
-                          Storage<S>::shifted ? wgt<T>(i) * sig(i) : T(0));
+        // w_i x (even part, odd part) of f*_i
+        T even = m.rho + (T(4.5) * cAc + ktr);
+        if (EQ == 1) even += m.rho * (T(4.5) * cu * cu - T(1.5) * uu);
+        const T odd = m.rho * cu * (odd_k + T(4.5) * cu * cu) + T(1.5) * cF;
+        const T w = wgt<T>(i);
+        Storage<S>::store(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)self), w * (even + odd),
+                          Storage<S>::shifted ? w * sig(i) : T(0));
+        Storage<S>::store(fout + ((uint32_t)(i + 1) * (uint32_t)n + (uint32_t)self), w * (even - odd),
+                          Storage<S>::shifted ? w * sig(i + 1) : T(0));
     }
 }
 
@@ -324,10 +343,29 @@ __device__ __forceinline__ Forces<T> sc_forces(const PsiAt &psi_at, uint32_t lin
 
 // S5: tau_mix from the density-weighted viscosity, p = rho_1 / rho in [0, 1].
 template <class T> __device__ __forceinline__ T tau_mix(T rho0, T rho1, const InstParam<T> &p) {
-    T q = rho0 / (rho0 + rho1);
+    T q = rho0 * (T(1) / (rho0 + rho1));
     q = q < T(0) ? T(0) : (q > T(1) ? T(1) : q);
     const T nu = q * p.nu[0] + (T(1) - q) * p.nu[1];
-    return nu / (T(1) / T(3)) + T(0.5);
+    return T(3) * nu + T(0.5);
+}
+
+// S5 for the cell: u_F = (j + F_tot / 2) / rho (Eq. 8) and the relaxation
+// factors 1 - 1/tau and 1 - 1/(2 tau) of the collision (one reciprocal each).
+template <class T> struct Relax {
+    T ux, uy, uz, omega, fcoef;
+};
+template <class T>
+__device__ __forceinline__ Relax<T> relax(const Moments<T> &m0, const Moments<T> &m1, const Forces<T> &F,
+                                          const InstParam<T> &p) {
+    const T inv = T(1) / (m0.rho + m1.rho);
+    Relax<T> r;
+    r.ux = (m0.jx + m1.jx + T(0.5) * (F.F[0][0] + F.F[1][0])) * inv;
+    r.uy = (m0.jy + m1.jy + T(0.5) * (F.F[0][1] + F.F[1][1])) * inv;
+    r.uz = (m0.jz + m1.jz + T(0.5) * (F.F[0][2] + F.F[1][2])) * inv;
+    const T itau = T(1) / tau_mix<T>(m0.rho, m1.rho, p);
+    r.omega = T(1) - itau;
+    r.fcoef = T(1) - T(0.5) * itau;
+    return r;
 }
 
 }  // namespace lbm

@@ -178,14 +178,8 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 2 : 1))
                     v1 = sm.sp[sl_][1][ly + 1 + cy(i)][lx + 1 + cx(i)];
                 };
                 const Forces<T> F = sc_forces<T>(psi_at, word, a0.rho, a1.rho, p, wall_model);
-                const T rho = a0.rho + a1.rho;
-                const T Fx = F.F[0][0] + F.F[1][0], Fy = F.F[0][1] + F.F[1][1], Fz = F.F[0][2] + F.F[1][2];
-                const T ux = (a0.jx + a1.jx) / rho + T(0.5) * (Fx / rho);
-                const T uy = (a0.jy + a1.jy) / rho + T(0.5) * (Fy / rho);
-                const T uz = (a0.jz + a1.jz) / rho + T(0.5) * (Fz / rho);
-                const T tau = tau_mix<T>(a0.rho, a1.rho, p);
-                const T omega = T(1) - T(1) / tau;
-                const T fcoef = T(1) - T(1) / (T(2) * tau);
+                const Relax<T> R = relax<T>(a0, a1, F, p);
+                const T ux = R.ux, uy = R.uy, uz = R.uz, omega = R.omega, fcoef = R.fcoef;
                 collide_store<S, EQ>(fob, g.n, (int)k, a0, ux, uy, uz, F.F[0][0], F.F[0][1], F.F[0][2], omega, fcoef,
                                      sig_for(0, a0.rho));
                 collide_store<S, EQ>(fob + kQ * g.n, g.n, (int)k, a1, ux, uy, uz, F.F[1][0], F.F[1][1], F.F[1][2],
@@ -245,9 +239,11 @@ static cudaError_t launch_fused_tile(const StepArgs &a, int zchunk) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    record_event(a, 0);
     k_fused<S, EQ, TX, TY><<<(unsigned)blocks, TX * TY, smem, a.stream>>>(
         (const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link, (T *)a.macro, a.g,
         (const InstParam<T> *)a.par, a.wall_model, a.write_macro, tiles_x, tiles_y, zchunk, nchunks);
+    record_event(a, 1);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,14 @@ struct StepArgs {
     const int *list_count = nullptr; // entries per instance (device)
     long long list_max = 0;          // largest entry count
     cudaStream_t stream;
+    // when non-NULL: events recorded before the first kernel and after each
+    // kernel of the launch (two-pass: 3 events, fused and cluster: 2)
+    cudaEvent_t *ev = nullptr;
 };
+
+inline void record_event(const StepArgs &a, int k) {
+    if (a.ev) cudaEventRecord(a.ev[k], a.stream);
+}
 
 struct InitArgs {
     lbm_precision precision;

@@ -169,25 +169,30 @@ __global__ void __launch_bounds__(256, 2) k_collide(const S *__restrict__ f, S *
         m0 = pull_moments<S>(f + fofs, g.n, self, up, sw, ref_at<S>(rin, rb + self));
         m1 = pull_moments<S>(f + fofs + kQ * g.n, g.n, self, up, sw, ref_at<S>(rin, rb + g.n + self));
     }
-    auto psi_at = [&](int i, T &a, T &c) {
+    // psi of both components at the 18 neighbours, loaded once: they feed the
+    // forces and (shifted storage) the reference densities of the stores
+    T q0[kQ], q1[kQ];
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
         const int j = own.dst(i);
-        a = __ldg(psi0 + j);
-        c = __ldg(psi1 + j);
+        q0[i] = __ldg(psi0 + j);
+        q1[i] = __ldg(psi1 + j);
+    }
+    auto psi_at = [&](int i, T &a, T &c) {
+        a = q0[i];
+        c = q1[i];
     };
     const Forces<T> F = sc_forces<T>(psi_at, word, m0.rho, m1.rho, p, wall_model);
-    const T rho = m0.rho + m1.rho;
-    const T Fx = F.F[0][0] + F.F[1][0], Fy = F.F[0][1] + F.F[1][1], Fz = F.F[0][2] + F.F[1][2];
-    // Eq. 8: u_F = u + g/2 with u = j/rho and g = F_tot/rho
-    const T ux = (m0.jx + m1.jx) / rho + T(0.5) * (Fx / rho);
-    const T uy = (m0.jy + m1.jy) / rho + T(0.5) * (Fy / rho);
-    const T uz = (m0.jz + m1.jz) / rho + T(0.5) * (Fz / rho);
-    const T tau = tau_mix<T>(m0.rho, m1.rho, p);
-    const T omega = T(1) - T(1) / tau;
-    const T fcoef = T(1) - T(1) / (T(2) * tau);
+    const Relax<T> R = relax<T>(m0, m1, F, p);
+    const T ux = R.ux, uy = R.uy, uz = R.uz, omega = R.omega, fcoef = R.fcoef;
+    // reference density of the cell each value streams into (own cell when the
+    // neighbour is SOLID and the value bounces back)
+    auto sig0 = [&](int i) -> T { return ref_value((i == 0 || ((word >> i) & 1u)) ? m0.rho : q0[i]); };
+    auto sig1 = [&](int i) -> T { return ref_value((i == 0 || ((word >> i) & 1u)) ? m1.rho : q1[i]); };
     collide_store<S, EQ>(fo + fofs, g.n, (int)k, m0, ux, uy, uz, F.F[0][0], F.F[0][1], F.F[0][2], omega, fcoef,
-                         sig_for(psi0, m0.rho));
+                         sig0);
     collide_store<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, m1, ux, uy, uz, F.F[1][0], F.F[1][1], F.F[1][2], omega,
-                         fcoef, sig_for(psi1, m1.rho));
+                         fcoef, sig1);
     if constexpr (Storage<S>::shifted) {
         rout[rb + k] = __float2half_rn((float)m0.rho);
         rout[rb + g.n + k] = __float2half_rn((float)m1.rho);
@@ -330,8 +335,10 @@ static cudaError_t launch_two_pass_t(const StepArgs &a) {
     // with cell lists only the non-solid cells get threads (ψ of SOLID cells is static)
     const long long span = a.list ? (a.list_max > 0 ? a.list_max : 1) : a.g.n;
     const dim3 grid((unsigned)((span + 255) / 256), (unsigned)a.batch, 1);
+    record_event(a, 0);
     k_psi<S><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, a.ref_in, a.link, (T *)a.psi, a.g,
                                          (const InstParam<T> *)a.par, a.list, a.list_count);
+    record_event(a, 1);
     if (a.eq_order == 0)
         k_collide<S, 0><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
                                                     (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
@@ -340,6 +347,7 @@ static cudaError_t launch_two_pass_t(const StepArgs &a) {
         k_collide<S, 1><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
                                                     (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
                                                     a.wall_model, a.write_macro, a.list, a.list_count);
+    record_event(a, 2);
     return cudaGetLastError();
 }
 

@@ -217,6 +217,25 @@ def lbm_launch_count(ctx) -> int:
     return int(library().lbm_launch_count(ctx))
 
 
+PARTS = ("psi", "collide", "fused", "cluster")
+
+
+def lbm_timing_begin(ctx, max_launches: int = 4096):
+    L = library()
+    L.lbm_timing_begin.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    return _check(L.lbm_timing_begin(ctx, int(max_launches)), ctx)
+
+
+def lbm_timing_end(ctx) -> dict:
+    """{part: (summed device ms, timed launches)} for the parts that ran."""
+    L = library()
+    L.lbm_timing_end.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    ms = np.zeros(len(PARTS))
+    n = (ctypes.c_longlong * len(PARTS))()
+    _check(L.lbm_timing_end(ctx, _dp(ms), n), ctx)
+    return {p: (float(ms[k]), int(n[k])) for k, p in enumerate(PARTS) if n[k] > 0}
+
+
 def lbm_destroy(ctx):
     library().lbm_destroy(ctx)
 

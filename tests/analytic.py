@@ -50,3 +50,23 @@ def layered_poiseuille(rho, nu, g):
 def single_phase_poiseuille(H, nu, g):
     s = np.arange(H) + 0.5
     return g * s * (H - s) / (2.0 * nu)
+
+
+def golden(name):
+    """Rows of a paper-value fixture under tests/golden/ (comment lines start
+    with '#'; first remaining line is the header) as a list of dicts, numbers
+    converted to float."""
+    import csv
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    lines = [ln for ln in open(path) if ln.strip() and not ln.lstrip().startswith("#")]
+    rows = []
+    for r in csv.DictReader(lines):
+        out = {}
+        for k, v in r.items():
+            try:
+                out[k] = float(v)
+            except ValueError:
+                out[k] = v
+        rows.append(out)
+    return rows

@@ -70,3 +70,20 @@ def test_structs_match_header(lbm):
     import ctypes
     assert ctypes.sizeof(lbm.lbm_config) == 7 * 4  # 7 ints
     assert ctypes.sizeof(lbm.lbm_instance_params) == 12 * 8
+
+
+def test_create_rejects_grids_beyond_32_bit_plane_offsets(lbm):
+    # 19 planes of 1024 x 1024 x 256 cells overflow the kernels' 32-bit offsets
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_config(1024, 1024, 256), lbm.make_params([dict(tau=(1.0, 1.0), G=-2.2)]))
+    assert e.value.status == 1
+    assert "cells per instance" in lbm.lbm_last_error()
+
+
+def test_timing_rejects_null_context(lbm):
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_timing_begin(None, 16)
+    assert e.value.status == 1
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_timing_end(None)
+    assert e.value.status == 1

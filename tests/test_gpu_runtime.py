@@ -92,3 +92,44 @@ def test_launch_counts(lbm):
     l0 = b.launches
     b.step(7)
     assert b.launches - l0 == 1
+
+
+def test_per_kernel_timing(lbm):
+    """Event timing brackets every launch of lbm_step: counts per part, times
+    positive and no larger than the wall time of the steps, results unchanged."""
+    import torch
+    for kernel, parts in (("two_pass", {"psi": 6, "collide": 6}), ("fused", {"fused": 6}),
+                          ("cluster", {"cluster": 1})):
+        a = _sim(lbm, precision="fp32", kernel=kernel)
+        b = _sim(lbm, precision="fp32", kernel=kernel)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lbm.lbm_timing_begin(a.ctx, 64)
+        e0.record()
+        a.step(6)
+        e1.record()
+        t = lbm.lbm_timing_end(a.ctx)
+        torch.cuda.synchronize()
+        assert {k: v[1] for k, v in t.items()} == parts, kernel
+        total = e0.elapsed_time(e1)
+        assert all(v[0] > 0 for v in t.values())
+        assert sum(v[0] for v in t.values()) <= total * 1.01 + 0.01
+        b.step(6)
+        np.testing.assert_array_equal(a.get_f(), b.get_f())
+        a.close()
+        b.close()
+
+
+def test_timing_capacity_and_state_errors(lbm):
+    a = _sim(lbm, precision="fp32", kernel="two_pass")
+    lbm.lbm_timing_begin(a.ctx, 4)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_timing_begin(a.ctx, 4)
+    assert e.value.status == 6
+    a.step(5)  # 10 launches: only the first 4 are timed
+    t = lbm.lbm_timing_end(a.ctx)
+    assert t["psi"][1] == 2 and t["collide"][1] == 2
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_timing_end(a.ctx)
+    assert e.value.status == 6
+    a.close()
