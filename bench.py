@@ -65,7 +65,11 @@ def alg_bytes_per_cell(part: str, precision: str) -> int:
 # (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its fluid cells),
 # keyed by kernel/precision/workload, with the hash of the kernel sources it was
 # taken on; any change of the sources voids it.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 128^3 packed spheres (837,994 non-solid cells), ncu --set full, one launch:
+    # 273.1 MB read + 103.1 MB written; traffic scales with the non-solid cells
+    "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db"},
+}
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cu", "lbm_fused.cu"]
 
 
@@ -220,7 +224,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", default="fp16s", choices=["fp32", "fp16s", "bf16s", "fp64"])
     ap.add_argument("--kernel", default="auto")
