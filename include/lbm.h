@@ -74,10 +74,15 @@ typedef enum {
 
 /* Kernel strategy for lbm_step. */
 typedef enum {
-    LBM_KERNEL_AUTO = 0,     /* cluster for instances of <= 32768 cells (n > 1 updates), else two-pass */
-    LBM_KERNEL_TWO_PASS = 1, /* density pre-pass, then stream+collide */
+    LBM_KERNEL_AUTO = 0,     /* cluster for instances of <= 32768 cells (n > 1 updates); else compact
+                                when at least 5 % of the cells are SOLID and the grid fits its
+                                coordinate limits; else two-pass */
+    LBM_KERNEL_TWO_PASS = 1, /* density pre-pass, then stream+collide, over the non-solid cells */
     LBM_KERNEL_FUSED = 2,    /* single read of f: z-marching tiles with a recomputed density halo */
-    LBM_KERNEL_CLUSTER = 3   /* persistent: one thread-block cluster per instance, n updates per launch */
+    LBM_KERNEL_CLUSTER = 3,  /* persistent: one thread-block cluster per instance, n updates per launch */
+    LBM_KERNEL_COMPACT = 4   /* two-pass on a compact layout that stores only the non-solid cells
+                                (in cell order; neighbours found from per-row occupancy words);
+                                needs nx <= 2048, ny <= 2048, nz <= 1024 */
 } lbm_kernel;
 
 typedef struct {
@@ -141,10 +146,11 @@ lbm_status lbm_reduce(lbm_ctx *ctx, double *out);
  * storage modes are expanded back to f = stored + w_i R), host array
  * f[batch][2][19][nz][ny][nx] with the direction order 0 rest, then pairs
  * +x,-x, +y,-y, +z,-z, (1,1,0),(-1,-1,0), (1,-1,0),(-1,1,0), (1,0,1),(-1,0,-1),
- * (1,0,-1),(-1,0,1), (0,1,1),(0,-1,-1), (0,1,-1),(0,-1,1).  Values in SOLID
- * cells are unspecified.  lbm_set_distributions uploads such an array (rounded
- * to the storage format) as the new state; the fields of the last update are
- * kept.  Errors: LBM_ERR_ARG (null), LBM_ERR_STATE (no fields yet). */
+ * (1,0,-1),(-1,0,1), (0,1,1),(0,-1,-1), (0,1,-1),(0,-1,1).  SOLID cells carry
+ * no distributions: they are exported as 0 and ignored on import.
+ * lbm_set_distributions uploads such an array (rounded to the storage format)
+ * as the new state; the fields of the last update are kept.
+ * Errors: LBM_ERR_ARG (null), LBM_ERR_STATE (no fields yet). */
 lbm_status lbm_get_distributions(lbm_ctx *ctx, double *f);
 lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *f);
 
@@ -161,7 +167,11 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes);
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
 
 /* Choose the kernel strategy (default LBM_KERNEL_AUTO).  LBM_ERR_ARG if the
- * strategy cannot run this configuration (e.g. CLUSTER on a large grid). */
+ * strategy cannot run this configuration (e.g. CLUSTER on a large grid,
+ * COMPACT beyond its coordinate limits).  The compact strategy keeps the
+ * distributions in its own layout; the library converts the state between the
+ * layouts when a step, an export or an import needs the other one (one
+ * gather of f, on the context's stream). */
 lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel);
 
 /* Tiling of the fused kernel: tile 0 = 32x8, 1 = 32x4, 2 = 64x4, 3 = 32x16

@@ -50,6 +50,13 @@ struct lbm_ctx {
     uint32_t *list = nullptr;  // non-solid cells of each instance, in cell order [batch][n]
     int *list_count = nullptr; // entries per instance
     long long list_max = 0;
+    long long nonsolid = 0;    // non-solid cells over all instances
+    // compact layout: 0 = f, ref dense; 1 = compact (LBM_KERNEL_COMPACT)
+    int layout = 0;
+    bool compact_ok = false;   // grid within the packed-coordinate limits
+    uint32_t *cxyz = nullptr, *clink = nullptr;
+    uint2 *rowtab = nullptr;
+    int words = 0;
     void *psi = nullptr, *macro = nullptr, *usnap = nullptr, *dpar = nullptr;
     double *partial = nullptr, *red_out = nullptr;
     int nblk = 0;
@@ -82,7 +89,7 @@ struct lbm_ctx {
     // events for one launcher call of `kind`, or NULL when it is not timed
     cudaEvent_t *events_for(lbm_kernel kind) {
         if (!timing) return nullptr;
-        const int kernels = kind == LBM_KERNEL_TWO_PASS ? 2 : 1;
+        const int kernels = (kind == LBM_KERNEL_TWO_PASS || kind == LBM_KERNEL_COMPACT) ? 2 : 1;
         const int nev = kernels + 1;
         if (timing_launches + kernels > timing_max || tev_used + nev > (int)tev.size()) return nullptr;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -185,7 +192,9 @@ lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
     if (ctx->kernel != LBM_KERNEL_AUTO) return ctx->kernel;
     if (ctx->g.n <= kClusterAutoCells && n > 1) return LBM_KERNEL_CLUSTER;
     // measured on GB300: the list-driven two-pass update beats the fused one on
-    // porous (1.9-2.2x) and all-fluid (1.2x) grids
+    // porous (1.9-2.2x) and all-fluid (1.2x) grids; with SOLID cells the
+    // compact layout avoids the dense layout's partly used sectors
+    if (ctx->compact_ok && (double)ctx->nonsolid <= 0.95 * (double)ctx->cells()) return LBM_KERNEL_COMPACT;
     return LBM_KERNEL_TWO_PASS;
 }
 
@@ -211,27 +220,88 @@ void default_tiling(const lbm_ctx *ctx, int &tile, int &zchunk) {
 // Lists of the non-solid cells of every instance (in cell order) for the
 // two-pass kernels, and the static pseudo-potential of the SOLID cells.
 // type_of(global cell index) gives the cell type.
+// With the compact layout available, also the packed coordinates of the listed
+// cells, their geometry words (gathered on the device from ctx->link, which
+// must hold the geometry already) and the per-row occupancy words.
 template <class F> lbm_status build_cell_lists(lbm_ctx *ctx, F type_of) {
     const long long n = ctx->g.n;
-    std::vector<uint32_t> lst((size_t)ctx->cfg.batch * n);
-    std::vector<int> cnt(ctx->cfg.batch);
-    long long mx = 0;
-    for (int b = 0; b < ctx->cfg.batch; ++b) {
-        int c = 0;
-        for (long long k = 0; k < n; ++k)
-            if (type_of((size_t)b * n + k) != 1u) lst[(size_t)b * n + c++] = (uint32_t)k;
-        cnt[b] = c;
-        if (c > mx) mx = c;
+    const int nx = ctx->g.nx, ny = ctx->g.ny, nz = ctx->g.nz, W = ctx->words;
+    const size_t rows = (size_t)ny * nz;
+    std::vector<uint32_t> lst((size_t)ctx->cfg.batch * n), xyz;
+    std::vector<uint2> tab;
+    if (ctx->compact_ok) {
+        xyz.assign((size_t)ctx->cfg.batch * n, 0u);
+        tab.assign((size_t)ctx->cfg.batch * (rows + 1) * W, make_uint2(0u, 0u));
     }
+    std::vector<int> cnt(ctx->cfg.batch);
+    long long mx = 0, total = 0;
+    for (int b = 0; b < ctx->cfg.batch; ++b) {
+        uint32_t c = 0;
+        for (size_t r = 0; r < rows; ++r) {
+            for (int x = 0; x < nx; ++x) {
+                const long long k = (long long)r * nx + x;
+                uint2 *e = ctx->compact_ok ? &tab[((size_t)b * (rows + 1) + r) * W + (x >> 5)] : nullptr;
+                if (e && (x & 31) == 0) e->x = c;
+                if (type_of((size_t)b * n + k) == 1u) continue;
+                lst[(size_t)b * n + c] = (uint32_t)k;
+                if (e) {
+                    e->y |= 1u << (x & 31);
+                    xyz[(size_t)b * n + c] = (uint32_t)x | ((uint32_t)(r % ny) << 11) | ((uint32_t)(r / ny) << 22);
+                }
+                ++c;
+            }
+        }
+        if (ctx->compact_ok)
+            for (int w = 0; w < W; ++w) tab[((size_t)b * (rows + 1) + rows) * W + w].x = c;
+        cnt[b] = (int)c;
+        total += c;
+        if ((long long)c > mx) mx = c;
+    }
+    ctx->list_max = mx;
+    ctx->nonsolid = total;
     LBM_CUDA(cudaMemcpyAsync(ctx->list, lst.data(), lst.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "cell list");
     LBM_CUDA(cudaMemcpyAsync(ctx->list_count, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice,
                              ctx->stream),
              "cell list");
     LBM_CUDA(launch_psi_solid(ctx->link, ctx->psi, ctx->fp64(), ctx->g, ctx->cfg.batch, ctx->dpar, ctx->stream),
              "solid psi");
-    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "cell list");
     ctx->launches += 1;
-    ctx->list_max = mx;
+    if (ctx->compact_ok) {
+        // the compact arrays use the instance stride kmax = list_max
+        std::vector<uint32_t> xyzc((size_t)ctx->cfg.batch * mx);
+        for (int b = 0; b < ctx->cfg.batch; ++b)
+            std::memcpy(&xyzc[(size_t)b * mx], &xyz[(size_t)b * n], (size_t)cnt[b] * 4);
+        LBM_CUDA(cudaMemcpyAsync(ctx->cxyz, xyzc.data(), xyzc.size() * 4, cudaMemcpyHostToDevice, ctx->stream),
+                 "compact coordinates");
+        LBM_CUDA(cudaMemcpyAsync(ctx->rowtab, tab.data(), tab.size() * sizeof(uint2), cudaMemcpyHostToDevice,
+                                 ctx->stream),
+                 "row table");
+        LBM_CUDA(launch_compact_links(ctx->list, ctx->list_count, ctx->link, ctx->clink, ctx->g, ctx->cfg.batch,
+                                      (uint32_t)mx, ctx->stream),
+                 "compact links");
+        ctx->launches += 1;
+    }
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "cell list");
+    return LBM_OK;
+}
+
+// Bring f and the reference densities of the current state into `want`
+// (0 dense, 1 compact), through the other buffer.  Leaving the compact layout
+// also restores psi of the SOLID cells, which compact updates overwrite.
+lbm_status ensure_layout(lbm_ctx *ctx, int want) {
+    if (ctx->layout == want) return LBM_OK;
+    LBM_CUDA(launch_layout(ctx->cfg.precision, want == 1, ctx->f[ctx->cur], ctx->f[ctx->cur ^ 1], ctx->ref[ctx->cur],
+                           ctx->ref[ctx->cur ^ 1], ctx->list, ctx->list_count, ctx->g, ctx->cfg.batch,
+                           (uint32_t)ctx->list_max, ctx->stream),
+             "layout conversion");
+    ctx->launches += 1;
+    if (want == 0) {
+        LBM_CUDA(launch_psi_solid(ctx->link, ctx->psi, ctx->fp64(), ctx->g, ctx->cfg.batch, ctx->dpar, ctx->stream),
+                 "solid psi");
+        ctx->launches += 1;
+    }
+    ctx->cur ^= 1;
+    ctx->layout = want;
     return LBM_OK;
 }
 
@@ -254,6 +324,11 @@ StepArgs step_args(lbm_ctx *ctx, int write_macro) {
     a.list = ctx->list;
     a.list_count = ctx->list_count;
     a.list_max = ctx->list_max;
+    a.cxyz = ctx->cxyz;
+    a.clink = ctx->clink;
+    a.rowtab = ctx->rowtab;
+    a.words = ctx->words;
+    a.kmax = (uint32_t)ctx->list_max;
     a.stream = ctx->stream;
     return a;
 }
@@ -335,6 +410,19 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
     }
     ctx->link = (uint32_t *)ctx->dalloc(cells * 4);
     ctx->list = (uint32_t *)ctx->dalloc(cells * 4);
+    ctx->compact_ok = cfg->nx <= kCompactMaxX && cfg->ny <= kCompactMaxY && cfg->nz <= kCompactMaxZ;
+    if (ctx->compact_ok) {
+        ctx->words = (cfg->nx + 31) / 32;
+        ctx->cxyz = (uint32_t *)ctx->dalloc(cells * 4);
+        ctx->clink = (uint32_t *)ctx->dalloc(cells * 4);
+        ctx->rowtab = (uint2 *)ctx->dalloc((size_t)cfg->batch * ((size_t)cfg->ny * cfg->nz + 1) * ctx->words *
+                                           sizeof(uint2));
+        if (!ctx->cxyz || !ctx->clink || !ctx->rowtab) {
+            g_last_error = "lbm_create: device allocation failed";
+            lbm_destroy(ctx);
+            return LBM_ERR_OOM;
+        }
+    }
     ctx->list_count = (int *)ctx->dalloc((size_t)cfg->batch * sizeof(int));
     if (!ctx->list || !ctx->list_count) {
         g_last_error = "lbm_create: device allocation failed";
@@ -379,10 +467,12 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
 
 lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
     if (!ctx) return LBM_ERR_ARG;
-    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_CLUSTER)
+    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_COMPACT)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: unknown strategy");
     if (kernel == LBM_KERNEL_CLUSTER && ctx->g.n > kClusterMaxCells)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: CLUSTER needs at most 65536 cells per instance");
+    if (kernel == LBM_KERNEL_COMPACT && !ctx->compact_ok)
+        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: COMPACT needs nx <= 2048, ny <= 2048, nz <= 1024");
     ctx->kernel = kernel;
     return LBM_OK;
 }
@@ -427,7 +517,7 @@ lbm_status lbm_timing_end(lbm_ctx *ctx, double *ms, long long *launches) {
         const auto &t = ctx->timed[k];
         cudaEvent_t *ev = &ctx->tev[t.first];
         float a = 0.f, b = 0.f;
-        if (t.kind == LBM_KERNEL_TWO_PASS) {
+        if (t.kind == LBM_KERNEL_TWO_PASS || t.kind == LBM_KERNEL_COMPACT) {
             e = cudaEventElapsedTime(&a, ev[0], ev[1]);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
             ms[LBM_PART_PSI] += a;
@@ -480,6 +570,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *cell_type) {
     if (s != LBM_OK) return s;
     ctx->has_geometry = true;
     ctx->has_fields = false;
+    ctx->layout = 0;
     return LBM_OK;
 }
 
@@ -515,6 +606,7 @@ lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho1, const double *rho2, 
     ctx->dfree(d);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_set_fields");
     ctx->launches += 1;
+    ctx->layout = 0;
     ctx->has_fields = true;
     ctx->since_snap = 0;
     return LBM_OK;
@@ -526,6 +618,10 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_step: call lbm_set_fields first");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
     const lbm_kernel k = resolve_kernel(ctx, n);
+    if (n > 0) {
+        const lbm_status ls = ensure_layout(ctx, k == LBM_KERNEL_COMPACT ? 1 : 0);
+        if (ls != LBM_OK) return ls;
+    }
     if (k == LBM_KERNEL_CLUSTER) {
         if (n > 0) {
             StepArgs a = step_args(ctx, 1);
@@ -544,8 +640,9 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     if (fused) default_tiling(ctx, tile, zchunk);
     for (int s = 0; s < n; ++s) {
         StepArgs a = step_args(ctx, s == n - 1);
-        a.ev = ctx->events_for(fused ? LBM_KERNEL_FUSED : LBM_KERNEL_TWO_PASS);
-        cudaError_t e = fused ? launch_fused(a, tile, zchunk) : launch_two_pass(a);
+        a.ev = ctx->events_for(k);
+        cudaError_t e = fused ? launch_fused(a, tile, zchunk)
+                              : (k == LBM_KERNEL_COMPACT ? launch_compact(a) : launch_two_pass(a));
         if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_step launch");
         ctx->launches += fused ? 1 : 2;
         ctx->cur ^= 1;
@@ -616,6 +713,7 @@ lbm_status lbm_get_distributions(lbm_ctx *ctx, double *f) {
     if (!ctx || !f) return ctx ? ctx->fail(LBM_ERR_ARG, "lbm_get_distributions: null argument") : LBM_ERR_ARG;
     if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_get_distributions: no fields yet");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    if (ensure_layout(ctx, 0) != LBM_OK) return LBM_ERR_CUDA;
     const size_t vals = ctx->cells() * 2 * 19;
     double *d = (double *)ctx->dalloc(vals * 8);
     if (!d) return ctx->fail(LBM_ERR_OOM, "lbm_get_distributions: device allocation failed");
@@ -633,6 +731,7 @@ lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *f) {
     if (!ctx || !f) return ctx ? ctx->fail(LBM_ERR_ARG, "lbm_set_distributions: null argument") : LBM_ERR_ARG;
     if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_set_distributions: call lbm_set_fields first");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    if (ensure_layout(ctx, 0) != LBM_OK) return LBM_ERR_CUDA;
     const size_t vals = ctx->cells() * 2 * 19;
     double *d = (double *)ctx->dalloc(vals * 8);
     if (!d) return ctx->fail(LBM_ERR_OOM, "lbm_set_distributions: device allocation failed");
@@ -651,7 +750,7 @@ namespace {
 struct StateHeader {
     char magic[8];
     uint32_t version;
-    uint32_t pad;
+    uint32_t layout;  // 0 dense, 1 compact
     lbm_config cfg;
     long long step, since_snap;
     uint64_t f_bytes, ref_bytes, link_bytes, macro_bytes, usnap_bytes;
@@ -665,6 +764,7 @@ lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t *bytes) {
     std::memcpy(h.magic, "LBMSTATE", 8);
     h.version = 2;
     h.cfg = ctx->cfg;
+    h.layout = (uint32_t)ctx->layout;
     h.step = ctx->step;
     h.since_snap = ctx->since_snap;
     h.f_bytes = ctx->f_bytes();
@@ -714,6 +814,8 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes) {
         h.macro_bytes != cells * 5 * ctx->tbytes() || h.usnap_bytes != cells * 3 * ctx->tbytes() ||
         bytes < sizeof(h) + h.f_bytes + h.ref_bytes + h.link_bytes + h.macro_bytes + h.usnap_bytes)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_state: size mismatch");
+    if (h.layout > 1 || (h.layout == 1 && !ctx->compact_ok))
+        return ctx->fail(LBM_ERR_ARG, "lbm_set_state: layout mismatch");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
     const char *p = (const char *)buf + sizeof(h);
     LBM_CUDA(cudaMemcpyAsync(ctx->f[ctx->cur], p, h.f_bytes, cudaMemcpyHostToDevice, ctx->stream), "set_state f");
@@ -740,6 +842,7 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes) {
     }
     ctx->step = h.step;
     ctx->since_snap = h.since_snap;
+    ctx->layout = (int)h.layout;
     ctx->has_geometry = ctx->has_fields = true;
     return LBM_OK;
 }
@@ -801,7 +904,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
         ctx->dfree(smac);
         return ctx->fail(LBM_ERR_OOM, "lbm_autotune: no room to save the state");
     }
-    const int cur0 = ctx->cur;
+    const int cur0 = ctx->cur, layout0 = ctx->layout;
     const long long step0 = ctx->step, snap0 = ctx->since_snap, launches0 = ctx->launches;
     const lbm_kernel k_save = ctx->kernel;
     const int t_save = ctx->tile, z_save = ctx->zchunk;
@@ -813,6 +916,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     };
     std::vector<Cand> cands;
     cands.push_back({LBM_KERNEL_TWO_PASS, -1, -1});
+    if (ctx->compact_ok) cands.push_back({LBM_KERNEL_COMPACT, -1, -1});
     if (ctx->g.n <= kClusterMaxCells) cands.push_back({LBM_KERNEL_CLUSTER, -1, -1});
     for (int t = 0; t < fused_tile_count(); ++t) {
         cands.push_back({LBM_KERNEL_FUSED, t, -1});
@@ -844,8 +948,12 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
             best = ms;
             pick = c;
         }
-        // restore the saved state for the next candidate
+        // restore the saved state for the next candidate (a compact trial
+        // overwrote psi of the SOLID cells, which the dense kernels read)
         ctx->cur = cur0;
+        if (ctx->layout != layout0 && layout0 == 0 && e == cudaSuccess)
+            e = launch_psi_solid(ctx->link, ctx->psi, ctx->fp64(), ctx->g, ctx->cfg.batch, ctx->dpar, ctx->stream);
+        ctx->layout = layout0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->f[cur0], sf, fb, cudaMemcpyDeviceToDevice, ctx->stream);
         if (e == cudaSuccess && rb)
             e = cudaMemcpyAsync(ctx->ref[cur0], sr, rb, cudaMemcpyDeviceToDevice, ctx->stream);
@@ -858,6 +966,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     ctx->dfree(sr);
     ctx->dfree(smac);
     ctx->cur = cur0;
+    ctx->layout = layout0;
     ctx->step = step0;
     ctx->since_snap = snap0;
     (void)launches0;
@@ -886,6 +995,11 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
     if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_run_to_steady: call lbm_set_fields first");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
     const int B = ctx->cfg.batch;
+    {
+        // convert the layout now: a conversion must not be captured into the graphs
+        const lbm_status ls = ensure_layout(ctx, resolve_kernel(ctx, check_every) == LBM_KERNEL_COMPACT ? 1 : 0);
+        if (ls != LBM_OK) return ls;
+    }
     // capture on a private stream ordered after the context's stream
     cudaStream_t cs = nullptr;
     LBM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "stream");

@@ -109,6 +109,53 @@ struct Nbr {
     __device__ __forceinline__ int dst(int i) const { return X[1 + cx(i)] + Y[1 + cy(i)] + Z[1 + cz(i)]; }
 };
 
+// Neighbours in the compact layout, where only the non-solid cells of an
+// instance are stored, in cell order: the compact index of a cell is the
+// number of non-solid cells before it.  Each row (y, z) of the instance is
+// described by 32-cell words {rank of the word's first cell, mask of its
+// non-solid cells} (tab[row][word]; one extra row at the end holds the total).
+// nb[j] is the compact index of x + c_j wherever that cell is not SOLID; at
+// SOLID neighbours it is meaningless and must not be dereferenced.
+struct CNbr {
+    uint32_t nb[kQ];
+    // linear offset of x - c_i / x + c_i within one plane of the compact layout
+    __device__ __forceinline__ uint32_t src(int i) const { return nb[opp(i)]; }
+    __device__ __forceinline__ uint32_t dst(int i) const { return nb[i]; }
+
+    // (x, y, z) with compact index k; tb = the instance's row table.
+    __device__ __forceinline__ void init(int x, int y, int z, uint32_t k, const uint2 *__restrict__ tb, int words,
+                                         const Grid &g) {
+        const int ys[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
+        const int zs[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
+        const bool first = x == 0, last = x == g.nx - 1;
+        const int w = x >> 5, xb = x & 31;
+        const uint32_t below = (1u << xb) - 1u;
+        // rank of the first cell of row r (r = rows: the instance's total)
+        auto row_rank = [&](int r) -> uint32_t { return __ldg(tb + (size_t)r * words).x; };
+        nb[0] = k;
+        // own row: neighbours along x are the adjacent compact indices unless x wraps
+        nb[1] = last ? row_rank(zs[1] * g.ny + ys[1]) : k + 1u;
+        nb[2] = first ? row_rank(zs[1] * g.ny + ys[1] + 1) - 1u : k - 1u;
+#pragma unroll
+        for (int j = 3; j < kQ; ++j) {
+            if (cx(j) != 0) continue;  // filled with the x = 0 member of its row below
+            const int r = zs[1 + cz(j)] * g.ny + ys[1 + cy(j)];
+            const uint2 e = __ldg(tb + (size_t)r * words + w);
+            const uint32_t at = e.x + __popc(e.y & below);  // rank of (x, row)
+            nb[j] = at;
+            // the +x and -x members of the same row (only the y or z face rows have them)
+#pragma unroll
+            for (int m = 7; m < kQ; ++m) {
+                if (cy(m) != cy(j) || cz(m) != cz(j) || cx(m) == 0) continue;
+                if (cx(m) > 0)
+                    nb[m] = last ? row_rank(r) : at + ((e.y >> xb) & 1u);
+                else
+                    nb[m] = (first ? row_rank(r + 1) : at) - 1u;
+            }
+        }
+    }
+};
+
 // Moments of the streamed distributions of one component (S1-S2).  In the
 // shifted storage formats they are summed over the stored deviations
 // d_i = f_i - w_i R (no cancellation against the rest equilibrium):
@@ -126,9 +173,9 @@ template <class T> struct Moments {
 // `rref` is the reference density R of the pulling cell (see Storage).
 // RO = true reads through the read-only data path (buffers not written by the
 // same launch); RO = false uses coherent loads (persistent kernels).
-template <class S, bool RO = true>
+template <class S, bool RO = true, class NB = Nbr>
 __device__ __forceinline__ Moments<typename Storage<S>::T>
-pull_moments(const S *__restrict__ fcomp, long long n, int self, const Nbr &nb, uint32_t links,
+pull_moments(const S *__restrict__ fcomp, long long n, int self, const NB &nb, uint32_t links,
              typename Storage<S>::T rref) {
     using T = typename Storage<S>::T;
     T v[kQ];  // stored values: deviations d_i in the shifted formats, f_i otherwise
@@ -162,9 +209,9 @@ pull_moments(const S *__restrict__ fcomp, long long n, int self, const Nbr &nb, 
 }
 
 // Density only (for the pseudo-potential pass), same summation order.
-template <class S, bool RO = true>
+template <class S, bool RO = true, class NB = Nbr>
 __device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restrict__ fcomp, long long n, int self,
-                                                              const Nbr &nb, uint32_t links,
+                                                              const NB &nb, uint32_t links,
                                                               typename Storage<S>::T rref) {
     using T = typename Storage<S>::T;
     T v[kQ];

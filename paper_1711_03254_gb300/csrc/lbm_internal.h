@@ -26,6 +26,13 @@ struct StepArgs {
     const uint32_t *list = nullptr;  // non-solid cells per instance [batch][n] (two-pass), or NULL
     const int *list_count = nullptr; // entries per instance (device)
     long long list_max = 0;          // largest entry count
+    // compact layout (LBM_KERNEL_COMPACT): arrays indexed by the compact index k
+    // (k-th non-solid cell of the instance), instance stride kmax
+    const uint32_t *cxyz = nullptr;  // packed coordinates x | y << 11 | z << 22
+    const uint32_t *clink = nullptr; // geometry words of the non-solid cells
+    const uint2 *rowtab = nullptr;   // [batch][rows + 1][words] {rank of the word's first cell, non-solid mask}
+    int words = 0;                   // 32-cell words per row
+    uint32_t kmax = 0;
     cudaStream_t stream;
     // when non-NULL: events recorded before the first kernel and after each
     // kernel of the launch (two-pass: 3 events, fused and cluster: 2)
@@ -81,5 +88,16 @@ cudaError_t launch_reduce(const ReduceArgs &a, int *launches);
 cudaError_t launch_f_convert(lbm_precision prec, const void *f, double *out, const double *in, void *fo,
                              const Ref *ref, const uint32_t *link, const Grid &g, int batch, cudaStream_t s);
 int reduce_blocks(long long n);
+
+// compact layout
+constexpr int kCompactMaxX = 2048, kCompactMaxY = 2048, kCompactMaxZ = 1024;
+cudaError_t launch_compact(const StepArgs &a);
+// geometry words of the listed cells: clink[b][k] = link[b][list[b][k]]
+cudaError_t launch_compact_links(const uint32_t *list, const int *count, const uint32_t *link, uint32_t *clink,
+                                 const Grid &g, int batch, uint32_t kmax, cudaStream_t s);
+// f and the reference densities between the dense and the compact layout
+cudaError_t launch_layout(lbm_precision prec, bool to_compact, const void *fin, void *fout, const Ref *rin, Ref *rout,
+                          const uint32_t *list, const int *count, const Grid &g, int batch, uint32_t kmax,
+                          cudaStream_t s);
 
 }  // namespace lbm

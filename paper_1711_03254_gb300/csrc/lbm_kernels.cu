@@ -303,6 +303,11 @@ __global__ void k_f_convert(const S *__restrict__ f, double *__restrict__ out, c
     if (k >= g.n) return;
     const int b = bc >> 1;
     const uint32_t word = link[(long long)b * g.n + k];
+    if (cell_type(word) == kSolid) {  // no distributions in SOLID cells
+        if (out)
+            for (int i = 0; i < kQ; ++i) out[((long long)bc * kQ + i) * g.n + k] = 0.0;
+        return;
+    }
     int x, y, z;
     cell_coords(k, g, x, y, z);
     Nbr nb;

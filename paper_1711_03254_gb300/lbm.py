@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
 LBM_FP64, LBM_FP32, LBM_FP32_F16S, LBM_FP32_BF16S = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP32_F16S, "bf16s": LBM_FP32_BF16S}
 LBM_KERNEL_AUTO, LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED, LBM_KERNEL_CLUSTER = 0, 1, 2, 3
-KERNELS = {"auto": 0, "two_pass": 1, "fused": 2, "cluster": 3}
+KERNELS = {"auto": 0, "two_pass": 1, "fused": 2, "cluster": 3, "compact": 4}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM", 4: "LBM_ERR_DIVERGED",
           5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 

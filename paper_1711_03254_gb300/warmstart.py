@@ -57,8 +57,10 @@ def case_inputs(c, S: int):
 
 
 def generate(cases, S: int = 64, steps: int = 3000, batch: int = 32, precision: str = "fp32"):
-    """Run the solver on every case; returns (inputs, targets, masks) arrays."""
-    X, Y, M = [], [], []
+    """Run the solver on every case; returns (inputs, targets, masks, kept case
+    indices).  Cases whose state is not finite, or whose velocity reaches the
+    sound speed, after `steps` updates are left out."""
+    X, Y, M, kept = [], [], [], []
     for k0 in range(0, len(cases), batch):
         cs = cases[k0:k0 + batch]
         geo = [case_geometry(c, S) for c in cs]
@@ -70,10 +72,14 @@ def generate(cases, S: int = 64, steps: int = 3000, batch: int = 32, precision: 
         r1, r2, u = sim.get_fields()
         sim.close()
         for j, c in enumerate(cs):
+            ok = all(np.isfinite(a[j]).all() for a in (r1, r2, u)) and float(np.abs(u[j]).max()) < 1 / math.sqrt(3)
+            if not ok:
+                continue
             X.append(surrogate.encode_inputs(geo[j][0], c["rho_s"], c["ratio"], c["incline"], 0.0, geo[j][2]))
             Y.append(surrogate.encode_targets(r1[j], r2[j], u[j]))
             M.append((geo[j][0] != W.SOLID).astype(np.uint8))
-    return np.stack(X), np.stack(Y), np.stack(M)
+            kept.append(k0 + j)
+    return np.stack(X), np.stack(Y), np.stack(M), kept
 
 
 def train(net, X, Y, M, iters: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50):
@@ -97,7 +103,10 @@ def train(net, X, Y, M, iters: int, lr: float = 1e-3, seed: int = 0, log_every: 
         a = lr * 0.5 * (1 + math.cos(math.pi * it / max(1, iters)))
         net.adam_step(lr=a)
         if it % log_every == 0 or it == iters - 1:
-            hist.append((it, float(loss.item())))
+            lv = float(loss.item())
+            hist.append((it, lv))
+            if not math.isfinite(lv):
+                raise FloatingPointError(f"training loss is not finite at iteration {it}")
     return hist
 
 
@@ -145,9 +154,10 @@ def experiment(n_train=512, n_test=8, S_train=64, S_test=128, gen_steps=3000, it
     plain and the learned initial fields.  Returns a summary dict."""
     import torch
     t0 = time.perf_counter()
-    X, Y, M = generate(sample_cases(n_train, seed_train), S=S_train, steps=gen_steps)
+    X, Y, M, kept = generate(sample_cases(n_train, seed_train), S=S_train, steps=gen_steps)
     t_gen = time.perf_counter() - t0
-    log(f"generated {len(X)} steady states at {S_train}^3 in {t_gen:.1f} s")
+    log(f"generated {len(X)} steady states at {S_train}^3 in {t_gen:.1f} s "
+        f"({n_train - len(kept)} of {n_train} cases left out: not finite or |u| >= c_s)")
     net = surrogate.UNet3D(batch, S_train, seed=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -172,7 +182,8 @@ def experiment(n_train=512, n_test=8, S_train=64, S_test=128, gen_steps=3000, it
                          warm_s=warm[1] + t_inf, warm_res=warm[2], infer_s=t_inf, max_density_diff=diff))
         log(f"case {len(rows)}: plain {plain[0]} updates {plain[1]:.2f} s | warm {warm[0]} updates "
             f"{warm[1] + t_inf:.2f} s (inference {t_inf:.3f} s) | max |d rho| {diff:.2e}")
-    return dict(train=dict(n=n_train, size=S_train, gen_steps=gen_steps, gen_s=t_gen, iters=iters, batch=batch,
+    return dict(train=dict(n=n_train, kept=len(kept), size=S_train, gen_steps=gen_steps, gen_s=t_gen, iters=iters,
+                           batch=batch,
                            train_s=t_train, tflops=flops / t_train / 1e12, loss=hist),
                 test=dict(n=n_test, size=S_test, tol=tol, check_every=check_every, max_steps=max_steps, rows=rows))
 

@@ -52,7 +52,7 @@ def _errs(g, o):
     return _rel(g[0], o[0]), _rel(g[1], o[1]), _rel(g[2], o[2])
 
 
-KERNELS = ["two_pass", "fused", "cluster"]
+KERNELS = ["two_pass", "fused", "cluster", "compact"]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -152,12 +152,14 @@ def test_reduced_precision_droplet(lbm, oracle_mod, precision, tol, kernel):
     assert _rel(g[0], o[0]) < tol and _rel(g[1], o[1]) < tol, e
 
 
+@pytest.mark.parametrize("kernel", ["two_pass", "compact"])
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 2e-3), ("bf16s", 1e-2)])
-def test_reduced_precision_walls(lbm, oracle_mod, precision, tol):
+def test_reduced_precision_walls(lbm, oracle_mod, precision, tol, kernel):
     shape = (13, 7, 9)
     t, r1, r2, u = _random_geometry(shape, 0.2, 31, lo=0.3, hi=0.7)
     p = [dict(tau=(0.7, 1.5), G=-1.8, rho_s=0.3, g=(1e-4, 0, 0))]
-    _, _, g, o = _pair(lbm, oracle_mod, shape, p, t[None], r1[None], r2[None], u[None], 20, precision=precision)
+    _, _, g, o = _pair(lbm, oracle_mod, shape, p, t[None], r1[None], r2[None], u[None], 20, precision=precision,
+                       kernel=kernel)
     e = _errs(g, o)
     assert _rel(g[0], o[0]) < tol and _rel(g[1], o[1]) < tol, e
 
@@ -191,18 +193,19 @@ def test_reductions_are_deterministic(lbm):
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_checkpoint_roundtrip_bitwise(lbm):
+@pytest.mark.parametrize("kernel", ["auto", "compact"])
+def test_checkpoint_roundtrip_bitwise(lbm, kernel):
     t, r1, r2, u = _random_geometry((10, 9, 8), 0.1, 51, lo=0.3, hi=0.7)
     p = [dict(tau=(0.9, 1.4), G=-2.0, rho_s=0.1, g=(1e-5, 0, 0))]
     for prec in ("fp64", "fp16s"):
-        a = lbm.Sim(10, 9, 8, p, precision=prec)
+        a = lbm.Sim(10, 9, 8, p, precision=prec, kernel=kernel)
         a.set_geometry(t[None])
         a.set_fields(r1[None], r2[None], u[None])
         a.step(10)
         st = a.get_state()
         a.step(10)
         fa = a.get_fields()
-        b = lbm.Sim(10, 9, 8, p, precision=prec)
+        b = lbm.Sim(10, 9, 8, p, precision=prec, kernel=kernel)
         b.set_state(st)
         b.step(10)
         fb = b.get_fields()
@@ -237,12 +240,13 @@ def test_divergence_is_flagged(lbm):
     sim.get_fields()
 
 
-def test_distributions_roundtrip(lbm, oracle_mod):
+@pytest.mark.parametrize("kernel", ["auto", "compact"])
+def test_distributions_roundtrip(lbm, oracle_mod, kernel):
     """FP64 distributions exported by the library step identically in the oracle."""
     shape = (9, 8, 7)
     t, r1, r2, u = _random_geometry(shape, 0.1, 61, lo=0.3, hi=0.7)
     p = [dict(tau=(0.8, 1.1), G=-2.0, rho_s=0.2)]
-    sim = lbm.Sim(*shape, p)
+    sim = lbm.Sim(*shape, p, kernel=kernel)
     sim.set_geometry(t[None])
     sim.set_fields(r1[None], r2[None], u[None])
     sim.step(7)
@@ -257,6 +261,35 @@ def test_distributions_roundtrip(lbm, oracle_mod):
     sim.set_f(f)
     sim.step(1)
     assert max(_errs(sim.get_fields(), ref.get_fields())) < 1e-13
+    assert np.all(f[:, :, :, t == W.SOLID] == 0.0)  # SOLID cells carry no distributions
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s", "bf16s"])
+def test_layouts_give_identical_bits(lbm, precision):
+    """The compact and the dense layout run the same arithmetic: a run that
+    switches strategy every few updates (converting the layout each time)
+    ends bitwise equal to a dense-only run, fields and distributions."""
+    shape = (37, 21, 11)
+    t, r1, r2, u = _random_geometry(shape, 0.3, 71, lo=0.3, hi=0.7)
+    p = [dict(tau=(0.8, 1.3), G=-1.9, rho_s=-0.2, g=(2e-5, 1e-5, 0)),
+         dict(tau=(1.1, 0.6), G=-2.1, rho_s=0.3, g=(0, 0, 3e-5))]
+    t2 = np.stack([t, np.roll(t, 5, axis=2)])
+    r1s, r2s, us = np.stack([r1, np.roll(r1, 5, axis=2)]), np.stack([r2, np.roll(r2, 5, axis=2)]), np.stack([u, u])
+    dense = lbm.Sim(*shape, p, precision=precision, kernel="two_pass")
+    mixed = lbm.Sim(*shape, p, precision=precision, kernel="compact")
+    for s_ in (dense, mixed):
+        s_.set_geometry(t2)
+        s_.set_fields(r1s, r2s, us)
+    for rnd in range(4):
+        dense.step(3)
+        lbm.lbm_set_kernel(mixed.ctx, "compact" if rnd % 2 == 0 else "two_pass")
+        mixed.step(3)
+    lbm.lbm_set_kernel(mixed.ctx, "compact")
+    mixed.step(2)
+    dense.step(2)
+    for x, y in zip(dense.get_fields(), mixed.get_fields()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(dense.get_f(), mixed.get_f())
 
 
 # ------------------------------------------------------------------ batched persistent launch (sweeps)
@@ -353,3 +386,18 @@ def test_batched_sweep_analytic_profile(lbm, precision):
         tol = 0.02 if layout == "121" else 0.06
         err = np.abs(ux - ref).max() / np.abs(ref).max()
         assert np.isfinite(err) and err < tol, (k, layout, nu1, nu2, err)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp16s", 1e-3)])
+def test_benchmark_workload_full_size(lbm, oracle_mod, precision, tol):
+    """The benchmark's own configuration: 256^3 packed spheres, AUTO kernel
+    (compact layout), every cell against the oracle after 3 updates."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    t, r1, r2, u = bench.workload(256, "spheres")
+    _, _, g, o = _pair(lbm, oracle_mod, (256, 256, 256), [bench.PARAMS], t[None], r1[None], r2[None], u[None], 3,
+                       precision=precision, wall_model=2)
+    e = _errs(g, o)
+    assert max(e) < tol, e

@@ -99,7 +99,7 @@ def test_per_kernel_timing(lbm):
     positive and no larger than the wall time of the steps, results unchanged."""
     import torch
     for kernel, parts in (("two_pass", {"psi": 6, "collide": 6}), ("fused", {"fused": 6}),
-                          ("cluster", {"cluster": 1})):
+                          ("cluster", {"cluster": 1}), ("compact", {"psi": 6, "collide": 6})):
         a = _sim(lbm, precision="fp32", kernel=kernel)
         b = _sim(lbm, precision="fp32", kernel=kernel)
         torch.cuda.synchronize()
