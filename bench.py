@@ -280,7 +280,9 @@ def main():
     # the dominant kernel of the step: largest summed event time
     part = max(timing, key=lambda k: timing[k][0])
     part_ms, part_launches = timing[part]
-    kernel_name = {"psi": "k_psi", "collide": "k_collide", "fused": "k_fused", "cluster": "k_cluster"}[part]
+    strategy = lbm.lbm_resolved_kernel(sim.ctx, args.steps)
+    suffix = "_c" if strategy == "compact" else ""
+    kernel_name = {"psi": "k_psi", "collide": "k_collide", "fused": "k_fused", "cluster": "k_cluster"}[part] + suffix
     per_cell = alg_bytes_per_cell(part, args.precision)
     updates_per_launch = args.steps if part == "cluster" else 1
     bytes_per_launch = per_cell * fluid * updates_per_launch
@@ -334,7 +336,8 @@ def main():
                                         f"nu {NU[0]}/{NU[1]} (ratio 100), G={G}, g=1e-6, wall model 2"
                                         if args.workload == "spheres" else
                                         f"periodic droplet {n}^3, R={n // 8}, tau 1/1, G={G}, no walls"),
-                           "storage": args.precision, "kernel": args.kernel, "fluid_cells": fluid,
+                           "storage": args.precision, "kernel": args.kernel, "strategy": strategy,
+                           "fluid_cells": fluid,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "mass_drift": mass_drift}

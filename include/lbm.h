@@ -174,6 +174,11 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
  * gather of f, on the context's stream). */
 lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel);
 
+/* The strategy lbm_step(ctx, n) would run now (AUTO resolved; it depends on
+ * the geometry, so call it after lbm_set_geometry).  Returns -1 for a NULL
+ * context. */
+int lbm_resolved_kernel(const lbm_ctx *ctx, int n);
+
 /* Tiling of the fused kernel: tile 0 = 32x8, 1 = 32x4, 2 = 64x4, 3 = 32x16
  * cells per thread block, each marching zchunk planes; -1 selects the
  * built-in choice.  Errors: LBM_ERR_ARG (out of range). */

@@ -479,6 +479,8 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
 
 long long lbm_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+int lbm_resolved_kernel(const lbm_ctx *ctx, int n) { return ctx ? (int)resolve_kernel(ctx, n) : -1; }
+
 lbm_status lbm_timing_begin(lbm_ctx *ctx, int max_launches) {
     if (!ctx) return LBM_ERR_ARG;
     if (max_launches < 1 || max_launches > 65536)

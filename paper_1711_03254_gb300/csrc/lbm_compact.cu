@@ -2,22 +2,75 @@
 //
 // Only the non-solid cells of an instance are stored, in cell order (x
 // fastest); the compact index k of a cell is the number of non-solid cells
-// before it.  Per instance b (stride kmax = the largest non-solid count):
-//   f[b][alpha][i][k], ref[b][alpha][k], psi[b][alpha][k],
+// before it.  The two components of a value are stored side by side, so one
+// 4-byte (FP16/BF16), 8-byte (FP32) or 16-byte (FP64) access moves both.
+// Per instance b (stride kmax = the largest non-solid count):
+//   f[b][i][k][alpha], ref[b][k][alpha], psi[b][k][alpha],
 //   cxyz[b][k] (packed coordinates), clink[b][k] (geometry word),
 //   rowtab[b][row][word] = {rank of the word's first cell, non-solid mask}.
 // On porous geometries the dense layout wastes most of each 32-byte sector on
 // SOLID cells and writes sectors only in part; here a warp's 32 cells read and
-// write contiguous runs of every plane.
+// write contiguous runs of every plane, and the component pairs halve the
+// load, store and address instructions.
 //
 //   k_psi_c      S1-S3 as k_psi: pull, sum to rho_alpha, store psi.
 //   k_collide_c  S1-S7 as k_collide.
-// The arithmetic is the same device code as the dense kernels (pull_moments,
-// sc_forces, relax, collide_store), so both layouts give identical bits.
+// The arithmetic is the same device code as the dense kernels (moments_of,
+// sc_forces, relax, collide_prep/collide_pair), in the same order, so both
+// layouts give identical bits.
 #include "lbm_internal.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
+
+// Both components of one stored value.
+template <class S> struct Pair;
+template <> struct Pair<double> {
+    using P = double2;
+    __device__ static __forceinline__ void load(const P *p, double &a, double &b) {
+        const P v = __ldg(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static __forceinline__ void store(P *p, double a, double b, double, double) { *p = make_double2(a, b); }
+};
+template <> struct Pair<float> {
+    using P = float2;
+    __device__ static __forceinline__ void load(const P *p, float &a, float &b) {
+        const P v = __ldg(p);
+        a = v.x + 0.f;  // as Storage<float>::load with a zero shift
+        b = v.y + 0.f;
+    }
+    __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
+        *p = make_float2(a - sa, b - sb);
+    }
+};
+template <> struct Pair<__half> {
+    using P = __half2;
+    __device__ static __forceinline__ void load(const P *p, float &a, float &b) {
+        const float2 v = __half22float2(__ldg(p));
+        a = v.x + 0.f;
+        b = v.y + 0.f;
+    }
+    __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
+        *p = __floats2half2_rn(a - sa, b - sb);
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    using P = __nv_bfloat162;
+    __device__ static __forceinline__ void load(const P *p, float &a, float &b) {
+        const float2 v = __bfloat1622float2(__ldg(p));
+        a = v.x + 0.f;
+        b = v.y + 0.f;
+    }
+    __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
+        *p = __floats2bfloat162_rn(a - sa, b - sb);
+    }
+};
+
+template <class T> struct Vec2;
+template <> struct Vec2<double> { using V = double2; };
+template <> struct Vec2<float> { using V = float2; };
 
 struct CompactCell {
     int x, y, z;
@@ -51,30 +104,53 @@ __device__ __forceinline__ bool outlet_source(const StepArgs &a, int b, const Co
     return true;
 }
 
+// Pull the 19 stored pairs of the cell with compact index sk (neighbours nb,
+// geometry word sw) into v0, v1 (bounce-back from SOLID neighbours).
 template <class S>
-__global__ void __launch_bounds__(256, 4) k_psi_c(StepArgs a) {
+__device__ __forceinline__ void pull_pairs(const typename Pair<S>::P *__restrict__ f, uint32_t n, uint32_t sk,
+                                           const CNbr &nb, uint32_t sw, typename Storage<S>::T (&v0)[kQ],
+                                           typename Storage<S>::T (&v1)[kQ]) {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const bool bb = (sw >> opp(i)) & 1u;
+        const uint32_t idx = bb ? (uint32_t)opp(i) * n + sk : (uint32_t)i * n + nb.src(i);
+        Pair<S>::load(f + idx, v0[i], v1[i]);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void ref_pair(const StepArgs &a, int b, uint32_t sk, typename Storage<S>::T &r0,
+                                         typename Storage<S>::T &r1) {
+    r0 = r1 = typename Storage<S>::T(0);
+    if constexpr (Storage<S>::shifted) {
+        const __half2 r = __ldg((const __half2 *)a.ref_in + (size_t)b * a.kmax + sk);
+        r0 = __low2float(r);
+        r1 = __high2float(r);
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(256, 3) k_psi_c(StepArgs a) {
     using T = typename Storage<S>::T;
+    using V = typename Vec2<T>::V;
     const int b = blockIdx.y;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (uint32_t)__ldg(a.list_count + b)) return;
     const CompactCell c = compact_cell(a, b, k);
     const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
-    T *psi = (T *)a.psi + (size_t)b * 2 * a.kmax;
+    V *psi = (V *)a.psi + (size_t)b * a.kmax;
     T p0, p1;
     if (cell_type(c.word) == kInlet) {
         p0 = p.rho_in[0];
         p1 = p.rho_in[1];
     } else {
-        const S *fb = (const S *)a.f_in + (size_t)b * 2 * kQ * a.kmax;
-        const size_t rb = (size_t)b * 2 * a.kmax;
+        const typename Pair<S>::P *f = (const typename Pair<S>::P *)a.f_in + (size_t)b * kQ * a.kmax;
         auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-            T r0 = T(0), r1 = T(0);
-            if constexpr (Storage<S>::shifted) {
-                r0 = (T)__half2float(a.ref_in[rb + sk]);
-                r1 = (T)__half2float(a.ref_in[rb + a.kmax + sk]);
-            }
-            p0 = pull_density<S, true, CNbr>(fb, a.kmax, (int)sk, nb, sw, r0);
-            p1 = pull_density<S, true, CNbr>(fb + kQ * (size_t)a.kmax, a.kmax, (int)sk, nb, sw, r1);
+            T v0[kQ], v1[kQ], r0, r1;
+            pull_pairs<S>(f, a.kmax, sk, nb, sw, v0, v1);
+            ref_pair<S>(a, b, sk, r0, r1);
+            p0 = density_of<T, Storage<S>::shifted>(v0, r0);
+            p1 = density_of<T, Storage<S>::shifted>(v1, r1);
         };
         CNbr own;
         own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
@@ -88,25 +164,27 @@ __global__ void __launch_bounds__(256, 4) k_psi_c(StepArgs a) {
             pull(own, k, c.word);
         }
     }
-    psi[k] = p0;
-    psi[a.kmax + k] = p1;
+    V out;
+    out.x = p0;
+    out.y = p1;
+    psi[k] = out;
 }
 
 template <class S, int EQ>
 __global__ void __launch_bounds__(256, 2) k_collide_c(StepArgs a) {
     using T = typename Storage<S>::T;
+    using V = typename Vec2<T>::V;
+    using P = typename Pair<S>::P;
     const int b = blockIdx.y;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (uint32_t)__ldg(a.list_count + b)) return;
     const CompactCell c = compact_cell(a, b, k);
     const uint32_t word = c.word;
     const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
-    const size_t n = a.kmax;
-    const size_t fofs = (size_t)b * 2 * kQ * n;
-    const size_t rb = (size_t)b * 2 * n;
-    S *fo = (S *)a.f_out;
-    const T *psi0 = (const T *)a.psi + rb;
-    const T *psi1 = psi0 + n;
+    const uint32_t n = a.kmax;
+    P *fo = (P *)a.f_out + (size_t)b * kQ * n;
+    const V *psi = (const V *)a.psi + (size_t)b * n;
+    __half2 *rout = (__half2 *)a.ref_out + (size_t)b * n;
     const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
     T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
     CNbr own;
@@ -118,20 +196,23 @@ __global__ void __launch_bounds__(256, 2) k_collide_c(StepArgs a) {
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
             const uint32_t j = ((word >> i) & 1u) ? k : own.dst(i);
-            q0[i] = __ldg(psi0 + j);
-            q1[i] = __ldg(psi1 + j);
+            const V q = __ldg(psi + j);
+            q0[i] = q.x;
+            q1[i] = q.y;
         }
     };
     if (cell_type(word) == kInlet) {
         load_psi();
-        auto s0 = [&](int i) -> T { return ref_value((i == 0 || ((word >> i) & 1u)) ? p.rho_in[0] : q0[i]); };
-        auto s1 = [&](int i) -> T { return ref_value((i == 0 || ((word >> i) & 1u)) ? p.rho_in[1] : q1[i]); };
-        store_equilibrium<S, EQ>(fo + fofs, n, (int)k, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], s0);
-        store_equilibrium<S, EQ>(fo + fofs + kQ * n, n, (int)k, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], s1);
-        if constexpr (Storage<S>::shifted) {
-            a.ref_out[rb + k] = __float2half_rn((float)p.rho_in[0]);
-            a.ref_out[rb + n + k] = __float2half_rn((float)p.rho_in[1]);
+        const T uu = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const bool self_ref = i == 0 || ((word >> i) & 1u);
+            const T s0 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[0] : q0[i]) : T(0);
+            const T s1 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[1] : q1[i]) : T(0);
+            Pair<S>::store(fo + (size_t)i * n + k, feq_dir<T, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
+                           feq_dir<T, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu), s0, s1);
         }
+        if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)p.rho_in[0], (float)p.rho_in[1]);
         if (a.write_macro) {
             mac[cell] = p.rho_in[0];
             mac[a.g.n + cell] = p.rho_in[1];
@@ -141,16 +222,14 @@ __global__ void __launch_bounds__(256, 2) k_collide_c(StepArgs a) {
         }
         return;
     }
-    const S *f = (const S *)a.f_in + fofs;
+    const P *f = (const P *)a.f_in + (size_t)b * kQ * n;
     Moments<T> m0, m1;
     auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-        T r0 = T(0), r1 = T(0);
-        if constexpr (Storage<S>::shifted) {
-            r0 = (T)__half2float(a.ref_in[rb + sk]);
-            r1 = (T)__half2float(a.ref_in[rb + n + sk]);
-        }
-        m0 = pull_moments<S, true, CNbr>(f, n, (int)sk, nb, sw, r0);
-        m1 = pull_moments<S, true, CNbr>(f + kQ * n, n, (int)sk, nb, sw, r1);
+        T v0[kQ], v1[kQ], r0, r1;
+        pull_pairs<S>(f, n, sk, nb, sw, v0, v1);
+        ref_pair<S>(a, b, sk, r0, r1);
+        m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
+        m1 = moments_of<T, Storage<S>::shifted>(v1, r1);
     };
     {
         int xu;
@@ -170,16 +249,34 @@ __global__ void __launch_bounds__(256, 2) k_collide_c(StepArgs a) {
     };
     const Forces<T> F = sc_forces<T>(psi_at, word, m0.rho, m1.rho, p, a.wall_model);
     const Relax<T> R = relax<T>(m0, m1, F, p);
-    auto sig0 = [&](int i) -> T { return ref_value((i == 0 || ((word >> i) & 1u)) ? m0.rho : q0[i]); };
-    auto sig1 = [&](int i) -> T { return ref_value((i == 0 || ((word >> i) & 1u)) ? m1.rho : q1[i]); };
-    collide_store<S, EQ>(fo + fofs, n, (int)k, m0, R.ux, R.uy, R.uz, F.F[0][0], F.F[0][1], F.F[0][2], R.omega,
-                         R.fcoef, sig0);
-    collide_store<S, EQ>(fo + fofs + kQ * n, n, (int)k, m1, R.ux, R.uy, R.uz, F.F[1][0], F.F[1][1], F.F[1][2],
-                         R.omega, R.fcoef, sig1);
-    if constexpr (Storage<S>::shifted) {
-        a.ref_out[rb + k] = __float2half_rn((float)m0.rho);
-        a.ref_out[rb + n + k] = __float2half_rn((float)m1.rho);
+    // reference density of the cell each value streams into (own cell when the
+    // neighbour is SOLID and the value bounces back)
+    auto sig = [&](int i, T own_rho, const T (&q)[kQ]) -> T {
+        return ref_value((i == 0 || ((word >> i) & 1u)) ? own_rho : q[i]);
+    };
+    const CollidePrep<T> c0 =
+        collide_prep<T, EQ>(m0, R.ux, R.uy, R.uz, F.F[0][0], F.F[0][1], F.F[0][2], R.omega, R.fcoef);
+    const CollidePrep<T> c1 =
+        collide_prep<T, EQ>(m1, R.ux, R.uy, R.uz, F.F[1][0], F.F[1][1], F.F[1][2], R.omega, R.fcoef);
+    {
+        const T w = wgt<T>(0);
+        Pair<S>::store(fo + k, collide_rest<T, EQ>(c0), collide_rest<T, EQ>(c1),
+                       Storage<S>::shifted ? w * sig(0, m0.rho, q0) : T(0),
+                       Storage<S>::shifted ? w * sig(0, m1.rho, q1) : T(0));
     }
+#pragma unroll
+    for (int i = 1; i < kQ; i += 2) {
+        T a_i, a_o, b_i, b_o;
+        collide_pair<T, EQ>(c0, i, a_i, a_o);
+        collide_pair<T, EQ>(c1, i, b_i, b_o);
+        const T w = wgt<T>(i);
+        Pair<S>::store(fo + (size_t)i * n + k, a_i, b_i, Storage<S>::shifted ? w * sig(i, m0.rho, q0) : T(0),
+                       Storage<S>::shifted ? w * sig(i, m1.rho, q1) : T(0));
+        Pair<S>::store(fo + (size_t)(i + 1) * n + k, a_o, b_o,
+                       Storage<S>::shifted ? w * sig(i + 1, m0.rho, q0) : T(0),
+                       Storage<S>::shifted ? w * sig(i + 1, m1.rho, q1) : T(0));
+    }
+    if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)m0.rho, (float)m1.rho);
     if (a.write_macro) {
         mac[cell] = m0.rho;
         mac[a.g.n + cell] = m1.rho;
@@ -198,26 +295,27 @@ __global__ void k_compact_links(const uint32_t *__restrict__ list, const int *__
     clink[(size_t)b * kmax + k] = link[(size_t)b * n + list[(size_t)b * n + k]];
 }
 
-// one thread per (non-solid cell, instance x component); all 19 planes
+// one thread per (instance, component, non-solid cell); all 19 planes.
+// dense f[b][alpha][i][cell], ref[b][alpha][cell] <-> compact f[b][i][k][alpha], ref[b][k][alpha]
 template <class S>
 __global__ void k_layout(bool to_compact, const S *__restrict__ fin, S *__restrict__ fout, const Ref *__restrict__ rin,
                          Ref *__restrict__ rout, const uint32_t *__restrict__ list, const int *__restrict__ count,
                          long long n, uint32_t kmax) {
     const int bc = blockIdx.y;  // b * 2 + alpha
-    const int b = bc >> 1;
+    const int b = bc >> 1, al = bc & 1;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (uint32_t)count[b]) return;
     const size_t cell = list[(size_t)b * n + k];
-    const size_t ds = (size_t)n, cs = (size_t)kmax;
     for (int i = 0; i < kQ; ++i) {
-        const size_t d = ((size_t)bc * kQ + i) * ds + cell, c = ((size_t)bc * kQ + i) * cs + k;
+        const size_t d = ((size_t)bc * kQ + i) * (size_t)n + cell;
+        const size_t c = (((size_t)b * kQ + i) * kmax + k) * 2 + al;
         if (to_compact)
             fout[c] = fin[d];
         else
             fout[d] = fin[c];
     }
     if (rin) {
-        const size_t d = (size_t)bc * n + cell, c = (size_t)bc * kmax + k;
+        const size_t d = (size_t)bc * n + cell, c = ((size_t)b * kmax + k) * 2 + al;
         if (to_compact)
             rout[c] = rin[d];
         else

@@ -173,6 +173,39 @@ template <class T> struct Moments {
 // `rref` is the reference density R of the pulling cell (see Storage).
 // RO = true reads through the read-only data path (buffers not written by the
 // same launch); RO = false uses coherent loads (persistent kernels).
+// Moments of the 19 stored values v of one component (R = rref in the shifted
+// formats, see Moments).
+template <class T, bool SHIFTED>
+__device__ __forceinline__ Moments<T> moments_of(const T (&v)[kQ], T rref) {
+    Moments<T> m;
+    T r = v[0];
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) r += v[i];
+    m.rd = r;
+    m.rho = SHIFTED ? rref + r : r;
+    m.jx = (v[1] - v[2]) + (v[7] - v[8]) + (v[9] - v[10]) + (v[11] - v[12]) + (v[13] - v[14]);
+    m.jy = (v[3] - v[4]) + (v[7] - v[8]) + (v[10] - v[9]) + (v[15] - v[16]) + (v[17] - v[18]);
+    m.jz = (v[5] - v[6]) + (v[11] - v[12]) + (v[14] - v[13]) + (v[15] - v[16]) + (v[18] - v[17]);
+    const T e_xy = (v[7] + v[8]) + (v[9] + v[10]);
+    const T e_xz = (v[11] + v[12]) + (v[13] + v[14]);
+    const T e_yz = (v[15] + v[16]) + (v[17] + v[18]);
+    m.pxx = (v[1] + v[2]) + e_xy + e_xz;
+    m.pyy = (v[3] + v[4]) + e_xy + e_yz;
+    m.pzz = (v[5] + v[6]) + e_xz + e_yz;
+    m.pxy = (v[7] + v[8]) - (v[9] + v[10]);
+    m.pxz = (v[11] + v[12]) - (v[13] + v[14]);
+    m.pyz = (v[15] + v[16]) - (v[17] + v[18]);
+    return m;
+}
+
+// Density of the 19 stored values v (same summation order as moments_of).
+template <class T, bool SHIFTED> __device__ __forceinline__ T density_of(const T (&v)[kQ], T rref) {
+    T r = v[0];
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) r += v[i];
+    return SHIFTED ? rref + r : r;
+}
+
 template <class S, bool RO = true, class NB = Nbr>
 __device__ __forceinline__ Moments<typename Storage<S>::T>
 pull_moments(const S *__restrict__ fcomp, long long n, int self, const NB &nb, uint32_t links,
@@ -187,25 +220,7 @@ pull_moments(const S *__restrict__ fcomp, long long n, int self, const NB &nb, u
                                 : (uint32_t)i * (uint32_t)n + (uint32_t)nb.src(i);
         v[i] = RO ? Storage<S>::load(fcomp + idx, T(0)) : Storage<S>::load_rw(fcomp + idx, T(0));
     }
-    Moments<T> m;
-    T r = v[0];
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) r += v[i];
-    m.rd = r;
-    m.rho = Storage<S>::shifted ? rref + r : r;
-    m.jx = (v[1] - v[2]) + (v[7] - v[8]) + (v[9] - v[10]) + (v[11] - v[12]) + (v[13] - v[14]);
-    m.jy = (v[3] - v[4]) + (v[7] - v[8]) + (v[10] - v[9]) + (v[15] - v[16]) + (v[17] - v[18]);
-    m.jz = (v[5] - v[6]) + (v[11] - v[12]) + (v[14] - v[13]) + (v[15] - v[16]) + (v[18] - v[17]);
-    const T e_xy = (v[7] + v[8]) + (v[9] + v[10]);
-    const T e_xz = (v[11] + v[12]) + (v[13] + v[14]);
-    const T e_yz = (v[15] + v[16]) + (v[17] + v[18]);
-    m.pxx = (v[1] + v[2]) + e_xy + e_xz;
-    m.pyy = (v[3] + v[4]) + e_xy + e_yz;
-    m.pzz = (v[5] + v[6]) + e_xz + e_yz;
-    m.pxy = (v[7] + v[8]) - (v[9] + v[10]);
-    m.pxz = (v[11] + v[12]) - (v[13] + v[14]);
-    m.pyz = (v[15] + v[16]) - (v[17] + v[18]);
-    return m;
+    return moments_of<T, Storage<S>::shifted>(v, rref);
 }
 
 // Density only (for the pseudo-potential pass), same summation order.
@@ -223,10 +238,7 @@ __device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restri
                                 : (uint32_t)i * (uint32_t)n + (uint32_t)nb.src(i);
         v[i] = RO ? Storage<S>::load(fcomp + idx, T(0)) : Storage<S>::load_rw(fcomp + idx, T(0));
     }
-    T r = v[0];
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) r += v[i];
-    return Storage<S>::shifted ? rref + r : r;
+    return density_of<T, Storage<S>::shifted>(v, rref);
 }
 
 // Equilibrium of Eq. 3 for direction i (EQ = 1 adds the quadratic terms).
@@ -247,6 +259,60 @@ __device__ __forceinline__ T feq_dir(int i, T rho, T ux, T uy, T uz, T uu) {
 // f*_i that are even in c (rest term of feq, the quadratic terms of Eq. 3 for
 // EQ = 1, H_i : A) are shared, the odd parts (the c.u terms of feq, the
 // first-order forcing) change sign, so each pair costs one evaluation.
+template <class T> struct CollidePrep {
+    T rho, ux, uy, uz, Fx, Fy, Fz, uu, odd_k;
+    T axx, ayy, azz, axy, axz, ayz, ktr;
+};
+
+template <class T, int EQ>
+__device__ __forceinline__ CollidePrep<T> collide_prep(const Moments<T> &m, T ux, T uy, T uz, T Fx, T Fy, T Fz,
+                                                       T omega, T fcoef) {
+    CollidePrep<T> c;
+    const T T0 = T(1) / T(3);
+    c.rho = m.rho;
+    c.ux = ux, c.uy = uy, c.uz = uz, c.Fx = Fx, c.Fy = Fy, c.Fz = Fz;
+    c.uu = ux * ux + uy * uy + uz * uz;
+    // Pi^neq = Pi - Pi^eq with Pi^eq = rho T0 I (+ rho u u for EQ = 1)
+    T nxx = m.pxx - m.rd * T0, nyy = m.pyy - m.rd * T0, nzz = m.pzz - m.rd * T0;
+    T nxy = m.pxy, nxz = m.pxz, nyz = m.pyz;
+    if (EQ == 1) {
+        nxx -= m.rho * ux * ux; nyy -= m.rho * uy * uy; nzz -= m.rho * uz * uz;
+        nxy -= m.rho * ux * uy; nxz -= m.rho * ux * uz; nyz -= m.rho * uy * uz;
+    }
+    c.axx = omega * nxx + fcoef * (T(2) * ux * Fx);
+    c.ayy = omega * nyy + fcoef * (T(2) * uy * Fy);
+    c.azz = omega * nzz + fcoef * (T(2) * uz * Fz);
+    c.axy = omega * nxy + fcoef * (ux * Fy + uy * Fx);
+    c.axz = omega * nxz + fcoef * (ux * Fz + uz * Fx);
+    c.ayz = omega * nyz + fcoef * (uy * Fz + uz * Fy);
+    c.ktr = -T(1.5) * (c.axx + c.ayy + c.azz);  // -(T0/(2 T0^2)) tr A
+    c.odd_k = T(3) - T(4.5) * c.uu;
+    return c;
+}
+
+// f*_0 (c = 0)
+template <class T, int EQ> __device__ __forceinline__ T collide_rest(const CollidePrep<T> &c) {
+    T e = c.rho;
+    if (EQ == 1) e = c.rho * (T(1) - T(1.5) * c.uu);
+    return wgt<T>(0) * (e + c.ktr);
+}
+
+// f*_i and f*_{i+1} for the opposite pair (i, i+1), i odd
+template <class T, int EQ> __device__ __forceinline__ void collide_pair(const CollidePrep<T> &c, int i, T &vi, T &vo) {
+    const T c0 = T(cx(i)), c1 = T(cy(i)), c2 = T(cz(i));
+    const T cu = c0 * c.ux + c1 * c.uy + c2 * c.uz;
+    const T cAc = c0 * c0 * c.axx + c1 * c1 * c.ayy + c2 * c2 * c.azz +
+                  T(2) * (c0 * c1 * c.axy + c0 * c2 * c.axz + c1 * c2 * c.ayz);
+    const T cF = c0 * c.Fx + c1 * c.Fy + c2 * c.Fz;
+    // w_i x (even part, odd part) of f*_i
+    T even = c.rho + (T(4.5) * cAc + c.ktr);
+    if (EQ == 1) even += c.rho * (T(4.5) * cu * cu - T(1.5) * c.uu);
+    const T odd = c.rho * cu * (c.odd_k + T(4.5) * cu * cu) + T(1.5) * cF;
+    const T w = wgt<T>(i);
+    vi = w * (even + odd);
+    vo = w * (even - odd);
+}
+
 template <class S, int EQ, class Sig>
 __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n, int self,
                                               const Moments<typename Storage<S>::T> &m,
@@ -256,45 +322,17 @@ __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n,
                                               typename Storage<S>::T omega, typename Storage<S>::T fcoef,
                                               const Sig &sig) {
     using T = typename Storage<S>::T;
-    const T T0 = T(1) / T(3);
-    const T uu = ux * ux + uy * uy + uz * uz;
-    // Pi^neq = Pi - Pi^eq with Pi^eq = rho T0 I (+ rho u u for EQ = 1)
-    T nxx = m.pxx - m.rd * T0, nyy = m.pyy - m.rd * T0, nzz = m.pzz - m.rd * T0;
-    T nxy = m.pxy, nxz = m.pxz, nyz = m.pyz;
-    if (EQ == 1) {
-        nxx -= m.rho * ux * ux; nyy -= m.rho * uy * uy; nzz -= m.rho * uz * uz;
-        nxy -= m.rho * ux * uy; nxz -= m.rho * ux * uz; nyz -= m.rho * uy * uz;
-    }
-    const T axx = omega * nxx + fcoef * (T(2) * ux * Fx);
-    const T ayy = omega * nyy + fcoef * (T(2) * uy * Fy);
-    const T azz = omega * nzz + fcoef * (T(2) * uz * Fz);
-    const T axy = omega * nxy + fcoef * (ux * Fy + uy * Fx);
-    const T axz = omega * nxz + fcoef * (ux * Fz + uz * Fx);
-    const T ayz = omega * nyz + fcoef * (uy * Fz + uz * Fy);
-    const T ktr = -T(1.5) * (axx + ayy + azz);  // -(T0/(2 T0^2)) tr A
-    // rest direction: c = 0
-    {
-        T e = m.rho;
-        if (EQ == 1) e = m.rho * (T(1) - T(1.5) * uu);
-        const T v = wgt<T>(0) * (e + ktr);
-        Storage<S>::store(fout + (uint32_t)self, v, Storage<S>::shifted ? wgt<T>(0) * sig(0) : T(0));
-    }
-    const T odd_k = T(3) - T(4.5) * uu;
+    const CollidePrep<T> c = collide_prep<T, EQ>(m, ux, uy, uz, Fx, Fy, Fz, omega, fcoef);
+    Storage<S>::store(fout + (uint32_t)self, collide_rest<T, EQ>(c),
+                      Storage<S>::shifted ? wgt<T>(0) * sig(0) : T(0));
 #pragma unroll
     for (int i = 1; i < kQ; i += 2) {
-        const T c0 = T(cx(i)), c1 = T(cy(i)), c2 = T(cz(i));
-        const T cu = c0 * ux + c1 * uy + c2 * uz;
-        const T cAc = c0 * c0 * axx + c1 * c1 * ayy + c2 * c2 * azz +
-                      T(2) * (c0 * c1 * axy + c0 * c2 * axz + c1 * c2 * ayz);
-        const T cF = c0 * Fx + c1 * Fy + c2 * Fz;
-        // w_i x (even part, odd part) of f*_i
-        T even = m.rho + (T(4.5) * cAc + ktr);
-        if (EQ == 1) even += m.rho * (T(4.5) * cu * cu - T(1.5) * uu);
-        const T odd = m.rho * cu * (odd_k + T(4.5) * cu * cu) + T(1.5) * cF;
+        T vi, vo;
+        collide_pair<T, EQ>(c, i, vi, vo);
         const T w = wgt<T>(i);
-        Storage<S>::store(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)self), w * (even + odd),
+        Storage<S>::store(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)self), vi,
                           Storage<S>::shifted ? w * sig(i) : T(0));
-        Storage<S>::store(fout + ((uint32_t)(i + 1) * (uint32_t)n + (uint32_t)self), w * (even - odd),
+        Storage<S>::store(fout + ((uint32_t)(i + 1) * (uint32_t)n + (uint32_t)self), vo,
                           Storage<S>::shifted ? w * sig(i + 1) : T(0));
     }
 }

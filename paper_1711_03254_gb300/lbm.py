@@ -217,6 +217,14 @@ def lbm_launch_count(ctx) -> int:
     return int(library().lbm_launch_count(ctx))
 
 
+def lbm_resolved_kernel(ctx, n: int = 2) -> str:
+    """Name of the strategy lbm_step(ctx, n) would run now."""
+    L = library()
+    L.lbm_resolved_kernel.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    k = int(L.lbm_resolved_kernel(ctx, int(n)))
+    return {v: name for name, v in KERNELS.items()}.get(k, str(k))
+
+
 PARTS = ("psi", "collide", "fused", "cluster")
 
 

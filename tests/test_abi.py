@@ -87,3 +87,7 @@ def test_timing_rejects_null_context(lbm):
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_timing_end(None)
     assert e.value.status == 1
+
+
+def test_resolved_kernel_null_context(lbm):
+    assert lbm.lbm_resolved_kernel(None) == "-1"
