@@ -191,11 +191,10 @@ lbm_status upload_params(lbm_ctx *ctx) {
 lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
     if (ctx->kernel != LBM_KERNEL_AUTO) return ctx->kernel;
     if (ctx->g.n <= kClusterAutoCells && n > 1) return LBM_KERNEL_CLUSTER;
-    // measured on GB300: the list-driven two-pass update beats the fused one on
-    // porous (1.9-2.2x) and all-fluid (1.2x) grids; with SOLID cells the
-    // compact layout avoids the dense layout's partly used sectors
-    if (ctx->compact_ok && (double)ctx->nonsolid <= 0.95 * (double)ctx->cells()) return LBM_KERNEL_COMPACT;
-    return LBM_KERNEL_TWO_PASS;
+    // measured on GB300: the two-pass update on the compact layout beats the
+    // dense two-pass one on porous (1.5x) and all-fluid (1.1x) grids, and the
+    // dense two-pass beats the fused one (1.2-2.2x)
+    return ctx->compact_ok ? LBM_KERNEL_COMPACT : LBM_KERNEL_TWO_PASS;
 }
 
 // Fused-kernel tiling when none was set: 32x8 columns (32x4 in FP64, whose

@@ -33,6 +33,7 @@ template <> struct Pair<double> {
         b = v.y;
     }
     __device__ static __forceinline__ void store(P *p, double a, double b, double, double) { *p = make_double2(a, b); }
+    __device__ static __forceinline__ void store_d(P *p, double a, double b) { *p = make_double2(a, b); }
 };
 template <> struct Pair<float> {
     using P = float2;
@@ -44,6 +45,7 @@ template <> struct Pair<float> {
     __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
         *p = make_float2(a - sa, b - sb);
     }
+    __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = make_float2(a, b); }
 };
 template <> struct Pair<__half> {
     using P = __half2;
@@ -55,6 +57,7 @@ template <> struct Pair<__half> {
     __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
         *p = __floats2half2_rn(a - sa, b - sb);
     }
+    __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = __floats2half2_rn(a, b); }
 };
 template <> struct Pair<__nv_bfloat16> {
     using P = __nv_bfloat162;
@@ -66,6 +69,7 @@ template <> struct Pair<__nv_bfloat16> {
     __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
         *p = __floats2bfloat162_rn(a - sa, b - sb);
     }
+    __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = __floats2bfloat162_rn(a, b); }
 };
 
 template <class T> struct Vec2;
@@ -258,23 +262,16 @@ __global__ void __launch_bounds__(256, 2) k_collide_c(StepArgs a) {
         collide_prep<T, EQ>(m0, R.ux, R.uy, R.uz, F.F[0][0], F.F[0][1], F.F[0][2], R.omega, R.fcoef);
     const CollidePrep<T> c1 =
         collide_prep<T, EQ>(m1, R.ux, R.uy, R.uz, F.F[1][0], F.F[1][1], F.F[1][2], R.omega, R.fcoef);
-    {
-        const T w = wgt<T>(0);
-        Pair<S>::store(fo + k, collide_rest<T, EQ>(c0), collide_rest<T, EQ>(c1),
-                       Storage<S>::shifted ? w * sig(0, m0.rho, q0) : T(0),
-                       Storage<S>::shifted ? w * sig(0, m1.rho, q1) : T(0));
-    }
+    auto ref0 = [&](int i) -> T { return Storage<S>::shifted ? sig(i, m0.rho, q0) : T(0); };
+    auto ref1 = [&](int i) -> T { return Storage<S>::shifted ? sig(i, m1.rho, q1) : T(0); };
+    Pair<S>::store_d(fo + k, collide_rest<T, EQ>(c0, ref0(0)), collide_rest<T, EQ>(c1, ref1(0)));
 #pragma unroll
     for (int i = 1; i < kQ; i += 2) {
         T a_i, a_o, b_i, b_o;
-        collide_pair<T, EQ>(c0, i, a_i, a_o);
-        collide_pair<T, EQ>(c1, i, b_i, b_o);
-        const T w = wgt<T>(i);
-        Pair<S>::store(fo + (size_t)i * n + k, a_i, b_i, Storage<S>::shifted ? w * sig(i, m0.rho, q0) : T(0),
-                       Storage<S>::shifted ? w * sig(i, m1.rho, q1) : T(0));
-        Pair<S>::store(fo + (size_t)(i + 1) * n + k, a_o, b_o,
-                       Storage<S>::shifted ? w * sig(i + 1, m0.rho, q0) : T(0),
-                       Storage<S>::shifted ? w * sig(i + 1, m1.rho, q1) : T(0));
+        collide_pair<T, EQ>(c0, i, ref0(i), ref0(i + 1), a_i, a_o);
+        collide_pair<T, EQ>(c1, i, ref1(i), ref1(i + 1), b_i, b_o);
+        Pair<S>::store_d(fo + (size_t)i * n + k, a_i, b_i);
+        Pair<S>::store_d(fo + (size_t)(i + 1) * n + k, a_o, b_o);
     }
     if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)m0.rho, (float)m1.rho);
     if (a.write_macro) {

@@ -57,6 +57,7 @@ template <> struct Storage<double> {
     __device__ static __forceinline__ double load(const double *p, double) { return __ldg(p); }
     __device__ static __forceinline__ double load_rw(const double *p, double) { return __ldcg(p); }
     __device__ static __forceinline__ void store(double *p, double v, double) { *p = v; }
+    __device__ static __forceinline__ void store_d(double *p, double d) { *p = d; }
 };
 template <> struct Storage<float> {
     using T = float;
@@ -64,6 +65,7 @@ template <> struct Storage<float> {
     __device__ static __forceinline__ float load(const float *p, float sh) { return __ldg(p) + sh; }
     __device__ static __forceinline__ float load_rw(const float *p, float sh) { return __ldcg(p) + sh; }
     __device__ static __forceinline__ void store(float *p, float v, float sh) { *p = v - sh; }
+    __device__ static __forceinline__ void store_d(float *p, float d) { *p = d; }
 };
 template <> struct Storage<__half> {
     using T = float;
@@ -73,6 +75,7 @@ template <> struct Storage<__half> {
     }
     __device__ static __forceinline__ float load_rw(const __half *p, float sh) { return __half2float(__ldcg(p)) + sh; }
     __device__ static __forceinline__ void store(__half *p, float v, float sh) { *p = __float2half_rn(v - sh); }
+    __device__ static __forceinline__ void store_d(__half *p, float d) { *p = __float2half_rn(d); }
 };
 template <> struct Storage<__nv_bfloat16> {
     using T = float;
@@ -86,6 +89,7 @@ template <> struct Storage<__nv_bfloat16> {
     __device__ static __forceinline__ void store(__nv_bfloat16 *p, float v, float sh) {
         *p = __float2bfloat16_rn(v - sh);
     }
+    __device__ static __forceinline__ void store_d(__nv_bfloat16 *p, float d) { *p = __float2bfloat16_rn(d); }
 };
 
 // -------------------------------------------------------------- neighbours
@@ -290,27 +294,32 @@ __device__ __forceinline__ CollidePrep<T> collide_prep(const Moments<T> &m, T ux
     return c;
 }
 
-// f*_0 (c = 0)
-template <class T, int EQ> __device__ __forceinline__ T collide_rest(const CollidePrep<T> &c) {
-    T e = c.rho;
-    if (EQ == 1) e = c.rho * (T(1) - T(1.5) * c.uu);
+// Stored value of f*_0 (c = 0): its deviation f*_0 - w_0 R from the rest
+// equilibrium of the reference density R of the cell it streams into (R = 0
+// in the unshifted format).  Forming rho - R first keeps FP32 from cancelling
+// two O(w rho) numbers.
+template <class T, int EQ> __device__ __forceinline__ T collide_rest(const CollidePrep<T> &c, T R) {
+    T e = c.rho - R;
+    if (EQ == 1) e = (c.rho - R) - T(1.5) * c.rho * c.uu;
     return wgt<T>(0) * (e + c.ktr);
 }
 
-// f*_i and f*_{i+1} for the opposite pair (i, i+1), i odd
-template <class T, int EQ> __device__ __forceinline__ void collide_pair(const CollidePrep<T> &c, int i, T &vi, T &vo) {
+// Stored values of f*_i and f*_{i+1} for the opposite pair (i, i+1), i odd,
+// with reference densities Ri, Ro (see collide_rest).
+template <class T, int EQ>
+__device__ __forceinline__ void collide_pair(const CollidePrep<T> &c, int i, T Ri, T Ro, T &vi, T &vo) {
     const T c0 = T(cx(i)), c1 = T(cy(i)), c2 = T(cz(i));
     const T cu = c0 * c.ux + c1 * c.uy + c2 * c.uz;
     const T cAc = c0 * c0 * c.axx + c1 * c1 * c.ayy + c2 * c2 * c.azz +
                   T(2) * (c0 * c1 * c.axy + c0 * c2 * c.axz + c1 * c2 * c.ayz);
     const T cF = c0 * c.Fx + c1 * c.Fy + c2 * c.Fz;
-    // w_i x (even part, odd part) of f*_i
-    T even = c.rho + (T(4.5) * cAc + c.ktr);
+    // w_i x (even part without the rest term, odd part) of f*_i
+    T even = T(4.5) * cAc + c.ktr;
     if (EQ == 1) even += c.rho * (T(4.5) * cu * cu - T(1.5) * c.uu);
     const T odd = c.rho * cu * (c.odd_k + T(4.5) * cu * cu) + T(1.5) * cF;
     const T w = wgt<T>(i);
-    vi = w * (even + odd);
-    vo = w * (even - odd);
+    vi = w * (((c.rho - Ri) + even) + odd);
+    vo = w * (((c.rho - Ro) + even) - odd);
 }
 
 template <class S, int EQ, class Sig>
@@ -323,17 +332,14 @@ __device__ __forceinline__ void collide_store(S *__restrict__ fout, long long n,
                                               const Sig &sig) {
     using T = typename Storage<S>::T;
     const CollidePrep<T> c = collide_prep<T, EQ>(m, ux, uy, uz, Fx, Fy, Fz, omega, fcoef);
-    Storage<S>::store(fout + (uint32_t)self, collide_rest<T, EQ>(c),
-                      Storage<S>::shifted ? wgt<T>(0) * sig(0) : T(0));
+    auto ref = [&](int i) -> T { return Storage<S>::shifted ? sig(i) : T(0); };
+    Storage<S>::store_d(fout + (uint32_t)self, collide_rest<T, EQ>(c, ref(0)));
 #pragma unroll
     for (int i = 1; i < kQ; i += 2) {
         T vi, vo;
-        collide_pair<T, EQ>(c, i, vi, vo);
-        const T w = wgt<T>(i);
-        Storage<S>::store(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)self), vi,
-                          Storage<S>::shifted ? w * sig(i) : T(0));
-        Storage<S>::store(fout + ((uint32_t)(i + 1) * (uint32_t)n + (uint32_t)self), vo,
-                          Storage<S>::shifted ? w * sig(i + 1) : T(0));
+        collide_pair<T, EQ>(c, i, ref(i), ref(i + 1), vi, vo);
+        Storage<S>::store_d(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)self), vi);
+        Storage<S>::store_d(fout + ((uint32_t)(i + 1) * (uint32_t)n + (uint32_t)self), vo);
     }
 }
 

@@ -11,8 +11,9 @@ generator:
     droplet taking the low or the high viscosity at random,
   * G = -1.8, no body force (the steady state is static).
 
-The solver's state after `steps` updates from the plain initial state (sharp
-droplet, fluid at rest) is the training target.  The warm start runs the
+The training target is the solver's state once every residual of its batch
+is below the tolerance (or after a cap on the updates), run from the plain
+initial state (sharp droplet, fluid at rest).  The warm start runs the
 network at 64^3 (inputs sampled every second cell for 128^3 problems) and
 upsamples its output by nearest neighbours; the solver then runs from those
 fields to the same residual as from the plain state.
@@ -56,11 +57,14 @@ def case_inputs(c, S: int):
     return surrogate.encode_inputs(t, c["rho_s"], c["ratio"], c["incline"], 0.0, r2), t, r1, r2, u
 
 
-def generate(cases, S: int = 64, steps: int = 3000, batch: int = 32, precision: str = "fp32"):
-    """Run the solver on every case; returns (inputs, targets, masks, kept case
-    indices).  Cases whose state is not finite, or whose velocity reaches the
-    sound speed, after `steps` updates are left out."""
-    X, Y, M, kept = [], [], [], []
+def generate(cases, S: int = 64, max_steps: int = 30000, tol: float = 1e-5, batch: int = 32, precision: str = "fp32",
+             check_every: int = 200):
+    """Run the solver from the plain initial state of every case towards its
+    steady state (all instances of a batch until each residual <= tol, at most
+    max_steps updates, graph-replayed); returns (inputs, targets, masks, kept
+    case indices, residuals of the kept cases).  Cases whose state is not
+    finite, or whose velocity reaches the sound speed, are left out."""
+    X, Y, M, kept, resid = [], [], [], [], []
     for k0 in range(0, len(cases), batch):
         cs = cases[k0:k0 + batch]
         geo = [case_geometry(c, S) for c in cs]
@@ -68,7 +72,10 @@ def generate(cases, S: int = 64, steps: int = 3000, batch: int = 32, precision: 
         sim = lbm.Sim(S, S, S, [case_params(c) for c in cs], precision=precision)
         sim.set_geometry(t)
         sim.set_fields(np.stack([g[1] for g in geo]), np.stack([g[2] for g in geo]), np.stack([g[3] for g in geo]))
-        sim.step(steps)
+        try:
+            _, res = lbm.lbm_run_to_steady(sim.ctx, check_every, tol, max_steps, len(cs))
+        except lbm.LbmError:  # a diverged instance: keep the finite ones below
+            res = np.full(len(cs), np.nan)
         r1, r2, u = sim.get_fields()
         sim.close()
         for j, c in enumerate(cs):
@@ -79,7 +86,8 @@ def generate(cases, S: int = 64, steps: int = 3000, batch: int = 32, precision: 
             Y.append(surrogate.encode_targets(r1[j], r2[j], u[j]))
             M.append((geo[j][0] != W.SOLID).astype(np.uint8))
             kept.append(k0 + j)
-    return np.stack(X), np.stack(Y), np.stack(M), kept
+            resid.append(float(res[j]))
+    return np.stack(X), np.stack(Y), np.stack(M), kept, resid
 
 
 def train(net, X, Y, M, iters: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50):
@@ -148,16 +156,17 @@ def steps_to_steady(c, S, init, tol, check_every=100, max_steps=20000, precision
     return done, dt, float(res[0]), fields
 
 
-def experiment(n_train=512, n_test=8, S_train=64, S_test=128, gen_steps=3000, iters=1500, batch=4, lr=1e-3,
-               tol=1e-5, check_every=100, max_steps=20000, seed_train=5, seed_test=6, log=print):
-    """Generate, train, and compare steps / wall time to steady state from the
-    plain and the learned initial fields.  Returns a summary dict."""
+def experiment(n_train=384, n_test=8, S_train=64, test_sizes=(64, 128), gen_max_steps=30000, iters=2000, batch=4,
+               lr=1e-3, tol=1e-5, check_every=100, max_steps=60000, seed_train=5, seed_test=6, log=print):
+    """Generate, train, and compare updates / wall time to steady state from
+    the plain and the learned initial fields.  Returns a summary dict."""
     import torch
     t0 = time.perf_counter()
-    X, Y, M, kept = generate(sample_cases(n_train, seed_train), S=S_train, steps=gen_steps)
+    X, Y, M, kept, gres = generate(sample_cases(n_train, seed_train), S=S_train, max_steps=gen_max_steps, tol=tol)
     t_gen = time.perf_counter() - t0
     log(f"generated {len(X)} steady states at {S_train}^3 in {t_gen:.1f} s "
-        f"({n_train - len(kept)} of {n_train} cases left out: not finite or |u| >= c_s)")
+        f"({n_train - len(kept)} of {n_train} cases left out: not finite or |u| >= c_s; "
+        f"median residual {np.median(gres):.2e})")
     net = surrogate.UNet3D(batch, S_train, seed=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -167,45 +176,50 @@ def experiment(n_train=512, n_test=8, S_train=64, S_test=128, gen_steps=3000, it
     flops = 3.0 * net.flops_per_sample() * batch * iters
     log(f"trained {iters} iterations in {t_train:.1f} s ({flops / t_train / 1e12:.1f} TFLOP/s), "
         f"loss {hist[0][1]:.4g} -> {hist[-1][1]:.4g}")
-    rows = []
-    for c in sample_cases(n_test, seed_test):
-        x, t, r1, r2, u = case_inputs(c, S_test)
-        plain = steps_to_steady(c, S_test, (t, (r1, r2, u)), tol, check_every, max_steps)
-        tw0 = time.perf_counter()
-        init = warm_fields(net, c, S_test)
-        torch.cuda.synchronize()
-        t_inf = time.perf_counter() - tw0
-        warm = steps_to_steady(c, S_test, init, tol, check_every, max_steps)
-        fluid = t != W.SOLID
-        diff = max(float(np.abs(plain[3][k][0][fluid] - warm[3][k][0][fluid]).max()) for k in (0, 1))
-        rows.append(dict(case=c, plain_steps=plain[0], plain_s=plain[1], plain_res=plain[2], warm_steps=warm[0],
-                         warm_s=warm[1] + t_inf, warm_res=warm[2], infer_s=t_inf, max_density_diff=diff))
-        log(f"case {len(rows)}: plain {plain[0]} updates {plain[1]:.2f} s | warm {warm[0]} updates "
-            f"{warm[1] + t_inf:.2f} s (inference {t_inf:.3f} s) | max |d rho| {diff:.2e}")
-    return dict(train=dict(n=n_train, kept=len(kept), size=S_train, gen_steps=gen_steps, gen_s=t_gen, iters=iters,
-                           batch=batch,
+    tests = []
+    for S_test in test_sizes:
+        rows = []
+        for c in sample_cases(n_test, seed_test):
+            x, t, r1, r2, u = case_inputs(c, S_test)
+            plain = steps_to_steady(c, S_test, (t, (r1, r2, u)), tol, check_every, max_steps)
+            tw0 = time.perf_counter()
+            init = warm_fields(net, c, S_test)
+            torch.cuda.synchronize()
+            t_inf = time.perf_counter() - tw0
+            warm = steps_to_steady(c, S_test, init, tol, check_every, max_steps)
+            fluid = t != W.SOLID
+            diff = max(float(np.abs(plain[3][k][0][fluid] - warm[3][k][0][fluid]).max()) for k in (0, 1))
+            rows.append(dict(case=c, plain_steps=plain[0], plain_s=plain[1], plain_res=plain[2],
+                             warm_steps=warm[0], warm_s=warm[1] + t_inf, warm_res=warm[2], infer_s=t_inf,
+                             max_density_diff=diff))
+            log(f"{S_test}^3 case {len(rows)}: plain {plain[0]} updates {plain[1]:.2f} s (res {plain[2]:.1e}) | "
+                f"warm {warm[0]} updates {warm[1] + t_inf:.2f} s (res {warm[2]:.1e}, inference {t_inf:.3f} s) | "
+                f"max |d rho| {diff:.2e}")
+        tests.append(dict(n=n_test, size=S_test, tol=tol, check_every=check_every, max_steps=max_steps, rows=rows))
+    return dict(train=dict(n=n_train, kept=len(kept), size=S_train, gen_max_steps=gen_max_steps,
+                           gen_residual_median=float(np.median(gres)), gen_s=t_gen, iters=iters, batch=batch,
                            train_s=t_train, tflops=flops / t_train / 1e12, loss=hist),
-                test=dict(n=n_test, size=S_test, tol=tol, check_every=check_every, max_steps=max_steps, rows=rows))
+                tests=tests)
 
 
 if __name__ == "__main__":
     import argparse
     import json
     ap = argparse.ArgumentParser(description="learned warm start: generate, train, compare steps to steady")
-    ap.add_argument("--n-train", type=int, default=512)
+    ap.add_argument("--n-train", type=int, default=384)
     ap.add_argument("--n-test", type=int, default=8)
     ap.add_argument("--size-train", type=int, default=64)
-    ap.add_argument("--size-test", type=int, default=128)
-    ap.add_argument("--gen-steps", type=int, default=3000)
-    ap.add_argument("--iters", type=int, default=1500)
+    ap.add_argument("--test-sizes", default="64,128")
+    ap.add_argument("--gen-max-steps", type=int, default=30000)
+    ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--tol", type=float, default=1e-5)
-    ap.add_argument("--max-steps", type=int, default=20000)
+    ap.add_argument("--max-steps", type=int, default=60000)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     from . import build
     build.build()
-    res = experiment(a.n_train, a.n_test, a.size_train, a.size_test, a.gen_steps, a.iters, tol=a.tol,
-                     max_steps=a.max_steps)
+    res = experiment(a.n_train, a.n_test, a.size_train, tuple(int(v) for v in a.test_sizes.split(",")),
+                     a.gen_max_steps, a.iters, tol=a.tol, max_steps=a.max_steps)
     js = json.dumps(res, default=float)
     if a.out:
         open(a.out, "w").write(js)
