@@ -70,7 +70,7 @@ NCU_TRAFFIC = {
     # 273.1 MB read + 103.1 MB written; traffic scales with the non-solid cells
     "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db"},
 }
-KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cu", "lbm_fused.cu"]
+KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cu", "lbm_fused.cu", "lbm_compact.cu"]
 
 
 def sources_hash() -> str:

@@ -57,13 +57,14 @@ def case_inputs(c, S: int):
     return surrogate.encode_inputs(t, c["rho_s"], c["ratio"], c["incline"], 0.0, r2), t, r1, r2, u
 
 
-def generate(cases, S: int = 64, max_steps: int = 30000, tol: float = 1e-5, batch: int = 32, precision: str = "fp32",
-             check_every: int = 200):
+def generate(cases, S: int = 64, max_steps: int = 25000, tol: float = 1e-5, batch: int = 32, precision: str = "fp32",
+             check_every: int = 500):
     """Run the solver from the plain initial state of every case towards its
-    steady state (all instances of a batch until each residual <= tol, at most
-    max_steps updates, graph-replayed); returns (inputs, targets, masks, kept
-    case indices, residuals of the kept cases).  Cases whose state is not
-    finite, or whose velocity reaches the sound speed, are left out."""
+    steady state: each batch of instances advances in chunks of check_every
+    updates until every instance has its residual <= tol or has diverged, or
+    max_steps is reached.  Returns (inputs, targets, masks, kept case indices,
+    residuals of the kept cases); cases whose state is not finite, or whose
+    velocity reaches the sound speed, are left out."""
     X, Y, M, kept, resid = [], [], [], [], []
     for k0 in range(0, len(cases), batch):
         cs = cases[k0:k0 + batch]
@@ -72,15 +73,22 @@ def generate(cases, S: int = 64, max_steps: int = 30000, tol: float = 1e-5, batc
         sim = lbm.Sim(S, S, S, [case_params(c) for c in cs], precision=precision)
         sim.set_geometry(t)
         sim.set_fields(np.stack([g[1] for g in geo]), np.stack([g[2] for g in geo]), np.stack([g[3] for g in geo]))
-        try:
-            _, res = lbm.lbm_run_to_steady(sim.ctx, check_every, tol, max_steps, len(cs))
-        except lbm.LbmError:  # a diverged instance: keep the finite ones below
-            res = np.full(len(cs), np.nan)
+        sim.reduce(allow_diverged=True)  # residual snapshot
+        bad = np.zeros(len(cs), bool)
+        res = np.full(len(cs), np.inf)
+        done = 0
+        while done < max_steps:
+            sim.step(check_every)
+            done += check_every
+            red = sim.reduce(allow_diverged=True)
+            res = red[:, 5]
+            bad |= ~np.isfinite(red).all(axis=1) | (red[:, 6] >= 1 / math.sqrt(3))
+            if np.all(bad | (res <= tol)):
+                break
         r1, r2, u = sim.get_fields()
         sim.close()
         for j, c in enumerate(cs):
-            ok = all(np.isfinite(a[j]).all() for a in (r1, r2, u)) and float(np.abs(u[j]).max()) < 1 / math.sqrt(3)
-            if not ok:
+            if bad[j] or not all(np.isfinite(a[j]).all() for a in (r1, r2, u)):
                 continue
             X.append(surrogate.encode_inputs(geo[j][0], c["rho_s"], c["ratio"], c["incline"], 0.0, geo[j][2]))
             Y.append(surrogate.encode_targets(r1[j], r2[j], u[j]))
@@ -118,24 +126,27 @@ def train(net, X, Y, M, iters: int, lr: float = 1e-3, seed: int = 0, log_every: 
     return hist
 
 
-def predict(net, x64):
-    """Network output for one 64^3 input (FP32 numpy [64,64,64,CIN])."""
+def predict(net, x):
+    """Network output for one input at the network's size (FP32 numpy [S,S,S,CIN])."""
     import torch
-    x = torch.zeros((net.N,) + x64.shape, dtype=torch.float32, device="cuda")
-    x[0] = torch.from_numpy(x64).cuda()
-    out = net.forward(x)
+    xb = torch.zeros((net.N,) + x.shape, dtype=torch.float32, device="cuda")
+    xb[0] = torch.from_numpy(x).cuda()
+    out = net.forward(xb)
     return out[0].float().cpu().numpy()
 
 
 def warm_fields(net, c, S: int):
-    """Initial fields for an S^3 case (S = 64 or 128) from the network."""
+    """Initial fields for an S^3 case from the network: run at the network's
+    size net.S (inputs sampled every S / net.S cells) and upsample the output
+    by nearest neighbours.  S must be a multiple of net.S."""
+    if S % net.S:
+        raise ValueError("warm_fields: the case size must be a multiple of the network size")
     x, t, r1, r2, u = case_inputs(c, S)
-    if S == 64:
+    f = S // net.S
+    if f == 1:
         out = predict(net, x)
     else:
-        f = S // 64
-        xs = np.ascontiguousarray(x[::f, ::f, ::f])
-        o = predict(net, xs)
+        o = predict(net, np.ascontiguousarray(x[::f, ::f, ::f]))
         out = o.repeat(f, 0).repeat(f, 1).repeat(f, 2)
     return t, surrogate.decode_fields(out, t)
 
@@ -156,7 +167,7 @@ def steps_to_steady(c, S, init, tol, check_every=100, max_steps=20000, precision
     return done, dt, float(res[0]), fields
 
 
-def experiment(n_train=384, n_test=8, S_train=64, test_sizes=(64, 128), gen_max_steps=30000, iters=2000, batch=4,
+def experiment(n_train=320, n_test=8, S_train=64, test_sizes=(64, 128), gen_max_steps=25000, iters=2000, batch=4,
                lr=1e-3, tol=1e-5, check_every=100, max_steps=60000, seed_train=5, seed_test=6, log=print):
     """Generate, train, and compare updates / wall time to steady state from
     the plain and the learned initial fields.  Returns a summary dict."""
@@ -206,11 +217,11 @@ if __name__ == "__main__":
     import argparse
     import json
     ap = argparse.ArgumentParser(description="learned warm start: generate, train, compare steps to steady")
-    ap.add_argument("--n-train", type=int, default=384)
+    ap.add_argument("--n-train", type=int, default=320)
     ap.add_argument("--n-test", type=int, default=8)
     ap.add_argument("--size-train", type=int, default=64)
     ap.add_argument("--test-sizes", default="64,128")
-    ap.add_argument("--gen-max-steps", type=int, default=30000)
+    ap.add_argument("--gen-max-steps", type=int, default=25000)
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--max-steps", type=int, default=60000)

@@ -1,0 +1,27 @@
+"""The learned warm start against the plain start, at a size that trains in
+seconds: 48^3 droplets on inclined walls (64 training cases run to their
+steady state by the solver, 400 Adam iterations), then 4 held-out cases run
+to the same residual from both starts.  The warm start must need fewer
+updates in total and converge to the same state (largest density difference
+between the two converged fields below 0.05)."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_warm_start_cuts_updates_to_steady():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_03254_gb300 import build
+    build.build()
+    from paper_1711_03254_gb300 import warmstart
+    res = warmstart.experiment(n_train=64, n_test=4, S_train=48, test_sizes=(48,), gen_max_steps=15000, iters=400,
+                               tol=1e-5, max_steps=30000, log=lambda *a: None)
+    rows = res["tests"][0]["rows"]
+    plain = sum(r["plain_steps"] for r in rows)
+    warm = sum(r["warm_steps"] for r in rows)
+    assert warm < plain, [(r["plain_steps"], r["warm_steps"]) for r in rows]
+    for r in rows:
+        if r["plain_res"] <= 1e-5 and r["warm_res"] <= 1e-5:
+            assert r["max_density_diff"] < 0.05, r
