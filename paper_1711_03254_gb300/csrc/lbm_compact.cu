@@ -133,8 +133,12 @@ __device__ __forceinline__ void ref_pair(const StepArgs &a, int b, uint32_t sk, 
     }
 }
 
+// threads per block: 128 for the update lets 5 blocks (20 warps) share an SM
+// within its registers
+constexpr int kPsiThreads = 256, kCollideThreads = 128;
+
 template <class S>
-__global__ void __launch_bounds__(256, 3) k_psi_c(StepArgs a) {
+__global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
     using T = typename Storage<S>::T;
     using V = typename Vec2<T>::V;
     const int b = blockIdx.y;
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(256, 3) k_psi_c(StepArgs a) {
 }
 
 template <class S, int EQ>
-__global__ void __launch_bounds__(256, 2) k_collide_c(StepArgs a) {
+__global__ void __launch_bounds__(kCollideThreads, 5) k_collide_c(StepArgs a) {
     using T = typename Storage<S>::T;
     using V = typename Vec2<T>::V;
     using P = typename Pair<S>::P;
@@ -246,24 +250,29 @@ __global__ void __launch_bounds__(256, 2) k_collide_c(StepArgs a) {
             pull(own, k, word);
         }
     }
-    load_psi();
-    auto psi_at = [&](int i, T &v0, T &v1) {
-        v0 = q0[i];
-        v1 = q1[i];
-    };
-    const Forces<T> F = sc_forces<T>(psi_at, word, m0.rho, m1.rho, p, a.wall_model);
+    // psi of both components at the 18 neighbours, streamed into the force sums;
+    // what the stores need of it is kept as FP16 reference pairs (the reference
+    // density of the cell each value streams into; own cell where SOLID)
+    ForceSums<T> bs;
+    bs.clear();
+    __half2 Rp[kQ];
+    Rp[0] = __floats2half2_rn((float)m0.rho, (float)m1.rho);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        const bool solid = (word >> i) & 1u;
+        const V q = __ldg(psi + (solid ? k : own.dst(i)));
+        bs.add(i, solid, q.x, q.y);
+        if constexpr (Storage<S>::shifted)
+            Rp[i] = __floats2half2_rn((float)(solid ? m0.rho : q.x), (float)(solid ? m1.rho : q.y));
+    }
+    const Forces<T> F = sc_forces_finish<T>(bs, word, m0.rho, m1.rho, p, a.wall_model);
     const Relax<T> R = relax<T>(m0, m1, F, p);
-    // reference density of the cell each value streams into (own cell when the
-    // neighbour is SOLID and the value bounces back)
-    auto sig = [&](int i, T own_rho, const T (&q)[kQ]) -> T {
-        return ref_value((i == 0 || ((word >> i) & 1u)) ? own_rho : q[i]);
-    };
     const CollidePrep<T> c0 =
         collide_prep<T, EQ>(m0, R.ux, R.uy, R.uz, F.F[0][0], F.F[0][1], F.F[0][2], R.omega, R.fcoef);
     const CollidePrep<T> c1 =
         collide_prep<T, EQ>(m1, R.ux, R.uy, R.uz, F.F[1][0], F.F[1][1], F.F[1][2], R.omega, R.fcoef);
-    auto ref0 = [&](int i) -> T { return Storage<S>::shifted ? sig(i, m0.rho, q0) : T(0); };
-    auto ref1 = [&](int i) -> T { return Storage<S>::shifted ? sig(i, m1.rho, q1) : T(0); };
+    auto ref0 = [&](int i) -> T { return Storage<S>::shifted ? (T)__low2float(Rp[i]) : T(0); };
+    auto ref1 = [&](int i) -> T { return Storage<S>::shifted ? (T)__high2float(Rp[i]) : T(0); };
     Pair<S>::store_d(fo + k, collide_rest<T, EQ>(c0, ref0(0)), collide_rest<T, EQ>(c1, ref1(0)));
 #pragma unroll
     for (int i = 1; i < kQ; i += 2) {
@@ -322,14 +331,16 @@ __global__ void k_layout(bool to_compact, const S *__restrict__ fin, S *__restri
 
 template <class S>
 static cudaError_t launch_compact_t(const StepArgs &a) {
-    const dim3 grid((unsigned)((a.list_max + 255) / 256 > 0 ? (a.list_max + 255) / 256 : 1), (unsigned)a.batch, 1);
+    const long long m = a.list_max > 0 ? a.list_max : 1;
+    const dim3 gp((unsigned)((m + kPsiThreads - 1) / kPsiThreads), (unsigned)a.batch, 1);
+    const dim3 gc((unsigned)((m + kCollideThreads - 1) / kCollideThreads), (unsigned)a.batch, 1);
     record_event(a, 0);
-    k_psi_c<S><<<grid, 256, 0, a.stream>>>(a);
+    k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
     record_event(a, 1);
     if (a.eq_order == 0)
-        k_collide_c<S, 0><<<grid, 256, 0, a.stream>>>(a);
+        k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
     else
-        k_collide_c<S, 1><<<grid, 256, 0, a.stream>>>(a);
+        k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
     record_event(a, 2);
     return cudaGetLastError();
 }

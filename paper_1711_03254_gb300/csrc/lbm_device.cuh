@@ -363,15 +363,17 @@ template <class T> struct Forces {
     T F[2][3];
 };
 
-template <class T, class PsiAt>
-__device__ __forceinline__ Forces<T> sc_forces(const PsiAt &psi_at, uint32_t links, T rho0, T rho1,
-                                               const InstParam<T> &p, int wall_model) {
-    T s[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};  // bulk sums for psi_1, psi_2
+// Bulk sums s[beta][axis] = sum_i ws_i c_i psi_beta(x + c_i) over the non-SOLID
+// neighbours, accumulated one neighbour at a time (i = 1..18 in order).
+template <class T> struct ForceSums {
+    T s[2][3];
+    __device__ __forceinline__ void clear() {
 #pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-        const bool solid = (links >> i) & 1u;
-        T p0, p1;
-        psi_at(i, p0, p1);
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s[b][a] = T(0);
+    }
+    __device__ __forceinline__ void add(int i, bool solid, T p0, T p1) {
         p0 = solid ? T(0) : p0;
         p1 = solid ? T(0) : p1;
         const T ws = T(2) * wgt<T>(i);
@@ -379,6 +381,14 @@ __device__ __forceinline__ Forces<T> sc_forces(const PsiAt &psi_at, uint32_t lin
         if (cy(i)) { s[0][1] += T(cy(i)) * ws * p0; s[1][1] += T(cy(i)) * ws * p1; }
         if (cz(i)) { s[0][2] += T(cz(i)) * ws * p0; s[1][2] += T(cz(i)) * ws * p1; }
     }
+};
+
+// S4 from the bulk sums: F^alpha = G rho_alpha sum ws c psi_beta (beta != alpha),
+// the wall part of Eq. 11 for the SOLID neighbours, and the body force.
+template <class T>
+__device__ __forceinline__ Forces<T> sc_forces_finish(const ForceSums<T> &bs, uint32_t links, T rho0, T rho1,
+                                                      const InstParam<T> &p, int wall_model) {
+    const T(&s)[2][3] = bs.s;
     Forces<T> out;
     const T r[2] = {rho0, rho1};
     // bulk part: F^alpha = G rho_alpha sum ws c psi_beta, beta != alpha
@@ -430,6 +440,20 @@ __device__ __forceinline__ Forces<T> sc_forces(const PsiAt &psi_at, uint32_t lin
         out.F[1][a] += r[1] * p.g[a];
     }
     return out;
+}
+
+template <class T, class PsiAt>
+__device__ __forceinline__ Forces<T> sc_forces(const PsiAt &psi_at, uint32_t links, T rho0, T rho1,
+                                               const InstParam<T> &p, int wall_model) {
+    ForceSums<T> bs;
+    bs.clear();
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        T p0, p1;
+        psi_at(i, p0, p1);
+        bs.add(i, (links >> i) & 1u, p0, p1);
+    }
+    return sc_forces_finish<T>(bs, links, rho0, rho1, p, wall_model);
 }
 
 // S5: tau_mix from the density-weighted viscosity, p = rho_1 / rho in [0, 1].
