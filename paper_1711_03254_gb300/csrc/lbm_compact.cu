@@ -133,9 +133,12 @@ __device__ __forceinline__ void ref_pair(const StepArgs &a, int b, uint32_t sk, 
     }
 }
 
-// threads per block: 128 for the update lets 5 blocks (20 warps) share an SM
-// within its registers
+// threads per block: 128 for the update lets 6 (16-bit storage), 5 (FP32) or
+// 4 (FP64, FP64 arithmetic) blocks share an SM within its registers; measured
+// on GB300, 6 blocks cost the FP32 kernel spills and 4 % time, 5 blocks cost
+// the FP16 kernel 1 %
 constexpr int kPsiThreads = 256, kCollideThreads = 128;
+template <class S> constexpr int collide_min_blocks() { return sizeof(S) == 2 ? 6 : (sizeof(S) == 4 ? 5 : 4); }
 
 template <class S>
 __global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
 }
 
 template <class S, int EQ>
-__global__ void __launch_bounds__(kCollideThreads, 5) k_collide_c(StepArgs a) {
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
     using T = typename Storage<S>::T;
     using V = typename Vec2<T>::V;
     using P = typename Pair<S>::P;

@@ -1,10 +1,11 @@
-"""The learned warm start against the plain start, at a size that trains in
-about a minute: 48^3 droplets on inclined walls (160 training cases run to
-their steady state by the solver, 1200 Adam iterations), then 6 held-out
-cases run to the same residual from both starts.  The warm start must need
+"""The learned warm start against the plain start, at the experiment's
+network size but a smaller training run (about two minutes): 64^3 droplets
+on inclined walls (192 training cases run to their steady state by the
+solver, 1500 Adam iterations), then 6 held-out cases run to the same residual
+from both starts.  The warm start must need
 fewer updates in total and converge to the same state (largest density
 difference between the two converged fields below 0.05).  The full-size
-experiment (64^3 training, 64^3 and 128^3 test cases) is
+experiment (320 training cases, 64^3 and 128^3 test cases) is
 paper_1711_03254_gb300.warmstart."""
 import pytest
 
@@ -18,8 +19,8 @@ def test_warm_start_cuts_updates_to_steady():
     from paper_1711_03254_gb300 import build
     build.build()
     from paper_1711_03254_gb300 import warmstart
-    res = warmstart.experiment(n_train=160, n_test=6, S_train=48, test_sizes=(48,), gen_max_steps=15000, iters=1200,
-                               tol=1e-5, max_steps=30000, log=lambda *a: None)
+    res = warmstart.experiment(n_train=192, n_test=6, S_train=64, test_sizes=(64,), gen_max_steps=25000, iters=1500,
+                               tol=1e-5, max_steps=40000, log=lambda *a: None)
     rows = res["tests"][0]["rows"]
     plain = sum(r["plain_steps"] for r in rows)
     warm = sum(r["warm_steps"] for r in rows)
