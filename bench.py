@@ -66,10 +66,18 @@ def alg_bytes_per_cell(part: str, precision: str) -> int:
 # keyed by kernel/precision/workload, with the hash of the kernel sources it was
 # taken on; any change of the sources voids it.
 NCU_TRAFFIC = {
-    # 128^3 packed spheres (837,994 non-solid cells), ncu --set full, one launch:
-    # 273.1 MB read + 103.1 MB written; traffic scales with the non-solid cells
+    # 128^3 packed spheres (837,994 non-solid cells), dense layout, ncu --set full:
+    # 273.1 MB read + 103.1 MB written in one launch
     "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db"},
+    # 192^3 packed spheres (2,830,487 non-solid cells; compact f 430 MB per buffer,
+    # larger than L2), ncu --set full: 274.2 MB read + 184.7 MB written in one launch
+    "k_collide_c/fp16s/spheres": {"bytes_per_fluid_cell": 162.1, "src": "27b1a433480a485c"},
 }
+# FP64 mode is bound by the FP64 pipe.  Executed FP64 flops per non-solid cell
+# (DADD + DMUL + 2 DFMA from ncu, 128^3 packed spheres, eq_order 0) and the
+# FP64 peak: 2 DFMA per clock per SM (152 SMs, 2.07 GHz) = 1.26 TFLOP/s.
+FP64_FLOPS = {"k_collide_c": {"flops_per_fluid_cell": 813.6, "src": "27b1a433480a485c"}}
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cu", "lbm_fused.cu", "lbm_compact.cu"]
 
 
@@ -296,12 +304,23 @@ def main():
     step_bytes = (2 * 38 * F_BYTES[args.precision] + 1) * fluid
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
+            "traffic_source": "ncu capture on a smaller case of the same geometry, scaled by non-solid cells"
+            if traffic is not None else None,
             "kernel": kernel_name, "algorithmic_bytes_per_fluid_cell": per_cell,
             "avg_launch_ms": round(avg_s * 1e3, 4), "launches": part_launches,
             "share_of_step": round(part_ms / ms, 4),
             "parts_ms": {k: round(v[0] / v[1], 4) for k, v in timing.items()},
             "step_min_bytes_per_fluid_cell": 2 * 38 * F_BYTES[args.precision] + 1,
             "step_frac": round(step_bytes / ((ms / args.steps) / 1e3) / 1e9 / hbm, 4)}
+
+    fl = FP64_FLOPS.get(kernel_name)
+    if args.precision == "fp64" and fl and fl["src"] == sources_hash():
+        # FP64 arithmetic: the FP64 pipe, not HBM, bounds the update
+        tf = fl["flops_per_fluid_cell"] * fluid * updates_per_launch / avg_s / 1e12
+        roof.update({"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 3),
+                     "unit": "TFLOP/s", "frac": round(tf / FP64_PEAK_TFLOPS, 4),
+                     "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
+                     "flops_per_fluid_cell": fl["flops_per_fluid_cell"]})
 
     # end to end through the C ABI with host buffers
     e2e = None

@@ -135,10 +135,11 @@ def predict(net, x):
     return out[0].float().cpu().numpy()
 
 
-def warm_fields(net, c, S: int):
+def warm_fields(net, c, S: int, velocity: bool = True):
     """Initial fields for an S^3 case from the network: run at the network's
     size net.S (inputs sampled every S / net.S cells) and upsample the output
-    by nearest neighbours.  S must be a multiple of net.S."""
+    by nearest neighbours.  S must be a multiple of net.S.  velocity=False
+    keeps the predicted densities and starts the fluid at rest."""
     if S % net.S:
         raise ValueError("warm_fields: the case size must be a multiple of the network size")
     x, t, r1, r2, u = case_inputs(c, S)
@@ -148,7 +149,10 @@ def warm_fields(net, c, S: int):
     else:
         o = predict(net, np.ascontiguousarray(x[::f, ::f, ::f]))
         out = o.repeat(f, 0).repeat(f, 1).repeat(f, 2)
-    return t, surrogate.decode_fields(out, t)
+    r1p, r2p, up = surrogate.decode_fields(out, t)
+    if not velocity:
+        up = np.zeros_like(up)
+    return t, (r1p, r2p, up)
 
 
 def steps_to_steady(c, S, init, tol, check_every=100, max_steps=20000, precision="fp32"):
@@ -193,19 +197,23 @@ def experiment(n_train=320, n_test=8, S_train=64, test_sizes=(64, 128), gen_max_
         for c in sample_cases(n_test, seed_test):
             x, t, r1, r2, u = case_inputs(c, S_test)
             plain = steps_to_steady(c, S_test, (t, (r1, r2, u)), tol, check_every, max_steps)
-            tw0 = time.perf_counter()
-            init = warm_fields(net, c, S_test)
-            torch.cuda.synchronize()
-            t_inf = time.perf_counter() - tw0
-            warm = steps_to_steady(c, S_test, init, tol, check_every, max_steps)
             fluid = t != W.SOLID
-            diff = max(float(np.abs(plain[3][k][0][fluid] - warm[3][k][0][fluid]).max()) for k in (0, 1))
-            rows.append(dict(case=c, plain_steps=plain[0], plain_s=plain[1], plain_res=plain[2],
-                             warm_steps=warm[0], warm_s=warm[1] + t_inf, warm_res=warm[2], infer_s=t_inf,
-                             max_density_diff=diff))
-            log(f"{S_test}^3 case {len(rows)}: plain {plain[0]} updates {plain[1]:.2f} s (res {plain[2]:.1e}) | "
-                f"warm {warm[0]} updates {warm[1] + t_inf:.2f} s (res {warm[2]:.1e}, inference {t_inf:.3f} s) | "
-                f"max |d rho| {diff:.2e}")
+            row = dict(case=c, plain_steps=plain[0], plain_s=plain[1], plain_res=plain[2])
+            msg = f"{S_test}^3 case {len(rows) + 1}: plain {plain[0]} updates {plain[1]:.2f} s (res {plain[2]:.1e})"
+            # "warm": predicted densities and velocity; "warm_rho": predicted densities, fluid at rest
+            for name, vel in (("warm", True), ("warm_rho", False)):
+                tw0 = time.perf_counter()
+                init = warm_fields(net, c, S_test, velocity=vel)
+                torch.cuda.synchronize()
+                t_inf = time.perf_counter() - tw0
+                warm = steps_to_steady(c, S_test, init, tol, check_every, max_steps)
+                diff = max(float(np.abs(plain[3][k][0][fluid] - warm[3][k][0][fluid]).max()) for k in (0, 1))
+                row.update({f"{name}_steps": warm[0], f"{name}_s": warm[1] + t_inf, f"{name}_res": warm[2],
+                            f"{name}_infer_s": t_inf, f"{name}_max_density_diff": diff})
+                msg += (f" | {name} {warm[0]} updates {warm[1] + t_inf:.2f} s (res {warm[2]:.1e}) "
+                        f"max |d rho| {diff:.1e}")
+            rows.append(row)
+            log(msg)
         tests.append(dict(n=n_test, size=S_test, tol=tol, check_every=check_every, max_steps=max_steps, rows=rows))
     return dict(train=dict(n=n_train, kept=len(kept), size=S_train, gen_max_steps=gen_max_steps,
                            gen_residual_median=float(np.median(gres)), gen_s=t_gen, iters=iters, batch=batch,
