@@ -34,6 +34,11 @@ template <> struct Pair<double> {
     }
     __device__ static __forceinline__ void store(P *p, double a, double b, double, double) { *p = make_double2(a, b); }
     __device__ static __forceinline__ void store_d(P *p, double a, double b) { *p = make_double2(a, b); }
+    __device__ static __forceinline__ void load_shared(const P *p, double &a, double &b) {
+        const P v = *p;
+        a = v.x;
+        b = v.y;
+    }
 };
 template <> struct Pair<float> {
     using P = float2;
@@ -46,6 +51,11 @@ template <> struct Pair<float> {
         *p = make_float2(a - sa, b - sb);
     }
     __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = make_float2(a, b); }
+    __device__ static __forceinline__ void load_shared(const P *p, float &a, float &b) {
+        const P v = *p;
+        a = v.x + 0.f;
+        b = v.y + 0.f;
+    }
 };
 template <> struct Pair<__half> {
     using P = __half2;
@@ -58,6 +68,11 @@ template <> struct Pair<__half> {
         *p = __floats2half2_rn(a - sa, b - sb);
     }
     __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = __floats2half2_rn(a, b); }
+    __device__ static __forceinline__ void load_shared(const P *p, float &a, float &b) {
+        const float2 v = __half22float2(*p);
+        a = v.x + 0.f;
+        b = v.y + 0.f;
+    }
 };
 template <> struct Pair<__nv_bfloat16> {
     using P = __nv_bfloat162;
@@ -70,6 +85,11 @@ template <> struct Pair<__nv_bfloat16> {
         *p = __floats2bfloat162_rn(a - sa, b - sb);
     }
     __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = __floats2bfloat162_rn(a, b); }
+    __device__ static __forceinline__ void load_shared(const P *p, float &a, float &b) {
+        const float2 v = __bfloat1622float2(*p);
+        a = v.x + 0.f;
+        b = v.y + 0.f;
+    }
 };
 
 template <class T> struct Vec2;
@@ -179,6 +199,105 @@ __global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
     out.x = p0;
     out.y = p1;
     psi[k] = out;
+}
+
+// ---------------------------------------------------------------- pipelined psi pass
+// k_psi_cp: the psi pass as a persistent kernel.  Each thread walks its cells
+// with a grid stride and, while it sums the values of one cell, the values of
+// its next cell are already on their way into shared memory (cp.async into
+// two per-thread stages).  Every thread reads only the slots its own copies
+// filled, after cp.async.wait_group, so no block barrier is needed.
+constexpr int kPsiPipeThreads = 128;
+constexpr bool kPsiPipelined = true;
+
+template <int BYTES> __device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <class S> constexpr size_t psi_pipe_smem() {
+    return 2 * ((size_t)kQ * sizeof(typename Pair<S>::P) + sizeof(__half2)) * kPsiPipeThreads;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kPsiPipeThreads) k_psi_cp(StepArgs a) {
+    using T = typename Storage<S>::T;
+    using V = typename Vec2<T>::V;
+    using P = typename Pair<S>::P;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P *vbuf = reinterpret_cast<P *>(smem_raw);                                          // [2][kQ][threads]
+    __half2 *rbuf = reinterpret_cast<__half2 *>(vbuf + 2 * kQ * kPsiPipeThreads);       // [2][threads]
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const uint32_t count = (uint32_t)__ldg(a.list_count + b);
+    const uint32_t stride = gridDim.x * kPsiPipeThreads;
+    const P *f = (const P *)a.f_in + (size_t)b * kQ * a.kmax;
+    const __half2 *rin = (const __half2 *)a.ref_in + (size_t)b * a.kmax;
+    V *psi = (V *)a.psi + (size_t)b * a.kmax;
+    const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
+
+    // start the copies of cell kk into stage st; returns its geometry word
+    auto issue = [&](uint32_t kk, int st) -> uint32_t {
+        const CompactCell c = compact_cell(a, b, kk);
+        if (cell_type(c.word) == kInlet) return c.word;
+        auto copies = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                const bool bb = (sw >> opp(i)) & 1u;
+                const uint32_t idx = bb ? (uint32_t)opp(i) * a.kmax + sk : (uint32_t)i * a.kmax + nb.src(i);
+                cp_async_ca<sizeof(P)>(&vbuf[(st * kQ + i) * kPsiPipeThreads + tid], f + idx);
+            }
+            if constexpr (Storage<S>::shifted) cp_async_ca<4>(&rbuf[st * kPsiPipeThreads + tid], rin + sk);
+        };
+        CNbr own;
+        own.init(c.x, c.y, c.z, kk, instance_tab(a, b), a.words, a.g);
+        int xu;
+        uint32_t ku, wu;
+        if (outlet_source(a, b, c, own, xu, ku, wu)) {
+            CNbr up;
+            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
+            copies(up, ku, wu);
+        } else {
+            copies(own, kk, c.word);
+        }
+        return c.word;
+    };
+
+    uint32_t k = blockIdx.x * kPsiPipeThreads + tid;
+    uint32_t word = k < count ? issue(k, 0) : 0u;
+    cp_async_commit_group();
+    int st = 0;
+    for (; k < count; k += stride) {
+        const uint32_t kn = k + stride;
+        const uint32_t word_n = kn < count ? issue(kn, st ^ 1) : 0u;
+        cp_async_commit_group();
+        cp_async_wait_one();  // this thread's copies of stage st have landed
+        T p0, p1;
+        if (cell_type(word) == kInlet) {
+            p0 = p.rho_in[0];
+            p1 = p.rho_in[1];
+        } else {
+            T v0[kQ], v1[kQ];
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) Pair<S>::load_shared(&vbuf[(st * kQ + i) * kPsiPipeThreads + tid], v0[i], v1[i]);
+            T r0 = T(0), r1 = T(0);
+            if constexpr (Storage<S>::shifted) {
+                const __half2 r = rbuf[st * kPsiPipeThreads + tid];
+                r0 = __low2float(r);
+                r1 = __high2float(r);
+            }
+            p0 = density_of<T, Storage<S>::shifted>(v0, r0);
+            p1 = density_of<T, Storage<S>::shifted>(v1, r1);
+        }
+        V out;
+        out.x = p0;
+        out.y = p1;
+        psi[k] = out;
+        word = word_n;
+        st ^= 1;
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
 }
 
 template <class S, int EQ>
@@ -338,7 +457,28 @@ static cudaError_t launch_compact_t(const StepArgs &a) {
     const dim3 gp((unsigned)((m + kPsiThreads - 1) / kPsiThreads), (unsigned)a.batch, 1);
     const dim3 gc((unsigned)((m + kCollideThreads - 1) / kCollideThreads), (unsigned)a.batch, 1);
     record_event(a, 0);
-    k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
+    if (kPsiPipelined) {
+        // persistent grid: as many blocks as fit on the device at once
+        static int per_sm = 0, sms = 0;
+        constexpr size_t smem = psi_pipe_smem<S>();
+        if (per_sm == 0) {
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess && smem > 48 * 1024)
+                e = cudaFuncSetAttribute(k_psi_cp<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_psi_cp<S>, kPsiPipeThreads, smem);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        }
+        const long long want = (long long)sms * per_sm / a.batch;
+        const long long need = (m + kPsiPipeThreads - 1) / kPsiPipeThreads;
+        const unsigned gx = (unsigned)(need < want ? need : (want > 0 ? want : 1));
+        k_psi_cp<S><<<dim3(gx, (unsigned)a.batch, 1), kPsiPipeThreads, smem, a.stream>>>(a);
+    } else {
+        k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
+    }
     record_event(a, 1);
     if (a.eq_order == 0)
         k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);

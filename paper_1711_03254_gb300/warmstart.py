@@ -172,7 +172,8 @@ def steps_to_steady(c, S, init, tol, check_every=100, max_steps=20000, precision
 
 
 def experiment(n_train=320, n_test=8, S_train=64, test_sizes=(64, 128), gen_max_steps=25000, iters=2000, batch=4,
-               lr=1e-3, tol=1e-5, check_every=100, max_steps=60000, seed_train=5, seed_test=6, log=print):
+               lr=1e-3, tol=1e-5, check_every=100, max_steps=60000, seed_train=5, seed_test=6, log=print,
+               variants=(("warm", True), ("warm_rho", False))):
     """Generate, train, and compare updates / wall time to steady state from
     the plain and the learned initial fields.  Returns a summary dict."""
     import torch
@@ -201,7 +202,7 @@ def experiment(n_train=320, n_test=8, S_train=64, test_sizes=(64, 128), gen_max_
             row = dict(case=c, plain_steps=plain[0], plain_s=plain[1], plain_res=plain[2])
             msg = f"{S_test}^3 case {len(rows) + 1}: plain {plain[0]} updates {plain[1]:.2f} s (res {plain[2]:.1e})"
             # "warm": predicted densities and velocity; "warm_rho": predicted densities, fluid at rest
-            for name, vel in (("warm", True), ("warm_rho", False)):
+            for name, vel in variants:
                 tw0 = time.perf_counter()
                 init = warm_fields(net, c, S_test, velocity=vel)
                 torch.cuda.synchronize()
