@@ -208,7 +208,9 @@ __global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
 // two per-thread stages).  Every thread reads only the slots its own copies
 // filled, after cp.async.wait_group, so no block barrier is needed.
 constexpr int kPsiPipeThreads = 128;
-constexpr bool kPsiPipelined = true;
+// measured on GB300 (256^3 packed spheres): 13 % faster for 16-bit storage,
+// 1.7x slower for FP32 pairs, so FP32 and FP64 keep the one-cell-per-thread pass
+template <class S> constexpr bool psi_pipelined() { return sizeof(S) == 2; }
 
 template <int BYTES> __device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -300,15 +302,18 @@ __global__ void __launch_bounds__(kPsiPipeThreads) k_psi_cp(StepArgs a) {
     asm volatile("cp.async.wait_all;\n" ::);
 }
 
-template <class S, int EQ>
-__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
+// The update of one non-INLET cell once its moments are known: psi of the 18
+// neighbours (nb_at(i) = compact index of x + c_i) streamed into the force
+// sums, with the FP16 reference pairs the stores need kept; relaxation,
+// collision and the stores of f, the reference pair and (last update) the
+// fields.
+template <class S, int EQ, class NbAt>
+__device__ __forceinline__ void update_cell(const StepArgs &a, int b, uint32_t k, const CompactCell &c,
+                                           const Moments<typename Storage<S>::T> &m0,
+                                           const Moments<typename Storage<S>::T> &m1, const NbAt &nb_at) {
     using T = typename Storage<S>::T;
     using V = typename Vec2<T>::V;
     using P = typename Pair<S>::P;
-    const int b = blockIdx.y;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
-    const CompactCell c = compact_cell(a, b, k);
     const uint32_t word = c.word;
     const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
     const uint32_t n = a.kmax;
@@ -316,62 +321,6 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
     const V *psi = (const V *)a.psi + (size_t)b * n;
     __half2 *rout = (__half2 *)a.ref_out + (size_t)b * n;
     const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
-    T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
-    CNbr own;
-    own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
-    // psi of both components at the 18 neighbours (own cell where SOLID: masked
-    // by the force and never used as a reference there)
-    T q0[kQ], q1[kQ];
-    auto load_psi = [&]() {
-#pragma unroll
-        for (int i = 1; i < kQ; ++i) {
-            const uint32_t j = ((word >> i) & 1u) ? k : own.dst(i);
-            const V q = __ldg(psi + j);
-            q0[i] = q.x;
-            q1[i] = q.y;
-        }
-    };
-    if (cell_type(word) == kInlet) {
-        load_psi();
-        const T uu = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            const bool self_ref = i == 0 || ((word >> i) & 1u);
-            const T s0 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[0] : q0[i]) : T(0);
-            const T s1 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[1] : q1[i]) : T(0);
-            Pair<S>::store(fo + (size_t)i * n + k, feq_dir<T, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
-                           feq_dir<T, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu), s0, s1);
-        }
-        if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)p.rho_in[0], (float)p.rho_in[1]);
-        if (a.write_macro) {
-            mac[cell] = p.rho_in[0];
-            mac[a.g.n + cell] = p.rho_in[1];
-            mac[2 * a.g.n + cell] = p.u_in[0];
-            mac[3 * a.g.n + cell] = p.u_in[1];
-            mac[4 * a.g.n + cell] = p.u_in[2];
-        }
-        return;
-    }
-    const P *f = (const P *)a.f_in + (size_t)b * kQ * n;
-    Moments<T> m0, m1;
-    auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-        T v0[kQ], v1[kQ], r0, r1;
-        pull_pairs<S>(f, n, sk, nb, sw, v0, v1);
-        ref_pair<S>(a, b, sk, r0, r1);
-        m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
-        m1 = moments_of<T, Storage<S>::shifted>(v1, r1);
-    };
-    {
-        int xu;
-        uint32_t ku, wu;
-        if (outlet_source(a, b, c, own, xu, ku, wu)) {
-            CNbr up;
-            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
-            pull(up, ku, wu);
-        } else {
-            pull(own, k, word);
-        }
-    }
     // psi of both components at the 18 neighbours, streamed into the force sums;
     // what the stores need of it is kept as FP16 reference pairs (the reference
     // density of the cell each value streams into; own cell where SOLID)
@@ -382,7 +331,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
         const bool solid = (word >> i) & 1u;
-        const V q = __ldg(psi + (solid ? k : own.dst(i)));
+        const V q = __ldg(psi + (solid ? k : nb_at(i)));
         bs.add(i, solid, q.x, q.y);
         if constexpr (Storage<S>::shifted)
             Rp[i] = __floats2half2_rn((float)(solid ? m0.rho : q.x), (float)(solid ? m1.rho : q.y));
@@ -406,12 +355,181 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
     }
     if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)m0.rho, (float)m1.rho);
     if (a.write_macro) {
+        T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
         mac[cell] = m0.rho;
         mac[a.g.n + cell] = m1.rho;
         mac[2 * a.g.n + cell] = R.ux;
         mac[3 * a.g.n + cell] = R.uy;
         mac[4 * a.g.n + cell] = R.uz;
     }
+}
+
+// An INLET cell: feq(rho_in, u_in), stored relative to the neighbours'
+// reference densities (nb_at as in update_cell).
+template <class S, int EQ, class NbAt>
+__device__ __forceinline__ void inlet_cell(const StepArgs &a, int b, uint32_t k, const CompactCell &c,
+                                          const NbAt &nb_at) {
+    using T = typename Storage<S>::T;
+    using V = typename Vec2<T>::V;
+    using P = typename Pair<S>::P;
+    const uint32_t word = c.word;
+    const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
+    const uint32_t n = a.kmax;
+    P *fo = (P *)a.f_out + (size_t)b * kQ * n;
+    const V *psi = (const V *)a.psi + (size_t)b * n;
+    const T uu = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const bool self_ref = i == 0 || ((word >> i) & 1u);
+        V q;
+        q.x = q.y = T(0);
+        if (!self_ref) q = __ldg(psi + nb_at(i));
+        const T s0 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[0] : q.x) : T(0);
+        const T s1 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[1] : q.y) : T(0);
+        Pair<S>::store(fo + (size_t)i * n + k, feq_dir<T, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
+                       feq_dir<T, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu), s0, s1);
+    }
+    if constexpr (Storage<S>::shifted)
+        ((__half2 *)a.ref_out)[(size_t)b * n + k] = __floats2half2_rn((float)p.rho_in[0], (float)p.rho_in[1]);
+    if (a.write_macro) {
+        const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
+        T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
+        mac[cell] = p.rho_in[0];
+        mac[a.g.n + cell] = p.rho_in[1];
+        mac[2 * a.g.n + cell] = p.u_in[0];
+        mac[3 * a.g.n + cell] = p.u_in[1];
+        mac[4 * a.g.n + cell] = p.u_in[2];
+    }
+}
+
+template <class S, int EQ>
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
+    using T = typename Storage<S>::T;
+    using P = typename Pair<S>::P;
+    const int b = blockIdx.y;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
+    const CompactCell c = compact_cell(a, b, k);
+    CNbr own;
+    own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
+    auto nb_at = [&](int i) -> uint32_t { return own.dst(i); };
+    if (cell_type(c.word) == kInlet) {
+        inlet_cell<S, EQ>(a, b, k, c, nb_at);
+        return;
+    }
+    const P *f = (const P *)a.f_in + (size_t)b * kQ * a.kmax;
+    Moments<T> m0, m1;
+    auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
+        T v0[kQ], v1[kQ], r0, r1;
+        pull_pairs<S>(f, a.kmax, sk, nb, sw, v0, v1);
+        ref_pair<S>(a, b, sk, r0, r1);
+        m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
+        m1 = moments_of<T, Storage<S>::shifted>(v1, r1);
+    };
+    {
+        int xu;
+        uint32_t ku, wu;
+        if (outlet_source(a, b, c, own, xu, ku, wu)) {
+            CNbr up;
+            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
+            pull(up, ku, wu);
+        } else {
+            pull(own, k, c.word);
+        }
+    }
+    update_cell<S, EQ>(a, b, k, c, m0, m1, nb_at);
+}
+
+// ---------------------------------------------------------------- pipelined update
+// k_collide_cp: the update as a persistent kernel, pipelined like k_psi_cp.
+// While a thread updates one cell, the 19 stored pairs and the reference pair
+// of its next cell are copied into shared memory (cp.async), and that cell's
+// 18 neighbour indices wait in shared memory for its psi loads.
+template <class S> constexpr bool collide_pipelined() { return sizeof(S) == 2; }
+constexpr int kCollidePipeThreads = 128;
+
+template <class S> constexpr size_t collide_pipe_smem() {
+    return 2 * ((size_t)kQ * sizeof(typename Pair<S>::P) + sizeof(__half2) + (kQ - 1) * sizeof(uint32_t)) *
+           kCollidePipeThreads;
+}
+
+template <class S, int EQ>
+__global__ void __launch_bounds__(kCollidePipeThreads, 5) k_collide_cp(StepArgs a) {
+    using T = typename Storage<S>::T;
+    using P = typename Pair<S>::P;
+    constexpr int NT = kCollidePipeThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P *vbuf = reinterpret_cast<P *>(smem_raw);                              // [2][kQ][NT]
+    __half2 *rbuf = reinterpret_cast<__half2 *>(vbuf + 2 * kQ * NT);        // [2][NT]
+    uint32_t *nbuf = reinterpret_cast<uint32_t *>(rbuf + 2 * NT);           // [2][kQ - 1][NT]
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const uint32_t count = (uint32_t)__ldg(a.list_count + b);
+    const uint32_t stride = gridDim.x * NT;
+    const P *f = (const P *)a.f_in + (size_t)b * kQ * a.kmax;
+    const __half2 *rin = (const __half2 *)a.ref_in + (size_t)b * a.kmax;
+
+    // start the copies of cell kk into stage st and park its neighbour indices
+    auto issue = [&](uint32_t kk, int st) -> CompactCell {
+        const CompactCell c = compact_cell(a, b, kk);
+        CNbr own;
+        own.init(c.x, c.y, c.z, kk, instance_tab(a, b), a.words, a.g);
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) nbuf[(st * (kQ - 1) + i - 1) * NT + tid] = own.dst(i);
+        if (cell_type(c.word) == kInlet) return c;
+        auto copies = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                const bool bb = (sw >> opp(i)) & 1u;
+                const uint32_t idx = bb ? (uint32_t)opp(i) * a.kmax + sk : (uint32_t)i * a.kmax + nb.src(i);
+                cp_async_ca<sizeof(P)>(&vbuf[(st * kQ + i) * NT + tid], f + idx);
+            }
+            if constexpr (Storage<S>::shifted) cp_async_ca<4>(&rbuf[st * NT + tid], rin + sk);
+        };
+        int xu;
+        uint32_t ku, wu;
+        if (outlet_source(a, b, c, own, xu, ku, wu)) {
+            CNbr up;
+            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
+            copies(up, ku, wu);
+        } else {
+            copies(own, kk, c.word);
+        }
+        return c;
+    };
+
+    uint32_t k = blockIdx.x * NT + tid;
+    CompactCell c{};
+    if (k < count) c = issue(k, 0);
+    cp_async_commit_group();
+    int st = 0;
+    for (; k < count; k += stride) {
+        const uint32_t kn = k + stride;
+        CompactCell cn{};
+        if (kn < count) cn = issue(kn, st ^ 1);
+        cp_async_commit_group();
+        cp_async_wait_one();  // this thread's copies of stage st have landed
+        const int s0 = st;
+        auto nb_at = [&](int i) -> uint32_t { return nbuf[(s0 * (kQ - 1) + i - 1) * NT + tid]; };
+        if (cell_type(c.word) == kInlet) {
+            inlet_cell<S, EQ>(a, b, k, c, nb_at);
+        } else {
+            T v0[kQ], v1[kQ];
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) Pair<S>::load_shared(&vbuf[(st * kQ + i) * NT + tid], v0[i], v1[i]);
+            T r0 = T(0), r1 = T(0);
+            if constexpr (Storage<S>::shifted) {
+                const __half2 r = rbuf[st * NT + tid];
+                r0 = __low2float(r);
+                r1 = __high2float(r);
+            }
+            const Moments<T> m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
+            const Moments<T> m1 = moments_of<T, Storage<S>::shifted>(v1, r1);
+            update_cell<S, EQ>(a, b, k, c, m0, m1, nb_at);
+        }
+        c = cn;
+        st ^= 1;
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
 }
 
 __global__ void k_compact_links(const uint32_t *__restrict__ list, const int *__restrict__ count,
@@ -451,13 +569,35 @@ __global__ void k_layout(bool to_compact, const S *__restrict__ fin, S *__restri
     }
 }
 
+// persistent grid of the pipelined update: as many blocks as fit at once
+template <class S, int EQ> static cudaError_t launch_collide_cp(const StepArgs &a, long long m) {
+    static int per_sm = 0, sms = 0;
+    constexpr size_t smem = collide_pipe_smem<S>();
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess && smem > 48 * 1024)
+            e = cudaFuncSetAttribute(k_collide_cp<S, EQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_cp<S, EQ>, kCollidePipeThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    const long long want = (long long)sms * per_sm / a.batch;
+    const long long need = (m + kCollidePipeThreads - 1) / kCollidePipeThreads;
+    const unsigned gx = (unsigned)(need < want ? need : (want > 0 ? want : 1));
+    k_collide_cp<S, EQ><<<dim3(gx, (unsigned)a.batch, 1), kCollidePipeThreads, smem, a.stream>>>(a);
+    return cudaSuccess;
+}
+
 template <class S>
 static cudaError_t launch_compact_t(const StepArgs &a) {
     const long long m = a.list_max > 0 ? a.list_max : 1;
     const dim3 gp((unsigned)((m + kPsiThreads - 1) / kPsiThreads), (unsigned)a.batch, 1);
     const dim3 gc((unsigned)((m + kCollideThreads - 1) / kCollideThreads), (unsigned)a.batch, 1);
     record_event(a, 0);
-    if (kPsiPipelined) {
+    if constexpr (psi_pipelined<S>()) {
         // persistent grid: as many blocks as fit on the device at once
         static int per_sm = 0, sms = 0;
         constexpr size_t smem = psi_pipe_smem<S>();
@@ -480,10 +620,15 @@ static cudaError_t launch_compact_t(const StepArgs &a) {
         k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
     }
     record_event(a, 1);
-    if (a.eq_order == 0)
-        k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
-    else
-        k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
+    if constexpr (collide_pipelined<S>()) {
+        const cudaError_t e = a.eq_order == 0 ? launch_collide_cp<S, 0>(a, m) : launch_collide_cp<S, 1>(a, m);
+        if (e != cudaSuccess) return e;
+    } else {
+        if (a.eq_order == 0)
+            k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
+        else
+            k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
+    }
     record_event(a, 2);
     return cudaGetLastError();
 }
