@@ -440,98 +440,6 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
     update_cell<S, EQ>(a, b, k, c, m0, m1, nb_at);
 }
 
-// ---------------------------------------------------------------- pipelined update
-// k_collide_cp: the update as a persistent kernel, pipelined like k_psi_cp.
-// While a thread updates one cell, the 19 stored pairs and the reference pair
-// of its next cell are copied into shared memory (cp.async), and that cell's
-// 18 neighbour indices wait in shared memory for its psi loads.
-template <class S> constexpr bool collide_pipelined() { return sizeof(S) == 2; }
-constexpr int kCollidePipeThreads = 128;
-
-template <class S> constexpr size_t collide_pipe_smem() {
-    return 2 * ((size_t)kQ * sizeof(typename Pair<S>::P) + sizeof(__half2) + (kQ - 1) * sizeof(uint32_t)) *
-           kCollidePipeThreads;
-}
-
-template <class S, int EQ>
-__global__ void __launch_bounds__(kCollidePipeThreads, 5) k_collide_cp(StepArgs a) {
-    using T = typename Storage<S>::T;
-    using P = typename Pair<S>::P;
-    constexpr int NT = kCollidePipeThreads;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    P *vbuf = reinterpret_cast<P *>(smem_raw);                              // [2][kQ][NT]
-    __half2 *rbuf = reinterpret_cast<__half2 *>(vbuf + 2 * kQ * NT);        // [2][NT]
-    uint32_t *nbuf = reinterpret_cast<uint32_t *>(rbuf + 2 * NT);           // [2][kQ - 1][NT]
-    const int b = blockIdx.y, tid = threadIdx.x;
-    const uint32_t count = (uint32_t)__ldg(a.list_count + b);
-    const uint32_t stride = gridDim.x * NT;
-    const P *f = (const P *)a.f_in + (size_t)b * kQ * a.kmax;
-    const __half2 *rin = (const __half2 *)a.ref_in + (size_t)b * a.kmax;
-
-    // start the copies of cell kk into stage st and park its neighbour indices
-    auto issue = [&](uint32_t kk, int st) -> CompactCell {
-        const CompactCell c = compact_cell(a, b, kk);
-        CNbr own;
-        own.init(c.x, c.y, c.z, kk, instance_tab(a, b), a.words, a.g);
-#pragma unroll
-        for (int i = 1; i < kQ; ++i) nbuf[(st * (kQ - 1) + i - 1) * NT + tid] = own.dst(i);
-        if (cell_type(c.word) == kInlet) return c;
-        auto copies = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-#pragma unroll
-            for (int i = 0; i < kQ; ++i) {
-                const bool bb = (sw >> opp(i)) & 1u;
-                const uint32_t idx = bb ? (uint32_t)opp(i) * a.kmax + sk : (uint32_t)i * a.kmax + nb.src(i);
-                cp_async_ca<sizeof(P)>(&vbuf[(st * kQ + i) * NT + tid], f + idx);
-            }
-            if constexpr (Storage<S>::shifted) cp_async_ca<4>(&rbuf[st * NT + tid], rin + sk);
-        };
-        int xu;
-        uint32_t ku, wu;
-        if (outlet_source(a, b, c, own, xu, ku, wu)) {
-            CNbr up;
-            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
-            copies(up, ku, wu);
-        } else {
-            copies(own, kk, c.word);
-        }
-        return c;
-    };
-
-    uint32_t k = blockIdx.x * NT + tid;
-    CompactCell c{};
-    if (k < count) c = issue(k, 0);
-    cp_async_commit_group();
-    int st = 0;
-    for (; k < count; k += stride) {
-        const uint32_t kn = k + stride;
-        CompactCell cn{};
-        if (kn < count) cn = issue(kn, st ^ 1);
-        cp_async_commit_group();
-        cp_async_wait_one();  // this thread's copies of stage st have landed
-        const int s0 = st;
-        auto nb_at = [&](int i) -> uint32_t { return nbuf[(s0 * (kQ - 1) + i - 1) * NT + tid]; };
-        if (cell_type(c.word) == kInlet) {
-            inlet_cell<S, EQ>(a, b, k, c, nb_at);
-        } else {
-            T v0[kQ], v1[kQ];
-#pragma unroll
-            for (int i = 0; i < kQ; ++i) Pair<S>::load_shared(&vbuf[(st * kQ + i) * NT + tid], v0[i], v1[i]);
-            T r0 = T(0), r1 = T(0);
-            if constexpr (Storage<S>::shifted) {
-                const __half2 r = rbuf[st * NT + tid];
-                r0 = __low2float(r);
-                r1 = __high2float(r);
-            }
-            const Moments<T> m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
-            const Moments<T> m1 = moments_of<T, Storage<S>::shifted>(v1, r1);
-            update_cell<S, EQ>(a, b, k, c, m0, m1, nb_at);
-        }
-        c = cn;
-        st ^= 1;
-    }
-    asm volatile("cp.async.wait_all;\n" ::);
-}
-
 __global__ void k_compact_links(const uint32_t *__restrict__ list, const int *__restrict__ count,
                                 const uint32_t *__restrict__ link, uint32_t *__restrict__ clink, long long n,
                                 uint32_t kmax) {
@@ -569,28 +477,6 @@ __global__ void k_layout(bool to_compact, const S *__restrict__ fin, S *__restri
     }
 }
 
-// persistent grid of the pipelined update: as many blocks as fit at once
-template <class S, int EQ> static cudaError_t launch_collide_cp(const StepArgs &a, long long m) {
-    static int per_sm = 0, sms = 0;
-    constexpr size_t smem = collide_pipe_smem<S>();
-    if (per_sm == 0) {
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess && smem > 48 * 1024)
-            e = cudaFuncSetAttribute(k_collide_cp<S, EQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_cp<S, EQ>, kCollidePipeThreads, smem);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
-    const long long want = (long long)sms * per_sm / a.batch;
-    const long long need = (m + kCollidePipeThreads - 1) / kCollidePipeThreads;
-    const unsigned gx = (unsigned)(need < want ? need : (want > 0 ? want : 1));
-    k_collide_cp<S, EQ><<<dim3(gx, (unsigned)a.batch, 1), kCollidePipeThreads, smem, a.stream>>>(a);
-    return cudaSuccess;
-}
-
 template <class S>
 static cudaError_t launch_compact_t(const StepArgs &a) {
     const long long m = a.list_max > 0 ? a.list_max : 1;
@@ -620,15 +506,13 @@ static cudaError_t launch_compact_t(const StepArgs &a) {
         k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
     }
     record_event(a, 1);
-    if constexpr (collide_pipelined<S>()) {
-        const cudaError_t e = a.eq_order == 0 ? launch_collide_cp<S, 0>(a, m) : launch_collide_cp<S, 1>(a, m);
-        if (e != cudaSuccess) return e;
-    } else {
-        if (a.eq_order == 0)
-            k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
-        else
-            k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
-    }
+    // (a persistent variant that prefetches the next cell with cp.async, as the
+    // psi pass does, measured 10 % slower here: the update is issue-bound, and
+    // the prefetch buffers cost occupancy and registers)
+    if (a.eq_order == 0)
+        k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
+    else
+        k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
     record_event(a, 2);
     return cudaGetLastError();
 }
