@@ -302,18 +302,15 @@ __global__ void __launch_bounds__(kPsiPipeThreads) k_psi_cp(StepArgs a) {
     asm volatile("cp.async.wait_all;\n" ::);
 }
 
-// The update of one non-INLET cell once its moments are known: psi of the 18
-// neighbours (nb_at(i) = compact index of x + c_i) streamed into the force
-// sums, with the FP16 reference pairs the stores need kept; relaxation,
-// collision and the stores of f, the reference pair and (last update) the
-// fields.
-template <class S, int EQ, class NbAt>
-__device__ __forceinline__ void update_cell(const StepArgs &a, int b, uint32_t k, const CompactCell &c,
-                                           const Moments<typename Storage<S>::T> &m0,
-                                           const Moments<typename Storage<S>::T> &m1, const NbAt &nb_at) {
+template <class S, int EQ>
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
     using T = typename Storage<S>::T;
     using V = typename Vec2<T>::V;
     using P = typename Pair<S>::P;
+    const int b = blockIdx.y;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
+    const CompactCell c = compact_cell(a, b, k);
     const uint32_t word = c.word;
     const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
     const uint32_t n = a.kmax;
@@ -321,6 +318,62 @@ __device__ __forceinline__ void update_cell(const StepArgs &a, int b, uint32_t k
     const V *psi = (const V *)a.psi + (size_t)b * n;
     __half2 *rout = (__half2 *)a.ref_out + (size_t)b * n;
     const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
+    T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
+    CNbr own;
+    own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
+    // psi of both components at the 18 neighbours (own cell where SOLID: masked
+    // by the force and never used as a reference there)
+    T q0[kQ], q1[kQ];
+    auto load_psi = [&]() {
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+            const uint32_t j = ((word >> i) & 1u) ? k : own.dst(i);
+            const V q = __ldg(psi + j);
+            q0[i] = q.x;
+            q1[i] = q.y;
+        }
+    };
+    if (cell_type(word) == kInlet) {
+        load_psi();
+        const T uu = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const bool self_ref = i == 0 || ((word >> i) & 1u);
+            const T s0 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[0] : q0[i]) : T(0);
+            const T s1 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[1] : q1[i]) : T(0);
+            Pair<S>::store(fo + (size_t)i * n + k, feq_dir<T, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
+                           feq_dir<T, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu), s0, s1);
+        }
+        if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)p.rho_in[0], (float)p.rho_in[1]);
+        if (a.write_macro) {
+            mac[cell] = p.rho_in[0];
+            mac[a.g.n + cell] = p.rho_in[1];
+            mac[2 * a.g.n + cell] = p.u_in[0];
+            mac[3 * a.g.n + cell] = p.u_in[1];
+            mac[4 * a.g.n + cell] = p.u_in[2];
+        }
+        return;
+    }
+    const P *f = (const P *)a.f_in + (size_t)b * kQ * n;
+    Moments<T> m0, m1;
+    auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
+        T v0[kQ], v1[kQ], r0, r1;
+        pull_pairs<S>(f, n, sk, nb, sw, v0, v1);
+        ref_pair<S>(a, b, sk, r0, r1);
+        m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
+        m1 = moments_of<T, Storage<S>::shifted>(v1, r1);
+    };
+    {
+        int xu;
+        uint32_t ku, wu;
+        if (outlet_source(a, b, c, own, xu, ku, wu)) {
+            CNbr up;
+            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
+            pull(up, ku, wu);
+        } else {
+            pull(own, k, word);
+        }
+    }
     // psi of both components at the 18 neighbours, streamed into the force sums;
     // what the stores need of it is kept as FP16 reference pairs (the reference
     // density of the cell each value streams into; own cell where SOLID)
@@ -331,7 +384,7 @@ __device__ __forceinline__ void update_cell(const StepArgs &a, int b, uint32_t k
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
         const bool solid = (word >> i) & 1u;
-        const V q = __ldg(psi + (solid ? k : nb_at(i)));
+        const V q = __ldg(psi + (solid ? k : own.dst(i)));
         bs.add(i, solid, q.x, q.y);
         if constexpr (Storage<S>::shifted)
             Rp[i] = __floats2half2_rn((float)(solid ? m0.rho : q.x), (float)(solid ? m1.rho : q.y));
@@ -355,89 +408,12 @@ __device__ __forceinline__ void update_cell(const StepArgs &a, int b, uint32_t k
     }
     if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)m0.rho, (float)m1.rho);
     if (a.write_macro) {
-        T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
         mac[cell] = m0.rho;
         mac[a.g.n + cell] = m1.rho;
         mac[2 * a.g.n + cell] = R.ux;
         mac[3 * a.g.n + cell] = R.uy;
         mac[4 * a.g.n + cell] = R.uz;
     }
-}
-
-// An INLET cell: feq(rho_in, u_in), stored relative to the neighbours'
-// reference densities (nb_at as in update_cell).
-template <class S, int EQ, class NbAt>
-__device__ __forceinline__ void inlet_cell(const StepArgs &a, int b, uint32_t k, const CompactCell &c,
-                                          const NbAt &nb_at) {
-    using T = typename Storage<S>::T;
-    using V = typename Vec2<T>::V;
-    using P = typename Pair<S>::P;
-    const uint32_t word = c.word;
-    const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
-    const uint32_t n = a.kmax;
-    P *fo = (P *)a.f_out + (size_t)b * kQ * n;
-    const V *psi = (const V *)a.psi + (size_t)b * n;
-    const T uu = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const bool self_ref = i == 0 || ((word >> i) & 1u);
-        V q;
-        q.x = q.y = T(0);
-        if (!self_ref) q = __ldg(psi + nb_at(i));
-        const T s0 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[0] : q.x) : T(0);
-        const T s1 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[1] : q.y) : T(0);
-        Pair<S>::store(fo + (size_t)i * n + k, feq_dir<T, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
-                       feq_dir<T, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu), s0, s1);
-    }
-    if constexpr (Storage<S>::shifted)
-        ((__half2 *)a.ref_out)[(size_t)b * n + k] = __floats2half2_rn((float)p.rho_in[0], (float)p.rho_in[1]);
-    if (a.write_macro) {
-        const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
-        T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
-        mac[cell] = p.rho_in[0];
-        mac[a.g.n + cell] = p.rho_in[1];
-        mac[2 * a.g.n + cell] = p.u_in[0];
-        mac[3 * a.g.n + cell] = p.u_in[1];
-        mac[4 * a.g.n + cell] = p.u_in[2];
-    }
-}
-
-template <class S, int EQ>
-__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
-    using T = typename Storage<S>::T;
-    using P = typename Pair<S>::P;
-    const int b = blockIdx.y;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
-    const CompactCell c = compact_cell(a, b, k);
-    CNbr own;
-    own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
-    auto nb_at = [&](int i) -> uint32_t { return own.dst(i); };
-    if (cell_type(c.word) == kInlet) {
-        inlet_cell<S, EQ>(a, b, k, c, nb_at);
-        return;
-    }
-    const P *f = (const P *)a.f_in + (size_t)b * kQ * a.kmax;
-    Moments<T> m0, m1;
-    auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-        T v0[kQ], v1[kQ], r0, r1;
-        pull_pairs<S>(f, a.kmax, sk, nb, sw, v0, v1);
-        ref_pair<S>(a, b, sk, r0, r1);
-        m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
-        m1 = moments_of<T, Storage<S>::shifted>(v1, r1);
-    };
-    {
-        int xu;
-        uint32_t ku, wu;
-        if (outlet_source(a, b, c, own, xu, ku, wu)) {
-            CNbr up;
-            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
-            pull(up, ku, wu);
-        } else {
-            pull(own, k, c.word);
-        }
-    }
-    update_cell<S, EQ>(a, b, k, c, m0, m1, nb_at);
 }
 
 __global__ void k_compact_links(const uint32_t *__restrict__ list, const int *__restrict__ count,
