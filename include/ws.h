@@ -29,7 +29,11 @@ extern "C" {
 #endif
 
 /* y = act(conv(x, w) + bias); y is BF16 (y_f32 = 0) or FP32 (y_f32 = 1) with
- * row stride ldy; relu != 0 applies max(., 0); bias may be NULL. */
+ * row stride ldy; relu != 0 applies max(., 0); bias may be NULL.  Runs as an
+ * implicit GEMM on the tcgen05 tensor cores: 128 positions x all Co output
+ * channels per thread block, accumulated in tensor memory.  Additional
+ * argument rules: Co <= 256, y 16-byte aligned, ldy a multiple of 8 (BF16)
+ * or 4 (FP32). */
 int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void *y, int ldy, int y_f32, int N,
                   int D, int H, int W, int Ci, int Co, int k, int relu, void *stream);
 
@@ -74,6 +78,11 @@ int ws_adam(float *w, float *m, float *v, float *g, void *wb, long long n, float
             float eps, float weight_decay, void *stream);
 
 /* FP32 -> BF16 copy into a channel slice: y[p][c] = x[p*ldx + c], c < C. */
+/* Waits for `stream`, then reports whether a tensor-core convolution since the
+ * last call gave up on a bounded wait for its matrix units (5; the affected
+ * outputs are not written) or not (0); clears the record.  2 on a CUDA error. */
+int ws_tc_status(void *stream);
+
 int ws_to_bf16(const float *x, int ldx, void *y, int ldy, long long P, int C, void *stream);
 
 #ifdef __cplusplus

@@ -9,8 +9,10 @@
 //   ws_conv3d_bwd_weight dW[co, t, ci] += sum_p dY[p, co] X[p + t - r, ci]: one GEMM per tap
 //                        (M = Co, N = Ci, K = positions), split over position chunks.
 //
-// The products use warp-level mma.sync m16n8k16 BF16 instructions fed by
-// ldmatrix from cp.async double-buffered shared-memory tiles.
+// The forward product (and so the data gradient) runs on the tcgen05 tensor
+// cores with the accumulator in tensor memory (k_conv_fwd_tc); the weight
+// gradient uses warp-level mma.sync m16n8k16 BF16 instructions fed by ldmatrix
+// from cp.async double-buffered shared-memory tiles.
 //
 // Activations are channels-last with a row stride (ld) and a channel offset,
 // so concatenations are views of one buffer.  Channel counts are multiples of
@@ -58,120 +60,214 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// ------------------------------------------------------------------ forward
+// ------------------------------------------------------------------ forward, tcgen05
+// The same implicit GEMM on the 5th-generation tensor cores: D[p, co] (FP32,
+// in tensor memory) += A[p, k] B[co, k] with A the gathered input rows and B
+// the weights, both K-major BF16 in shared memory, issued by one thread as
+// tcgen05.mma (M = 128 positions, N = Co <= 256, K = 16 per instruction).
+// Operand tiles use the no-swizzle canonical layout: 8-row x 16-byte core
+// matrices, the two core matrices of a 16-wide K chunk 128 B apart (leading
+// byte offset) and consecutive 8-row groups 256 B apart (stride byte offset).
+// Two shared-memory stages of 4 K chunks each: cp.async fills one stage while
+// the tensor cores work on the other; an mbarrier per stage, signalled by
+// tcgen05.commit, says when a stage's MMAs are done.  Every wait is bounded:
+// on expiry the kernel records the fault in g_tc_timeout and stops issuing.
+constexpr int TBM = 128, TKC = 4, TTHREADS = 128;
 
-constexpr int FBM = 128, FBN = 64, FBK = 16, FPAD = 8;
-constexpr int FTHREADS = 256;
+__device__ int g_tc_timeout;
 
-// X: [P][ldx] (channel offset already applied), Wt: [Co][KV][Ci], Y: [P][ldy]
-template <bool OUT_F32>
-__global__ void __launch_bounds__(FTHREADS) k_conv_fwd(const bf16 *__restrict__ X, int ldx, const bf16 *__restrict__ Wt,
-                                                       const float *__restrict__ bias, void *__restrict__ Y, int ldy,
-                                                       Act a, int Ci, int Co, int k, int relu) {
-    __shared__ __align__(16) bf16 sA[2][FBM][FBK + FPAD];
-    __shared__ __align__(16) bf16 sB[2][FBN][FBK + FPAD];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 3, wn = warp >> 2;  // 4 x 2 warps, 32 x 32 each
-    const long long P = (long long)a.N * a.D * a.H * a.W;
-    const long long m0 = (long long)blockIdx.x * FBM;
-    const int n0 = blockIdx.y * FBN;
-    const int r = k / 2, KV = k * k * k;
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-    // the A row and half-row this thread loads
-    const int arow = tid >> 1, ahalf = (tid & 1) * 8;
-    const long long p = m0 + arow;
-    int pn = 0, pz = 0, py = 0, px = 0;
-    const bool prow = p < P;
-    if (prow) {
-        long long q = p;
-        px = (int)(q % a.W); q /= a.W;
-        py = (int)(q % a.H); q /= a.H;
-        pz = (int)(q % a.D); q /= a.D;
-        pn = (int)q;
+// shared-memory matrix descriptor: no swizzle, K-major canonical layout
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+    return d;                // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (long it = 0; it < (1L << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
     }
-    const int brow = tid >> 1, bhalf = (tid & 1) * 8;  // threads 0..127 load B
-    const int nchunk = Ci / FBK;
-    const int iters = KV * nchunk;
+    atomicExch(&g_tc_timeout, 1);
+    return false;
+}
 
-    auto load_stage = [&](int it, int st) {
-        const int t = it / nchunk, c0 = (it - t * nchunk) * FBK;
-        const int tz = t / (k * k), ty = (t / k) % k, tx = t % k;
-        const int zz = pz + tz - r, yy = py + ty - r, xx = px + tx - r;
-        const bool ok = prow && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-        const long long src = ok ? ((((long long)pn * a.D + zz) * a.H + yy) * a.W + xx) * ldx + c0 + ahalf : 0;
-        cp_async16(&sA[st][arow][ahalf], X + src, ok);
-        if (tid < FBN * 2) {
-            const int co = n0 + brow;
-            const bool okb = co < Co;
-            const long long bsrc = okb ? ((long long)co * KV + t) * Ci + c0 + bhalf : 0;
-            cp_async16(&sB[st][brow][bhalf], Wt + bsrc, okb);
+template <bool OUT_F32>
+__global__ void __launch_bounds__(TTHREADS) k_conv_fwd_tc(const bf16 *__restrict__ X, int ldx,
+                                                         const bf16 *__restrict__ Wt, const float *__restrict__ bias,
+                                                         void *__restrict__ Y, int ldy, Act a, int Ci, int Co, int k,
+                                                         int relu, int tmem_cols) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int BN = Co;
+    const uint32_t a_chunk = TBM * 32, b_chunk = (uint32_t)BN * 32;
+    const uint32_t stage_bytes = TKC * (a_chunk + b_chunk);
+    unsigned char *stage0 = sm;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 2 * stage_bytes);  // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    const long long P = (long long)a.N * a.D * a.H * a.W;
+    const long long m0 = (long long)blockIdx.x * TBM;
+    const int r = k / 2, KV = k * k * k, cchunks = Ci / 16;
+    const int nkc = KV * cchunks, nkb = (nkc + TKC - 1) / TKC;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = *tslot;
+
+    // the two A rows this thread gathers (rows tid >> 1 and 64 + (tid >> 1)), half kh = tid & 1
+    const int kh = tid & 1;
+    int pn[2], pz[2], py[2], px[2];
+    bool prow[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const long long p = m0 + j * 64 + (tid >> 1);
+        prow[j] = p < P;
+        long long q = prow[j] ? p : 0;
+        px[j] = (int)(q % a.W); q /= a.W;
+        py[j] = (int)(q % a.H); q /= a.H;
+        pz[j] = (int)(q % a.D); q /= a.D;
+        pn[j] = (int)q;
+    }
+    auto load_block = [&](int kb, int st) {
+        unsigned char *sa = stage0 + st * stage_bytes;
+        unsigned char *sb = sa + TKC * a_chunk;
+        for (int c = 0; c < TKC; ++c) {
+            const int kc = kb * TKC + c;
+            if (kc >= nkc) break;
+            const int t = kc / cchunks, c0 = (kc - t * cchunks) * 16;
+            const int tz = t / (k * k), ty = (t / k) % k, tx = t % k;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int row = j * 64 + (tid >> 1);
+                const int zz = pz[j] + tz - r, yy = py[j] + ty - r, xx = px[j] + tx - r;
+                const bool ok = prow[j] && zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                const long long src =
+                    ok ? ((((long long)pn[j] * a.D + zz) * a.H + yy) * a.W + xx) * ldx + c0 + kh * 8 : 0;
+                cp_async16(sa + c * a_chunk + ((row >> 3) * 2 + kh) * 128 + (row & 7) * 16, X + src, ok);
+            }
+            for (int q = tid; q < BN * 2; q += TTHREADS) {
+                const int n = q >> 1, h = q & 1;
+                const long long src = ((long long)n * KV + t) * Ci + c0 + h * 8;
+                cp_async16(sb + c * b_chunk + ((n >> 3) * 2 + h) * 128 + (n & 7) * 16, Wt + src, true);
+            }
         }
         cp_async_commit();
     };
 
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-
-    load_stage(0, 0);
-    for (int it = 0; it < iters; ++it) {
-        const int st = it & 1;
-        cp_async_wait0();
-        __syncthreads();
-        if (it + 1 < iters) load_stage(it + 1, st ^ 1);
-        unsigned af[2][4], bfr[2][4];
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi) {
-            const int row = wm * 32 + mi * 16 + ((lane >> 3) & 1) * 8 + (lane & 7);
-            const int col = (lane >> 4) * 8;
-            ldmatrix_x4(af[mi], &sA[st][row][col]);
-        }
-#pragma unroll
-        for (int nj = 0; nj < 2; ++nj) {
-            const int mtx = lane >> 3;
-            const int row = wn * 32 + nj * 16 + (mtx >> 1) * 8 + (lane & 7);
-            const int col = (mtx & 1) * 8;
-            ldmatrix_x4(bfr[nj], &sB[st][row][col]);
-        }
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni)
-                mma_bf16(acc[mi][ni], af[mi], bfr[ni >> 1][(ni & 1) * 2], bfr[ni >> 1][(ni & 1) * 2 + 1]);
-        __syncthreads();
-    }
-
-    // epilogue: bias, ReLU, store
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const long long row = m0 + wm * 32 + mi * 16 + (lane >> 2) + h * 8;
-                const int col = n0 + wn * 32 + ni * 8 + (lane & 3) * 2;
-                if (row >= P || col >= Co) continue;
-                float v0 = acc[mi][ni][h * 2], v1 = acc[mi][ni][h * 2 + 1];
-                if (bias) {
-                    v0 += bias[col];
-                    v1 += bias[col + 1];
-                }
-                if (relu) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                if (OUT_F32) {
-                    float2 *dst = reinterpret_cast<float2 *>((float *)Y + row * ldy + col);
-                    *dst = make_float2(v0, v1);
-                } else {
-                    __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>((bf16 *)Y + row * ldy + col);
-                    *dst = __floats2bfloat162_rn(v0, v1);
+    const uint32_t idesc = umma_idesc_bf16(TBM, BN);
+    bool ok_run = true;
+    load_block(0, 0);
+    for (int kb = 0; kb < nkb && ok_run; ++kb) {
+        const int st = kb & 1;
+        if (kb + 1 < nkb) {
+            const int s1 = (kb + 1) & 1;
+            if (kb + 1 >= 2) {
+                // the stage is free once the MMAs of block kb - 1 are done (uniform decision)
+                const bool okw = mbar_wait(smem_u32(&mbar[s1]), (uint32_t)(((kb - 1) >> 1) & 1));
+                if (!__syncthreads_and(okw)) {
+                    ok_run = false;
+                    break;
                 }
             }
+            load_block(kb + 1, s1);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t sa = smem_u32(stage0 + st * stage_bytes), sb = sa + TKC * a_chunk;
+            for (int c = 0; c < TKC; ++c) {
+                const int kc = kb * TKC + c;
+                if (kc >= nkc) break;
+                const uint64_t ad = umma_desc(sa + c * a_chunk, 128, 256);
+                const uint64_t bd = umma_desc(sb + c * b_chunk, 128, 256);
+                const uint32_t acc = kc > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&mbar[st])));
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+    if (ok_run) {
+        const bool okw = mbar_wait(smem_u32(&mbar[(nkb - 1) & 1]), (uint32_t)(((nkb - 1) >> 1) & 1));
+        ok_run = __syncthreads_and(okw);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+    if (ok_run) {
+        // epilogue: warp w owns accumulator rows (TMEM lanes) 32 w .. 32 w + 31
+        const long long row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+            if (row < P) {
+                float o[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float x = __uint_as_float(v[e]);
+                    if (bias) x += bias[c0 + e];
+                    if (relu) x = fmaxf(x, 0.f);
+                    o[e] = x;
+                }
+                if (OUT_F32) {
+                    float4 *dst = reinterpret_cast<float4 *>((float *)Y + row * ldy + c0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) dst[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
+                } else {
+                    __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>((bf16 *)Y + row * ldy + c0);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) dst[e] = __floats2bfloat162_rn(o[2 * e], o[2 * e + 1]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols));
+    }
 }
 
 // W' [Ci][KV][Co] = W [Co][KV-1-t][Ci]: backward-data weights
@@ -313,6 +409,7 @@ using namespace ws;
 
 static bool bad_channels(int c) { return c < 16 || (c % 16) != 0; }
 
+
 extern "C" {
 
 int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void *y, int ldy, int y_f32, int N, int D,
@@ -320,16 +417,29 @@ int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void
     if (!x || !w || !y || N < 1 || D < 1 || H < 1 || W < 1 || (k != 1 && k != 3)) return 1;
     if (bad_channels(Ci) || bad_channels(Co) || ldx < Ci || ldy < Co || (ldx % 8) || (ldy % 2)) return 1;
     if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(w) & 15)) return 1;
+    // one CTA per 128 positions and all Co channels (N = Co <= 256 in one MMA)
+    if (Co > 256 || (ldy % (y_f32 ? 4 : 8)) || (reinterpret_cast<uintptr_t>(y) & 15)) return 1;
     Act a{N, D, H, W};
     const long long P = (long long)N * D * H * W;
-    const dim3 grid((unsigned)((P + FBM - 1) / FBM), (unsigned)((Co + FBN - 1) / FBN), 1);
     cudaStream_t s = (cudaStream_t)stream;
+    const int cols = Co <= 32 ? 32 : (Co <= 64 ? 64 : (Co <= 128 ? 128 : 256));
+    const size_t smem = 2 * (size_t)TKC * (TBM * 32 + (size_t)Co * 32) + 2 * sizeof(uint64_t) + 16;
+    static bool attr[2] = {false, false};
+    if (!attr[y_f32 ? 1 : 0]) {
+        const cudaError_t e = y_f32 ? cudaFuncSetAttribute(k_conv_fwd_tc<true>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024)
+                                    : cudaFuncSetAttribute(k_conv_fwd_tc<false>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        if (e != cudaSuccess) return 2;
+        attr[y_f32 ? 1 : 0] = true;
+    }
+    const dim3 grid((unsigned)((P + TBM - 1) / TBM), 1, 1);
     if (y_f32)
-        k_conv_fwd<true><<<grid, FTHREADS, 0, s>>>((const bf16 *)x, ldx, (const bf16 *)w, bias, y, ldy, a, Ci, Co, k,
-                                                   relu);
+        k_conv_fwd_tc<true><<<grid, TTHREADS, smem, s>>>((const bf16 *)x, ldx, (const bf16 *)w, bias, y, ldy, a, Ci,
+                                                         Co, k, relu, cols);
     else
-        k_conv_fwd<false><<<grid, FTHREADS, 0, s>>>((const bf16 *)x, ldx, (const bf16 *)w, bias, y, ldy, a, Ci, Co, k,
-                                                    relu);
+        k_conv_fwd_tc<false><<<grid, TTHREADS, smem, s>>>((const bf16 *)x, ldx, (const bf16 *)w, bias, y, ldy, a,
+                                                          Ci, Co, k, relu, cols);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -366,6 +476,16 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
         k_bias_grad<<<g2, 256, 0, s>>>((const bf16 *)dy, ldy, db, P, Co);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+int ws_tc_status(void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    int flag = 0;
+    const int zero = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return 2;
+    if (cudaMemcpyFromSymbol(&flag, g_tc_timeout, sizeof(int)) != cudaSuccess) return 2;
+    if (flag && cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int)) != cudaSuccess) return 2;
+    return flag ? 5 : 0;
 }
 
 }  // extern "C"

@@ -30,9 +30,10 @@ def _lib():
         L.ws_mse_loss.argtypes = [vp, i, vp, vp, vp, vp, i, vp, ll, i, vp]
         L.ws_adam.argtypes = [vp, vp, vp, vp, vp, ll, f, f, f, f, f, vp]
         L.ws_to_bf16.argtypes = [vp, i, vp, i, ll, i, vp]
+        L.ws_tc_status.argtypes = [vp]
         for name in ("ws_conv3d_fwd", "ws_conv3d_flip_weights", "ws_conv3d_bwd_weight", "ws_avgpool2",
                      "ws_avgpool2_bwd", "ws_upsample2", "ws_upsample2_bwd", "ws_relu_bwd", "ws_mse_loss", "ws_adam",
-                     "ws_to_bf16"):
+                     "ws_to_bf16", "ws_tc_status"):
             getattr(L, name).restype = ctypes.c_int
         _sig_done = True
     return L
@@ -132,3 +133,9 @@ def ws_to_bf16(x, y):
     C = y.shape[-1]
     P = y.numel() // C if y.is_contiguous() else x.numel() // x.shape[-1]
     _ok(_lib().ws_to_bf16(x.data_ptr(), _ld(x), y.data_ptr(), _ld(y), P, C, _stream()), "ws_to_bf16")
+
+
+def ws_tc_status() -> int:
+    """0 when no tensor-core convolution since the last call gave up on a
+    bounded wait, 5 otherwise (waits for the current stream; clears the record)."""
+    return int(_lib().ws_tc_status(_stream()))

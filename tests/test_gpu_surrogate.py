@@ -34,7 +34,8 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("shape,Ci,Co,k", [((2, 6, 5, 7), 32, 48, 3), ((1, 9, 4, 3), 16, 16, 3),
-                                           ((1, 8, 8, 8), 96, 64, 3), ((2, 5, 6, 7), 48, 32, 1)])
+                                           ((1, 8, 8, 8), 96, 64, 3), ((2, 5, 6, 7), 48, 32, 1),
+                                           ((1, 8, 8, 12), 64, 224, 3)])
 def test_conv_forward_and_gradients(env, shape, Ci, Co, k):
     torch, ws, conv = env
     rng = np.random.default_rng(sum(shape) + Ci + Co + k)
@@ -72,6 +73,7 @@ def test_conv_forward_and_gradients(env, shape, Ci, Co, k):
     rdw, rdb = conv.conv3d_bwd_weight(x, dy, k)
     assert _rel(dw.cpu().numpy(), rdw) < 2e-5
     assert _rel(db.cpu().numpy(), rdb) < 2e-5
+    assert ws.ws_tc_status() == 0  # no tensor-core wait gave up
 
 
 def test_pool_upsample_relu(env):
