@@ -91,3 +91,29 @@ def test_timing_rejects_null_context(lbm):
 
 def test_resolved_kernel_null_context(lbm):
     assert lbm.lbm_resolved_kernel(None) == "-1"
+
+
+def _declared_ws():
+    txt = open(os.path.join(ROOT, "include", "ws.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ws_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_surrogate_boundary_exported_and_bound(lbm):
+    from paper_1711_03254_gb300 import ws
+    names = _declared_ws()
+    assert "ws_conv3d_fwd" in names and "ws_tc_status" in names
+    lib = lbm.library()
+    for name in names:
+        assert hasattr(lib, name), name
+        assert callable(getattr(ws, name, None)), name
+
+
+def test_surrogate_rejects_bad_arguments_before_launch(lbm):
+    # channel counts must be multiples of 16; nothing is launched (no GPU needed)
+    from paper_1711_03254_gb300 import ws
+    L = ws._lib()
+    assert L.ws_conv3d_fwd(None, 16, None, None, None, 16, 0, 1, 1, 1, 1, 16, 16, 3, 0, None) == 1
+    p = 1 << 12  # any non-null, 16-byte aligned value: argument checks come first
+    assert L.ws_conv3d_fwd(p, 24, p, None, p, 24, 0, 1, 2, 2, 2, 24, 16, 3, 0, None) == 1
+    assert L.ws_conv3d_fwd(p, 16, p, None, p, 512, 0, 1, 2, 2, 2, 16, 512, 3, 0, None) == 1
