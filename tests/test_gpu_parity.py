@@ -401,3 +401,50 @@ def test_benchmark_workload_full_size(lbm, oracle_mod, precision, tol):
                        precision=precision, wall_model=2)
     e = _errs(g, o)
     assert max(e) < tol, e
+
+
+@pytest.mark.parametrize("kernel", ["two_pass", "compact", "fused"])
+@pytest.mark.parametrize("shape", [(1, 9, 7), (5, 1, 3), (4, 6, 1), (1, 1, 8)])
+def test_fp64_degenerate_axes(lbm, oracle_mod, shape, kernel):
+    """Axes of length 1 (the neighbour along that axis is the cell itself):
+    cell by cell against the oracle, with walls."""
+    t, r1, r2, u = _random_geometry(shape, 0.15, 91 + sum(shape), lo=0.3, hi=0.7)
+    if not (t == W.FLUID).any():
+        t.flat[0] = W.FLUID
+    r1[t == W.SOLID] = 0
+    r2[t == W.SOLID] = 0
+    p = [dict(tau=(0.8, 1.3), G=-1.6, rho_s=0.2, g=(1e-4, 0, 2e-5))]
+    _, _, g, o = _pair(lbm, oracle_mod, shape, p, t[None], r1[None], r2[None], u[None], 15, wall_model=2,
+                       kernel=kernel)
+    e = _errs(g, o)
+    assert max(e) < 1e-12, e
+
+
+def test_zero_updates_and_empty_steps(lbm, oracle_mod):
+    """lbm_step(0) changes nothing and launches nothing."""
+    t, r1, r2, u = _random_geometry((9, 8, 7), 0.2, 93, lo=0.3, hi=0.7)
+    sim = lbm.Sim(9, 8, 7, [dict(tau=(0.9, 1.1), G=-1.8)])
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    f0 = sim.get_f()
+    l0 = sim.launches
+    sim.step(0)
+    assert sim.launches == l0
+    assert np.array_equal(sim.get_f(), f0)
+
+
+def test_compact_limits_fall_back(lbm):
+    """Beyond the compact layout's coordinate limits AUTO runs the dense
+    two-pass update and an explicit request for COMPACT is refused."""
+    # 2049 x 4 x 4 = 32 784 cells: above the cluster kernel's AUTO range
+    sim = lbm.Sim(2049, 4, 4, [dict(tau=(1.0, 1.0), G=-1.8)], precision="fp32")
+    t = np.zeros((1, 4, 4, 2049), np.uint8)
+    sim.set_geometry(t)
+    assert lbm.lbm_resolved_kernel(sim.ctx, 10) == "two_pass"
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_kernel(sim.ctx, "compact")
+    assert e.value.status == 1
+    small = lbm.Sim(64, 64, 16, [dict(tau=(1.0, 1.0), G=-1.8)], precision="fp32")
+    small.set_geometry(np.zeros((1, 16, 64, 64), np.uint8))
+    assert lbm.lbm_resolved_kernel(small.ctx, 10) == "compact"
+    assert lbm.lbm_resolved_kernel(small.ctx, 1) == "compact"
