@@ -6,13 +6,13 @@
 //                        optional ReLU, BF16 or FP32 output.
 //   ws_conv3d_bwd_data   the same kernel on dY with the weights flipped and transposed
 //                        (ws_conv3d_flip_weights).
-//   ws_conv3d_bwd_weight dW[co, t, ci] += sum_p dY[p, co] X[p + t - r, ci]: one GEMM per tap
-//                        (M = Co, N = Ci, K = positions), split over position chunks.
+//   ws_conv3d_bwd_weight dW[co, t, ci] += sum_p dY[p, co] X[p + t - r, ci]: rows (t, ci) x Co
+//                        (M = taps x Ci, N = Co, K = positions), split over position chunks.
 //
-// The forward product (and so the data gradient) runs on the tcgen05 tensor
-// cores with the accumulator in tensor memory (k_conv_fwd_tc); the weight
-// gradient uses warp-level mma.sync m16n8k16 BF16 instructions fed by ldmatrix
-// from cp.async double-buffered shared-memory tiles.
+// All three products run on the tcgen05 tensor cores with the accumulator in
+// tensor memory: k_conv_fwd_tc (forward, and the data gradient through the
+// flipped weights) and k_conv_wgrad_tc (weight gradient), fed by cp.async
+// double-buffered shared-memory stages.
 //
 // Activations are channels-last with a row stride (ld) and a channel offset,
 // so concatenations are views of one buffer.  Channel counts are multiples of
@@ -40,25 +40,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool va
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-__device__ __forceinline__ void ldmatrix_x4(unsigned (&r)[4], const void *p) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(s));
-}
-__device__ __forceinline__ void ldmatrix_x4_trans(unsigned (&r)[4], const void *p) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(s));
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 // ------------------------------------------------------------------ forward, tcgen05
 // The same implicit GEMM on the 5th-generation tensor cores: D[p, co] (FP32,
@@ -281,108 +262,160 @@ __global__ void k_flip_weights(const bf16 *__restrict__ W, bf16 *__restrict__ Wf
     Wf[((long long)ci * KV + (KV - 1 - t)) * Co + co] = W[i];
 }
 
-// ------------------------------------------------------------------ backward weight
+// ------------------------------------------------------------------ backward weight, tcgen05
+// dW[co][t][ci] += sum_p X[p + t - r][ci] dY[p][co] as D[m][co] with rows
+// m = t * Ci + ci (M = 128 rows of (tap, channel) per block, so the 32-channel
+// layers fill the MMA), N = Co <= 256, K = positions of one chunk.  Both
+// operands are MN-major in shared memory (for one position, 8 consecutive
+// channels form a 16-byte row of a core matrix): the two core matrices of a
+// 16-position K chunk sit 128 B apart, 8-row groups 256 B apart.  Blocks of
+// 64 positions, two stages, bounded mbarrier waits as in k_conv_fwd_tc; the
+// result is added to dW with FP32 atomics (one block per (row tile, chunk)).
+constexpr int WTK = 64, WTTHREADS = 128;
 
-constexpr int WBM = 64, WBN = 64, WBK = 32, WPAD = 8;
-constexpr int WTHREADS = 256;
-
-// dW[co][t][ci] += sum_{p in chunk} dY[p][co] X[p + t - r][ci]
-__global__ void __launch_bounds__(WTHREADS) k_conv_wgrad(const bf16 *__restrict__ X, int ldx,
-                                                         const bf16 *__restrict__ dY, int ldy,
-                                                         float *__restrict__ dW, Act a, int Ci, int Co, int k,
-                                                         long long chunk) {
-    __shared__ __align__(16) bf16 sY[2][WBK][WBM + WPAD];  // [p][co]
-    __shared__ __align__(16) bf16 sX[2][WBK][WBN + WPAD];  // [p][ci]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 1, wn = warp >> 1;  // 2 x 4 warps: 32 (co) x 16 (ci) each
-    const int KV = k * k * k, r = k / 2;
-    const int t = blockIdx.z % KV;
-    const long long kc = blockIdx.z / KV;  // position chunk
-    const int co0 = blockIdx.y * WBM;
-    const int ci0 = blockIdx.x * WBN;
+__global__ void __launch_bounds__(WTTHREADS) k_conv_wgrad_tc(const bf16 *__restrict__ X, int ldx,
+                                                            const bf16 *__restrict__ dY, int ldy,
+                                                            float *__restrict__ dW, Act a, int Ci, int Co, int k,
+                                                            long long chunk, int tmem_cols, uint32_t lbo,
+                                                            uint32_t sbo) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t a_chunk = 128 * 32, b_chunk = (uint32_t)Co * 32;  // one 16-position K chunk
+    const uint32_t stage_bytes = 4 * (a_chunk + b_chunk);
+    unsigned char *stage0 = sm;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 2 * stage_bytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    const int KV = k * k * k, r = k / 2, rows = KV * Ci;
+    const int m0 = blockIdx.x * 128;
     const long long P = (long long)a.N * a.D * a.H * a.W;
-    const long long pbeg = kc * chunk, pend = pbeg + chunk < P ? pbeg + chunk : P;
-    const int tz = t / (k * k), ty = (t / k) % k, tx = t % k;
+    const long long pbeg = (long long)blockIdx.y * chunk, pend = pbeg + chunk < P ? pbeg + chunk : P;
+    const int nkb = (int)((pend - pbeg + WTK - 1) / WTK);
 
-    // load mapping: 32 rows (positions) x 64 channels = 32 x 8 vectors of 16 B: 256 threads, one each
-    const int lrow = tid >> 3, lcol = (tid & 7) * 8;
-    auto load_stage = [&](long long pb, int st) {
-        const long long p = pb + lrow;
-        bool okp = p < pend;
-        long long srcx = 0, srcy = 0;
-        bool okx = false;
-        if (okp) {
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = *tslot;
+
+    // this thread copies position j = tid & 63 of each block, for row groups
+    // g = (tid >> 6) + 2 q of A and channel groups of B
+    const int j = tid & 63, g0 = tid >> 6;
+    auto load_block = [&](int kb, int st) {
+        unsigned char *sa = stage0 + st * stage_bytes;
+        unsigned char *sb = sa + 4 * a_chunk;
+        const long long p = pbeg + (long long)kb * WTK + j;
+        const bool pin = p < pend;
+        int pn = 0, pz = 0, py = 0, px = 0;
+        if (pin) {
             long long q = p;
-            const int px = (int)(q % a.W); q /= a.W;
-            const int py = (int)(q % a.H); q /= a.H;
-            const int pz = (int)(q % a.D); q /= a.D;
-            const int pn = (int)q;
-            const int zz = pz + tz - r, yy = py + ty - r, xx = px + tx - r;
-            okx = zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            if (okx) srcx = ((((long long)pn * a.D + zz) * a.H + yy) * a.W + xx) * ldx + ci0 + lcol;
-            srcy = p * ldy + co0 + lcol;
+            px = (int)(q % a.W); q /= a.W;
+            py = (int)(q % a.H); q /= a.H;
+            pz = (int)(q % a.D); q /= a.D;
+            pn = (int)q;
         }
-        const bool oky = okp && co0 + lcol < Co;
-        okx = okx && ci0 + lcol < Ci;
-        cp_async16(&sY[st][lrow][lcol], dY + (oky ? srcy : 0), oky);
-        cp_async16(&sX[st][lrow][lcol], X + (okx ? srcx : 0), okx);
+        const uint32_t off = (uint32_t)((j >> 3) & 1) * 128 + (uint32_t)(j & 7) * 16;  // K group, row
+        const int c = j >> 4;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int g = g0 + 2 * q;
+            const int row0 = m0 + 8 * g;
+            bool ok = pin && row0 < rows;
+            long long src = 0;
+            if (ok) {
+                const int t = row0 / Ci, ci0 = row0 - t * Ci;
+                const int tz = t / (k * k), ty = (t / k) % k, tx = t % k;
+                const int zz = pz + tz - r, yy = py + ty - r, xx = px + tx - r;
+                ok = zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                if (ok) src = ((((long long)pn * a.D + zz) * a.H + yy) * a.W + xx) * ldx + ci0;
+            }
+            cp_async16(sa + c * a_chunk + g * 256 + off, X + src, ok);
+        }
+        for (int ng = g0; ng < Co / 8; ng += 2) {
+            const long long src = pin ? p * ldy + 8 * ng : 0;
+            cp_async16(sb + c * b_chunk + ng * 256 + off, dY + src, pin);
+        }
         cp_async_commit();
     };
 
-    float acc[2][2][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-
-    const int iters = (int)((pend - pbeg + WBK - 1) / WBK);
-    if (iters > 0) load_stage(pbeg, 0);
-    for (int it = 0; it < iters; ++it) {
-        const int st = it & 1;
-        cp_async_wait0();
-        __syncthreads();
-        if (it + 1 < iters) load_stage(pbeg + (long long)(it + 1) * WBK, st ^ 1);
-#pragma unroll
-        for (int ks = 0; ks < WBK / 16; ++ks) {
-            // A = dY^T (m = co, k = p): smem [p][co] holds A transposed -> ldmatrix.trans
-            unsigned af[2][4];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const int mtx = lane >> 3;
-                const int prow = ks * 16 + (mtx >> 1) * 8 + (lane & 7);
-                const int ccol = wm * 32 + mi * 16 + (mtx & 1) * 8;
-                ldmatrix_x4_trans(af[mi], &sY[st][prow][ccol]);
+    // MN-major A and B (bits 15, 16), FP32 accumulator, BF16 operands
+    const uint32_t idesc = umma_idesc_bf16(128, Co) | (1u << 15) | (1u << 16);
+    bool ok_run = nkb > 0;
+    if (ok_run) load_block(0, 0);
+    for (int kb = 0; kb < nkb && ok_run; ++kb) {
+        const int st = kb & 1;
+        if (kb + 1 < nkb) {
+            const int s1 = (kb + 1) & 1;
+            if (kb + 1 >= 2) {
+                const bool okw = mbar_wait(smem_u32(&mbar[s1]), (uint32_t)(((kb - 1) >> 1) & 1));
+                if (!__syncthreads_and(okw)) {
+                    ok_run = false;
+                    break;
+                }
             }
-            // B (k = p, n = ci): smem [p][ci] is k-major -> ldmatrix.trans gives the col-major fragment
-            unsigned bfr[4];
-            {
-                const int mtx = lane >> 3;
-                const int prow = ks * 16 + (mtx & 1) * 8 + (lane & 7);
-                const int ccol = wn * 16 + (mtx >> 1) * 8;
-                ldmatrix_x4_trans(bfr, &sX[st][prow][ccol]);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 2; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni * 2], bfr[ni * 2 + 1]);
+            load_block(kb + 1, s1);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
         }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);
         __syncthreads();
-    }
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int co = co0 + wm * 32 + mi * 16 + (lane >> 2) + h * 8;
-                const int ci = ci0 + wn * 16 + ni * 8 + (lane & 3) * 2;
-                if (co >= Co || ci >= Ci) continue;
-                float *dst = dW + ((long long)co * KV + t) * Ci + ci;
-                atomicAdd(dst, acc[mi][ni][h * 2]);
-                atomicAdd(dst + 1, acc[mi][ni][h * 2 + 1]);
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t sa = smem_u32(stage0 + st * stage_bytes), sb = sa + 4 * a_chunk;
+            for (int c = 0; c < 4; ++c) {
+                const uint64_t ad = umma_desc(sa + c * a_chunk, lbo, sbo);
+                const uint64_t bd = umma_desc(sb + c * b_chunk, lbo, sbo);
+                const uint32_t acc = (kb > 0 || c > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&mbar[st])));
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+    if (ok_run) {
+        const bool okw = mbar_wait(smem_u32(&mbar[(nkb - 1) & 1]), (uint32_t)(((nkb - 1) >> 1) & 1));
+        ok_run = __syncthreads_and(okw);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    if (ok_run) {
+        const int row = m0 + warp * 32 + lane;
+        const int t = row / Ci, ci = row - (row / Ci) * Ci;
+        for (int c0 = 0; c0 < Co; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+            if (row < rows)
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    atomicAdd(dW + ((long long)(c0 + e) * KV + t) * Ci + ci, __uint_as_float(v[e]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols));
+    }
 }
 
 // db[co] += sum_p dY[p][co]
@@ -408,6 +441,10 @@ __global__ void k_bias_grad(const bf16 *__restrict__ dY, int ldy, float *__restr
 using namespace ws;
 
 static bool bad_channels(int c) { return c < 16 || (c % 16) != 0; }
+
+// byte offsets of the weight gradient's MN-major operand descriptors: between
+// the two core matrices of a K chunk (leading) and between 8-row groups (stride)
+constexpr uint32_t kWgradLbo = 128, kWgradSbo = 256;
 
 
 extern "C" {
@@ -456,20 +493,27 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
                          int W, int Ci, int Co, int k, void *stream) {
     if (!x || !dy || !dw || N < 1 || D < 1 || H < 1 || W < 1 || (k != 1 && k != 3)) return 1;
     if (bad_channels(Ci) || bad_channels(Co) || ldx < Ci || ldy < Co || (ldx % 8) || (ldy % 8)) return 1;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(dy) & 15) || Co > 256) return 1;
     Act a{N, D, H, W};
     const long long P = (long long)N * D * H * W;
     const int KV = k * k * k;
-    long long chunk = 4096;
-    long long nk = (P + chunk - 1) / chunk;
-    if (nk * KV > 60000) {  // grid.z limit
-        nk = 60000 / KV;
-        chunk = (P + nk - 1) / nk;
-        chunk = (chunk + WBK - 1) / WBK * WBK;
-        nk = (P + chunk - 1) / chunk;
+    // rows (tap, channel) in tiles of 128, one block per (row tile, chunk of 4096 positions)
+    const long long chunk = 4096;
+    const long long nk = (P + chunk - 1) / chunk;
+    if (nk > 65535) return 1;
+    const int cols = Co <= 32 ? 32 : (Co <= 64 ? 64 : (Co <= 128 ? 128 : 256));
+    const size_t smem = 2 * 4 * (size_t)(128 * 32 + Co * 32) + 2 * sizeof(uint64_t) + 16;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024) !=
+            cudaSuccess)
+            return 2;
+        attr = true;
     }
-    const dim3 grid((unsigned)((Ci + WBN - 1) / WBN), (unsigned)((Co + WBM - 1) / WBM), (unsigned)(nk * KV));
     cudaStream_t s = (cudaStream_t)stream;
-    k_conv_wgrad<<<grid, WTHREADS, 0, s>>>((const bf16 *)x, ldx, (const bf16 *)dy, ldy, dw, a, Ci, Co, k, chunk);
+    const dim3 grid((unsigned)((KV * Ci + 127) / 128), (unsigned)nk, 1);
+    k_conv_wgrad_tc<<<grid, WTTHREADS, smem, s>>>((const bf16 *)x, ldx, (const bf16 *)dy, ldy, dw, a, Ci, Co, k, chunk,
+                                                  cols, kWgradLbo, kWgradSbo);
     if (db) {
         const long long blocks = (P + 8 * 64 - 1) / (8 * 64);
         const dim3 g2((unsigned)(blocks < 1024 ? blocks : 1024), (unsigned)((Co + 31) / 32), 1);
