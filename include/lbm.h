@@ -64,7 +64,9 @@ typedef enum {
  * the other modes.  LBM_FP32 and the 16-bit modes store each value as its
  * deviation f_i - w_i R from a rest equilibrium, rounded to nearest even,
  * where R is the density (rounded to FP16, kept per cell and component) that
- * the cell the value streams into had at its last update. */
+ * the cell the value streams into had at its last update.  FP16 holds that
+ * deviation times 2^12 (an exact power of two), to keep small deviations out of
+ * FP16's subnormal range. */
 typedef enum {
     LBM_FP64 = 0,
     LBM_FP32 = 1,

@@ -57,21 +57,23 @@ template <> struct Pair<float> {
         b = v.y + 0.f;
     }
 };
-template <> struct Pair<__half> {
+template <> struct Pair<__half> {  // values scaled as in Storage<__half>
     using P = __half2;
     __device__ static __forceinline__ void load(const P *p, float &a, float &b) {
         const float2 v = __half22float2(__ldg(p));
-        a = v.x + 0.f;
-        b = v.y + 0.f;
+        a = v.x * kF16Unscale + 0.f;
+        b = v.y * kF16Unscale + 0.f;
     }
     __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
-        *p = __floats2half2_rn(a - sa, b - sb);
+        *p = __floats2half2_rn((a - sa) * kF16Scale, (b - sb) * kF16Scale);
     }
-    __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = __floats2half2_rn(a, b); }
+    __device__ static __forceinline__ void store_d(P *p, float a, float b) {
+        *p = __floats2half2_rn(a * kF16Scale, b * kF16Scale);
+    }
     __device__ static __forceinline__ void load_shared(const P *p, float &a, float &b) {
         const float2 v = __half22float2(*p);
-        a = v.x + 0.f;
-        b = v.y + 0.f;
+        a = v.x * kF16Unscale + 0.f;
+        b = v.y * kF16Unscale + 0.f;
     }
 };
 template <> struct Pair<__nv_bfloat16> {
