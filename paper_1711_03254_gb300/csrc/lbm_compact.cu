@@ -155,12 +155,13 @@ __device__ __forceinline__ void ref_pair(const StepArgs &a, int b, uint32_t sk, 
     }
 }
 
-// threads per block: 128 for the update lets 6 (16-bit storage), 5 (FP32) or
-// 4 (FP64, FP64 arithmetic) blocks share an SM within its registers; measured
-// on GB300, 6 blocks cost the FP32 kernel spills and 4 % time, 5 blocks cost
-// the FP16 kernel 1 %
+// threads per block: 128 for the update lets 7 (16-bit storage), 5 (FP32) or
+// 4 (FP64, FP64 arithmetic) blocks share an SM within its registers.  Measured
+// on GB300 (256^3 packed spheres): 16-bit storage 6 / 7 / 8 blocks 0.396 /
+// 0.381 / 0.385 ms (7 and 8 spill 44 and 92 B to L1); FP32 at 6 blocks spills
+// and loses 4 % against 5.
 constexpr int kPsiThreads = 256, kCollideThreads = 128;
-template <class S> constexpr int collide_min_blocks() { return sizeof(S) == 2 ? 6 : (sizeof(S) == 4 ? 5 : 4); }
+template <class S> constexpr int collide_min_blocks() { return sizeof(S) == 2 ? 7 : (sizeof(S) == 4 ? 5 : 4); }
 
 template <class S>
 __global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
