@@ -70,13 +70,13 @@ NCU_TRAFFIC = {
     # 273.1 MB read + 103.1 MB written in one launch
     "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db"},
     # 192^3 packed spheres (2,830,487 non-solid cells; compact f 430 MB per buffer,
-    # larger than L2), ncu --set full: 274.2 MB read + 184.7 MB written in one launch
-    "k_collide_c/fp16s/spheres": {"bytes_per_fluid_cell": 162.1, "src": "a750f8b1db421af1"},
+    # larger than L2), ncu --set full: 274.3 MB read + 187.8 MB written in one launch
+    "k_collide_c/fp16s/spheres": {"bytes_per_fluid_cell": 163.3, "src": "00274a162abe3a82"},
 }
 # FP64 mode is bound by the FP64 pipe.  Executed FP64 flops per non-solid cell
 # (DADD + DMUL + 2 DFMA from ncu, 128^3 packed spheres, eq_order 0) and the
 # FP64 peak: 2 DFMA per clock per SM (152 SMs, 2.07 GHz) = 1.26 TFLOP/s.
-FP64_FLOPS = {"k_collide_c": {"flops_per_fluid_cell": 813.7, "src": "a750f8b1db421af1"}}
+FP64_FLOPS = {"k_collide_c": {"flops_per_fluid_cell": 813.7, "src": "00274a162abe3a82"}}
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cu", "lbm_fused.cu", "lbm_compact.cu"]
 
