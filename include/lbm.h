@@ -76,8 +76,7 @@ typedef enum {
 
 /* Kernel strategy for lbm_step. */
 typedef enum {
-    LBM_KERNEL_AUTO = 0,     /* cluster for instances of <= 32768 cells (n > 1 updates); else compact
-                                when the grid fits its coordinate limits; else two-pass */
+    LBM_KERNEL_AUTO = 0,     /* compact when the grid fits its coordinate limits, else two-pass */
     LBM_KERNEL_TWO_PASS = 1, /* density pre-pass, then stream+collide, over the non-solid cells */
     LBM_KERNEL_FUSED = 2,    /* single read of f: z-marching tiles with a recomputed density halo */
     LBM_KERNEL_CLUSTER = 3,  /* persistent: one thread-block cluster per instance, n updates per launch */

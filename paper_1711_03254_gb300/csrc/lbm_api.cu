@@ -22,7 +22,6 @@ thread_local std::string g_last_error;
 constexpr double kMaxSpeed = 0.57735026918962576;
 // the persistent cluster kernel loops each thread over cells of its instance
 constexpr long long kClusterMaxCells = 65536;
-constexpr long long kClusterAutoCells = 32768;
 
 size_t storage_bytes(lbm_precision p) {
     switch (p) {
@@ -185,15 +184,15 @@ lbm_status upload_params(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
-// Strategy for an n-update call.  AUTO: the persistent cluster kernel for
-// small instances advanced by several updates at once (launch overhead
-// dominates there), the fused kernel otherwise.
+// Strategy for an n-update call.  AUTO: the compact two-pass update when the
+// grid fits its packed coordinates, the dense two-pass one otherwise.
 lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
+    (void)n;
     if (ctx->kernel != LBM_KERNEL_AUTO) return ctx->kernel;
-    if (ctx->g.n <= kClusterAutoCells && n > 1) return LBM_KERNEL_CLUSTER;
     // measured on GB300: the two-pass update on the compact layout beats the
-    // dense two-pass one on porous (1.5x) and all-fluid (1.1x) grids, and the
-    // dense two-pass beats the fused one (1.2-2.2x)
+    // dense two-pass one on porous (1.5x) and all-fluid (1.1x) grids, the fused
+    // one (2-4x), and the persistent cluster kernel on every small case tried
+    // (16^3 to 32^3, 1 to 16 instances: 1.4-10x)
     return ctx->compact_ok ? LBM_KERNEL_COMPACT : LBM_KERNEL_TWO_PASS;
 }
 

@@ -436,7 +436,6 @@ def test_zero_updates_and_empty_steps(lbm, oracle_mod):
 def test_compact_limits_fall_back(lbm):
     """Beyond the compact layout's coordinate limits AUTO runs the dense
     two-pass update and an explicit request for COMPACT is refused."""
-    # 2049 x 4 x 4 = 32 784 cells: above the cluster kernel's AUTO range
     sim = lbm.Sim(2049, 4, 4, [dict(tau=(1.0, 1.0), G=-1.8)], precision="fp32")
     t = np.zeros((1, 4, 4, 2049), np.uint8)
     sim.set_geometry(t)
