@@ -78,7 +78,7 @@ NCU_TRAFFIC = {
 # FP64 peak: 2 DFMA per clock per SM (152 SMs, 2.07 GHz) = 1.26 TFLOP/s.
 FP64_FLOPS = {"k_collide_c": {"flops_per_fluid_cell": 813.7, "src": "00274a162abe3a82"}}
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
-KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cu", "lbm_fused.cu", "lbm_compact.cu"]
+KERNEL_SOURCES = ["lbm_device.cuh", "lbm_pair2.cuh", "lbm_kernels.cu", "lbm_fused.cu", "lbm_compact.cu"]
 
 
 def sources_hash() -> str:
@@ -289,8 +289,12 @@ def main():
     part = max(timing, key=lambda k: timing[k][0])
     part_ms, part_launches = timing[part]
     strategy = lbm.lbm_resolved_kernel(sim.ctx, args.steps)
-    suffix = "_c" if strategy == "compact" else ""
-    kernel_name = {"psi": "k_psi", "collide": "k_collide", "fused": "k_fused", "cluster": "k_cluster"}[part] + suffix
+    kernel_name = {"psi": "k_psi", "collide": "k_collide", "fused": "k_fused", "cluster": "k_cluster"}[part]
+    if strategy == "compact":
+        # compact layout: packed-pair update for the FP32-arithmetic storages,
+        # pipelined psi pass for the 16-bit ones
+        kernel_name += {"psi": "_cp" if F_BYTES[args.precision] == 2 else "_c",
+                        "collide": "_c" if args.precision == "fp64" else "_c2"}[part]
     per_cell = alg_bytes_per_cell(part, args.precision)
     updates_per_launch = args.steps if part == "cluster" else 1
     bytes_per_launch = per_cell * fluid * updates_per_launch

@@ -13,13 +13,14 @@
 // write contiguous runs of every plane, and the component pairs halve the
 // load, store and address instructions.
 //
-//   k_psi_c      S1-S3 as k_psi: pull, sum to rho_alpha, store psi.
-//   k_collide_c  S1-S7 as k_collide.
-// The arithmetic is the same device code as the dense kernels (moments_of,
-// sc_forces, relax, collide_prep/collide_pair), in the same order, so both
-// layouts give identical bits.
+//   k_psi_c, k_psi_cp  S1-S3 as k_psi: pull, sum to rho_alpha, store psi.
+//   k_collide_c        S1-S7 as k_collide (FP64: the scalar device code of
+//                      the dense kernels, so both layouts give identical bits).
+//   k_collide_c2       S1-S7 for the FP32-arithmetic storages, both components
+//                      as packed FP32 pairs (lbm_pair2.cuh).
 #include "lbm_internal.h"
 #include "lbm_device.cuh"
+#include "lbm_pair2.cuh"
 
 namespace lbm {
 
@@ -98,6 +99,38 @@ template <class T> struct Vec2;
 template <> struct Vec2<double> { using V = double2; };
 template <> struct Vec2<float> { using V = float2; };
 
+// Both components of a stored value as one FP32 pair in storage units, for
+// the packed-pair arithmetic (FP32 and 16-bit storages).  kUnscale takes a
+// sum of stored values to FP32 units and kScale a result back (2^-12 and 2^12
+// for the scaled FP16 deviations, exact powers of two).
+template <class S> struct Pair2;
+template <> struct Pair2<float> {
+    using P = float2;
+    static constexpr bool kScaled = false;
+    static constexpr float kUnscale = 1.f, kScale = 1.f;
+    __device__ static __forceinline__ float2 load(const P *p) { return __ldg(p); }
+    __device__ static __forceinline__ float2 load_shared(const P *p) { return *p; }
+    __device__ static __forceinline__ void store(P *p, float2 v) { *p = v; }
+};
+template <> struct Pair2<__half> {
+    using P = __half2;
+    static constexpr bool kScaled = true;
+    static constexpr float kUnscale = kF16Unscale, kScale = kF16Scale;
+    __device__ static __forceinline__ float2 load(const P *p) { return __half22float2(__ldg(p)); }
+    __device__ static __forceinline__ float2 load_shared(const P *p) { return __half22float2(*p); }
+    __device__ static __forceinline__ void store(P *p, float2 v) { *p = __float22half2_rn(v); }
+};
+template <> struct Pair2<__nv_bfloat16> {
+    using P = __nv_bfloat162;
+    static constexpr bool kScaled = false;
+    static constexpr float kUnscale = 1.f, kScale = 1.f;
+    __device__ static __forceinline__ float2 load(const P *p) { return __bfloat1622float2(__ldg(p)); }
+    __device__ static __forceinline__ float2 load_shared(const P *p) { return __bfloat1622float2(*p); }
+    __device__ static __forceinline__ void store(P *p, float2 v) { *p = __float22bfloat162_rn(v); }
+};
+// FP32 arithmetic (packed pairs) for every storage but FP64
+template <class S> constexpr bool packed_pairs() { return sizeof(S) < 8; }
+
 struct CompactCell {
     int x, y, z;
     uint32_t word;
@@ -155,6 +188,22 @@ __device__ __forceinline__ void ref_pair(const StepArgs &a, int b, uint32_t sk, 
     }
 }
 
+// pull_pairs for the packed-pair path: the 19 stored pairs in storage units.
+template <class S>
+__device__ __forceinline__ void pull_pairs2(const typename Pair2<S>::P *__restrict__ f, uint32_t n, uint32_t sk,
+                                            const CNbr &nb, uint32_t sw, float2 (&v)[kQ]) {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const bool bb = (sw >> opp(i)) & 1u;
+        const uint32_t idx = bb ? (uint32_t)opp(i) * n + sk : (uint32_t)i * n + nb.src(i);
+        v[i] = Pair2<S>::load(f + idx);
+    }
+}
+
+__device__ __forceinline__ float2 ref_pair2(const StepArgs &a, int b, uint32_t sk) {
+    return __half22float2(__ldg((const __half2 *)a.ref_in + (size_t)b * a.kmax + sk));
+}
+
 // threads per block: 128 for the update lets 7 (16-bit storage), 5 (FP32) or
 // 4 (FP64, FP64 arithmetic) blocks share an SM within its registers.  Measured
 // on GB300 (256^3 packed spheres): 16-bit storage 6 / 7 / 8 blocks 0.396 /
@@ -180,11 +229,19 @@ __global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
     } else {
         const typename Pair<S>::P *f = (const typename Pair<S>::P *)a.f_in + (size_t)b * kQ * a.kmax;
         auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-            T v0[kQ], v1[kQ], r0, r1;
-            pull_pairs<S>(f, a.kmax, sk, nb, sw, v0, v1);
-            ref_pair<S>(a, b, sk, r0, r1);
-            p0 = density_of<T, Storage<S>::shifted>(v0, r0);
-            p1 = density_of<T, Storage<S>::shifted>(v1, r1);
+            if constexpr (packed_pairs<S>()) {
+                float2 v[kQ];
+                pull_pairs2<S>(f, a.kmax, sk, nb, sw, v);
+                const float2 d = density2<Pair2<S>::kScaled>(v, ref_pair2(a, b, sk), Pair2<S>::kUnscale);
+                p0 = d.x;
+                p1 = d.y;
+            } else {
+                T v0[kQ], v1[kQ], r0, r1;
+                pull_pairs<S>(f, a.kmax, sk, nb, sw, v0, v1);
+                ref_pair<S>(a, b, sk, r0, r1);
+                p0 = density_of<T, Storage<S>::shifted>(v0, r0);
+                p1 = density_of<T, Storage<S>::shifted>(v1, r1);
+            }
         };
         CNbr own;
         own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
@@ -221,6 +278,7 @@ template <int BYTES> __device__ __forceinline__ void cp_async_ca(void *smem, con
 }
 __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <class S> constexpr size_t psi_pipe_smem() {
     return 2 * ((size_t)kQ * sizeof(typename Pair<S>::P) + sizeof(__half2)) * kPsiPipeThreads;
@@ -283,17 +341,28 @@ __global__ void __launch_bounds__(kPsiPipeThreads) k_psi_cp(StepArgs a) {
             p0 = p.rho_in[0];
             p1 = p.rho_in[1];
         } else {
-            T v0[kQ], v1[kQ];
+            if constexpr (packed_pairs<S>()) {
+                float2 v[kQ];
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) Pair<S>::load_shared(&vbuf[(st * kQ + i) * kPsiPipeThreads + tid], v0[i], v1[i]);
-            T r0 = T(0), r1 = T(0);
-            if constexpr (Storage<S>::shifted) {
-                const __half2 r = rbuf[st * kPsiPipeThreads + tid];
-                r0 = __low2float(r);
-                r1 = __high2float(r);
+                for (int i = 0; i < kQ; ++i) v[i] = Pair2<S>::load_shared(&vbuf[(st * kQ + i) * kPsiPipeThreads + tid]);
+                const float2 d = density2<Pair2<S>::kScaled>(v, __half22float2(rbuf[st * kPsiPipeThreads + tid]),
+                                                             Pair2<S>::kUnscale);
+                p0 = d.x;
+                p1 = d.y;
+            } else {
+                T v0[kQ], v1[kQ];
+#pragma unroll
+                for (int i = 0; i < kQ; ++i)
+                    Pair<S>::load_shared(&vbuf[(st * kQ + i) * kPsiPipeThreads + tid], v0[i], v1[i]);
+                T r0 = T(0), r1 = T(0);
+                if constexpr (Storage<S>::shifted) {
+                    const __half2 r = rbuf[st * kPsiPipeThreads + tid];
+                    r0 = __low2float(r);
+                    r1 = __high2float(r);
+                }
+                p0 = density_of<T, Storage<S>::shifted>(v0, r0);
+                p1 = density_of<T, Storage<S>::shifted>(v1, r1);
             }
-            p0 = density_of<T, Storage<S>::shifted>(v0, r0);
-            p1 = density_of<T, Storage<S>::shifted>(v1, r1);
         }
         V out;
         out.x = p0;
@@ -456,6 +525,118 @@ __global__ void k_layout(bool to_compact, const S *__restrict__ fin, S *__restri
     }
 }
 
+// k_collide_c2: the update of k_collide_c with both components as packed FP32
+// pairs (lbm_pair2.cuh), for the FP32 and 16-bit storages.  Same steps and
+// memory accesses; the neighbour psi pairs enter the force sums unselected
+// (the cell's own pair at SOLID neighbours, removed in forces2), and the
+// storage scale of FP16 is folded into the moment sums and the weights.
+template <class S, int EQ>
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c2(StepArgs a) {
+    using P = typename Pair2<S>::P;
+    const int b = blockIdx.y;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
+    const CompactCell c = compact_cell(a, b, k);
+    const uint32_t word = c.word;
+    const InstParam<float> &p = ((const InstParam<float> *)a.par)[b];
+    const uint32_t n = a.kmax;
+    const float2 *psi = (const float2 *)a.psi + (size_t)b * n;
+    __half2 *rout = (__half2 *)a.ref_out + (size_t)b * n;
+    const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
+    float *mac = (float *)a.macro + (long long)b * 5 * a.g.n;
+    CNbr own;
+    own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
+    if (cell_type(word) == kInlet) {
+        // equilibrium at (rho_in, u_in) as deviations from the reference pairs
+        typename Pair<S>::P *fo = (typename Pair<S>::P *)a.f_out + (size_t)b * kQ * n;
+        const float uu = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const bool self_ref = i == 0 || ((word >> i) & 1u);
+            const float2 q = self_ref ? make_float2(p.rho_in[0], p.rho_in[1]) : __ldg(psi + own.dst(i));
+            Pair<S>::store(fo + (size_t)i * n + k, feq_dir<float, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
+                           feq_dir<float, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu),
+                           wgt<float>(i) * ref_value(q.x), wgt<float>(i) * ref_value(q.y));
+        }
+        rout[k] = __floats2half2_rn(p.rho_in[0], p.rho_in[1]);
+        if (a.write_macro) {
+            mac[cell] = p.rho_in[0];
+            mac[a.g.n + cell] = p.rho_in[1];
+            mac[2 * a.g.n + cell] = p.u_in[0];
+            mac[3 * a.g.n + cell] = p.u_in[1];
+            mac[4 * a.g.n + cell] = p.u_in[2];
+        }
+        return;
+    }
+    // the psi pairs of the 18 neighbours (the cell's own at SOLID ones) start
+    // on their way into this thread's shared-memory slots now, so that their
+    // latency overlaps the pull of f; no other thread reads the slots
+    __shared__ float2 qs[kQ - 1][kCollideThreads];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        const bool solid = (word >> i) & 1u;
+        cp_async_ca<8>(&qs[i - 1][tid], psi + (solid ? k : own.dst(i)));
+    }
+    cp_async_commit_group();
+    const P *f = (const P *)a.f_in + (size_t)b * kQ * n;
+    P *fo = (P *)a.f_out + (size_t)b * kQ * n;
+    Moments2 m;
+    auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
+        float2 v[kQ];
+        pull_pairs2<S>(f, n, sk, nb, sw, v);
+        m = moments2<Pair2<S>::kScaled>(v, ref_pair2(a, b, sk), Pair2<S>::kUnscale);
+    };
+    {
+        int xu;
+        uint32_t ku, wu;
+        if (outlet_source(a, b, c, own, xu, ku, wu)) {
+            CNbr up;
+            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
+            pull(up, ku, wu);
+        } else {
+            pull(own, k, word);
+        }
+    }
+    // psi pairs of the 18 neighbours into the force sums; the stores keep the
+    // FP16 reference pair of each direction (the density of the cell the
+    // value streams into; the cell's own at SOLID neighbours)
+    const __half2 rho_h = __float22half2_rn(m.rho);
+    ForceSums2 bs;
+    bs.clear();
+    __half2 Rp[kQ];
+    Rp[0] = rho_h;
+    cp_async_wait_all();
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        const bool solid = (word >> i) & 1u;
+        const float2 q = qs[i - 1][tid];
+        bs.add(i, q);
+        Rp[i] = solid ? rho_h : __float22half2_rn(q);
+    }
+    const float2 psi_own = (word & 0x7FFFEu) ? __ldg(psi + k) : bc2(0.f);
+    const Forces2 F = forces2(bs, psi_own, word, m.rho, p, a.wall_model);
+    const Relax<float> R = relax2(m, F, p);
+    const Prep2 cp = prep2<EQ>(m, R, F);
+    constexpr float sc = Pair2<S>::kScale;
+    Pair2<S>::store(fo + k, rest2<EQ>(cp, __half22float2(Rp[0]), sc));
+#pragma unroll
+    for (int i = 1; i < kQ; i += 2) {
+        float2 vi, vo;
+        pair2<EQ>(cp, i, __half22float2(Rp[i]), __half22float2(Rp[i + 1]), sc, vi, vo);
+        Pair2<S>::store(fo + (size_t)i * n + k, vi);
+        Pair2<S>::store(fo + (size_t)(i + 1) * n + k, vo);
+    }
+    rout[k] = rho_h;
+    if (a.write_macro) {
+        mac[cell] = m.rho.x;
+        mac[a.g.n + cell] = m.rho.y;
+        mac[2 * a.g.n + cell] = R.ux;
+        mac[3 * a.g.n + cell] = R.uy;
+        mac[4 * a.g.n + cell] = R.uz;
+    }
+}
+
 template <class S>
 static cudaError_t launch_compact_t(const StepArgs &a) {
     const long long m = a.list_max > 0 ? a.list_max : 1;
@@ -488,10 +669,17 @@ static cudaError_t launch_compact_t(const StepArgs &a) {
     // (a persistent variant that prefetches the next cell with cp.async, as the
     // psi pass does, measured 10 % slower here: the update is issue-bound, and
     // the prefetch buffers cost occupancy and registers)
-    if (a.eq_order == 0)
-        k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
-    else
-        k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
+    if constexpr (packed_pairs<S>()) {
+        if (a.eq_order == 0)
+            k_collide_c2<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
+        else
+            k_collide_c2<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
+    } else {
+        if (a.eq_order == 0)
+            k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
+        else
+            k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
+    }
     record_event(a, 2);
     return cudaGetLastError();
 }

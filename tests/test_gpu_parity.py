@@ -264,22 +264,32 @@ def test_distributions_roundtrip(lbm, oracle_mod, kernel):
     assert np.all(f[:, :, :, t == W.SOLID] == 0.0)  # SOLID cells carry no distributions
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s", "bf16s"])
-def test_layouts_give_identical_bits(lbm, precision):
-    """The compact and the dense layout run the same arithmetic: a run that
-    switches strategy every few updates (converting the layout each time)
-    ends bitwise equal to a dense-only run, fields and distributions."""
+LAYOUT_BOUND = {"fp32": 1e-5, "fp16s": 1e-3, "bf16s": 6e-3}
+
+
+def _layout_case(lbm, precision, kernel):
     shape = (37, 21, 11)
     t, r1, r2, u = _random_geometry(shape, 0.3, 71, lo=0.3, hi=0.7)
     p = [dict(tau=(0.8, 1.3), G=-1.9, rho_s=-0.2, g=(2e-5, 1e-5, 0)),
          dict(tau=(1.1, 0.6), G=-2.1, rho_s=0.3, g=(0, 0, 3e-5))]
     t2 = np.stack([t, np.roll(t, 5, axis=2)])
     r1s, r2s, us = np.stack([r1, np.roll(r1, 5, axis=2)]), np.stack([r2, np.roll(r2, 5, axis=2)]), np.stack([u, u])
-    dense = lbm.Sim(*shape, p, precision=precision, kernel="two_pass")
-    mixed = lbm.Sim(*shape, p, precision=precision, kernel="compact")
-    for s_ in (dense, mixed):
-        s_.set_geometry(t2)
-        s_.set_fields(r1s, r2s, us)
+    s_ = lbm.Sim(*shape, p, precision=precision, kernel=kernel)
+    s_.set_geometry(t2)
+    s_.set_fields(r1s, r2s, us)
+    return s_
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s", "bf16s"])
+def test_layouts_agree(lbm, precision):
+    """A run that switches between the compact and the dense strategy every
+    few updates (converting the layout each time) against a dense-only run.
+    FP64 runs the same scalar arithmetic in both layouts and ends bitwise
+    equal, fields and distributions.  The FP32-arithmetic storages run the
+    compact update on packed FP32 pairs, rounded in another order, so there
+    the two agree within the precision's parity bound."""
+    dense = _layout_case(lbm, precision, "two_pass")
+    mixed = _layout_case(lbm, precision, "compact")
     for rnd in range(4):
         dense.step(3)
         lbm.lbm_set_kernel(mixed.ctx, "compact" if rnd % 2 == 0 else "two_pass")
@@ -287,9 +297,31 @@ def test_layouts_give_identical_bits(lbm, precision):
     lbm.lbm_set_kernel(mixed.ctx, "compact")
     mixed.step(2)
     dense.step(2)
-    for x, y in zip(dense.get_fields(), mixed.get_fields()):
+    if precision == "fp64":
+        for x, y in zip(dense.get_fields(), mixed.get_fields()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(dense.get_f(), mixed.get_f())
+    else:
+        g, o = mixed.get_fields(), dense.get_fields()
+        e = _errs(g, o)
+        assert _rel(g[0], o[0]) < LAYOUT_BOUND[precision] and _rel(g[1], o[1]) < LAYOUT_BOUND[precision], e
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s", "bf16s"])
+def test_layout_conversion_is_exact(lbm, precision):
+    """Converting the state between the compact and the dense layout changes
+    no bit: compact updates interrupted by reads of f (each converts to the
+    dense layout, the next update back) end bitwise equal to the same
+    updates run without interruption."""
+    straight = _layout_case(lbm, precision, "compact")
+    broken = _layout_case(lbm, precision, "compact")
+    straight.step(6)
+    for _ in range(3):
+        broken.step(2)
+        broken.get_f()
+    for x, y in zip(straight.get_fields(), broken.get_fields()):
         assert np.array_equal(x, y)
-    assert np.array_equal(dense.get_f(), mixed.get_f())
+    assert np.array_equal(straight.get_f(), broken.get_f())
 
 
 # ------------------------------------------------------------------ batched persistent launch (sweeps)
