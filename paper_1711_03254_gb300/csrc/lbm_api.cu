@@ -216,70 +216,48 @@ void default_tiling(const lbm_ctx *ctx, int &tile, int &zchunk) {
 }
 
 // Lists of the non-solid cells of every instance (in cell order) for the
-// two-pass kernels, and the static pseudo-potential of the SOLID cells.
-// type_of(global cell index) gives the cell type.
-// With the compact layout available, also the packed coordinates of the listed
-// cells, their geometry words (gathered on the device from ctx->link, which
-// must hold the geometry already) and the per-row occupancy words.
-template <class F> lbm_status build_cell_lists(lbm_ctx *ctx, F type_of) {
-    const long long n = ctx->g.n;
-    const int nx = ctx->g.nx, ny = ctx->g.ny, nz = ctx->g.nz, W = ctx->words;
-    const size_t rows = (size_t)ny * nz;
-    std::vector<uint32_t> lst((size_t)ctx->cfg.batch * n), xyz;
-    std::vector<uint2> tab;
-    if (ctx->compact_ok) {
-        xyz.assign((size_t)ctx->cfg.batch * n, 0u);
-        tab.assign((size_t)ctx->cfg.batch * (rows + 1) * W, make_uint2(0u, 0u));
+// two-pass kernels, and the static pseudo-potential of the SOLID cells, built
+// on the device from the geometry words in ctx->link.  With the compact layout
+// available, also the packed coordinates of the listed cells, their geometry
+// words and the per-row occupancy words.  One read-back of the per-instance
+// counts sets the compact stride kmax (the largest count).
+lbm_status build_cell_lists(lbm_ctx *ctx) {
+    const int B = ctx->cfg.batch;
+    const size_t rows = (size_t)ctx->g.ny * ctx->g.nz;
+    uint32_t *rowcnt = (uint32_t *)ctx->dalloc((size_t)B * rows * 4);
+    if (!rowcnt) return ctx->fail(LBM_ERR_OOM, "cell lists: device allocation failed");
+    uint2 *tab = ctx->compact_ok ? ctx->rowtab : nullptr;
+    std::vector<int> cnt(B);
+    cudaError_t e = launch_row_counts(ctx->link, ctx->g, B, rowcnt, ctx->list_count, tab, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cnt.data(), ctx->list_count, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        ctx->dfree(rowcnt);
+        return ctx->cuda_fail(e, "cell lists");
     }
-    std::vector<int> cnt(ctx->cfg.batch);
     long long mx = 0, total = 0;
-    for (int b = 0; b < ctx->cfg.batch; ++b) {
-        uint32_t c = 0;
-        for (size_t r = 0; r < rows; ++r) {
-            for (int x = 0; x < nx; ++x) {
-                const long long k = (long long)r * nx + x;
-                uint2 *e = ctx->compact_ok ? &tab[((size_t)b * (rows + 1) + r) * W + (x >> 5)] : nullptr;
-                if (e && (x & 31) == 0) e->x = c;
-                if (type_of((size_t)b * n + k) == 1u) continue;
-                lst[(size_t)b * n + c] = (uint32_t)k;
-                if (e) {
-                    e->y |= 1u << (x & 31);
-                    xyz[(size_t)b * n + c] = (uint32_t)x | ((uint32_t)(r % ny) << 11) | ((uint32_t)(r / ny) << 22);
-                }
-                ++c;
-            }
-        }
-        if (ctx->compact_ok)
-            for (int w = 0; w < W; ++w) tab[((size_t)b * (rows + 1) + rows) * W + w].x = c;
-        cnt[b] = (int)c;
-        total += c;
-        if ((long long)c > mx) mx = c;
+    for (int b = 0; b < B; ++b) {
+        total += cnt[b];
+        if ((long long)cnt[b] > mx) mx = cnt[b];
     }
     ctx->list_max = mx;
     ctx->nonsolid = total;
-    LBM_CUDA(cudaMemcpyAsync(ctx->list, lst.data(), lst.size() * 4, cudaMemcpyHostToDevice, ctx->stream), "cell list");
-    LBM_CUDA(cudaMemcpyAsync(ctx->list_count, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice,
-                             ctx->stream),
-             "cell list");
-    LBM_CUDA(launch_psi_solid(ctx->link, ctx->psi, ctx->fp64(), ctx->g, ctx->cfg.batch, ctx->dpar, ctx->stream),
-             "solid psi");
-    ctx->launches += 1;
-    if (ctx->compact_ok) {
-        // the compact arrays use the instance stride kmax = list_max
-        std::vector<uint32_t> xyzc((size_t)ctx->cfg.batch * mx);
-        for (int b = 0; b < ctx->cfg.batch; ++b)
-            std::memcpy(&xyzc[(size_t)b * mx], &xyz[(size_t)b * n], (size_t)cnt[b] * 4);
-        LBM_CUDA(cudaMemcpyAsync(ctx->cxyz, xyzc.data(), xyzc.size() * 4, cudaMemcpyHostToDevice, ctx->stream),
-                 "compact coordinates");
-        LBM_CUDA(cudaMemcpyAsync(ctx->rowtab, tab.data(), tab.size() * sizeof(uint2), cudaMemcpyHostToDevice,
-                                 ctx->stream),
-                 "row table");
-        LBM_CUDA(launch_compact_links(ctx->list, ctx->list_count, ctx->link, ctx->clink, ctx->g, ctx->cfg.batch,
-                                      (uint32_t)mx, ctx->stream),
-                 "compact links");
-        ctx->launches += 1;
-    }
-    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "cell list");
+    const size_t cells = ctx->cells();
+    e = cudaMemsetAsync(ctx->list, 0, cells * 4, ctx->stream);
+    if (e == cudaSuccess && ctx->compact_ok) e = cudaMemsetAsync(ctx->cxyz, 0, cells * 4, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_row_fill(ctx->link, ctx->g, B, rowcnt, ctx->list, ctx->compact_ok ? ctx->cxyz : nullptr, tab,
+                            (uint32_t)mx, ctx->stream);
+    if (e == cudaSuccess) e = launch_psi_solid(ctx->link, ctx->psi, ctx->fp64(), ctx->g, B, ctx->dpar, ctx->stream);
+    if (e == cudaSuccess && ctx->compact_ok)
+        e = launch_compact_links(ctx->list, ctx->list_count, ctx->link, ctx->clink, ctx->g, B, (uint32_t)mx,
+                                 ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    ctx->dfree(rowcnt);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cell lists");
+    ctx->launches += ctx->compact_ok ? 5 : 4;
     return LBM_OK;
 }
 
@@ -548,25 +526,37 @@ lbm_status lbm_set_tiling(lbm_ctx *ctx, int tile, int zchunk) {
 lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *cell_type) {
     if (!ctx || !cell_type) return ctx ? ctx->fail(LBM_ERR_ARG, "lbm_set_geometry: null argument") : LBM_ERR_ARG;
     const size_t cells = ctx->cells();
-    for (int b = 0; b < ctx->cfg.batch; ++b) {
-        bool any_fluid = false;
-        for (long long k = 0; k < ctx->g.n; ++k) {
-            const uint8_t t = cell_type[(size_t)b * ctx->g.n + k];
-            if (t > 3) return ctx->fail(LBM_ERR_ARG, "lbm_set_geometry: cell type above 3");
-            any_fluid |= t == 0;
-        }
-        if (!any_fluid) return ctx->fail(LBM_ERR_ARG, "lbm_set_geometry: an instance has no FLUID cell");
-    }
+    const int B = ctx->cfg.batch;
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
-    uint8_t *dt = (uint8_t *)ctx->dalloc(cells);
+    // the types are checked on the device, before anything of the context changes
+    uint8_t *dt = (uint8_t *)ctx->dalloc(cells + sizeof(int) * (size_t)(B + 1) + 16);
     if (!dt) return ctx->fail(LBM_ERR_OOM, "lbm_set_geometry: device allocation failed");
+    int *dflags = (int *)(dt + ((cells + 15) / 16) * 16);
+    std::vector<int> flags((size_t)B + 1);
     cudaError_t e = cudaMemcpyAsync(dt, cell_type, cells, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = launch_links(dt, ctx->link, ctx->g, ctx->cfg.batch, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dflags, 0, flags.size() * sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = launch_check_types(dt, ctx->g, B, dflags, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(flags.data(), dflags, flags.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        ctx->dfree(dt);
+        return ctx->cuda_fail(e, "lbm_set_geometry");
+    }
+    ctx->launches += 1;
+    const char *bad = flags[0] ? "lbm_set_geometry: cell type above 3" : nullptr;
+    for (int b = 0; b < B && !bad; ++b)
+        if (!flags[1 + b]) bad = "lbm_set_geometry: an instance has no FLUID cell";
+    if (bad) {
+        ctx->dfree(dt);
+        return ctx->fail(LBM_ERR_ARG, bad);
+    }
+    e = launch_links(dt, ctx->link, ctx->g, B, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     ctx->dfree(dt);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_set_geometry");
     ctx->launches += 1;
-    lbm_status s = build_cell_lists(ctx, [&](size_t gk) { return (uint32_t)cell_type[gk]; });
+    lbm_status s = build_cell_lists(ctx);
     if (s != LBM_OK) return s;
     ctx->has_geometry = true;
     ctx->has_fields = false;
@@ -831,13 +821,8 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes) {
     LBM_CUDA(cudaMemcpyAsync(ctx->usnap, p, h.usnap_bytes, cudaMemcpyHostToDevice, ctx->stream), "set_state usnap");
     LBM_CUDA(cudaStreamSynchronize(ctx->stream), "set_state sync");
     {
-        const uint32_t *words = reinterpret_cast<const uint32_t *>((const char *)buf + sizeof(h) + h.f_bytes +
-                                                                   h.ref_bytes);
-        lbm_status s = build_cell_lists(ctx, [&](size_t gk) {
-            uint32_t w;
-            std::memcpy(&w, words + gk, 4);
-            return (w >> 24) & 3u;
-        });
+        // the geometry words are on the device now
+        lbm_status s = build_cell_lists(ctx);
         if (s != LBM_OK) return s;
     }
     ctx->step = h.step;

@@ -89,6 +89,18 @@ cudaError_t launch_f_convert(lbm_precision prec, const void *f, double *out, con
                              const Ref *ref, const uint32_t *link, const Grid &g, int batch, cudaStream_t s);
 int reduce_blocks(long long n);
 
+// geometry set-up (lbm_setup.cu).  flags[0] = 1 if a type is above 3,
+// flags[1 + b] = 1 if instance b has a FLUID cell (flags zeroed by the caller).
+cudaError_t launch_check_types(const uint8_t *type, const Grid &g, int batch, int *flags, cudaStream_t s);
+// rowcnt[b][row] = exclusive offsets of the non-solid cells of each row,
+// count[b] = non-solid cells of instance b; closing table row = count[b].
+cudaError_t launch_row_counts(const uint32_t *link, const Grid &g, int batch, uint32_t *rowcnt, int *count,
+                              uint2 *tab, cudaStream_t s);
+// list[b][rank] (stride n), cxyz[b][rank] (stride kmax) and the row table
+// from the offsets of launch_row_counts; cxyz and tab may be NULL.
+cudaError_t launch_row_fill(const uint32_t *link, const Grid &g, int batch, uint32_t *rowstart, uint32_t *list,
+                            uint32_t *cxyz, uint2 *tab, uint32_t kmax, cudaStream_t s);
+
 // compact layout
 constexpr int kCompactMaxX = 2048, kCompactMaxY = 2048, kCompactMaxZ = 1024;
 cudaError_t launch_compact(const StepArgs &a);
