@@ -136,14 +136,18 @@ struct CompactCell {
     uint32_t word;
 };
 
-__device__ __forceinline__ CompactCell compact_cell(const StepArgs &a, int b, uint32_t k) {
+// cell from its packed coordinates p and geometry word
+__device__ __forceinline__ CompactCell unpack_cell(uint32_t p, uint32_t word) {
     CompactCell c;
-    const uint32_t p = __ldg(a.cxyz + (size_t)b * a.kmax + k);
     c.x = (int)(p & 2047u);
     c.y = (int)((p >> 11) & 2047u);
     c.z = (int)(p >> 22);
-    c.word = __ldg(a.clink + (size_t)b * a.kmax + k);
+    c.word = word;
     return c;
+}
+
+__device__ __forceinline__ CompactCell compact_cell(const StepArgs &a, int b, uint32_t k) {
+    return unpack_cell(__ldg(a.cxyz + (size_t)b * a.kmax + k), __ldg(a.clink + (size_t)b * a.kmax + k));
 }
 
 __device__ __forceinline__ const uint2 *instance_tab(const StepArgs &a, int b) {
@@ -301,8 +305,14 @@ __global__ void __launch_bounds__(kPsiPipeThreads) k_psi_cp(StepArgs a) {
     const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
 
     // start the copies of cell kk into stage st; returns its geometry word
-    auto issue = [&](uint32_t kk, int st) -> uint32_t {
-        const CompactCell c = compact_cell(a, b, kk);
+    // the packed coordinates and word of a cell are loaded one iteration before
+    // its copies are issued, so that issuing waits only for the row tables
+    const uint32_t *cxyz = a.cxyz + (size_t)b * a.kmax, *clink = a.clink + (size_t)b * a.kmax;
+    auto raw = [&](uint32_t kk, uint2 &pw) {
+        if (kk < count) pw = make_uint2(__ldg(cxyz + kk), __ldg(clink + kk));
+    };
+    auto issue = [&](uint32_t kk, uint2 pw, int st) -> uint32_t {
+        const CompactCell c = unpack_cell(pw.x, pw.y);
         if (cell_type(c.word) == kInlet) return c.word;
         auto copies = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
 #pragma unroll
@@ -328,12 +338,18 @@ __global__ void __launch_bounds__(kPsiPipeThreads) k_psi_cp(StepArgs a) {
     };
 
     uint32_t k = blockIdx.x * kPsiPipeThreads + tid;
-    uint32_t word = k < count ? issue(k, 0) : 0u;
+    uint2 pw0 = make_uint2(0u, 0u), pw1 = make_uint2(0u, 0u);
+    raw(k, pw0);
+    raw(k + stride, pw1);
+    uint32_t word = k < count ? issue(k, pw0, 0) : 0u;
     cp_async_commit_group();
     int st = 0;
     for (; k < count; k += stride) {
         const uint32_t kn = k + stride;
-        const uint32_t word_n = kn < count ? issue(kn, st ^ 1) : 0u;
+        uint2 pw2 = make_uint2(0u, 0u);
+        raw(kn + stride, pw2);
+        const uint32_t word_n = kn < count ? issue(kn, pw1, st ^ 1) : 0u;
+        pw1 = pw2;
         cp_async_commit_group();
         cp_async_wait_one();  // this thread's copies of stage st have landed
         T p0, p1;
