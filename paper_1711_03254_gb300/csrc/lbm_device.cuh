@@ -140,15 +140,12 @@ struct CNbr {
                                          const Grid &g) {
         const int ys[3] = {y == 0 ? g.ny - 1 : y - 1, y, y == g.ny - 1 ? 0 : y + 1};
         const int zs[3] = {z == 0 ? g.nz - 1 : z - 1, z, z == g.nz - 1 ? 0 : z + 1};
-        const bool first = x == 0, last = x == g.nx - 1;
         const int w = x >> 5, xb = x & 31;
         const uint32_t below = (1u << xb) - 1u;
-        // rank of the first cell of row r (r = rows: the instance's total)
-        auto row_rank = [&](int r) -> uint32_t { return __ldg(tb + (size_t)r * words).x; };
+        // own row: neighbours along x are the adjacent compact indices
         nb[0] = k;
-        // own row: neighbours along x are the adjacent compact indices unless x wraps
-        nb[1] = last ? row_rank(zs[1] * g.ny + ys[1]) : k + 1u;
-        nb[2] = first ? row_rank(zs[1] * g.ny + ys[1] + 1) - 1u : k - 1u;
+        nb[1] = k + 1u;
+        nb[2] = k - 1u;
 #pragma unroll
         for (int j = 3; j < kQ; ++j) {
             if (cx(j) != 0) continue;  // filled with the x = 0 member of its row below
@@ -156,15 +153,28 @@ struct CNbr {
             const uint2 e = __ldg(tb + (size_t)r * words + w);
             const uint32_t at = e.x + __popc(e.y & below);  // rank of (x, row)
             nb[j] = at;
-            // the +x and -x members of the same row (only the y or z face rows have them)
+            // the +x and -x members of the same row (only the y or z face rows have
+            // them): rank(x + 1) = rank(x) + [x non-solid], rank(x - 1) = rank(x) - 1
 #pragma unroll
             for (int m = 7; m < kQ; ++m) {
                 if (cy(m) != cy(j) || cz(m) != cz(j) || cx(m) == 0) continue;
-                if (cx(m) > 0)
-                    nb[m] = last ? row_rank(r) : at + ((e.y >> xb) & 1u);
-                else
-                    nb[m] = (first ? row_rank(r + 1) : at) - 1u;
+                nb[m] = cx(m) > 0 ? at + ((e.y >> xb) & 1u) : at - 1u;
             }
+        }
+        // x = 0 or nx - 1: the members across the periodic x boundary are the
+        // first (+x from nx - 1) or last (-x from 0) non-solid cell of their row
+        if (x == 0 || x == g.nx - 1) wrap_x(x, ys, zs, tb, words, g);
+    }
+
+    __device__ __forceinline__ void wrap_x(int x, const int (&ys)[3], const int (&zs)[3], const uint2 *__restrict__ tb,
+                                        int words, const Grid &g) {
+        auto row_rank = [&](int r) -> uint32_t { return __ldg(tb + (size_t)r * words).x; };
+#pragma unroll
+        for (int m = 1; m < kQ; ++m) {
+            if (cx(m) == 0) continue;
+            const int r = zs[1 + cz(m)] * g.ny + ys[1 + cy(m)];
+            if (cx(m) > 0 && x == g.nx - 1) nb[m] = row_rank(r);
+            if (cx(m) < 0 && x == 0) nb[m] = row_rank(r + 1) - 1u;
         }
     }
 };
