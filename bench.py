@@ -63,27 +63,29 @@ def alg_bytes_per_cell(part: str, precision: str) -> int:
     return 76 * s + 4 + 2 * ref  # fused, and each update of a cluster launch
 # DRAM traffic of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its fluid cells),
-# keyed by kernel/precision/workload, with the hash of the kernel sources it was
-# taken on; any change of the sources voids it.
+# keyed by kernel/precision/workload, with the hash of the source files the
+# kernel is built from at the time of the capture; any change of them voids it.
+COMPACT_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_pair2.cuh", "lbm_compact.cu"]
+DENSE_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_kernels.cu"]
 NCU_TRAFFIC = {
     # 128^3 packed spheres (837,994 non-solid cells), dense layout, ncu --set full:
     # 273.1 MB read + 103.1 MB written in one launch
-    "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db"},
+    "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db", "files": DENSE_SOURCES},
     # 192^3 packed spheres (2,830,487 non-solid cells; compact f 430 MB per buffer,
-    # larger than L2), ncu --set full: 274.3 MB read + 187.8 MB written in one launch
-    "k_collide_c/fp16s/spheres": {"bytes_per_fluid_cell": 163.3, "src": "00274a162abe3a82"},
+    # larger than L2), ncu --set full: 274.2 MB read + 192.3 MB written in one launch
+    "k_collide_c2/fp16s/spheres": {"bytes_per_fluid_cell": 164.8, "src": "4ac21a08ce947105",
+                                   "files": COMPACT_SOURCES},
 }
 # FP64 mode is bound by the FP64 pipe.  Executed FP64 flops per non-solid cell
 # (DADD + DMUL + 2 DFMA from ncu, 128^3 packed spheres, eq_order 0) and the
 # FP64 peak: 2 DFMA per clock per SM (152 SMs, 2.07 GHz) = 1.26 TFLOP/s.
-FP64_FLOPS = {"k_collide_c": {"flops_per_fluid_cell": 813.7, "src": "00274a162abe3a82"}}
+FP64_FLOPS = {"k_collide_c": {"flops_per_fluid_cell": 813.7, "src": "4ac21a08ce947105", "files": COMPACT_SOURCES}}
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
-KERNEL_SOURCES = ["lbm_device.cuh", "lbm_pair2.cuh", "lbm_kernels.cu", "lbm_fused.cu", "lbm_compact.cu"]
 
 
-def sources_hash() -> str:
+def sources_hash(files=COMPACT_SOURCES) -> str:
     h = hashlib.sha256()
-    for s in KERNEL_SOURCES:
+    for s in files:
         p = os.path.join(ROOT, "paper_1711_03254_gb300", "csrc", s)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -303,7 +305,7 @@ def main():
     key = f"{kernel_name}/{args.precision}/{args.workload}"
     tr = NCU_TRAFFIC.get(key)
     traffic = None
-    if tr and tr.get("src") == sources_hash():
+    if tr and tr.get("src") == sources_hash(tr["files"]):
         traffic = round(tr["bytes_per_fluid_cell"] * fluid * updates_per_launch)
     step_bytes = (2 * 38 * F_BYTES[args.precision] + 1) * fluid
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -318,7 +320,7 @@ def main():
             "step_frac": round(step_bytes / ((ms / args.steps) / 1e3) / 1e9 / hbm, 4)}
 
     fl = FP64_FLOPS.get(kernel_name)
-    if args.precision == "fp64" and fl and fl["src"] == sources_hash():
+    if args.precision == "fp64" and fl and fl["src"] == sources_hash(fl["files"]):
         # FP64 arithmetic: the FP64 pipe, not HBM, bounds the update
         tf = fl["flops_per_fluid_cell"] * fluid * updates_per_launch / avg_s / 1e12
         roof.update({"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 3),

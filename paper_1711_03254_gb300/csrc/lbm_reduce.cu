@@ -23,7 +23,7 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// Block-wide reduction of kRedVals values (the 8th is a max).
+// Block-wide reduction of kRedVals values (the 8th is a max), written by thread 0.
 __device__ void block_reduce(double (&acc)[kRedVals], double *out) {
     __shared__ double sh[kRedThreads / 32][kRedVals];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -66,8 +66,11 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(const T *__restr
         const double uu = ux * ux + uy * uy + uz * uz;
         acc[6] += uu;
         const bool finite = isfinite(r1) && isfinite(r2) && isfinite(uu);
-        acc[7] = fmax(acc[7], finite ? sqrt(uu) : 0.0);
-        acc[8] += finite ? 0.0 : 1.0;
+        // max |u|^2 here, its root once in k_reduce_final (sqrt is monotonic and
+        // correctly rounded, so the result is the same); GB300's FP64 pipe is
+        // what bounds this pass
+        acc[7] = fmax(acc[7], finite ? uu : 0.0);
+        if (!finite) acc[8] += 1.0;
         us[k] = mac[2 * g.n + k];
         us[g.n + k] = mac[3 * g.n + k];
         us[2 * g.n + k] = mac[4 * g.n + k];
@@ -84,6 +87,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double *__re
         for (int c = 0; c < kRedVals; ++c) acc[c] = c == 7 ? fmax(acc[c], p[c]) : acc[c] + p[c];
     }
     block_reduce(acc, out + (long long)b * kRedVals);
+    if (threadIdx.x == 0) out[(long long)b * kRedVals + 7] = sqrt(out[(long long)b * kRedVals + 7]);
 }
 
 int reduce_blocks(long long n) {
