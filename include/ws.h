@@ -44,8 +44,11 @@ int ws_conv3d_flip_weights(const void *w, void *wf, int Co, int Ci, int k, void 
 /* dw[co][t][ci] += sum_p dy[p][co] x[p + t - k/2][ci] and db[co] += sum_p dy[p][co]
  * (db may be NULL).  Accumulates: clear dw and db first.  Runs on the tcgen05
  * tensor cores with rows (tap, ci) in tiles of 128 and N = Co <= 256; x and dy
- * 16-byte aligned; chunks of 4096 positions add into dw with FP32 atomics, so
- * the summation order (and the last bits) varies from run to run. */
+ * 16-byte aligned.  Each chunk of 4096 positions writes its partial sums into a
+ * workspace the library holds (grown on demand with cudaMalloc, after draining
+ * the stream); the chunks are then added into dw in chunk order, so repeated
+ * calls give identical bits.  Errors: 1 bad argument, 2 allocation or launch
+ * failure. */
 int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float *dw, float *db, int N, int D, int H,
                          int W, int Ci, int Co, int k, void *stream);
 

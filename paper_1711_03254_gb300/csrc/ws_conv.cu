@@ -269,13 +269,15 @@ __global__ void k_flip_weights(const bf16 *__restrict__ W, bf16 *__restrict__ Wf
 // operands are MN-major in shared memory (for one position, 8 consecutive
 // channels form a 16-byte row of a core matrix): the two core matrices of a
 // 16-position K chunk sit 128 B apart, 8-row groups 256 B apart.  Blocks of
-// 64 positions, two stages, bounded mbarrier waits as in k_conv_fwd_tc; the
-// result is added to dW with FP32 atomics (one block per (row tile, chunk)).
+// 64 positions, two stages, bounded mbarrier waits as in k_conv_fwd_tc.  One
+// block per (row tile, chunk) writes its partial tile part[chunk][row][co];
+// k_wgrad_sum adds the chunks into dW in chunk order, so the result does not
+// depend on scheduling.
 constexpr int WTK = 64, WTTHREADS = 128;
 
 __global__ void __launch_bounds__(WTTHREADS) k_conv_wgrad_tc(const bf16 *__restrict__ X, int ldx,
                                                             const bf16 *__restrict__ dY, int ldy,
-                                                            float *__restrict__ dW, Act a, int Ci, int Co, int k,
+                                                            float *__restrict__ part, Act a, int Ci, int Co, int k,
                                                             long long chunk, int tmem_cols, uint32_t lbo,
                                                             uint32_t sbo) {
     extern __shared__ __align__(128) unsigned char sm[];
@@ -390,9 +392,11 @@ __global__ void __launch_bounds__(WTTHREADS) k_conv_wgrad_tc(const bf16 *__restr
         ok_run = __syncthreads_and(okw);
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    // this block's partial rows: part[chunk][m0 + 0..127][0..Co)
+    float *prow = part + ((size_t)blockIdx.y * gridDim.x * 128 + (size_t)(m0 + warp * 32 + lane)) * Co;
+    if (!ok_run)
+        for (int c = 0; c < Co; ++c) prow[c] = 0.f;  // the status flag reports the failure
     if (ok_run) {
-        const int row = m0 + warp * 32 + lane;
-        const int t = row / Ci, ci = row - (row / Ci) * Ci;
         for (int c0 = 0; c0 < Co; c0 += 16) {
             uint32_t v[16];
             const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
@@ -404,10 +408,10 @@ __global__ void __launch_bounds__(WTTHREADS) k_conv_wgrad_tc(const bf16 *__restr
                   "=r"(v[15])
                 : "r"(addr));
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-            if (row < rows)
 #pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    atomicAdd(dW + ((long long)(c0 + e) * KV + t) * Ci + ci, __uint_as_float(v[e]));
+            for (int e = 0; e < 16; e += 4)
+                *reinterpret_cast<float4 *>(prow + c0 + e) = make_float4(
+                    __uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -418,8 +422,20 @@ __global__ void __launch_bounds__(WTTHREADS) k_conv_wgrad_tc(const bf16 *__restr
     }
 }
 
-// db[co] += sum_p dY[p][co]
-__global__ void k_bias_grad(const bf16 *__restrict__ dY, int ldy, float *__restrict__ db, long long P, int Co) {
+// dW[co][t][ci] += sum over the nk chunks of part[chunk][t * Ci + ci][co], in chunk order
+__global__ void k_wgrad_sum(const float *__restrict__ part, int nk, int rows_pad, int rows, int Co, int KV, int Ci,
+                            float *__restrict__ dW) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)rows * Co) return;
+    const int row = (int)(e / Co), co = (int)(e - (long long)row * Co);
+    float s = 0.f;
+    for (int c = 0; c < nk; ++c) s += part[((size_t)c * rows_pad + row) * Co + co];
+    const int t = row / Ci, ci = row - t * Ci;
+    dW[((long long)co * KV + t) * Ci + ci] += s;
+}
+
+// bpart[block][co] = this block's sum of dY[p][co]; k_bias_sum adds the blocks in order
+__global__ void k_bias_grad(const bf16 *__restrict__ dY, int ldy, float *__restrict__ bpart, long long P, int Co) {
     const int co = blockIdx.y * 32 + (threadIdx.x & 31);
     const int lanes = blockDim.x / 32;
     float s = 0.f;
@@ -432,8 +448,36 @@ __global__ void k_bias_grad(const bf16 *__restrict__ dY, int ldy, float *__restr
     if (threadIdx.x < 32 && co < Co) {
         float t = 0.f;
         for (int w = 0; w < lanes; ++w) t += sh[w][threadIdx.x];
-        atomicAdd(db + co, t);
+        bpart[(size_t)blockIdx.x * Co + co] = t;
     }
+}
+
+__global__ void k_bias_sum(const float *__restrict__ bpart, int nblk, int Co, float *__restrict__ db) {
+    const int co = blockIdx.x * blockDim.x + threadIdx.x;
+    if (co >= Co) return;
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += bpart[(size_t)b * Co + co];
+    db[co] += s;
+}
+
+// Library-held scratch for the weight-gradient partials, grown on demand
+// (the stream is drained before a smaller buffer is replaced).
+float *grad_workspace(size_t bytes, cudaStream_t s) {
+    static float *buf = nullptr;
+    static size_t have = 0;
+    if (bytes <= have) return buf;
+    if (buf) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return nullptr;
+        cudaFree(buf);
+        buf = nullptr;
+        have = 0;
+    }
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+        buf = nullptr;
+        return nullptr;
+    }
+    have = bytes;
+    return buf;
 }
 
 }  // namespace ws
@@ -511,13 +555,23 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
         attr = true;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const dim3 grid((unsigned)((KV * Ci + 127) / 128), (unsigned)nk, 1);
-    k_conv_wgrad_tc<<<grid, WTTHREADS, smem, s>>>((const bf16 *)x, ldx, (const bf16 *)dy, ldy, dw, a, Ci, Co, k, chunk,
-                                                  cols, kWgradLbo, kWgradSbo);
+    const int rows = KV * Ci, tiles = (rows + 127) / 128;
+    const long long bias_blocks = (P + 8 * 64 - 1) / (8 * 64);
+    const int nbb = (int)(bias_blocks < 1024 ? bias_blocks : 1024);
+    // partial tiles [nk][tiles * 128][Co], then the bias partials [nbb][Co]
+    const size_t wpart = (size_t)nk * tiles * 128 * Co;
+    float *ws_buf = grad_workspace((wpart + (size_t)nbb * Co) * sizeof(float), s);
+    if (!ws_buf) return 2;
+    const dim3 grid((unsigned)tiles, (unsigned)nk, 1);
+    k_conv_wgrad_tc<<<grid, WTTHREADS, smem, s>>>((const bf16 *)x, ldx, (const bf16 *)dy, ldy, ws_buf, a, Ci, Co, k,
+                                                  chunk, cols, kWgradLbo, kWgradSbo);
+    const long long elems = (long long)rows * Co;
+    k_wgrad_sum<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(ws_buf, (int)nk, tiles * 128, rows, Co, KV, Ci, dw);
     if (db) {
-        const long long blocks = (P + 8 * 64 - 1) / (8 * 64);
-        const dim3 g2((unsigned)(blocks < 1024 ? blocks : 1024), (unsigned)((Co + 31) / 32), 1);
-        k_bias_grad<<<g2, 256, 0, s>>>((const bf16 *)dy, ldy, db, P, Co);
+        float *bpart = ws_buf + wpart;
+        const dim3 g2((unsigned)nbb, (unsigned)((Co + 31) / 32), 1);
+        k_bias_grad<<<g2, 256, 0, s>>>((const bf16 *)dy, ldy, bpart, P, Co);
+        k_bias_sum<<<(Co + 255) / 256, 256, 0, s>>>(bpart, nbb, Co, db);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

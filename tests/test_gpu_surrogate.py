@@ -73,6 +73,13 @@ def test_conv_forward_and_gradients(env, shape, Ci, Co, k):
     rdw, rdb = conv.conv3d_bwd_weight(x, dy, k)
     assert _rel(dw.cpu().numpy(), rdw) < 2e-5
     assert _rel(db.cpu().numpy(), rdb) < 2e-5
+    # the chunks are summed in a fixed order: a second call gives the same bits,
+    # and the call accumulates into what dw and db hold
+    dw2, db2 = torch.zeros_like(dw), torch.zeros_like(db)
+    ws.ws_conv3d_bwd_weight(xv, dyt, dw2, db2, k)
+    assert torch.equal(dw, dw2) and torch.equal(db, db2)
+    ws.ws_conv3d_bwd_weight(xv, dyt, dw2, db2, k)
+    assert _rel(dw2.cpu().numpy(), 2 * rdw) < 2e-5 and _rel(db2.cpu().numpy(), 2 * rdb) < 2e-5
     assert ws.ws_tc_status() == 0  # no tensor-core wait gave up
 
 

@@ -26,6 +26,7 @@ def test_warm_start_cuts_updates_to_steady():
     rows = res["tests"][0]["rows"]
     plain = sum(r["plain_steps"] for r in rows)
     warm = sum(r[f"{VARIANT}_steps"] for r in rows)
+    print("updates to steady, plain / warm:", [(r["plain_steps"], r[f"{VARIANT}_steps"]) for r in rows], plain, warm)
     assert warm < plain, [(r["plain_steps"], r[f"{VARIANT}_steps"]) for r in rows]
     for r in rows:
         if r["plain_res"] <= 1e-5 and r[f"{VARIANT}_res"] <= 1e-5:
