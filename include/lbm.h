@@ -111,8 +111,12 @@ typedef struct {
  * On failure *out is NULL. */
 lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_instance, lbm_ctx **out);
 
-/* Upload the cell types, host uint8 [batch][nz][ny][nx] with values 0..3.
- * Errors: LBM_ERR_ARG (null, value > 3, an instance without any FLUID cell). */
+/* Upload the cell types, host uint8 [batch][nz][ny][nx] with values 0..3
+ * (page-locked host memory makes the copy a DMA).  The types are checked, and
+ * the cell lists and compact row tables built, on the device; the call returns
+ * when they are done.  On LBM_ERR_ARG nothing of the context changes.
+ * Errors: LBM_ERR_ARG (null, value > 3, an instance without any FLUID cell),
+ * LBM_ERR_OOM (scratch allocation), LBM_ERR_CUDA. */
 lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *cell_type);
 
 /* Initialise every non-solid cell to f = feq(rho_alpha, u) (Eq. 3, no force
