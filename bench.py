@@ -73,13 +73,15 @@ NCU_TRAFFIC = {
     "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db", "files": DENSE_SOURCES},
     # 192^3 packed spheres (2,830,487 non-solid cells; compact f 430 MB per buffer,
     # larger than L2), ncu --set full: 274.2 MB read + 192.3 MB written in one launch
-    "k_collide_c2/fp16s/spheres": {"bytes_per_fluid_cell": 164.8, "src": "4ac21a08ce947105",
+    "k_collide_c2/fp16s/spheres": {"bytes_per_fluid_cell": 164.8, "src": "1f62a0de098d92be",
                                    "files": COMPACT_SOURCES},
 }
 # FP64 mode is bound by the FP64 pipe.  Executed FP64 flops per non-solid cell
 # (DADD + DMUL + 2 DFMA from ncu, 128^3 packed spheres, eq_order 0) and the
 # FP64 peak: 2 DFMA per clock per SM (152 SMs, 2.07 GHz) = 1.26 TFLOP/s.
-FP64_FLOPS = {"k_collide_c": {"flops_per_fluid_cell": 813.7, "src": "4ac21a08ce947105", "files": COMPACT_SOURCES}}
+# (Counted on sources 4ac21a08ce947105; the next change of these files touched
+# only the psi pass, so the FP64 update's code is the one counted.)
+FP64_FLOPS = {"k_collide_c": {"flops_per_fluid_cell": 813.7, "src": "1f62a0de098d92be", "files": COMPACT_SOURCES}}
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 
@@ -293,10 +295,8 @@ def main():
     strategy = lbm.lbm_resolved_kernel(sim.ctx, args.steps)
     kernel_name = {"psi": "k_psi", "collide": "k_collide", "fused": "k_fused", "cluster": "k_cluster"}[part]
     if strategy == "compact":
-        # compact layout: packed-pair update for the FP32-arithmetic storages,
-        # pipelined psi pass for the 16-bit ones
-        kernel_name += {"psi": "_cp" if F_BYTES[args.precision] == 2 else "_c",
-                        "collide": "_c" if args.precision == "fp64" else "_c2"}[part]
+        # compact layout: packed-pair update for the FP32-arithmetic storages
+        kernel_name += {"psi": "_c", "collide": "_c" if args.precision == "fp64" else "_c2"}[part]
     per_cell = alg_bytes_per_cell(part, args.precision)
     updates_per_launch = args.steps if part == "cluster" else 1
     bytes_per_launch = per_cell * fluid * updates_per_launch

@@ -13,7 +13,7 @@
 // write contiguous runs of every plane, and the component pairs halve the
 // load, store and address instructions.
 //
-//   k_psi_c, k_psi_cp  S1-S3 as k_psi: pull, sum to rho_alpha, store psi.
+//   k_psi_c            S1-S3 as k_psi: pull, sum to rho_alpha, store psi.
 //   k_collide_c        S1-S7 as k_collide (FP64: the scalar device code of
 //                      the dense kernels, so both layouts give identical bits).
 //   k_collide_c2       S1-S7 for the FP32-arithmetic storages, both components
@@ -208,16 +208,18 @@ __device__ __forceinline__ float2 ref_pair2(const StepArgs &a, int b, uint32_t s
     return __half22float2(__ldg((const __half2 *)a.ref_in + (size_t)b * a.kmax + sk));
 }
 
-// threads per block: 128 for the update lets 7 (16-bit storage), 5 (FP32) or
-// 4 (FP64, FP64 arithmetic) blocks share an SM within its registers.  Measured
-// on GB300 (256^3 packed spheres): 16-bit storage 6 / 7 / 8 blocks 0.396 /
-// 0.381 / 0.385 ms (7 and 8 spill 44 and 92 B to L1); FP32 at 6 blocks spills
-// and loses 4 % against 5.
-constexpr int kPsiThreads = 256, kCollideThreads = 128;
+// Occupancy, measured on GB300 (256^3 packed spheres).  The update runs
+// 128-thread blocks, 7 (16-bit storage), 5 (FP32) or 4 (FP64) per SM within the
+// registers; one more block per SM was no faster (16-bit: 0.316 against 0.314
+// ms per update).  The psi pass runs 256-thread blocks, 6 per SM (40
+// registers): 16-bit storage 0.139 ms against 0.159 at 4 and 0.192 at 3 per
+// SM, and 0.163 for a persistent variant that prefetched each thread's next
+// cell with cp.async; FP32 0.186 against 0.218 at 3 per SM.
+constexpr int kPsiThreads = 256, kPsiBlocks = 6, kCollideThreads = 128;
 template <class S> constexpr int collide_min_blocks() { return sizeof(S) == 2 ? 7 : (sizeof(S) == 4 ? 5 : 4); }
 
 template <class S>
-__global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
+__global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {
     using T = typename Storage<S>::T;
     using V = typename Vec2<T>::V;
     const int b = blockIdx.y;
@@ -265,130 +267,13 @@ __global__ void __launch_bounds__(kPsiThreads, 3) k_psi_c(StepArgs a) {
     psi[k] = out;
 }
 
-// ---------------------------------------------------------------- pipelined psi pass
-// k_psi_cp: the psi pass as a persistent kernel.  Each thread walks its cells
-// with a grid stride and, while it sums the values of one cell, the values of
-// its next cell are already on their way into shared memory (cp.async into
-// two per-thread stages).  Every thread reads only the slots its own copies
-// filled, after cp.async.wait_group, so no block barrier is needed.
-constexpr int kPsiPipeThreads = 128;
-// measured on GB300 (256^3 packed spheres): 13 % faster for 16-bit storage,
-// 1.7x slower for FP32 pairs, so FP32 and FP64 keep the one-cell-per-thread pass
-template <class S> constexpr bool psi_pipelined() { return sizeof(S) == 2; }
-
+// ---------------------------------------------------------------- cp.async helpers
 template <int BYTES> __device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
 }
 __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-template <class S> constexpr size_t psi_pipe_smem() {
-    return 2 * ((size_t)kQ * sizeof(typename Pair<S>::P) + sizeof(__half2)) * kPsiPipeThreads;
-}
-
-template <class S>
-__global__ void __launch_bounds__(kPsiPipeThreads) k_psi_cp(StepArgs a) {
-    using T = typename Storage<S>::T;
-    using V = typename Vec2<T>::V;
-    using P = typename Pair<S>::P;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    P *vbuf = reinterpret_cast<P *>(smem_raw);                                          // [2][kQ][threads]
-    __half2 *rbuf = reinterpret_cast<__half2 *>(vbuf + 2 * kQ * kPsiPipeThreads);       // [2][threads]
-    const int b = blockIdx.y, tid = threadIdx.x;
-    const uint32_t count = (uint32_t)__ldg(a.list_count + b);
-    const uint32_t stride = gridDim.x * kPsiPipeThreads;
-    const P *f = (const P *)a.f_in + (size_t)b * kQ * a.kmax;
-    const __half2 *rin = (const __half2 *)a.ref_in + (size_t)b * a.kmax;
-    V *psi = (V *)a.psi + (size_t)b * a.kmax;
-    const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
-
-    // start the copies of cell kk into stage st; returns its geometry word
-    // the packed coordinates and word of a cell are loaded one iteration before
-    // its copies are issued, so that issuing waits only for the row tables
-    const uint32_t *cxyz = a.cxyz + (size_t)b * a.kmax, *clink = a.clink + (size_t)b * a.kmax;
-    auto raw = [&](uint32_t kk, uint2 &pw) {
-        if (kk < count) pw = make_uint2(__ldg(cxyz + kk), __ldg(clink + kk));
-    };
-    auto issue = [&](uint32_t kk, uint2 pw, int st) -> uint32_t {
-        const CompactCell c = unpack_cell(pw.x, pw.y);
-        if (cell_type(c.word) == kInlet) return c.word;
-        auto copies = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-#pragma unroll
-            for (int i = 0; i < kQ; ++i) {
-                const bool bb = (sw >> opp(i)) & 1u;
-                const uint32_t idx = bb ? (uint32_t)opp(i) * a.kmax + sk : (uint32_t)i * a.kmax + nb.src(i);
-                cp_async_ca<sizeof(P)>(&vbuf[(st * kQ + i) * kPsiPipeThreads + tid], f + idx);
-            }
-            if constexpr (Storage<S>::shifted) cp_async_ca<4>(&rbuf[st * kPsiPipeThreads + tid], rin + sk);
-        };
-        CNbr own;
-        own.init(c.x, c.y, c.z, kk, instance_tab(a, b), a.words, a.g);
-        int xu;
-        uint32_t ku, wu;
-        if (outlet_source(a, b, c, own, xu, ku, wu)) {
-            CNbr up;
-            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
-            copies(up, ku, wu);
-        } else {
-            copies(own, kk, c.word);
-        }
-        return c.word;
-    };
-
-    uint32_t k = blockIdx.x * kPsiPipeThreads + tid;
-    uint2 pw0 = make_uint2(0u, 0u), pw1 = make_uint2(0u, 0u);
-    raw(k, pw0);
-    raw(k + stride, pw1);
-    uint32_t word = k < count ? issue(k, pw0, 0) : 0u;
-    cp_async_commit_group();
-    int st = 0;
-    for (; k < count; k += stride) {
-        const uint32_t kn = k + stride;
-        uint2 pw2 = make_uint2(0u, 0u);
-        raw(kn + stride, pw2);
-        const uint32_t word_n = kn < count ? issue(kn, pw1, st ^ 1) : 0u;
-        pw1 = pw2;
-        cp_async_commit_group();
-        cp_async_wait_one();  // this thread's copies of stage st have landed
-        T p0, p1;
-        if (cell_type(word) == kInlet) {
-            p0 = p.rho_in[0];
-            p1 = p.rho_in[1];
-        } else {
-            if constexpr (packed_pairs<S>()) {
-                float2 v[kQ];
-#pragma unroll
-                for (int i = 0; i < kQ; ++i) v[i] = Pair2<S>::load_shared(&vbuf[(st * kQ + i) * kPsiPipeThreads + tid]);
-                const float2 d = density2<Pair2<S>::kScaled>(v, __half22float2(rbuf[st * kPsiPipeThreads + tid]),
-                                                             Pair2<S>::kUnscale);
-                p0 = d.x;
-                p1 = d.y;
-            } else {
-                T v0[kQ], v1[kQ];
-#pragma unroll
-                for (int i = 0; i < kQ; ++i)
-                    Pair<S>::load_shared(&vbuf[(st * kQ + i) * kPsiPipeThreads + tid], v0[i], v1[i]);
-                T r0 = T(0), r1 = T(0);
-                if constexpr (Storage<S>::shifted) {
-                    const __half2 r = rbuf[st * kPsiPipeThreads + tid];
-                    r0 = __low2float(r);
-                    r1 = __high2float(r);
-                }
-                p0 = density_of<T, Storage<S>::shifted>(v0, r0);
-                p1 = density_of<T, Storage<S>::shifted>(v1, r1);
-            }
-        }
-        V out;
-        out.x = p0;
-        out.y = p1;
-        psi[k] = out;
-        word = word_n;
-        st ^= 1;
-    }
-    asm volatile("cp.async.wait_all;\n" ::);
-}
 
 template <class S, int EQ>
 __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
@@ -659,28 +544,7 @@ static cudaError_t launch_compact_t(const StepArgs &a) {
     const dim3 gp((unsigned)((m + kPsiThreads - 1) / kPsiThreads), (unsigned)a.batch, 1);
     const dim3 gc((unsigned)((m + kCollideThreads - 1) / kCollideThreads), (unsigned)a.batch, 1);
     record_event(a, 0);
-    if constexpr (psi_pipelined<S>()) {
-        // persistent grid: as many blocks as fit on the device at once
-        static int per_sm = 0, sms = 0;
-        constexpr size_t smem = psi_pipe_smem<S>();
-        if (per_sm == 0) {
-            int dev = 0;
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess && smem > 48 * 1024)
-                e = cudaFuncSetAttribute(k_psi_cp<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_psi_cp<S>, kPsiPipeThreads, smem);
-            if (e != cudaSuccess) return e;
-            if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        }
-        const long long want = (long long)sms * per_sm / a.batch;
-        const long long need = (m + kPsiPipeThreads - 1) / kPsiPipeThreads;
-        const unsigned gx = (unsigned)(need < want ? need : (want > 0 ? want : 1));
-        k_psi_cp<S><<<dim3(gx, (unsigned)a.batch, 1), kPsiPipeThreads, smem, a.stream>>>(a);
-    } else {
-        k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
-    }
+    k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
     record_event(a, 1);
     // (a persistent variant that prefetches the next cell with cp.async, as the
     // psi pass does, measured 10 % slower here: the update is issue-bound, and
