@@ -470,3 +470,40 @@ def test_layered_poiseuille_ratio_1000(oracle_mod, layout, tol, nu1, nu2, g):
     ref = _integral_profile(a2, b2, nu1, nu2, g)
     assert np.all(np.isfinite(ux))
     assert np.abs(ux - ref).max() / np.abs(ref).max() < tol
+
+
+# ---------------------------------------------------------------- inlet / outlet
+
+@pytest.mark.parametrize("eq_order", [0, 1])
+def test_inlet_outlet_uniform_flow(oracle_mod, eq_order):
+    """INLET plane at x = 0 holding feq(rho_in, u_in), OUTLET plane at x = nx - 1
+    copying its upstream neighbour, periodic in y and z, no coupling.  From
+    rest the channel settles to a uniform flow along x.  In that state the
+    populations the inlet streams across its face (the five with c_x = +1)
+    must equal the interior's own, which are equilibria at the interior's
+    (rho_alpha, u).  For u along x all five share E(u) = 1 + 3u (printed
+    Eq. 3; the two u^3 terms cancel) or 1 + 3u + 3u^2 (with the quadratic
+    terms), so each component obeys rho_alpha E(u) = rho_in_alpha E(u_in).
+    The flux rho u is not carried over: this inlet fixes a mix of density
+    and velocity, not the flux."""
+    nx, ny, nz = 24, 3, 2
+    t = np.full((nz, ny, nx), W.FLUID, np.uint8)
+    t[:, :, 0] = W.INLET
+    t[:, :, nx - 1] = W.OUTLET
+    u_in, rho_in = 0.02, (0.6, 0.4)
+    p = [dict(tau=(0.8, 1.3), G=0.0, rho_in=rho_in, u_in=(u_in, 0.0, 0.0))]
+    sim = oracle_mod.OracleSim(nx, ny, nz, p, eq_order=eq_order)
+    sim.set_geometry(t[None])
+    sim.set_fields(np.full((1,) + t.shape, rho_in[0]), np.full((1,) + t.shape, rho_in[1]),
+                   np.zeros((1,) + t.shape + (3,)))
+    sim.step(3000)
+    r1, r2, u = sim.get_fields()
+    inner = (0, slice(None), slice(None), slice(1, None))
+    ux = u[inner + (0,)]
+    assert np.abs(u[inner + (slice(1, 3),)]).max() < 1e-15
+    assert ux.max() - ux.min() < 1e-12
+    E = (lambda w: 1 + 3 * w + 3 * w * w) if eq_order == 1 else (lambda w: 1 + 3 * w)
+    assert np.abs(r1[inner] * E(ux) - rho_in[0] * E(u_in)).max() < 1e-12
+    assert np.abs(r2[inner] * E(ux) - rho_in[1] * E(u_in)).max() < 1e-12
+    # the state is a real flow, not the inlet state copied through
+    assert 0.5 * u_in < ux.mean() < u_in
