@@ -3,8 +3,9 @@
 Each test checks the oracle against something other than its own formulas:
 lattice identities, moment identities of each collision ingredient, exact
 conservation laws, a closed form of the interaction stencil on a sinusoid,
-symmetries, the Laplace law with the surface tensions of Sec. 3.1, and the
-steady layered Poiseuille profile of Sec. 3.2.
+symmetries, the Laplace law with the surface tensions of Sec. 3.1, the
+steady layered Poiseuille profile of Sec. 3.2, and the uniform-flow state
+that the INLET/OUTLET planes must reach.
 """
 import itertools
 import math
