@@ -47,7 +47,9 @@ int ws_conv3d_flip_weights(const void *w, void *wf, int Co, int Ci, int k, void 
  * 16-byte aligned.  Each chunk of 4096 positions writes its partial sums into a
  * workspace the library holds (grown on demand with cudaMalloc, after draining
  * the stream); the chunks are then added into dw in chunk order, so repeated
- * calls give identical bits.  Errors: 1 bad argument, 2 allocation or launch
+ * calls give identical bits.  The workspace is one per process: calls that
+ * could overlap on the GPU (other streams, other host threads) race on it, so
+ * issue them on one stream.  Errors: 1 bad argument, 2 allocation or launch
  * failure. */
 int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float *dw, float *db, int N, int D, int H,
                          int W, int Ci, int Co, int k, void *stream);
