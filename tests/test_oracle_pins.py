@@ -3,7 +3,8 @@
 Each test checks the oracle against something other than its own formulas:
 lattice identities, moment identities of each collision ingredient, exact
 conservation laws, a closed form of the interaction stencil on a sinusoid,
-symmetries, the Laplace law with the surface tensions of Sec. 3.1, the
+symmetries (component exchange, the reflections and axis exchanges of the
+cube), the Laplace law with the surface tensions of Sec. 3.1, the
 steady layered Poiseuille profile of Sec. 3.2, and the uniform-flow state
 that the INLET/OUTLET planes must reach.
 """
@@ -317,6 +318,83 @@ def test_component_exchange_symmetry(oracle_mod):
     (a1, b1, u1), (a2, b2, u2) = outs
     assert np.allclose(a1, b2, atol=1e-13) and np.allclose(b1, a2, atol=1e-13)
     assert np.allclose(u1, u2, atol=1e-13)
+
+
+def _symmetry_case(seed):
+    """Random SOLID cells, random densities and velocities on a box with three
+    different sides, so that no axis can stand in for another."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = 9, 7, 5
+    t = np.where(rng.random((nz, ny, nx)) < 0.2, W.SOLID, W.FLUID).astype(np.uint8)
+    r1 = np.where(t == W.SOLID, 0.0, rng.uniform(0.3, 0.7, t.shape))
+    r2 = np.where(t == W.SOLID, 0.0, rng.uniform(0.3, 0.7, t.shape))
+    u = rng.uniform(-0.02, 0.02, t.shape + (3,))
+    u[t == W.SOLID] = 0
+    return t, r1, r2, u
+
+
+def _run(oracle_mod, t, r1, r2, u, p, eq_order, wall_model, steps=20):
+    nz, ny, nx = t.shape
+    sim = oracle_mod.OracleSim(nx, ny, nz, [p], eq_order=eq_order, wall_model=wall_model)
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    sim.step(steps)
+    a, b, v = sim.get_fields()
+    return a[0], b[0], v[0]
+
+
+@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 1), (0, 0)])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_mirror_symmetry(oracle_mod, axis, eq_order, wall_model):
+    """Reflecting the geometry, the fields and the body force through a plane
+    (x, y or z reversed, that velocity component negated) reflects the whole
+    evolution: D3Q19, the wall rules and the interaction stencil are symmetric
+    under the reflections of the cube.  A wrong entry in the velocity table,
+    a wrong opposite direction or a wrong sign in a wall sum breaks it."""
+    t, r1, r2, u = _symmetry_case(11 + axis)
+    g = np.array([3e-5, -2e-5, 1e-5])
+    p = dict(tau=(0.7, 1.6), G=-1.6, rho_s=0.25, g=tuple(g))
+    arr_axis = 2 - axis  # arrays are [z][y][x]
+    flip = lambda a: np.flip(a, axis=arr_axis)
+
+    def flip_u(v):
+        w = flip(v).copy()
+        w[..., axis] *= -1
+        return w
+    gm = g.copy()
+    gm[axis] *= -1
+    pm = dict(p, g=tuple(gm))
+    a1, b1, u1 = _run(oracle_mod, t, r1, r2, u, p, eq_order, wall_model)
+    a2, b2, u2 = _run(oracle_mod, flip(t), flip(r1), flip(r2), flip_u(u), pm, eq_order, wall_model)
+    assert np.abs(flip(a2) - a1).max() < 1e-12 and np.abs(flip(b2) - b1).max() < 1e-12
+    assert np.abs(flip_u(u2) - u1).max() < 1e-13
+
+
+@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 0)])
+@pytest.mark.parametrize("axes", [(0, 1), (1, 2), (0, 2)])
+def test_axis_exchange_symmetry(oracle_mod, axes, eq_order, wall_model):
+    """Exchanging two axes of the geometry, the fields, the velocities and the
+    body force exchanges them in the result (the other symmetry of the cube
+    that D3Q19 keeps).  A direction whose components are listed in the wrong
+    order breaks it."""
+    t, r1, r2, u = _symmetry_case(23 + sum(axes))
+    g = np.array([3e-5, -2e-5, 1e-5])
+    p = dict(tau=(1.2, 0.6), G=-1.9, rho_s=-0.2, g=tuple(g))
+    i, j = axes
+    ai, aj = 2 - i, 2 - j  # array axes of the two coordinates
+    swap = lambda a: np.ascontiguousarray(np.swapaxes(a, ai, aj))
+
+    def swap_u(v):
+        w = swap(v)[..., [0, 1, 2]].copy()
+        w[..., [i, j]] = w[..., [j, i]]
+        return w
+    gs = g.copy()
+    gs[[i, j]] = gs[[j, i]]
+    ps = dict(p, g=tuple(gs))
+    a1, b1, u1 = _run(oracle_mod, t, r1, r2, u, p, eq_order, wall_model)
+    a2, b2, u2 = _run(oracle_mod, swap(t), swap(r1), swap(r2), swap_u(u), ps, eq_order, wall_model)
+    assert np.abs(swap(a2) - a1).max() < 1e-12 and np.abs(swap(b2) - b1).max() < 1e-12
+    assert np.abs(swap_u(u2) - u1).max() < 1e-13
 
 
 # ---------------------------------------------------------------- Laplace law (Sec. 3.1)
