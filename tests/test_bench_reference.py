@@ -1,0 +1,28 @@
+"""The reference arm of bench.py (the FP64 oracle timed on the host cores)
+keeps the benchmark's JSON contract: one line, the GPU arm's metric and
+unit, the untimed warm-up and timed sample counts it was given, and the
+cpu_baseline and e2e objects.  Runs on the CPU (about 45 s)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == "MLUPS (fluid-cell updates per second, 2-comp D3Q19)" and d["unit"] == "MLUPS"
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "64^3" in cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == "MLUPS"
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
