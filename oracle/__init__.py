@@ -9,9 +9,12 @@ contraction); this module compiles it with gcc and exposes it through ctypes.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
+import shutil
 import subprocess
+import tempfile
 import threading
 
 import numpy as np
@@ -25,14 +28,18 @@ _lib = None
 Q = 19
 
 
+def _compile(src: str, out: str) -> None:
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (gcc, -O2, OpenMP, no FP contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+        _compile(_SRC, _LIB)
     return _LIB
 
 
@@ -47,36 +54,69 @@ class _Params(ctypes.Structure):
                 ("u_in", ctypes.c_double * 3)]
 
 
+def _load(path: str):
+    L = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    L.oracle_create.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Params), ctypes.POINTER(vp)]
+    L.oracle_destroy.argtypes = [vp]
+    L.oracle_set_geometry.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8)]
+    L.oracle_set_fields.argtypes = [vp, dp, dp, dp]
+    L.oracle_step.argtypes = [vp, ctypes.c_int]
+    L.oracle_get_fields.argtypes = [vp, dp, dp, dp]
+    L.oracle_get_f.argtypes = [vp, dp]
+    L.oracle_set_f.argtypes = [vp, dp]
+    L.oracle_reduce.argtypes = [vp, dp]
+    L.oracle_get_force.argtypes = [vp, dp]
+    L.oracle_step_count.argtypes = [vp]
+    L.oracle_step_count.restype = ctypes.c_long
+    L.oracle_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(ctypes.c_int)]
+    L.oracle_feq.argtypes = [ctypes.c_double, dp, ctypes.c_int, dp]
+    L.oracle_pi_neq.argtypes = [dp, dp, dp]
+    L.oracle_regularize.argtypes = [dp, dp]
+    L.oracle_forcing.argtypes = [dp, dp, ctypes.c_double, ctypes.c_int, dp]
+    L.oracle_tau_mix.argtypes = [ctypes.c_double, ctypes.c_double, dp]
+    L.oracle_tau_mix.restype = ctypes.c_double
+    L.oracle_collide_cell.argtypes = [dp, dp, dp, ctypes.c_int, dp, dp, dp, dp]
+    L.oracle_wall_potential.argtypes = [ctypes.c_double, dp]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            dp = ctypes.POINTER(ctypes.c_double)
-            vp = ctypes.c_void_p
-            L.oracle_create.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Params), ctypes.POINTER(vp)]
-            L.oracle_destroy.argtypes = [vp]
-            L.oracle_set_geometry.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8)]
-            L.oracle_set_fields.argtypes = [vp, dp, dp, dp]
-            L.oracle_step.argtypes = [vp, ctypes.c_int]
-            L.oracle_get_fields.argtypes = [vp, dp, dp, dp]
-            L.oracle_get_f.argtypes = [vp, dp]
-            L.oracle_set_f.argtypes = [vp, dp]
-            L.oracle_reduce.argtypes = [vp, dp]
-            L.oracle_get_force.argtypes = [vp, dp]
-            L.oracle_step_count.argtypes = [vp]
-            L.oracle_step_count.restype = ctypes.c_long
-            L.oracle_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), dp, ctypes.POINTER(ctypes.c_int)]
-            L.oracle_feq.argtypes = [ctypes.c_double, dp, ctypes.c_int, dp]
-            L.oracle_pi_neq.argtypes = [dp, dp, dp]
-            L.oracle_regularize.argtypes = [dp, dp]
-            L.oracle_forcing.argtypes = [dp, dp, ctypes.c_double, ctypes.c_int, dp]
-            L.oracle_tau_mix.argtypes = [ctypes.c_double, ctypes.c_double, dp]
-            L.oracle_tau_mix.restype = ctypes.c_double
-            L.oracle_collide_cell.argtypes = [dp, dp, dp, ctypes.c_int, dp, dp, dp, dp]
-            L.oracle_wall_potential.argtypes = [ctypes.c_double, dp]
-            _lib = L
+            _lib = _load(build())
     return _lib
+
+
+@contextlib.contextmanager
+def planted(old: str, new: str):
+    """Mutation check for the pins: inside the block every function of this
+    module runs an oracle compiled from a copy of lbm_oracle.c in which the
+    text `old` (exactly one occurrence) is replaced by `new`.  A pin that still
+    passes with a plausible slip planted this way cannot catch that slip."""
+    global _lib
+    text = open(_SRC).read()
+    if text.count(old) != 1:
+        raise ValueError(f"planted: {old!r} occurs {text.count(old)} times in the oracle source")
+    d = tempfile.mkdtemp(prefix="oracle_planted_")
+    try:
+        src = os.path.join(d, "lbm_oracle_planted.c")
+        with open(src, "w") as fh:
+            fh.write(text.replace(old, new))
+        so = os.path.join(d, "liboracle_planted.so")
+        _compile(src, so)
+        mutant = _load(so)
+        with _lock:
+            saved, _lib = _lib, mutant
+        try:
+            yield
+        finally:
+            with _lock:
+                _lib = saved
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
 
 
 def _dp(a: np.ndarray):
