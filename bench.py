@@ -8,10 +8,14 @@ model 2, FP32 arithmetic, storage selected by --precision (default 16-bit
 shifted).  A step is one update of the whole domain.  f (>= 1.27 GB) is larger
 than L2, so no flush is needed between steps.
 
-The roofline object is for the dominant kernel of the step: its algorithmic
-bytes per launch (per-fluid-cell bytes below x fluid cells) over its average
-launch time, taken with CUDA events around every launch on the launching
-stream during the timed region (lbm_timing_begin / lbm_timing_end).
+The roofline object is for the dominant kernel of the step: the method's
+algorithmic bytes per fluid-cell update (f read once and written once, 38
+values each way per component pair, plus the cell-type byte: 76 s + 1 for
+storage size s) times the fluid cells, over the kernel's average launch time,
+taken with CUDA events around every launch on the launching stream during the
+timed region (lbm_timing_begin / lbm_timing_end).  `step_frac` puts the same
+bytes over the whole step, and `kernel_impl_frac` puts the bytes the dominant
+kernel itself must move in this design over its launch time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16s|bf16s]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
@@ -25,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -65,7 +70,7 @@ def alg_bytes_per_cell(part: str, precision: str) -> int:
 # (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its fluid cells),
 # keyed by kernel/precision/workload, with the hash of the source files the
 # kernel is built from at the time of the capture; any change of them voids it.
-COMPACT_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_pair2.cuh", "lbm_compact.cu"]
+COMPACT_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_pair2.cuh", "lbm_compact.cuh", "lbm_compact.cu"]
 DENSE_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_kernels.cu"]
 NCU_TRAFFIC = {
     # 128^3 packed spheres (837,994 non-solid cells), dense layout, ncu --set full:
@@ -101,7 +106,11 @@ def workload(n=N, kind="spheres"):
     from paper_1711_03254_gb300 import workloads as W
     if kind == "droplet":
         return W.droplet(n, n, n, n / 8.0)
-    cache = f"/tmp/lbm_spheres_{n}.npz"
+    # the generated geometry is cached under a name that carries a hash of the
+    # generator's source, so an edited generator never reuses an old file
+    gen = os.path.join(ROOT, "paper_1711_03254_gb300", "workloads.py")
+    tag = hashlib.sha256(open(gen, "rb").read()).hexdigest()[:12]
+    cache = os.path.join(tempfile.gettempdir(), f"lbm_spheres_{n}_{tag}.npz")
     if os.path.exists(cache):
         z = np.load(cache)
         return z["t"], z["r1"], z["r2"], z["u"]
@@ -322,27 +331,38 @@ def main():
     if strategy == "compact":
         # compact layout: packed-pair update for the FP32-arithmetic storages
         kernel_name += {"psi": "_c", "collide": "_c" if args.precision == "fp64" else "_c2"}[part]
-    per_cell = alg_bytes_per_cell(part, args.precision)
+    # the method's own bytes per fluid-cell update (f in + f out + type byte):
+    # the roofline's algorithmic figure for the dominant kernel and the step
+    method_bytes = 2 * 38 * F_BYTES[args.precision] + 1
+    impl_bytes = alg_bytes_per_cell(part, args.precision)  # what this kernel moves at least
     updates_per_launch = args.steps if part == "cluster" else 1
-    bytes_per_launch = per_cell * fluid * updates_per_launch
     avg_s = part_ms / part_launches / 1e3
-    achieved = bytes_per_launch / avg_s / 1e9
+    achieved = method_bytes * fluid * updates_per_launch / avg_s / 1e9
     key = f"{kernel_name}/{args.precision}/{args.workload}"
     tr = NCU_TRAFFIC.get(key)
     traffic = None
     if tr and tr.get("src") == sources_hash(tr["files"]):
         traffic = round(tr["bytes_per_fluid_cell"] * fluid * updates_per_launch)
-    step_bytes = (2 * 38 * F_BYTES[args.precision] + 1) * fluid
+    step_s = (ms / args.steps) / 1e3
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
-            "traffic_source": "ncu capture on a smaller case of the same geometry, scaled by non-solid cells"
-            if traffic is not None else None,
-            "kernel": kernel_name, "algorithmic_bytes_per_fluid_cell": per_cell,
+            "traffic_source": tr.get("how") if traffic is not None else None,
+            "kernel": kernel_name, "algorithmic_bytes_per_fluid_cell": method_bytes,
             "avg_launch_ms": round(avg_s * 1e3, 4), "launches": part_launches,
             "share_of_step": round(part_ms / ms, 4),
             "parts_ms": {k: round(v[0] / v[1], 4) for k, v in timing.items()},
-            "step_min_bytes_per_fluid_cell": 2 * 38 * F_BYTES[args.precision] + 1,
-            "step_frac": round(step_bytes / ((ms / args.steps) / 1e3) / 1e9 / hbm, 4)}
+            # the whole step (every kernel of an update) on the method's bytes
+            "step_frac": round(method_bytes * fluid / step_s / 1e9 / hbm, 4),
+            # the dominant kernel on the bytes it must move in this design
+            # (psi, coordinates, links, reference densities besides f)
+            "kernel_impl_bytes_per_fluid_cell": impl_bytes,
+            "kernel_impl_frac": round(impl_bytes * fluid * updates_per_launch / avg_s / 1e9 / hbm, 4)}
+    if tr and traffic is not None:
+        # measured DRAM bytes of one step over the method's bytes
+        step_tr = tr.get("step_bytes_per_fluid_cell")
+        if step_tr:
+            roof["step_traffic_bytes_per_fluid_cell"] = step_tr
+            roof["wasted_traffic_ratio"] = round(step_tr / method_bytes, 3)
 
     fl = FP64_FLOPS.get(kernel_name)
     if args.precision == "fp64" and fl and fl["src"] == sources_hash(fl["files"]):

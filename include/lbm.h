@@ -56,7 +56,7 @@ typedef enum {
     LBM_ERR_CUDA = 2,     /* a CUDA runtime call failed (message in lbm_last_error) */
     LBM_ERR_OOM = 3,      /* device allocation failed */
     LBM_ERR_DIVERGED = 4, /* non-finite value, or |u_F| above the sound speed 1/sqrt(3), found by lbm_reduce */
-    LBM_ERR_TIMEOUT = 5,  /* reserved for bounded device-side waits */
+    LBM_ERR_TIMEOUT = 5,  /* lbm_run_to_steady used up its update budget before the tolerance */
     LBM_ERR_STATE = 6     /* call out of order (e.g. step before set_fields) */
 } lbm_status;
 
@@ -105,10 +105,17 @@ typedef struct {
 } lbm_instance_params;
 
 /* Create a context for cfg->batch instances with per-instance parameters
- * per_instance[batch] (host array, copied).  Allocates the device buffers.
- * Errors: LBM_ERR_ARG (null pointers, a dimension < 1, batch < 1,
- * tau <= 1/2, eq_order or wall_model out of range), LBM_ERR_OOM, LBM_ERR_CUDA.
- * On failure *out is NULL. */
+ * per_instance[batch] (host array, copied).  The parameters are those the
+ * paper states its problems with: the relaxation times of the pure components
+ * (Eq. 5, nu_k = T0 (tau_k - 1/2)), the coupling G of Eq. 7, the single
+ * wettability parameter rho^s of the wall potential (Eq. 11 and the mapping to
+ * rho^s_1, rho^s_2 kept beside it), and the body force of Sec. 3.2.
+ * Allocates the device buffers.
+ * Errors: LBM_ERR_ARG (null pointers, a dimension < 1, batch < 1 or
+ * batch > 32767, more than 226 million cells per instance, tau <= 1/2, a
+ * non-finite parameter, precision, eq_order or wall_model out of range),
+ * LBM_ERR_OOM (an allocation through the hook returned NULL), LBM_ERR_CUDA.
+ * On failure *out is NULL and nothing stays allocated. */
 lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_instance, lbm_ctx **out);
 
 /* Upload the cell types, host uint8 [batch][nz][ny][nx] with values 0..3
@@ -126,9 +133,15 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *cell_type);
 lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho1, const double *rho2, const double *u);
 
 /* Advance every instance by n >= 0 updates (asynchronous on the context's
- * stream).  The densities and velocity u_F of the last update are kept for
- * lbm_get_fields / lbm_reduce.  Errors: LBM_ERR_ARG (n < 0),
- * LBM_ERR_STATE (no fields), LBM_ERR_CUDA (launch failure). */
+ * stream).  One update is the streaming-collision step of Eq. 1 / Eq. 9 with
+ * the steps S1-S7 above: pull streaming and halfway bounce-back (Sec. 2,
+ * volumetric wall in its voxel-aligned case), moments (Eq. 4), the
+ * pseudo-potential and Shan-Chen force with the wall term (Eq. 7, Eq. 11),
+ * u_F and the density-weighted tau_mix (Eq. 5, 6, 8), and the regularised
+ * collision with forcing (Eq. 3, Eq. 9, Eq. 10).  The densities and velocity
+ * u_F of the last update are kept for lbm_get_fields / lbm_reduce.
+ * Errors: LBM_ERR_ARG (n < 0), LBM_ERR_STATE (no fields), LBM_ERR_CUDA
+ * (launch failure). */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
 
 /* Copy the macroscopic fields of the last update (or of lbm_set_fields) to
@@ -137,7 +150,11 @@ lbm_status lbm_step(lbm_ctx *ctx, int n);
  * that field.  Synchronises the stream. */
 lbm_status lbm_get_fields(lbm_ctx *ctx, double *rho1, double *rho2, double *u);
 
-/* FP64 reductions per instance over non-solid cells, written to the host
+/* FP64 reductions per instance over non-solid cells (no counterpart in the
+ * paper, which states no convergence test: M1 and M2 are the per-component
+ * masses that Eq. 1 conserves, P the momentum that the forcing of Eq. 9 changes
+ * by the total force, and the residual the steady-state test of the
+ * warm-start comparison), written to the host
  * array out[batch][7] = {M1, M2, Px, Py, Pz, residual, max|u_F|} with
  * P = sum rho u_F and residual = |u - u_prev|_2 / (k |u|_2 + 1e-30), where
  * u_prev and k are the velocity at and the updates since the previous
@@ -203,7 +220,10 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
  * check_every updates and the reduction are captured once as a CUDA graph and
  * replayed.  *steps_done and residual[batch] (may be NULL) receive the update
  * count and the last residuals.  Returns LBM_ERR_DIVERGED if a reduction sees a
- * non-finite value.  Errors: LBM_ERR_ARG (check_every < 1, max_steps < 0). */
+ * non-finite value or |u_F| above the lattice sound speed (as lbm_reduce), and
+ * LBM_ERR_TIMEOUT if max_steps were used up first (both leave a valid state;
+ * *steps_done and residual are filled either way).
+ * Errors: LBM_ERR_ARG (check_every < 1, max_steps < 0). */
 lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_steps, int *steps_done,
                              double *residual);
 

@@ -85,12 +85,12 @@ int ws_mse_loss(const float *pred, int ldp, const float *target, const uint8_t *
 int ws_adam(float *w, float *m, float *v, float *g, void *wb, long long n, float lr_t, float beta1, float beta2,
             float eps, float weight_decay, void *stream);
 
-/* FP32 -> BF16 copy into a channel slice: y[p][c] = x[p*ldx + c], c < C. */
 /* Waits for `stream`, then reports whether a tensor-core convolution since the
  * last call gave up on a bounded wait for its matrix units (5; the affected
  * outputs are not written) or not (0); clears the record.  2 on a CUDA error. */
 int ws_tc_status(void *stream);
 
+/* FP32 -> BF16 copy into a channel slice: y[p][c] = x[p*ldx + c], c < C. */
 int ws_to_bf16(const float *x, int ldx, void *y, int ldy, long long P, int C, void *stream);
 
 #ifdef __cplusplus

@@ -22,6 +22,7 @@ thread_local std::string g_last_error;
 constexpr double kMaxSpeed = 0.57735026918962576;
 // the persistent cluster kernel loops each thread over cells of its instance
 constexpr long long kClusterMaxCells = 65536;
+constexpr int kMaxBatch = 32767;
 
 size_t storage_bytes(lbm_precision p) {
     switch (p) {
@@ -332,6 +333,12 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
     }
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || cfg->batch < 1) {
         g_last_error = "lbm_create: every dimension and the batch must be >= 1";
+        return LBM_ERR_ARG;
+    }
+    // instances run along gridDim.y (at most 65535), the layout conversion
+    // along 2 * batch of it
+    if (cfg->batch > kMaxBatch) {
+        g_last_error = "lbm_create: at most 32767 instances per context";
         return LBM_ERR_ARG;
     }
     // kernels index one component's 19 planes with 32-bit offsets
@@ -1036,7 +1043,7 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
     if (e == cudaSuccess) e = cudaEventRecord(ev, user);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
     int done = 0;
-    bool diverged = false;
+    bool diverged = false, conv = false;
     const lbm_kernel kres = resolve_kernel(ctx, check_every);
     const long long launches_per_replay =
         (kres == LBM_KERNEL_CLUSTER ? 1 : (kres == LBM_KERNEL_FUSED ? check_every : 2LL * check_every)) + 2;
@@ -1050,12 +1057,14 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
         ctx->cur ^= (check_every & 1);
         ctx->step += check_every;
         ctx->launches += launches_per_replay;
-        bool conv = true;
+        conv = true;
         for (int b = 0; b < B; ++b) {
             const double *r = hres + (size_t)b * 9;
             const double res = std::sqrt(r[5]) / ((double)check_every * std::sqrt(r[6]) + 1e-30);
             if (residual) residual[b] = res;
-            if (r[8] > 0 || !std::isfinite(res)) diverged = true;
+            // the same divergence test as lbm_reduce: a non-finite value, or
+            // |u_F| above the lattice sound speed
+            if (r[8] > 0 || !std::isfinite(res) || r[7] > kMaxSpeed) diverged = true;
             if (!(res <= tol)) conv = false;
         }
         if (diverged || conv) break;
@@ -1068,7 +1077,9 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
     if (hres) cudaFreeHost(hres);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_run_to_steady");
-    if (diverged) return ctx->fail(LBM_ERR_DIVERGED, "lbm_run_to_steady: non-finite value");
+    if (diverged)
+        return ctx->fail(LBM_ERR_DIVERGED, "lbm_run_to_steady: non-finite value or |u_F| above the lattice sound speed");
+    if (!conv) return ctx->fail(LBM_ERR_TIMEOUT, "lbm_run_to_steady: max_steps used up before the tolerance");
     return LBM_OK;
 }
 

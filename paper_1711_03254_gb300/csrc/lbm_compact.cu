@@ -18,195 +18,9 @@
 //                      the dense kernels, so both layouts give identical bits).
 //   k_collide_c2       S1-S7 for the FP32-arithmetic storages, both components
 //                      as packed FP32 pairs (lbm_pair2.cuh).
-#include "lbm_internal.h"
-#include "lbm_device.cuh"
-#include "lbm_pair2.cuh"
+#include "lbm_compact.cuh"
 
 namespace lbm {
-
-// Both components of one stored value.
-template <class S> struct Pair;
-template <> struct Pair<double> {
-    using P = double2;
-    __device__ static __forceinline__ void load(const P *p, double &a, double &b) {
-        const P v = __ldg(p);
-        a = v.x;
-        b = v.y;
-    }
-    __device__ static __forceinline__ void store(P *p, double a, double b, double, double) { *p = make_double2(a, b); }
-    __device__ static __forceinline__ void store_d(P *p, double a, double b) { *p = make_double2(a, b); }
-    __device__ static __forceinline__ void load_shared(const P *p, double &a, double &b) {
-        const P v = *p;
-        a = v.x;
-        b = v.y;
-    }
-};
-template <> struct Pair<float> {
-    using P = float2;
-    __device__ static __forceinline__ void load(const P *p, float &a, float &b) {
-        const P v = __ldg(p);
-        a = v.x + 0.f;  // as Storage<float>::load with a zero shift
-        b = v.y + 0.f;
-    }
-    __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
-        *p = make_float2(a - sa, b - sb);
-    }
-    __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = make_float2(a, b); }
-    __device__ static __forceinline__ void load_shared(const P *p, float &a, float &b) {
-        const P v = *p;
-        a = v.x + 0.f;
-        b = v.y + 0.f;
-    }
-};
-template <> struct Pair<__half> {  // values scaled as in Storage<__half>
-    using P = __half2;
-    __device__ static __forceinline__ void load(const P *p, float &a, float &b) {
-        const float2 v = __half22float2(__ldg(p));
-        a = v.x * kF16Unscale + 0.f;
-        b = v.y * kF16Unscale + 0.f;
-    }
-    __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
-        *p = __floats2half2_rn((a - sa) * kF16Scale, (b - sb) * kF16Scale);
-    }
-    __device__ static __forceinline__ void store_d(P *p, float a, float b) {
-        *p = __floats2half2_rn(a * kF16Scale, b * kF16Scale);
-    }
-    __device__ static __forceinline__ void load_shared(const P *p, float &a, float &b) {
-        const float2 v = __half22float2(*p);
-        a = v.x * kF16Unscale + 0.f;
-        b = v.y * kF16Unscale + 0.f;
-    }
-};
-template <> struct Pair<__nv_bfloat16> {
-    using P = __nv_bfloat162;
-    __device__ static __forceinline__ void load(const P *p, float &a, float &b) {
-        const float2 v = __bfloat1622float2(__ldg(p));
-        a = v.x + 0.f;
-        b = v.y + 0.f;
-    }
-    __device__ static __forceinline__ void store(P *p, float a, float b, float sa, float sb) {
-        *p = __floats2bfloat162_rn(a - sa, b - sb);
-    }
-    __device__ static __forceinline__ void store_d(P *p, float a, float b) { *p = __floats2bfloat162_rn(a, b); }
-    __device__ static __forceinline__ void load_shared(const P *p, float &a, float &b) {
-        const float2 v = __bfloat1622float2(*p);
-        a = v.x + 0.f;
-        b = v.y + 0.f;
-    }
-};
-
-template <class T> struct Vec2;
-template <> struct Vec2<double> { using V = double2; };
-template <> struct Vec2<float> { using V = float2; };
-
-// Both components of a stored value as one FP32 pair in storage units, for
-// the packed-pair arithmetic (FP32 and 16-bit storages).  kUnscale takes a
-// sum of stored values to FP32 units and kScale a result back (2^-12 and 2^12
-// for the scaled FP16 deviations, exact powers of two).
-template <class S> struct Pair2;
-template <> struct Pair2<float> {
-    using P = float2;
-    static constexpr bool kScaled = false;
-    static constexpr float kUnscale = 1.f, kScale = 1.f;
-    __device__ static __forceinline__ float2 load(const P *p) { return __ldg(p); }
-    __device__ static __forceinline__ float2 load_shared(const P *p) { return *p; }
-    __device__ static __forceinline__ void store(P *p, float2 v) { *p = v; }
-};
-template <> struct Pair2<__half> {
-    using P = __half2;
-    static constexpr bool kScaled = true;
-    static constexpr float kUnscale = kF16Unscale, kScale = kF16Scale;
-    __device__ static __forceinline__ float2 load(const P *p) { return __half22float2(__ldg(p)); }
-    __device__ static __forceinline__ float2 load_shared(const P *p) { return __half22float2(*p); }
-    __device__ static __forceinline__ void store(P *p, float2 v) { *p = __float22half2_rn(v); }
-};
-template <> struct Pair2<__nv_bfloat16> {
-    using P = __nv_bfloat162;
-    static constexpr bool kScaled = false;
-    static constexpr float kUnscale = 1.f, kScale = 1.f;
-    __device__ static __forceinline__ float2 load(const P *p) { return __bfloat1622float2(__ldg(p)); }
-    __device__ static __forceinline__ float2 load_shared(const P *p) { return __bfloat1622float2(*p); }
-    __device__ static __forceinline__ void store(P *p, float2 v) { *p = __float22bfloat162_rn(v); }
-};
-// FP32 arithmetic (packed pairs) for every storage but FP64
-template <class S> constexpr bool packed_pairs() { return sizeof(S) < 8; }
-
-struct CompactCell {
-    int x, y, z;
-    uint32_t word;
-};
-
-// cell from its packed coordinates p and geometry word
-__device__ __forceinline__ CompactCell unpack_cell(uint32_t p, uint32_t word) {
-    CompactCell c;
-    c.x = (int)(p & 2047u);
-    c.y = (int)((p >> 11) & 2047u);
-    c.z = (int)(p >> 22);
-    c.word = word;
-    return c;
-}
-
-__device__ __forceinline__ CompactCell compact_cell(const StepArgs &a, int b, uint32_t k) {
-    return unpack_cell(__ldg(a.cxyz + (size_t)b * a.kmax + k), __ldg(a.clink + (size_t)b * a.kmax + k));
-}
-
-__device__ __forceinline__ const uint2 *instance_tab(const StepArgs &a, int b) {
-    return a.rowtab + (size_t)b * ((size_t)a.g.ny * a.g.nz + 1) * a.words;
-}
-
-// For an OUTLET cell whose upstream (-x) neighbour is neither SOLID nor
-// OUTLET, the update pulls that neighbour's streamed values: returns true and
-// its position, compact index and word.  False for every other cell.
-__device__ __forceinline__ bool outlet_source(const StepArgs &a, int b, const CompactCell &c, const CNbr &own,
-                                              int &xu, uint32_t &ku, uint32_t &wu) {
-    if (cell_type(c.word) != kOutlet || ((c.word >> 2) & 1u)) return false;
-    ku = own.nb[2];  // x - 1, not SOLID
-    wu = __ldg(a.clink + (size_t)b * a.kmax + ku);
-    if (cell_type(wu) == kOutlet) return false;
-    xu = c.x == 0 ? a.g.nx - 1 : c.x - 1;
-    return true;
-}
-
-// Pull the 19 stored pairs of the cell with compact index sk (neighbours nb,
-// geometry word sw) into v0, v1 (bounce-back from SOLID neighbours).
-template <class S>
-__device__ __forceinline__ void pull_pairs(const typename Pair<S>::P *__restrict__ f, uint32_t n, uint32_t sk,
-                                           const CNbr &nb, uint32_t sw, typename Storage<S>::T (&v0)[kQ],
-                                           typename Storage<S>::T (&v1)[kQ]) {
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const bool bb = (sw >> opp(i)) & 1u;
-        const uint32_t idx = bb ? (uint32_t)opp(i) * n + sk : (uint32_t)i * n + nb.src(i);
-        Pair<S>::load(f + idx, v0[i], v1[i]);
-    }
-}
-
-template <class S>
-__device__ __forceinline__ void ref_pair(const StepArgs &a, int b, uint32_t sk, typename Storage<S>::T &r0,
-                                         typename Storage<S>::T &r1) {
-    r0 = r1 = typename Storage<S>::T(0);
-    if constexpr (Storage<S>::shifted) {
-        const __half2 r = __ldg((const __half2 *)a.ref_in + (size_t)b * a.kmax + sk);
-        r0 = __low2float(r);
-        r1 = __high2float(r);
-    }
-}
-
-// pull_pairs for the packed-pair path: the 19 stored pairs in storage units.
-template <class S>
-__device__ __forceinline__ void pull_pairs2(const typename Pair2<S>::P *__restrict__ f, uint32_t n, uint32_t sk,
-                                            const CNbr &nb, uint32_t sw, float2 (&v)[kQ]) {
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const bool bb = (sw >> opp(i)) & 1u;
-        const uint32_t idx = bb ? (uint32_t)opp(i) * n + sk : (uint32_t)i * n + nb.src(i);
-        v[i] = Pair2<S>::load(f + idx);
-    }
-}
-
-__device__ __forceinline__ float2 ref_pair2(const StepArgs &a, int b, uint32_t sk) {
-    return __half22float2(__ldg((const __half2 *)a.ref_in + (size_t)b * a.kmax + sk));
-}
 
 // Occupancy, measured on GB300 (256^3 packed spheres).  The update runs
 // 128-thread blocks, 7 (16-bit storage), 5 (FP32) or 4 (FP64) per SM within the
@@ -266,14 +80,6 @@ __global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {
     out.y = p1;
     psi[k] = out;
 }
-
-// ---------------------------------------------------------------- cp.async helpers
-template <int BYTES> __device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
-}
-__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <class S, int EQ>
 __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {

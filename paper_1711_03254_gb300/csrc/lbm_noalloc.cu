@@ -124,9 +124,19 @@ extern "C" lbm_status lbm_field_sums_static(const double *rho1, const double *rh
         }
         scratch = g_sym_ptr[dev];
     }
+    // cudaLaunchKernel returns the error of this launch itself, so an error
+    // left pending by some other launch on this thread is neither reported
+    // here nor cleared
     cudaStream_t s = (cudaStream_t)stream;
-    k_static_partial<<<dim3(kStaticBlocks, (unsigned)batch, 1), kStaticThreads, 0, s>>>(rho1, rho2, u, cell_type,
-                                                                                      ncells, scratch);
-    k_static_final<<<batch, kStaticThreads, 0, s>>>(scratch, out);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    long long n = ncells;
+    void *pargs[] = {(void *)&rho1, (void *)&rho2, (void *)&u, (void *)&cell_type, (void *)&n, (void *)&scratch};
+    if (cudaLaunchKernel((const void *)k_static_partial, dim3(kStaticBlocks, (unsigned)batch, 1),
+                         dim3(kStaticThreads, 1, 1), pargs, 0, s) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    const double *sc = scratch;
+    void *fargs[] = {(void *)&sc, (void *)&out};
+    if (cudaLaunchKernel((const void *)k_static_final, dim3((unsigned)batch, 1, 1), dim3(kStaticThreads, 1, 1), fargs,
+                         0, s) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    return LBM_OK;
 }

@@ -324,11 +324,13 @@ def lbm_autotune(ctx, steps_per_trial: int = 5, cache_path: str | None = None):
 
 
 def lbm_run_to_steady(ctx, check_every: int, tol: float, max_steps: int, batch: int):
-    """Advance until every residual <= tol; returns (updates done, residuals)."""
+    """Advance until every residual <= tol; returns (updates done, residuals).
+    Running out of max_steps (LBM_ERR_TIMEOUT) is not an error here: the
+    caller sees it in the residuals."""
     done = ctypes.c_int(0)
     res = np.zeros(batch)
     rc = library().lbm_run_to_steady(ctx, int(check_every), float(tol), int(max_steps), ctypes.byref(done), _dp(res))
-    _check(rc, ctx)
+    _check(rc, ctx, allow=(5,))
     return done.value, res
 
 

@@ -2,9 +2,15 @@
 
 Tolerances (relative to the field's scale, max over cells):
   FP64 storage + FP64 arithmetic   1e-11  (after the whole run)
-  FP32                              1e-5
-  FP16 / BF16 shifted storage       1e-3 / 6e-3 (rounding of the stored deviation;
-                                    BF16 keeps 8 mantissa bits)
+  FP32                              1e-5 on the densities and on u_F
+  FP16 / BF16 shifted storage       densities 1e-3 / 6e-3, u_F 1e-2 / 6e-2 on the
+                                    32^3 droplet after 1000 updates (rounding of the
+                                    stored deviation: FP16 keeps 11 significant
+                                    bits, BF16 8).  The velocity bound is looser:
+                                    the storage leaves an absolute velocity error of
+                                    ~2e-5 (FP16), set while the sharp initial
+                                    interface drives |u_F| ~ 0.2, against a final
+                                    spurious current of ~7e-3.
 """
 import numpy as np
 import pytest
@@ -141,27 +147,37 @@ def test_fp64_batched_instances(lbm, oracle_mod, kernel):
     assert max(_errs(g, o)) < 1e-12
 
 
+# (densities, u_F) bounds per storage
+DROPLET_BOUNDS = {"fp32": (1e-5, 1e-5), "fp16s": (1e-3, 1e-2), "bf16s": (6e-3, 6e-2)}
+WALL_BOUNDS = {"fp32": (1e-5, 1e-5), "fp16s": (2e-3, 2e-3), "bf16s": (1e-2, 2e-2)}
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 1e-3), ("bf16s", 6e-3)])
-def test_reduced_precision_droplet(lbm, oracle_mod, precision, tol, kernel):
-    """32^3 droplet, 1000 updates: FP32 arithmetic with FP32 / 16-bit storage."""
+@pytest.mark.parametrize("precision", ["fp32", "fp16s", "bf16s"])
+def test_reduced_precision_droplet(lbm, oracle_mod, precision, kernel):
+    """32^3 droplet, 1000 updates: FP32 arithmetic with FP32 / 16-bit storage;
+    densities and u_F against the oracle within the storage's bounds."""
     t, r1, r2, u = W.droplet(32, 32, 32, 8.0)
     p = [dict(tau=(1.0, 1.0), G=-2.2)]
     _, _, g, o = _pair(lbm, oracle_mod, (32, 32, 32), p, t, r1, r2, u, 1000, precision=precision, kernel=kernel)
     e = _errs(g, o)
-    assert _rel(g[0], o[0]) < tol and _rel(g[1], o[1]) < tol, e
+    rb, ub = DROPLET_BOUNDS[precision]
+    assert e[0] < rb and e[1] < rb and e[2] < ub, e
 
 
 @pytest.mark.parametrize("kernel", ["two_pass", "compact"])
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 2e-3), ("bf16s", 1e-2)])
-def test_reduced_precision_walls(lbm, oracle_mod, precision, tol, kernel):
+@pytest.mark.parametrize("precision", ["fp32", "fp16s", "bf16s"])
+def test_reduced_precision_walls(lbm, oracle_mod, precision, kernel):
+    """Random walls, wetting wall potential and a body force, 20 updates:
+    densities and u_F within the storage's bounds."""
     shape = (13, 7, 9)
     t, r1, r2, u = _random_geometry(shape, 0.2, 31, lo=0.3, hi=0.7)
     p = [dict(tau=(0.7, 1.5), G=-1.8, rho_s=0.3, g=(1e-4, 0, 0))]
     _, _, g, o = _pair(lbm, oracle_mod, shape, p, t[None], r1[None], r2[None], u[None], 20, precision=precision,
                        kernel=kernel)
     e = _errs(g, o)
-    assert _rel(g[0], o[0]) < tol and _rel(g[1], o[1]) < tol, e
+    rb, ub = WALL_BOUNDS[precision]
+    assert e[0] < rb and e[1] < rb and e[2] < ub, e
 
 
 def test_reductions_match_oracle(lbm, oracle_mod):

@@ -133,3 +133,69 @@ def test_timing_capacity_and_state_errors(lbm):
         lbm.lbm_timing_end(a.ctx)
     assert e.value.status == 6
     a.close()
+
+
+def test_allocator_hook_failure_is_oom(lbm):
+    """An allocator hook that returns NULL makes lbm_create fail with
+    LBM_ERR_OOM and leave nothing allocated; a hook that fails only on a later
+    request (the scratch of lbm_set_geometry) gives LBM_ERR_OOM there, and the
+    context stays usable once the hook allows allocations again."""
+    import torch
+    live = {}
+
+    def alloc_ok(n, s):
+        p = int(torch.cuda.caching_allocator_alloc(int(n), torch.cuda.current_device(), s))
+        live[p] = n
+        return p
+
+    def release(p, s):
+        live.pop(int(p), None)
+        torch.cuda.caching_allocator_delete(int(p))
+
+    try:
+        lbm.lbm_set_allocator(lambda n, s: 0, release)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.Sim(8, 8, 8, [dict(tau=(1.0, 1.0), G=-2.0)], precision="fp32")
+        assert e.value.status == 3
+
+        budget = {"left": None}
+
+        def alloc_limited(n, s):
+            if budget["left"] is not None:
+                if budget["left"] <= 0:
+                    return 0
+                budget["left"] -= 1
+            return alloc_ok(n, s)
+
+        lbm.lbm_set_allocator(alloc_limited, release)
+        t, r1, r2, u = W.droplet(8, 8, 8, 2.0)
+        s = lbm.Sim(8, 8, 8, [dict(tau=(1.0, 1.0), G=-2.0)], precision="fp32")
+        budget["left"] = 0
+        with pytest.raises(lbm.LbmError) as e:
+            s.set_geometry(t[None])
+        assert e.value.status == 3
+        budget["left"] = None
+        s.set_geometry(t[None])
+        s.set_fields(r1[None], r2[None], u[None])
+        s.step(3)
+        assert np.isfinite(s.reduce()).all()
+        s.close()
+        assert not live
+    finally:
+        lbm.lbm_set_allocator()
+
+
+def test_run_to_steady_reports_timeout(lbm):
+    """A tolerance the run cannot reach within max_steps returns
+    LBM_ERR_TIMEOUT from the C ABI with the update count and residual filled;
+    the Python binding hands them back without raising."""
+    import ctypes
+    a = _sim(lbm, precision="fp32")
+    done = ctypes.c_int(-1)
+    res = np.full(1, -1.0)
+    rc = lbm.library().lbm_run_to_steady(a.ctx, 10, 0.0, 30, ctypes.byref(done),
+                                         res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert rc == 5 and done.value == 30 and res[0] > 0
+    done2, res2 = lbm.lbm_run_to_steady(a.ctx, 10, 0.0, 20, 1)
+    assert done2 == 20 and res2[0] > 0
+    a.close()
