@@ -49,6 +49,11 @@ def params(nu=NU, G=G):
 PARAMS = params()
 # all-fluid droplet check case: tau = 1 for both components (nu = 1/6)
 DROPLET_PARAMS = params(nu=(1 / 6, 1 / 6))
+# rough channel 512 x 256 x 256: defending component 1 at nu = 1.7, invading
+# component 2 at nu = 0.0017 (ratio 1000), wetting walls (rho^s = 0.2 favours
+# the invading component), periodic ends driven by a body force of 1e-5 along x
+ROUGH_PARAMS = dict(tau=(1.7 * 3 + 0.5, 0.0017 * 3 + 0.5), G=G, rho_s=0.2, g=(1e-5, 0.0, 0.0))
+WORKLOAD_PARAMS = {"spheres": PARAMS, "droplet": DROPLET_PARAMS, "rough": ROUGH_PARAMS}
 F_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
 
 
@@ -65,6 +70,10 @@ def alg_bytes_per_cell(part: str, precision: str) -> int:
         return 38 * s + 4 + 4 + ref + 2 * t
     if part == "collide":
         return 76 * s + 4 + 4 + 2 * t + 2 * ref
+    if part == "fused_compact":
+        # f once each way, reference pairs, packed coordinates and geometry word;
+        # psi stays on chip
+        return 76 * s + 4 + 4 + 2 * ref
     return 76 * s + 4 + 2 * ref  # fused, and each update of a cluster launch
 # DRAM traffic of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its fluid cells),
@@ -100,12 +109,15 @@ def sources_hash(files=COMPACT_SOURCES) -> str:
 
 
 def workload(n=N, kind="spheres"):
-    """The packed-sphere benchmark geometry, or (kind="droplet") an all-fluid
+    """The packed-sphere benchmark geometry n^3; (kind="droplet") an all-fluid
     periodic box with one droplet of radius n/8, used to see the kernel without
-    SOLID cells."""
+    SOLID cells; (kind="rough") the rough channel 2n x n x n with periodic ends
+    and an invading slug of component 2 in its first 32 planes."""
     from paper_1711_03254_gb300 import workloads as W
     if kind == "droplet":
         return W.droplet(n, n, n, n / 8.0)
+    if kind == "rough":
+        return W.rough_channel(2 * n, n, n, seed=4, invaded_length=32, ends="periodic")
     # the generated geometry is cached under a name that carries a hash of the
     # generator's source, so an edited generator never reuses an old file
     gen = os.path.join(ROOT, "paper_1711_03254_gb300", "workloads.py")
@@ -277,7 +289,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=N)
-    ap.add_argument("--workload", default="spheres", choices=["spheres", "droplet"])
+    ap.add_argument("--workload", default="spheres", choices=["spheres", "droplet", "rough"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -290,11 +302,12 @@ def main():
     lbm.use_torch_allocator()
     n = args.size
     t, r1, r2, u = workload(n, args.workload)
+    nz, ny, nx = t.shape
     fluid = int((t != 1).sum())
     stream = torch.cuda.current_stream()
 
-    par = PARAMS if args.workload == "spheres" else DROPLET_PARAMS
-    sim = lbm.Sim(n, n, n, [par], precision=args.precision, kernel=args.kernel)
+    par = WORKLOAD_PARAMS[args.workload]
+    sim = lbm.Sim(nx, ny, nz, [par], precision=args.precision, kernel=args.kernel)
     lbm.lbm_set_stream(sim.ctx, stream.cuda_stream)
     sim.set_geometry(t[None])
     sim.set_fields(r1[None], r2[None], u[None])
@@ -331,10 +344,13 @@ def main():
     if strategy == "compact":
         # compact layout: packed-pair update for the FP32-arithmetic storages
         kernel_name += {"psi": "_c", "collide": "_c" if args.precision == "fp64" else "_c2"}[part]
+    if strategy == "fused_compact":
+        kernel_name = "k_fused_c"
     # the method's own bytes per fluid-cell update (f in + f out + type byte):
     # the roofline's algorithmic figure for the dominant kernel and the step
     method_bytes = 2 * 38 * F_BYTES[args.precision] + 1
-    impl_bytes = alg_bytes_per_cell(part, args.precision)  # what this kernel moves at least
+    # what this kernel moves at least
+    impl_bytes = alg_bytes_per_cell("fused_compact" if strategy == "fused_compact" else part, args.precision)
     updates_per_launch = args.steps if part == "cluster" else 1
     avg_s = part_ms / part_launches / 1e3
     achieved = method_bytes * fluid * updates_per_launch / avg_s / 1e9
@@ -377,7 +393,7 @@ def main():
     e2e = None
     if ws == 1:
         ke = max(1, min(args.steps, 100))
-        sim2 = lbm.Sim(n, n, n, [par], precision=args.precision, kernel=args.kernel)
+        sim2 = lbm.Sim(nx, ny, nz, [par], precision=args.precision, kernel=args.kernel)
         lbm.lbm_set_stream(sim2.ctx, stream.cuda_stream)
 
         def pinned(a):

@@ -80,9 +80,14 @@ typedef enum {
     LBM_KERNEL_TWO_PASS = 1, /* density pre-pass, then stream+collide, over the non-solid cells */
     LBM_KERNEL_FUSED = 2,    /* single read of f: z-marching tiles with a recomputed density halo */
     LBM_KERNEL_CLUSTER = 3,  /* persistent: one thread-block cluster per instance, n updates per launch */
-    LBM_KERNEL_COMPACT = 4   /* two-pass on a compact layout that stores only the non-solid cells
+    LBM_KERNEL_COMPACT = 4,  /* two-pass on a compact layout that stores only the non-solid cells
                                 (in cell order; neighbours found from per-row occupancy words);
                                 needs nx <= 2048, ny <= 2048, nz <= 1024 */
+    LBM_KERNEL_FUSED_COMPACT = 5 /* single read of f on the compact layout: thread-block clusters
+                                march bands of rows along z, densities kept in shared memory;
+                                FP32 arithmetic only; where a plane's rows do not fit in shared
+                                memory the compact two-pass update runs instead (see
+                                lbm_resolved_kernel) */
 } lbm_kernel;
 
 typedef struct {
@@ -143,6 +148,48 @@ lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho1, const double *rho2, 
  * Errors: LBM_ERR_ARG (n < 0), LBM_ERR_STATE (no fields), LBM_ERR_CUDA
  * (launch failure). */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Split update for a decomposition of one domain into z-slabs (one process
+ * and context per slab; no counterpart in the paper, which runs one domain).
+ * Each context holds its slab plus one ghost plane on either side (periodic in
+ * z inside the context).  Per update the caller
+ *   1. puts into its lower ghost plane the LBM_PLANE_F_UP values of the lower
+ *      neighbour's last slab plane, and into its upper ghost plane the
+ *      LBM_PLANE_F_DOWN values of the upper neighbour's first slab plane
+ *      (the post-collision values that stream across the faces, Eq. 1);
+ *   2. runs lbm_step_part(ctx, 0): the density pass, psi of every cell (Eq. 7);
+ *   3. puts the neighbours' psi of those planes into its ghost planes
+ *      (LBM_PLANE_PSI: the interaction force of Eq. 7 reaches one cell);
+ *   4. runs lbm_step_part(ctx, 1): the collision pass, completing the update.
+ * The slab cells then match the single-domain update bit for bit; the ghost
+ * cells hold meaningless values (also in lbm_get_fields and lbm_reduce).
+ * Needs the compact layout's limits (the split update is the compact
+ * two-pass one, whatever lbm_set_kernel chose); part 1 must follow part 0, and
+ * lbm_step is refused in between (LBM_ERR_STATE).
+ * Errors: LBM_ERR_ARG (part not 0 or 1, grid beyond the compact limits),
+ * LBM_ERR_STATE (no fields, parts out of order), LBM_ERR_CUDA. */
+lbm_status lbm_step_part(lbm_ctx *ctx, int part);
+
+typedef enum {
+    LBM_PLANE_F_UP = 0,   /* f* of the 5 directions with c_z = +1: [5][cells of the plane] pairs */
+    LBM_PLANE_F_DOWN = 1, /* f* of the 5 directions with c_z = -1 */
+    LBM_PLANE_PSI = 2     /* psi pairs of the plane's cells: [cells] */
+} lbm_plane_part;
+
+/* Bytes of one plane's part (instance 0): cells of plane z x (5 f pairs, or
+ * one psi pair); an f pair is both components in the storage format (2 x 8,
+ * 4 or 2 bytes, as stored: deviations from the reference densities in the
+ * shifted modes), a psi pair 2 x 8 (FP64) or 2 x 4 bytes.  Cells are the
+ * plane's non-solid cells in cell order.  Errors: LBM_ERR_ARG (batch != 1, part
+ * or plane out of range), LBM_ERR_STATE (no geometry within the compact
+ * limits). */
+lbm_status lbm_plane_bytes(lbm_ctx *ctx, int what, int z, size_t *bytes);
+
+/* Copy one plane's part between the context's current state and buf (host or
+ * device memory, lbm_plane_bytes long; to_buf != 0 reads the context, 0
+ * writes it).  Synchronises the stream.  Errors as lbm_plane_bytes, plus
+ * LBM_ERR_ARG (null buf), LBM_ERR_CUDA. */
+lbm_status lbm_plane_copy(lbm_ctx *ctx, int what, int z, void *buf, int to_buf);
 
 /* Copy the macroscopic fields of the last update (or of lbm_set_fields) to
  * host FP64 arrays rho1, rho2 [batch][nz][ny][nx], u [batch][nz][ny][nx][3]

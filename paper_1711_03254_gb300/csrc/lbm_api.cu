@@ -1,5 +1,6 @@
 // Host runtime behind the C ABI of include/lbm.h: context, device buffers,
 // argument checks, kernel dispatch, read-back and checkpoints.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -51,12 +52,15 @@ struct lbm_ctx {
     int *list_count = nullptr; // entries per instance
     long long list_max = 0;
     long long nonsolid = 0;    // non-solid cells over all instances
-    // compact layout: 0 = f, ref dense; 1 = compact (LBM_KERNEL_COMPACT)
+    // compact layout: 0 = f, ref dense; 1 = compact (LBM_KERNEL_COMPACT, LBM_KERNEL_FUSED_COMPACT)
     int layout = 0;
     bool compact_ok = false;   // grid within the packed-coordinate limits
     uint32_t *cxyz = nullptr, *clink = nullptr;
     uint2 *rowtab = nullptr;
     int words = 0;
+    FcPlan fplan{};  // single-read fused update on the compact layout (ok when it fits)
+    std::vector<uint32_t> plane_start;  // compact index of each plane's first cell (instance 0), nz + 1
+    bool half_step = false;             // the density pass of a split update has run
     void *psi = nullptr, *macro = nullptr, *usnap = nullptr, *dpar = nullptr;
     double *partial = nullptr, *red_out = nullptr;
     int nblk = 0;
@@ -189,6 +193,9 @@ lbm_status upload_params(lbm_ctx *ctx) {
 // grid fits its packed coordinates, the dense two-pass one otherwise.
 lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
     (void)n;
+    // the fused compact update needs its rows and lag buffer to fit in shared
+    // memory; where they do not, its layout's two-pass update runs
+    if (ctx->kernel == LBM_KERNEL_FUSED_COMPACT) return ctx->fplan.ok ? LBM_KERNEL_FUSED_COMPACT : LBM_KERNEL_COMPACT;
     if (ctx->kernel != LBM_KERNEL_AUTO) return ctx->kernel;
     // measured on GB300: the two-pass update on the compact layout beats the
     // dense two-pass one on porous (1.5x) and all-fluid (1.1x) grids, the fused
@@ -196,6 +203,8 @@ lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
     // (16^3 to 32^3, 1 to 16 instances: 1.4-10x)
     return ctx->compact_ok ? LBM_KERNEL_COMPACT : LBM_KERNEL_TWO_PASS;
 }
+
+bool uses_compact_layout(lbm_kernel k) { return k == LBM_KERNEL_COMPACT || k == LBM_KERNEL_FUSED_COMPACT; }
 
 // Fused-kernel tiling when none was set: 32x8 columns (32x4 in FP64, whose
 // ring buffers are twice as large), z chunks sized for about eight CTAs per SM.
@@ -214,6 +223,42 @@ void default_tiling(const lbm_ctx *ctx, int &tile, int &zchunk) {
         zchunk = (int)((ctx->g.nz + chunks - 1) / chunks);
         if (zchunk < 8) zchunk = ctx->g.nz < 8 ? ctx->g.nz : 8;
     }
+}
+
+// Plan of the single-read fused update on the compact layout: its lag buffer
+// holds the non-solid cells of one group of rows of one plane, so the largest
+// such count over the geometry (from the rows' first compact indices) sizes it.
+lbm_status plan_fused_compact(lbm_ctx *ctx) {
+    ctx->fplan = FcPlan{};
+    ctx->plane_start.clear();
+    if (!ctx->compact_ok) return LBM_OK;
+    const int B = ctx->cfg.batch, ny = ctx->g.ny, nz = ctx->g.nz, rc = fusedc_rows_per_cta();
+    const size_t rows = (size_t)ny * nz;
+    std::vector<uint32_t> start((size_t)B * (rows + 1));
+    for (int b = 0; b < B; ++b) {
+        const uint2 *src = ctx->rowtab + (size_t)b * (rows + 1) * ctx->words;
+        LBM_CUDA(cudaMemcpy2DAsync(start.data() + (size_t)b * (rows + 1), sizeof(uint32_t), src,
+                                   sizeof(uint2) * ctx->words, sizeof(uint32_t), rows + 1, cudaMemcpyDeviceToHost,
+                                   ctx->stream),
+                 "fused plan: row starts");
+    }
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "fused plan: row starts");
+    ctx->plane_start.resize((size_t)nz + 1);
+    for (int z = 0; z <= nz; ++z) ctx->plane_start[z] = start[(size_t)z * ny];
+    if (ctx->fp64()) return LBM_OK;
+    long long cap = 0;
+    for (int b = 0; b < B; ++b) {
+        const uint32_t *st = start.data() + (size_t)b * (rows + 1);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; y += rc) {
+                const size_t r0 = (size_t)z * ny + y, r1 = (size_t)z * ny + std::min(y + rc, ny);
+                cap = std::max<long long>(cap, (long long)st[r1] - (long long)st[r0]);
+            }
+    }
+    LBM_CUDA(fusedc_plan(ctx->cfg.precision, ctx->cfg.eq_order, ctx->g, B, (int)std::max<long long>(cap, 1),
+                         ctx->fplan),
+             "fused plan");
+    return LBM_OK;
 }
 
 // Lists of the non-solid cells of every instance (in cell order) for the
@@ -259,7 +304,7 @@ lbm_status build_cell_lists(lbm_ctx *ctx) {
     ctx->dfree(rowcnt);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "cell lists");
     ctx->launches += ctx->compact_ok ? 5 : 4;
-    return LBM_OK;
+    return plan_fused_compact(ctx);
 }
 
 // Bring f and the reference densities of the current state into `want`
@@ -450,12 +495,14 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
 
 lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
     if (!ctx) return LBM_ERR_ARG;
-    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_COMPACT)
+    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_FUSED_COMPACT)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: unknown strategy");
     if (kernel == LBM_KERNEL_CLUSTER && ctx->g.n > kClusterMaxCells)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: CLUSTER needs at most 65536 cells per instance");
     if (kernel == LBM_KERNEL_COMPACT && !ctx->compact_ok)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: COMPACT needs nx <= 2048, ny <= 2048, nz <= 1024");
+    if (kernel == LBM_KERNEL_FUSED_COMPACT && (!ctx->compact_ok || ctx->fp64()))
+        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: FUSED_COMPACT needs the compact layout and FP32 arithmetic");
     ctx->kernel = kernel;
     return LBM_OK;
 }
@@ -511,7 +558,8 @@ lbm_status lbm_timing_end(lbm_ctx *ctx, double *ms, long long *launches) {
             launches[LBM_PART_COLLIDE] += 1;
         } else {
             e = cudaEventElapsedTime(&a, ev[0], ev[1]);
-            const int p = t.kind == LBM_KERNEL_FUSED ? LBM_PART_FUSED : LBM_PART_CLUSTER;
+            const int p = (t.kind == LBM_KERNEL_FUSED || t.kind == LBM_KERNEL_FUSED_COMPACT) ? LBM_PART_FUSED
+                                                                                         : LBM_PART_CLUSTER;
             ms[p] += a;
             launches[p] += 1;
         }
@@ -567,6 +615,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *cell_type) {
     if (s != LBM_OK) return s;
     ctx->has_geometry = true;
     ctx->has_fields = false;
+    ctx->half_step = false;
     ctx->layout = 0;
     return LBM_OK;
 }
@@ -605,6 +654,7 @@ lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho1, const double *rho2, 
     ctx->launches += 1;
     ctx->layout = 0;
     ctx->has_fields = true;
+    ctx->half_step = false;
     ctx->since_snap = 0;
     return LBM_OK;
 }
@@ -613,10 +663,11 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     if (!ctx) return LBM_ERR_ARG;
     if (n < 0) return ctx->fail(LBM_ERR_ARG, "lbm_step: negative step count");
     if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_step: call lbm_set_fields first");
+    if (ctx->half_step) return ctx->fail(LBM_ERR_STATE, "lbm_step: finish the split update (lbm_step_part 1) first");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
     const lbm_kernel k = resolve_kernel(ctx, n);
     if (n > 0) {
-        const lbm_status ls = ensure_layout(ctx, k == LBM_KERNEL_COMPACT ? 1 : 0);
+        const lbm_status ls = ensure_layout(ctx, uses_compact_layout(k) ? 1 : 0);
         if (ls != LBM_OK) return ls;
     }
     if (k == LBM_KERNEL_CLUSTER) {
@@ -633,19 +684,100 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
         return LBM_OK;
     }
     const bool fused = k == LBM_KERNEL_FUSED;
+    const bool one_launch = fused || k == LBM_KERNEL_FUSED_COMPACT;
     int tile = ctx->tile, zchunk = ctx->zchunk;
     if (fused) default_tiling(ctx, tile, zchunk);
     for (int s = 0; s < n; ++s) {
         StepArgs a = step_args(ctx, s == n - 1);
         a.ev = ctx->events_for(k);
         cudaError_t e = fused ? launch_fused(a, tile, zchunk)
-                              : (k == LBM_KERNEL_COMPACT ? launch_compact(a) : launch_two_pass(a));
+                        : k == LBM_KERNEL_FUSED_COMPACT ? launch_fusedc(a, ctx->fplan)
+                        : (k == LBM_KERNEL_COMPACT ? launch_compact(a) : launch_two_pass(a));
         if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_step launch");
-        ctx->launches += fused ? 1 : 2;
+        ctx->launches += one_launch ? 1 : 2;
         ctx->cur ^= 1;
     }
     ctx->step += n;
     ctx->since_snap += n;
+    return LBM_OK;
+}
+
+lbm_status lbm_step_part(lbm_ctx *ctx, int part) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (part != 0 && part != 1) return ctx->fail(LBM_ERR_ARG, "lbm_step_part: part must be 0 or 1");
+    if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_step_part: call lbm_set_fields first");
+    if (!ctx->compact_ok) return ctx->fail(LBM_ERR_ARG, "lbm_step_part: needs the compact layout's limits");
+    if ((part == 1) != ctx->half_step)
+        return ctx->fail(LBM_ERR_STATE, part ? "lbm_step_part: run the density pass (part 0) first"
+                                             : "lbm_step_part: the collision pass (part 1) is pending");
+    LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    const lbm_status ls = ensure_layout(ctx, 1);
+    if (ls != LBM_OK) return ls;
+    StepArgs a = step_args(ctx, 1);
+    LBM_CUDA(launch_compact(a, part == 0 ? 1 : 2), "lbm_step_part launch");
+    ctx->launches += 1;
+    if (part == 1) {
+        ctx->cur ^= 1;
+        ctx->step += 1;
+        ctx->since_snap += 1;
+    }
+    ctx->half_step = part == 0;
+    return LBM_OK;
+}
+
+// D3Q19 directions (this library's order) with c_z = +1 and c_z = -1
+static const int kUpDirs[5] = {5, 11, 14, 15, 18};
+static const int kDownDirs[5] = {6, 12, 13, 16, 17};
+
+static lbm_status plane_args(lbm_ctx *ctx, int what, int z, size_t &cells, size_t &unit) {
+    if (ctx->cfg.batch != 1) return ctx->fail(LBM_ERR_ARG, "plane copy: one instance per context only");
+    if (what < LBM_PLANE_F_UP || what > LBM_PLANE_PSI) return ctx->fail(LBM_ERR_ARG, "plane copy: unknown part");
+    if (z < 0 || z >= ctx->g.nz) return ctx->fail(LBM_ERR_ARG, "plane copy: plane out of range");
+    if (!ctx->compact_ok || ctx->plane_start.size() != (size_t)ctx->g.nz + 1)
+        return ctx->fail(LBM_ERR_STATE, "plane copy: needs a geometry within the compact layout's limits");
+    cells = ctx->plane_start[z + 1] - ctx->plane_start[z];
+    const size_t pair_f = 2 * storage_bytes(ctx->cfg.precision), pair_psi = 2 * ctx->tbytes();
+    unit = what == LBM_PLANE_PSI ? pair_psi : 5 * pair_f;
+    return LBM_OK;
+}
+
+lbm_status lbm_plane_bytes(lbm_ctx *ctx, int what, int z, size_t *bytes) {
+    if (!ctx || !bytes) return ctx ? ctx->fail(LBM_ERR_ARG, "lbm_plane_bytes: null argument") : LBM_ERR_ARG;
+    size_t cells = 0, unit = 0;
+    const lbm_status s = plane_args(ctx, what, z, cells, unit);
+    if (s != LBM_OK) return s;
+    *bytes = cells * unit;
+    return LBM_OK;
+}
+
+lbm_status lbm_plane_copy(lbm_ctx *ctx, int what, int z, void *buf, int to_buf) {
+    if (!ctx || !buf) return ctx ? ctx->fail(LBM_ERR_ARG, "lbm_plane_copy: null argument") : LBM_ERR_ARG;
+    if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_plane_copy: call lbm_set_fields first");
+    size_t cells = 0, unit = 0;
+    const lbm_status s = plane_args(ctx, what, z, cells, unit);
+    if (s != LBM_OK) return s;
+    LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    const lbm_status ls = ensure_layout(ctx, 1);
+    if (ls != LBM_OK) return ls;
+    const size_t k0 = ctx->plane_start[z];
+    char *b = (char *)buf;
+    if (what == LBM_PLANE_PSI) {
+        char *d = (char *)ctx->psi + k0 * unit;
+        LBM_CUDA(cudaMemcpyAsync(to_buf ? (void *)b : (void *)d, to_buf ? (const void *)d : (const void *)b,
+                                 cells * unit, cudaMemcpyDefault, ctx->stream),
+                 "lbm_plane_copy");
+    } else {
+        const size_t pair = unit / 5, kmax = (size_t)ctx->list_max;
+        const int *dirs = what == LBM_PLANE_F_UP ? kUpDirs : kDownDirs;
+        for (int m = 0; m < 5; ++m) {
+            char *d = (char *)ctx->f[ctx->cur] + ((size_t)dirs[m] * kmax + k0) * pair;
+            char *h = b + (size_t)m * cells * pair;
+            LBM_CUDA(cudaMemcpyAsync(to_buf ? (void *)h : (void *)d, to_buf ? (const void *)d : (const void *)h,
+                                     cells * pair, cudaMemcpyDefault, ctx->stream),
+                     "lbm_plane_copy");
+        }
+    }
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "lbm_plane_copy");
     return LBM_OK;
 }
 
@@ -836,6 +968,7 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes) {
     ctx->since_snap = h.since_snap;
     ctx->layout = (int)h.layout;
     ctx->has_geometry = ctx->has_fields = true;
+    ctx->half_step = false;
     return LBM_OK;
 }
 
@@ -909,6 +1042,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     std::vector<Cand> cands;
     cands.push_back({LBM_KERNEL_TWO_PASS, -1, -1});
     if (ctx->compact_ok) cands.push_back({LBM_KERNEL_COMPACT, -1, -1});
+    if (ctx->fplan.ok) cands.push_back({LBM_KERNEL_FUSED_COMPACT, -1, -1});
     if (ctx->g.n <= kClusterMaxCells) cands.push_back({LBM_KERNEL_CLUSTER, -1, -1});
     for (int t = 0; t < fused_tile_count(); ++t) {
         cands.push_back({LBM_KERNEL_FUSED, t, -1});
@@ -989,7 +1123,7 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
     const int B = ctx->cfg.batch;
     {
         // convert the layout now: a conversion must not be captured into the graphs
-        const lbm_status ls = ensure_layout(ctx, resolve_kernel(ctx, check_every) == LBM_KERNEL_COMPACT ? 1 : 0);
+        const lbm_status ls = ensure_layout(ctx, uses_compact_layout(resolve_kernel(ctx, check_every)) ? 1 : 0);
         if (ls != LBM_OK) return ls;
     }
     // capture on a private stream ordered after the context's stream
@@ -1046,7 +1180,9 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
     bool diverged = false, conv = false;
     const lbm_kernel kres = resolve_kernel(ctx, check_every);
     const long long launches_per_replay =
-        (kres == LBM_KERNEL_CLUSTER ? 1 : (kres == LBM_KERNEL_FUSED ? check_every : 2LL * check_every)) + 2;
+        (kres == LBM_KERNEL_CLUSTER ? 1
+         : (kres == LBM_KERNEL_FUSED || kres == LBM_KERNEL_FUSED_COMPACT) ? check_every
+                                                                         : 2LL * check_every) + 2;
     ctx->since_snap = 0;  // the first replay measures against the current snapshot
     while (e == cudaSuccess && done + check_every <= max_steps) {
         e = cudaGraphLaunch(exec[ctx->cur], cs);  // graphs are indexed by the side holding the state

@@ -344,38 +344,43 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
     }
 }
 
+// parts: bit 0 the density pass, bit 1 the collision pass (both: one update;
+// one at a time: the split update of a domain decomposition, with the ghost
+// planes exchanged in between)
 template <class S>
-static cudaError_t launch_compact_t(const StepArgs &a) {
+static cudaError_t launch_compact_t(const StepArgs &a, int parts) {
     const long long m = a.list_max > 0 ? a.list_max : 1;
     const dim3 gp((unsigned)((m + kPsiThreads - 1) / kPsiThreads), (unsigned)a.batch, 1);
     const dim3 gc((unsigned)((m + kCollideThreads - 1) / kCollideThreads), (unsigned)a.batch, 1);
     record_event(a, 0);
-    k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
+    if (parts & 1) k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
     record_event(a, 1);
     // (a persistent variant that prefetches the next cell with cp.async, as the
     // psi pass does, measured 10 % slower here: the update is issue-bound, and
     // the prefetch buffers cost occupancy and registers)
-    if constexpr (packed_pairs<S>()) {
-        if (a.eq_order == 0)
-            k_collide_c2<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
-        else
-            k_collide_c2<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
-    } else {
-        if (a.eq_order == 0)
-            k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
-        else
-            k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
+    if (parts & 2) {
+        if constexpr (packed_pairs<S>()) {
+            if (a.eq_order == 0)
+                k_collide_c2<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
+            else
+                k_collide_c2<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
+        } else {
+            if (a.eq_order == 0)
+                k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
+            else
+                k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
+        }
     }
     record_event(a, 2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const StepArgs &a) {
+cudaError_t launch_compact(const StepArgs &a, int parts) {
     switch (a.precision) {
-    case LBM_FP64: return launch_compact_t<double>(a);
-    case LBM_FP32: return launch_compact_t<float>(a);
-    case LBM_FP32_F16S: return launch_compact_t<__half>(a);
-    case LBM_FP32_BF16S: return launch_compact_t<__nv_bfloat16>(a);
+    case LBM_FP64: return launch_compact_t<double>(a, parts);
+    case LBM_FP32: return launch_compact_t<float>(a, parts);
+    case LBM_FP32_F16S: return launch_compact_t<__half>(a, parts);
+    case LBM_FP32_BF16S: return launch_compact_t<__nv_bfloat16>(a, parts);
     }
     return cudaErrorInvalidValue;
 }

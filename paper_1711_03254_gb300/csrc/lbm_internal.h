@@ -103,7 +103,19 @@ cudaError_t launch_row_fill(const uint32_t *link, const Grid &g, int batch, uint
 
 // compact layout
 constexpr int kCompactMaxX = 2048, kCompactMaxY = 2048, kCompactMaxZ = 1024;
-cudaError_t launch_compact(const StepArgs &a);
+
+// single-read fused update on the compact layout (lbm_fusedc.cu)
+struct FcPlan {
+    int bands = 0, chunks = 0, units = 0;  // bands of rows x z chunks x instances
+    int lag_cap = 0;                       // cells per lag slot
+    int clusters = 0;                      // clusters launched (co-resident)
+    size_t smem = 0;                       // dynamic shared memory per CTA
+    bool ok = false;                       // fits this geometry and device
+};
+int fusedc_rows_per_cta();
+cudaError_t fusedc_plan(lbm_precision prec, int eq_order, const Grid &g, int batch, int lag_cap, FcPlan &out);
+cudaError_t launch_fusedc(const StepArgs &a, const FcPlan &p);
+cudaError_t launch_compact(const StepArgs &a, int parts = 3);
 // geometry words of the listed cells: clink[b][k] = link[b][list[b][k]]
 cudaError_t launch_compact_links(const uint32_t *list, const int *count, const uint32_t *link, uint32_t *clink,
                                  const Grid &g, int batch, uint32_t kmax, cudaStream_t s);

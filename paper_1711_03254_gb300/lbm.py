@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
 LBM_FP64, LBM_FP32, LBM_FP32_F16S, LBM_FP32_BF16S = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP32_F16S, "bf16s": LBM_FP32_BF16S}
 LBM_KERNEL_AUTO, LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED, LBM_KERNEL_CLUSTER = 0, 1, 2, 3
-KERNELS = {"auto": 0, "two_pass": 1, "fused": 2, "cluster": 3, "compact": 4}
+KERNELS = {"auto": 0, "two_pass": 1, "fused": 2, "cluster": 3, "compact": 4, "fused_compact": 5}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM", 4: "LBM_ERR_DIVERGED",
           5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 
@@ -79,9 +79,12 @@ def library() -> ctypes.CDLL:
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_destroy.argtypes = [vp]
         L.lbm_destroy.restype = None
+        L.lbm_step_part.argtypes = [vp, ctypes.c_int]
+        L.lbm_plane_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+        L.lbm_plane_copy.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
         for name in ("lbm_create", "lbm_set_geometry", "lbm_set_fields", "lbm_step", "lbm_get_fields",
                      "lbm_reduce", "lbm_get_distributions", "lbm_set_distributions", "lbm_get_state", "lbm_set_state", "lbm_set_stream", "lbm_set_kernel", "lbm_set_tiling", "lbm_autotune", "lbm_run_to_steady",
-                     "lbm_set_allocator"):
+                     "lbm_set_allocator", "lbm_step_part", "lbm_plane_bytes", "lbm_plane_copy"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -309,6 +312,36 @@ class Sim:
     @property
     def launches(self):
         return lbm_launch_count(self.ctx)
+
+
+PLANE_PARTS = {"f_up": 0, "f_down": 1, "psi": 2}
+
+
+def lbm_step_part(ctx, part: int):
+    """Half of a split update: 0 the density pass, 1 the collision pass."""
+    _check(library().lbm_step_part(ctx, int(part)), ctx)
+
+
+def lbm_plane_bytes(ctx, what: str, z: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(library().lbm_plane_bytes(ctx, PLANE_PARTS[what], int(z), ctypes.byref(n)), ctx)
+    return n.value
+
+
+def lbm_plane_get(ctx, what: str, z: int) -> np.ndarray:
+    """One plane's crossing distributions or psi pairs as raw bytes (uint8)."""
+    buf = np.empty(lbm_plane_bytes(ctx, what, z), dtype=np.uint8)
+    if buf.size:
+        _check(library().lbm_plane_copy(ctx, PLANE_PARTS[what], int(z), buf.ctypes.data, 1), ctx)
+    return buf
+
+
+def lbm_plane_set(ctx, what: str, z: int, buf: np.ndarray):
+    b = np.ascontiguousarray(buf, dtype=np.uint8)
+    if b.size != lbm_plane_bytes(ctx, what, z):
+        raise ValueError("plane buffer has the wrong size")
+    if b.size:
+        _check(library().lbm_plane_copy(ctx, PLANE_PARTS[what], int(z), b.ctypes.data, 0), ctx)
 
 
 def lbm_last_error(ctx=None) -> str:

@@ -14,8 +14,9 @@ Workloads (the paper's validation geometries, Sec. 3, in synthetic form):
   * ``packed_spheres`` porous medium of overlapping spheres with a 1 % minority
                        of droplets (stand-in for the packed-sphere geometry of
                        Sec. 3.5);
-  * ``rough_channel``  channel with seeded wall bumps, inlet and outlet planes
-                       (the displacement / fingering geometry family, Sec. 3.6-3.7);
+  * ``rough_channel``  channel with seeded wall bumps, with inlet and outlet
+                       planes or periodic ends (the displacement / fingering
+                       geometry family, Sec. 3.6-3.7);
   * ``inclined_droplet`` droplet on an inclined wall (Sec. 3.4).
 """
 from __future__ import annotations
@@ -172,13 +173,17 @@ def packed_spheres(n: int = 256, r: float = 12.0, porosity: float = 0.40, seed: 
 
 
 def rough_channel(nx: int = 512, ny: int = 256, nz: int = 256, seed: int = 4, hmax: float = 4.0,
-                  bumps_per_kcell: float = 0.5, invaded_length: int = 8):
-    """Channel along x with SOLID walls on the y and z faces, seeded hemispherical
-    bumps of height <= hmax on those walls, an INLET plane at x = 0 and an
-    OUTLET plane at x = nx - 1.  The invading component 2 fills the first
-    ``invaded_length`` planes; component 1 (defending) fills the rest.
-    Returns (cell_type, rho1, rho2, u).
+                  bumps_per_kcell: float = 0.5, invaded_length: int = 8, ends: str = "inlet_outlet"):
+    """Channel along x with SOLID walls on the y and z faces and seeded
+    hemispherical bumps of height <= hmax on those walls.  ends="inlet_outlet":
+    an INLET plane at x = 0 and an OUTLET plane at x = nx - 1; ends="periodic":
+    none (the channel is periodic along x and driven by a body force, as the
+    displacement and fingering channels of Sec. 3.6 and 3.7 are).  The invading
+    component 2 fills the first ``invaded_length`` planes; component 1
+    (defending) fills the rest.  Returns (cell_type, rho1, rho2, u).
     """
+    if ends not in ("inlet_outlet", "periodic"):
+        raise ValueError("ends must be 'inlet_outlet' or 'periodic'")
     rng = np.random.default_rng(seed)
     solid = np.zeros((nz, ny, nx), dtype=bool)
     solid[:, 0, :] = True
@@ -201,8 +206,9 @@ def rough_channel(nx: int = 512, ny: int = 256, nz: int = 256, seed: int = 4, hm
             c = np.array([[z, y, x]])
         _stamp_spheres(solid, c, h)
     t = np.where(solid, SOLID, FLUID).astype(np.uint8)
-    t[:, :, 0][~solid[:, :, 0]] = INLET
-    t[:, :, nx - 1][~solid[:, :, nx - 1]] = OUTLET
+    if ends == "inlet_outlet":
+        t[:, :, 0][~solid[:, :, 0]] = INLET
+        t[:, :, nx - 1][~solid[:, :, nx - 1]] = OUTLET
     fluid = ~solid
     xs = np.arange(nx)[None, None, :]
     comp2 = fluid & (xs < invaded_length)
