@@ -328,11 +328,17 @@ def lbm_plane_bytes(ctx, what: str, z: int) -> int:
     return n.value
 
 
+def lbm_plane_copy(ctx, what: str, z: int, buf_ptr: int, to_buf: bool):
+    """Copy one plane's part between the context and the buffer at buf_ptr
+    (host or device address, lbm_plane_bytes long)."""
+    _check(library().lbm_plane_copy(ctx, PLANE_PARTS[what], int(z), buf_ptr, 1 if to_buf else 0), ctx)
+
+
 def lbm_plane_get(ctx, what: str, z: int) -> np.ndarray:
     """One plane's crossing distributions or psi pairs as raw bytes (uint8)."""
     buf = np.empty(lbm_plane_bytes(ctx, what, z), dtype=np.uint8)
     if buf.size:
-        _check(library().lbm_plane_copy(ctx, PLANE_PARTS[what], int(z), buf.ctypes.data, 1), ctx)
+        lbm_plane_copy(ctx, what, z, buf.ctypes.data, True)
     return buf
 
 
@@ -341,7 +347,7 @@ def lbm_plane_set(ctx, what: str, z: int, buf: np.ndarray):
     if b.size != lbm_plane_bytes(ctx, what, z):
         raise ValueError("plane buffer has the wrong size")
     if b.size:
-        _check(library().lbm_plane_copy(ctx, PLANE_PARTS[what], int(z), b.ctypes.data, 0), ctx)
+        lbm_plane_copy(ctx, what, z, b.ctypes.data, False)
 
 
 def lbm_last_error(ctx=None) -> str:
