@@ -207,14 +207,14 @@ def max_over_ranks(x: float, ws: int) -> float:
     return replicas.max_over_ranks(x)
 
 
-def cpu_baseline(t, r1, r2, u, target_s=15.0, crop=64):
+def cpu_baseline(t, r1, r2, u, target_s=15.0, crop=64, params=None, name="256^3 packed-sphere workload"):
     """Time the FP64 oracle, as it stands, on host cores over a bounded sample:
     a crop^3 corner of the same geometry for as many updates as fit ~target_s."""
     import oracle
     oracle.build()
     c = (slice(0, crop),) * 3
     tc, a, b, v = t[c].copy(), r1[c].copy(), r2[c].copy(), u[c].copy()
-    sim = oracle.OracleSim(crop, crop, crop, [PARAMS])
+    sim = oracle.OracleSim(crop, crop, crop, [params or PARAMS])
     sim.set_geometry(tc[None])
     sim.set_fields(a[None], b[None], v[None])
     sim.step(1)
@@ -228,7 +228,7 @@ def cpu_baseline(t, r1, r2, u, target_s=15.0, crop=64):
     fluid = int((tc != 1).sum())
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": fluid * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{crop}^3 corner of the 256^3 packed-sphere workload, {steps} updates, FP64"}
+            "sample": f"{crop}^3 corner of the {name}, {steps} updates, FP64"}
 
 
 def run_reference(args):
@@ -418,17 +418,22 @@ def main():
 
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(t, r1, r2, u)
+        cb = cpu_baseline(t, r1, r2, u, params=par,
+                          name={"spheres": f"{n}^3 packed-sphere workload", "droplet": f"{n}^3 droplet workload",
+                                "rough": f"{2 * n}x{n}x{n} rough channel"}[args.workload])
 
     if rank == 0:
         line = {"metric": "MLUPS (fluid-cell updates per second, 2-comp D3Q19)", "value": round(mlups, 1),
                 "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-                "config": {"workload": (f"packed spheres {n}^3, r=12, porosity 0.40, 1% minority r=4, "
-                                        f"nu {NU[0]}/{NU[1]} (ratio 100), G={G}, g=1e-6, wall model 2"
-                                        if args.workload == "spheres" else
-                                        f"periodic droplet {n}^3, R={n // 8}, tau 1/1, G={G}, no walls"),
+                "config": {"workload": {
+                    "spheres": (f"packed spheres {n}^3, r=12, porosity 0.40, 1% minority r=4, "
+                                f"nu {NU[0]}/{NU[1]} (ratio 100), G={G}, g=1e-6, wall model 2"),
+                    "droplet": f"periodic droplet {n}^3, R={n // 8}, tau 1/1, G={G}, no walls",
+                    "rough": (f"rough channel {2 * n}x{n}x{n}, walls on y and z with seeded bumps <= 4, "
+                              f"periodic ends, invading slug nu 0.0017 vs defending nu 1.7 (ratio 1000), "
+                              f"G={G}, rho^s 0.2, g=1e-5 along x, wall model 2")}[args.workload],
                            "storage": args.precision, "kernel": args.kernel, "strategy": strategy,
                            "fluid_cells": fluid,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},

@@ -6,34 +6,40 @@
 // Here f is pulled once, and psi never goes through HBM.
 //
 // Work decomposition.  A thread-block cluster of kFcCluster CTAs owns a band of
-// kFcCluster * kFcRows rows (y) of one instance and marches a chunk of planes
-// [za, zb) along z.  CTA r of the cluster owns rows y0 + r kFcRows ... of the
-// band.  For every plane p = za - 1 ... zb:
-//   A  pull the 19 stored pairs of every non-solid cell of the CTA's rows in
-//      plane p (S1), sum them to the density pair (S2, S3) and write it to a
-//      ring of psi planes in shared memory; the pulled pairs, the reference
-//      densities, the coordinates and the geometry word go to a lag buffer in
-//      shared memory (planes za ... zb - 1 only).  The two rows just outside the
-//      band (y0 - 1 and the row after the band, wrapped) are pulled for their
-//      densities only, shared out over the cluster's CTAs and written into the
-//      ring of the CTA that borders them (distributed shared memory).
-//   -- cluster barrier: psi of plane p is complete in every CTA --
-//   B  collide plane p - 1 (S4-S7): moments from the lag buffer, psi of the 18
-//      neighbours from the ring (rows of the neighbouring CTAs through
-//      distributed shared memory), and store f* and the reference densities.
-// Planes za - 1 and zb are recomputed halos (their densities only); the
-// recompute costs 2 / (zb - za) of a chunk's pulls.  The rows just outside a
-// band cost 2 / (kFcCluster kFcRows) of a plane's pulls.
+// kFcCluster rows (y) of one instance, one row per CTA, and marches a chunk of
+// planes [za, zb) along z; planes za - 1 and zb are recomputed halos (their
+// densities only).  The two rows just outside the band are pulled for their
+// densities too, their cells shared out over the cluster's CTAs.
 //
-// Synchronisation.  The ring holds kFcSlots = 4 planes, so the plane written by
-// A(p + 1) is none of the three read by B(p), and one cluster barrier per plane
-// suffices: the slot A(p + 2) overwrites was last read in B(p), which every CTA
-// finished before arriving at the barrier of plane p + 1.  The lag buffer has
-// two slots and is private to each thread: thread t pulls cells t, t + T, ...
-// of a plane in A and collides the same cells in B.  A barrier ends every
-// chunk (the next chunk restarts the ring) and the kernel, so no CTA leaves
-// while another can still read its shared memory.  The barriers are the
-// hardware cluster barrier (no software spin-wait).
+// Pipeline.  Iteration `it` handles plane p = za - 1 + it:
+//   S1  wait for the copies issued in the previous iteration; CTA barrier.
+//   S2  densities (S2, S3 of the update) of plane p's cells from their pulled
+//       pairs in the lag buffer, into the ring of psi planes in shared memory;
+//       the outside rows' densities go into the ring of the CTA that borders
+//       them (distributed shared memory).
+//   S3  cluster barrier: psi of plane p is complete in every CTA.
+//   S4  issue the pulls of plane p + 1 (S1 of the update) as asynchronous
+//       copies (cp.async) straight into the lag buffer; the neighbour indices
+//       come from the row table staged in shared memory.
+//   S5  stage the coordinates and geometry words of plane p + 2's cells and
+//       the row table of plane p + 3 (asynchronous copies).
+//   S6  collide plane p - 1 (S4-S7): moments from the lag buffer, psi of the
+//       18 neighbours from the ring (rows of the neighbouring CTAs through
+//       distributed shared memory), store f* and the reference densities.
+// The copies of S4 and S5 are in flight while S6 computes, so the collision
+// hides the memory latency of the next plane, and every memory access of a
+// cell's pull is issued at once (no chain of dependent loads).
+//
+// Synchronisation.  The psi ring holds 4 planes, so the plane S2 writes is none
+// of the three S6 of the previous iteration read; the slot S2 overwrites two
+// iterations later was last read before the cluster barrier in between.  The
+// lag buffer has 3 slots (plane p + 1 in flight, plane p waiting for its
+// collision, plane p - 1 being collided) and is private to each thread: thread
+// t pulls cells t, t + T, ... of its row in every plane and collides the same
+// cells.  Staged row tables and geometry are shared and published by the CTA
+// barrier of S1.  A cluster barrier ends every chunk and the kernel, so no CTA
+// leaves while another can still read its shared memory.  All barriers are
+// hardware barriers (no software spin-wait).
 //
 // The arithmetic is that of k_collide_c2 (same operations in the same order:
 // at a SOLID neighbour the cell's own psi pair enters the force sums and
@@ -46,77 +52,130 @@ namespace cg = cooperative_groups;
 
 namespace lbm {
 
-constexpr int kFcThreads = 256;  // threads per CTA
-constexpr int kFcCluster = 8;    // CTAs per cluster (the portable maximum)
-constexpr int kFcRows = 2;       // rows of the band per CTA
+constexpr int kFcThreads = 128;  // threads per CTA
+constexpr int kFcCluster = 8;    // CTAs per cluster = rows per band
 constexpr int kFcSlots = 4;      // planes of the psi ring
-constexpr int kFcBand = kFcCluster * kFcRows;
-constexpr int kFcExtra = 3;      // lag words besides the pairs: reference pair, coordinates, geometry word
+constexpr int kFcLag = 3;        // lag slots of the own row's cells
+constexpr int kFcHLag = 2;       // lag slots of the outside rows' cells
+constexpr int kFcTabPlanes = 4;  // planes of the staged row table
+constexpr int kFcTabRows = 9;    // staged rows per plane: y-1..y+1 around the own row and both outside rows
 
-int fusedc_rows_per_cta() { return kFcRows; }
+int fusedc_rows_per_cta() { return 1; }
 
-template <class S> __host__ __device__ constexpr size_t fusedc_lag_cell_bytes() {
-    return kQ * sizeof(typename Pair2<S>::P) + kFcExtra * 4;
-}
+__host__ __device__ constexpr size_t fc_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// One lag slot, rounded up to 16 bytes so that the second slot's pairs stay
-// aligned for every pair size.
-template <class S> __host__ __device__ constexpr size_t fusedc_lag_slot_bytes(int lag_cap) {
-    return ((size_t)lag_cap * fusedc_lag_cell_bytes<S>() + 15) & ~(size_t)15;
-}
+// Shared-memory layout of one CTA (the same arithmetic on host and device).
+template <class S> struct FcLayout {
+    using P = typename Pair2<S>::P;
+    int nx, words, cap, hcap;
+    __host__ __device__ FcLayout(int nx_, int words_, int cap_)
+        : nx(nx_), words(words_), cap(cap_), hcap((2 * cap_ + kFcCluster - 1) / kFcCluster) {}
+    // psi ring: [slot][row: outside-low, own, outside-high][x = -1 .. nx]
+    __host__ __device__ size_t ring_bytes() const { return fc_align16((size_t)kFcSlots * 3 * (nx + 2) * 8); }
+    // own lag slot: pairs [kQ][cap], then reference pair, geometry word, coordinates [cap]
+    __host__ __device__ size_t lag_bytes() const { return fc_align16((size_t)cap * (kQ * sizeof(P) + 12)); }
+    // outside-row lag slot: pairs [kQ][hcap], then reference pair, coordinates [hcap]
+    __host__ __device__ size_t hlag_bytes() const { return fc_align16((size_t)hcap * (kQ * sizeof(P) + 8)); }
+    // geometry stage slot: coordinates, then words, of the own and outside cells [cap + hcap]
+    __host__ __device__ size_t geo_bytes() const { return fc_align16((size_t)(cap + hcap) * 8); }
+    __host__ __device__ size_t tab_bytes() const { return fc_align16((size_t)kFcTabPlanes * kFcTabRows * words * 8); }
+    __host__ __device__ size_t total() const {
+        return ring_bytes() + kFcLag * lag_bytes() + kFcHLag * hlag_bytes() + 2 * geo_bytes() + tab_bytes();
+    }
+};
 
 template <class S> size_t fusedc_smem_bytes(int nx, int lag_cap) {
-    const size_t ring = (size_t)kFcSlots * (kFcRows + 2) * (size_t)(nx + 2) * sizeof(float2);
-    return ring + 2 * fusedc_lag_slot_bytes<S>(lag_cap);
+    return FcLayout<S>(nx, (nx + 31) / 32, lag_cap).total();
 }
 
-// First compact index of row y of plane p (y == ny: the first cell of the next
-// plane, or the instance's total after the last plane).
-__device__ __forceinline__ uint32_t fc_row_start(const uint2 *__restrict__ tab, int words, const Grid &g, int p,
-                                                 int y) {
-    const size_t r = (size_t)p * g.ny + y;
-    return __ldg(tab + r * words).x;
+// Neighbour indices of a cell from the staged row table (as CNbr::init, which
+// reads the table in global memory).  p[dz + 1] points at the staged words of
+// row y - 1 of plane z + dz; rows y and y + 1 follow, `words` apart.
+struct FcRows {
+    const uint2 *p[3];
+    __device__ __forceinline__ const uint2 *row(int dz, int dy, int words) const {
+        return p[1 + dz] + (1 + dy) * words;
+    }
+};
+
+__device__ __forceinline__ uint32_t fc_rank_end(const uint2 *row, int words) {
+    const uint2 e = row[words - 1];
+    return e.x + __popc(e.y);
 }
 
-// A: pull the cell with compact index k; returns its density pair and, for the
-// lag buffer, its stored pairs, reference pair, coordinates and word.
+__device__ __forceinline__ void fc_nbr(CNbr &nb, int x, uint32_t k, const FcRows &R, int words, int nx) {
+    const int w = x >> 5, xb = x & 31;
+    const uint32_t below = (1u << xb) - 1u;
+    nb.nb[0] = k;
+    nb.nb[1] = k + 1u;
+    nb.nb[2] = k - 1u;
+#pragma unroll
+    for (int j = 3; j < kQ; ++j) {
+        if (cx(j) != 0) continue;
+        const uint2 e = R.row(cz(j), cy(j), words)[w];
+        const uint32_t at = e.x + __popc(e.y & below);
+        nb.nb[j] = at;
+#pragma unroll
+        for (int m = 7; m < kQ; ++m) {
+            if (cy(m) != cy(j) || cz(m) != cz(j) || cx(m) == 0) continue;
+            nb.nb[m] = cx(m) > 0 ? at + ((e.y >> xb) & 1u) : at - 1u;
+        }
+    }
+    if (x == 0 || x == nx - 1) {
+#pragma unroll
+        for (int m = 1; m < kQ; ++m) {
+            if (cx(m) == 0) continue;
+            const uint2 *row = R.row(cz(m), cy(m), words);
+            if (cx(m) > 0 && x == nx - 1) nb.nb[m] = row[0].x;
+            if (cx(m) < 0 && x == 0) nb.nb[m] = fc_rank_end(row, words) - 1u;
+        }
+    }
+}
+
+// Issue the pull of one cell (S1 of the update) as asynchronous copies of its
+// 19 stored pairs and its reference pair into lag entries dst_pairs[i * stride]
+// and dst_ref.  OUTLET cells pull their upstream neighbour's values (as
+// outlet_source); INLET cells pull nothing.
 template <class S>
-__device__ __forceinline__ float2 fc_pull(const StepArgs &a, int b, const uint2 *__restrict__ tab,
-                                          const typename Pair2<S>::P *__restrict__ f,
-                                          const __half2 *__restrict__ rin, const InstParam<float> &prm, uint32_t k,
-                                          typename Pair2<S>::P (&raw)[kQ], __half2 &R, uint32_t &pxyz,
-                                          uint32_t &word) {
-    pxyz = __ldg(a.cxyz + (size_t)b * a.kmax + k);
-    word = __ldg(a.clink + (size_t)b * a.kmax + k);
-    const CompactCell c = unpack_cell(pxyz, word);
-    if (cell_type(word) == kInlet) {
-        R = __floats2half2_rn(prm.rho_in[0], prm.rho_in[1]);
-        return make_float2(prm.rho_in[0], prm.rho_in[1]);
+__device__ __forceinline__ void fc_issue_pull(const StepArgs &a, int b, const typename Pair2<S>::P *f,
+                                              const __half2 *rin, uint32_t k, int x, uint32_t word,
+                                              const FcRows &R, typename Pair2<S>::P *dst_pairs, size_t stride,
+                                              uint32_t *dst_ref) {
+    using P = typename Pair2<S>::P;
+    if (cell_type(word) == kInlet) return;
+    const int nx = a.g.nx;
+    CNbr nb;
+    fc_nbr(nb, x, k, R, a.words, nx);
+    uint32_t sk = k, sw = word;
+    if (cell_type(word) == kOutlet && !((word >> 2) & 1u)) {
+        const uint32_t ku = nb.nb[2];
+        const uint32_t wu = __ldg(a.clink + (size_t)b * a.kmax + ku);
+        if (cell_type(wu) != kOutlet) {
+            fc_nbr(nb, x == 0 ? nx - 1 : x - 1, ku, R, a.words, nx);
+            sk = ku;
+            sw = wu;
+        }
     }
     const uint32_t n = a.kmax;
-    auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) -> float2 {
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            const bool bb = (sw >> opp(i)) & 1u;
-            const uint32_t idx = bb ? (uint32_t)opp(i) * n + sk : (uint32_t)i * n + nb.src(i);
-            raw[i] = __ldg(f + idx);
-        }
-        R = __ldg(rin + sk);
-        float2 v[kQ];
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) v[i] = Pair2<S>::load_shared(&raw[i]);
-        return density2<Pair2<S>::kScaled>(v, __half22float2(R), Pair2<S>::kUnscale);
-    };
-    CNbr own;
-    own.init(c.x, c.y, c.z, k, tab, a.words, a.g);
-    int xu;
-    uint32_t ku, wu;
-    if (outlet_source(a, b, c, own, xu, ku, wu)) {
-        CNbr up;
-        up.init(xu, c.y, c.z, ku, tab, a.words, a.g);
-        return pull(up, ku, wu);
+    for (int i = 0; i < kQ; ++i) {
+        const bool bb = (sw >> opp(i)) & 1u;
+        const uint32_t idx = bb ? (uint32_t)opp(i) * n + sk : (uint32_t)i * n + nb.src(i);
+        cp_async_ca<sizeof(P)>(dst_pairs + (size_t)i * stride, f + idx);
     }
-    return pull(own, k, word);
+    cp_async_ca<4>(dst_ref, rin + sk);
+}
+
+// Density pair of a pulled cell from its lag entry (as density2 over the same
+// stored values, in the same order).
+template <class S>
+__device__ __forceinline__ float2 fc_density(const typename Pair2<S>::P *pairs, size_t stride, uint32_t ref_bits) {
+    float2 v[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) v[i] = Pair2<S>::load_shared(pairs + (size_t)i * stride);
+    __half2 R;
+    memcpy(&R, &ref_bits, 4);
+    return density2<Pair2<S>::kScaled>(v, __half22float2(R), Pair2<S>::kUnscale);
 }
 
 // psi pair of cell x (plus its periodic images at x = -1 and x = nx) into one
@@ -127,9 +186,8 @@ __device__ __forceinline__ void fc_ring_store(float2 *row, int x, int nx, float2
     if (x == nx - 1) row[0] = v;
 }
 
-// 16-bit storage: two CTAs per SM within the registers (128; a few bytes of
-// spill); FP32 storage keeps one, its lag buffer fills most of an SM's shared
-// memory anyway
+// 16-bit storage: two CTAs per SM within the shared memory; FP32 storage: one
+// (its lag buffer takes most of an SM's shared memory)
 template <class S> constexpr int fc_min_blocks() { return sizeof(S) == 2 ? 2 : 1; }
 
 template <class S, int EQ>
@@ -142,120 +200,219 @@ __global__ void __launch_bounds__(kFcThreads, fc_min_blocks<S>()) k_fused_c(Step
     const int nclusters = gridDim.x / kFcCluster;
     const int tid = threadIdx.x;
     const Grid g = a.g;
-    const int nx = g.nx;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, words = a.words;
+    const FcLayout<S> L(nx, words, fp.lag_cap);
+    const int cap = L.cap, hcap = L.hcap;
     const int ringw = nx + 2;
-    const size_t slot_elems = (size_t)(kFcRows + 2) * ringw;  // float2 per ring slot
-    float2 *ring = (float2 *)fc_smem;
-    unsigned char *lag_base = fc_smem + kFcSlots * slot_elems * sizeof(float2);
-    const int cap = fp.lag_cap;
-    const size_t lag_slot_bytes = fusedc_lag_slot_bytes<S>(cap);
-    auto lag_pairs = [&](int s) { return (P *)(lag_base + s * lag_slot_bytes); };
-    auto lag_words = [&](int s) { return (uint32_t *)(lag_base + s * lag_slot_bytes + (size_t)kQ * cap * sizeof(P)); };
-    // ring row `lr` (-1 ... kFcRows) of slot 0 in this CTA
-    auto ring_row = [&](int lr) { return ring + (size_t)(lr + 1) * ringw; };
+    unsigned char *sp = fc_smem;
+    float2 *ring = (float2 *)sp;
+    sp += L.ring_bytes();
+    unsigned char *lag0 = sp;
+    sp += kFcLag * L.lag_bytes();
+    unsigned char *hlag0 = sp;
+    sp += kFcHLag * L.hlag_bytes();
+    uint32_t *geo0 = (uint32_t *)sp;
+    sp += 2 * L.geo_bytes();
+    uint2 *tab0 = (uint2 *)sp;
+    // lag slot s: pairs [kQ][cap], then fields f = 0 reference pair, 1 word, 2 coordinates [cap]
+    auto lag_pairs = [&](int s) { return (P *)(lag0 + s * L.lag_bytes()); };
+    auto lag_u32 = [&](int s, int fld) {
+        return (uint32_t *)(lag0 + s * L.lag_bytes() + (size_t)kQ * cap * sizeof(P)) + (size_t)fld * cap;
+    };
+    auto hlag_pairs = [&](int s) { return (P *)(hlag0 + s * L.hlag_bytes()); };
+    auto hlag_u32 = [&](int s, int fld) {
+        return (uint32_t *)(hlag0 + s * L.hlag_bytes() + (size_t)kQ * hcap * sizeof(P)) + (size_t)fld * hcap;
+    };
+    // geometry stage slot s: field 0 coordinates, 1 words [cap + hcap]
+    auto geo = [&](int s, int fld) { return geo0 + (size_t)s * (L.geo_bytes() / 4) + (size_t)fld * (cap + hcap); };
+    // staged row table: [plane slot][row 0..8][word]
+    auto tab_row = [&](int pslot, int r) { return tab0 + ((size_t)pslot * kFcTabRows + r) * words; };
+    auto ring_row = [&](int slot, int ri) { return ring + ((size_t)slot * 3 + ri) * ringw; };
+    const size_t slot_elems = (size_t)3 * ringw;
     const uint32_t n = a.kmax;
 
     for (int u = cid; u < fp.units; u += nclusters) {
         const int b = u / (fp.bands * fp.chunks);
         const int rem = u - b * fp.bands * fp.chunks;
         const int band = rem / fp.chunks, chunk = rem - (rem / fp.chunks) * fp.chunks;
-        const int y0 = band * kFcBand;
-        const int band_end = min(y0 + kFcBand, g.ny);
-        const int yc0 = y0 + crank * kFcRows;
-        const int rows_c = max(0, min(yc0 + kFcRows, band_end) - yc0);
-        const int last_rank = (band_end - 1 - y0) / kFcRows;  // owns the band's last row
-        const int last_rows = band_end - (y0 + last_rank * kFcRows);
-        const int za = (int)((long long)chunk * g.nz / fp.chunks);
-        const int zb = (int)((long long)(chunk + 1) * g.nz / fp.chunks);
-        const int y_lo = y0 == 0 ? g.ny - 1 : y0 - 1;
-        const int y_hi = band_end == g.ny ? 0 : band_end;
+        const int y0 = band * kFcCluster;
+        const int band_end = min(y0 + kFcCluster, ny);
+        const int y = y0 + crank;
+        const bool has_row = y < band_end;
+        const int last = band_end - 1 - y0;  // rank owning the band's last row
+        const int za = (int)((long long)chunk * nz / fp.chunks);
+        const int zb = (int)((long long)(chunk + 1) * nz / fp.chunks);
+        const int Z = zb - za;
+        const int y_lo = y0 == 0 ? ny - 1 : y0 - 1;
+        const int y_hi = band_end == ny ? 0 : band_end;
         const uint2 *tab = instance_tab(a, b);
         const InstParam<float> &prm = ((const InstParam<float> *)a.par)[b];
         const P *f = (const P *)a.f_in + (size_t)b * kQ * n;
         P *fo = (P *)a.f_out + (size_t)b * kQ * n;
         const __half2 *rin = (const __half2 *)a.ref_in + (size_t)b * n;
         __half2 *rout = (__half2 *)a.ref_out + (size_t)b * n;
+        const uint32_t *cxyz = a.cxyz + (size_t)b * n, *clink = a.clink + (size_t)b * n;
         float *mac = (float *)a.macro + (long long)b * 5 * g.n;
-        // the band's outside rows live in CTA 0 (row -1) and in the CTA that owns
-        // the last row (row last_rows)
-        float2 *lo_row = cl.map_shared_rank(ring_row(-1), 0);
-        float2 *hi_row = cl.map_shared_rank(ring_row(last_rows), (unsigned)last_rank);
-        // rows y - 1 and y + 1 of this CTA's first and last rows
-        float2 *below0 = crank > 0 ? cl.map_shared_rank(ring_row(kFcRows - 1), (unsigned)(crank - 1)) : ring_row(-1);
-        float2 *above_last = crank == last_rank ? ring_row(rows_c)
-                                                : cl.map_shared_rank(ring_row(0), (unsigned)min(crank + 1, kFcCluster - 1));
-        uint32_t k0_prev = 0;
-        int n_prev = 0;
-        const int Z = zb - za;
-        for (int it = 0; it < Z + 2; ++it) {
-            int p = za - 1 + it;
-            p = p < 0 ? p + g.nz : (p >= g.nz ? p - g.nz : p);
-            const int slot = it & (kFcSlots - 1);
-            const bool halo_plane = it == 0 || it == Z + 1;
-            const size_t soff = (size_t)slot * slot_elems;
-            // ---------------------------------------------------------------- A
-            const uint32_t k0 = rows_c > 0 ? fc_row_start(tab, a.words, g, p, yc0) : 0u;
-            const uint32_t k1 = rows_c > 0 ? fc_row_start(tab, a.words, g, p, yc0 + rows_c) : 0u;
-            const int n_own = (int)(k1 - k0);
-            P *lp = lag_pairs(it & 1);
-            uint32_t *lw = lag_words(it & 1);
-            for (int j = tid; j < n_own; j += kFcThreads) {
-                P raw[kQ];
-                __half2 R;
-                uint32_t pxyz, word;
-                const float2 rho = fc_pull<S>(a, b, tab, f, rin, prm, k0 + (uint32_t)j, raw, R, pxyz, word);
-                const CompactCell c = unpack_cell(pxyz, word);
-                fc_ring_store(ring + soff + (size_t)(c.y - yc0 + 1) * ringw, c.x, nx, rho);
-                if (!halo_plane) {
+        // psi rows y - 1 and y + 1: the neighbouring CTAs' own rows, or the
+        // band's outside rows kept by CTA 0 (low) and the last CTA (high)
+        float2 *row_lo = crank > 0 ? cl.map_shared_rank(ring_row(0, 1), (unsigned)(crank - 1)) : ring_row(0, 0);
+        float2 *row_hi = crank < last ? cl.map_shared_rank(ring_row(0, 1), (unsigned)min(crank + 1, kFcCluster - 1))
+                                      : ring_row(0, 2);
+        float2 *out_lo = cl.map_shared_rank(ring_row(0, 0), 0);
+        float2 *out_hi = cl.map_shared_rank(ring_row(0, 2), (unsigned)last);
+        auto plane_of = [&](int it) {
+            int p = (za - 1 + it) % nz;
+            return p < 0 ? p + nz : p;
+        };
+        auto wrap_y = [&](int yy) { return yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy); };
+        auto tslot = [](int it) { return (it + 1) & (kFcTabPlanes - 1); };
+        // rows staged per plane: own y-1, y, y+1 (0..2), outside-low (3..5), outside-high (6..8)
+        auto stage_tab = [&](int it) {
+            const int p = plane_of(it);
+            const int ps = tslot(it);
+            const int ys[3] = {y, y_lo, y_hi};
+            for (int e = tid; e < kFcTabRows * words; e += kFcThreads) {
+                const int r = e / words, w = e - r * words;
+                const int yy = wrap_y(ys[r / 3] + (r % 3) - 1);
+                cp_async_ca<8>(tab_row(ps, r) + w, tab + ((size_t)p * ny + yy) * words + w);
+            }
+        };
+        // cells of plane `it`: own row [k0, k0 + n_own), outside rows [l0, l0 + nl) and [h0, h0 + nh)
+        struct Range {
+            uint32_t k0, l0, h0;
+            int n_own, nl, nh;
+        };
+        auto ranges = [&](int it) {
+            const int ps = tslot(it);
+            Range r;
+            r.k0 = has_row ? tab_row(ps, 1)[0].x : 0u;
+            r.n_own = has_row ? (int)(fc_rank_end(tab_row(ps, 1), words) - r.k0) : 0;
+            r.l0 = tab_row(ps, 4)[0].x;
+            r.nl = (int)(fc_rank_end(tab_row(ps, 4), words) - r.l0);
+            r.h0 = tab_row(ps, 7)[0].x;
+            r.nh = (int)(fc_rank_end(tab_row(ps, 7), words) - r.h0);
+            return r;
+        };
+        auto stage_geo = [&](int it) {
+            const Range r = ranges(it);
+            uint32_t *gx = geo(it & 1, 0), *gw = geo(it & 1, 1);
+            for (int j = tid; j < r.n_own; j += kFcThreads) {
+                cp_async_ca<4>(gx + j, cxyz + r.k0 + j);
+                cp_async_ca<4>(gw + j, clink + r.k0 + j);
+            }
+            for (int m = 0, h = crank + kFcCluster * tid; h < r.nl + r.nh; ++m, h += kFcCluster * kFcThreads) {
+                const uint32_t k = h < r.nl ? r.l0 + (uint32_t)h : r.h0 + (uint32_t)(h - r.nl);
+                const int e = cap + m * kFcThreads + tid;
+                cp_async_ca<4>(gx + e, cxyz + k);
+                cp_async_ca<4>(gw + e, clink + k);
+            }
+        };
+        // the staged row pointers around row index `mid` (1: own, 4: low, 7: high) for plane `it`
+        auto rows_at = [&](int it, int mid) {
+            FcRows R;
 #pragma unroll
-                    for (int i = 0; i < kQ; ++i) lp[(size_t)i * cap + j] = raw[i];
-                    lw[j] = *(const uint32_t *)&R;
-                    lw[cap + j] = pxyz;
-                    lw[2 * cap + j] = word;
-                }
+            for (int dz = 0; dz < 3; ++dz) R.p[dz] = tab_row(tslot(it - 1 + dz), mid - 1);
+            return R;
+        };
+        auto issue_pulls = [&](int it, const Range &r) {
+            const uint32_t *gx = geo(it & 1, 0), *gw = geo(it & 1, 1);
+            const int ls = it % kFcLag, hs = it & 1;
+            P *lp = lag_pairs(ls);
+            uint32_t *lref = lag_u32(ls, 0), *lword = lag_u32(ls, 1), *lxyz = lag_u32(ls, 2);
+            const FcRows Ro = rows_at(it, 1);
+            for (int j = tid; j < r.n_own; j += kFcThreads) {
+                const uint32_t pxyz = gx[j], word = gw[j];
+                lword[j] = word;
+                lxyz[j] = pxyz;
+                fc_issue_pull<S>(a, b, f, rin, r.k0 + (uint32_t)j, (int)(pxyz & 2047u), word, Ro, lp + j, cap,
+                                 lref + j);
             }
+            P *hp = hlag_pairs(hs);
+            uint32_t *href = hlag_u32(hs, 0), *hxyz = hlag_u32(hs, 1);
+            const FcRows Rl = rows_at(it, 4), Rh = rows_at(it, 7);
+            // (Rh is Rl shifted by three staged rows in every plane)
+            for (int m = 0, h = crank + kFcCluster * tid; h < r.nl + r.nh; ++m, h += kFcCluster * kFcThreads) {
+                const bool low = h < r.nl;
+                const uint32_t k = low ? r.l0 + (uint32_t)h : r.h0 + (uint32_t)(h - r.nl);
+                const int e = m * kFcThreads + tid;
+                const uint32_t pxyz = gx[cap + e], word = gw[cap + e];
+                hxyz[e] = pxyz | (low ? 0u : 0x80000000u);
+                fc_issue_pull<S>(a, b, f, rin, k, (int)(pxyz & 2047u), word, low ? Rl : Rh, hp + e, hcap,
+                                 href + e);
+            }
+        };
+
+        // prologue: row tables of planes -1 .. 2, geometry of planes 0 and 1, pulls of plane 0
+        for (int it = -1; it <= 2; ++it) stage_tab(it);
+        cp_async_commit_group();
+        cp_async_wait_all();
+        __syncthreads();
+        stage_geo(0);
+        stage_geo(1);
+        cp_async_commit_group();
+        cp_async_wait_all();
+        __syncthreads();
+        Range rng_cur = ranges(0), rng_prev{};
+        issue_pulls(0, rng_cur);
+        cp_async_commit_group();
+        for (int it = 0; it < Z + 2; ++it) {
+            const int slot = it & (kFcSlots - 1);
+            // ---------------------------------------------------------------- S1
+            cp_async_wait_all();
+            __syncthreads();
+            // ---------------------------------------------------------------- S2
             {
-                // the two rows outside the band, shared out over the cluster
-                const uint32_t l0 = fc_row_start(tab, a.words, g, p, y_lo);
-                const uint32_t l1 = y_lo + 1 < g.ny ? fc_row_start(tab, a.words, g, p, y_lo + 1)
-                                                    : fc_row_start(tab, a.words, g, p, g.ny);
-                const uint32_t h0 = fc_row_start(tab, a.words, g, p, y_hi);
-                const uint32_t h1 = y_hi + 1 < g.ny ? fc_row_start(tab, a.words, g, p, y_hi + 1)
-                                                    : fc_row_start(tab, a.words, g, p, g.ny);
-                const int nl = (int)(l1 - l0), nh = (int)(h1 - h0);
-                for (int h = crank * kFcThreads + tid; h < nl + nh; h += kFcCluster * kFcThreads) {
-                    const bool low = h < nl;
-                    const uint32_t k = low ? l0 + (uint32_t)h : h0 + (uint32_t)(h - nl);
-                    P raw[kQ];
-                    __half2 R;
-                    uint32_t pxyz, word;
-                    const float2 rho = fc_pull<S>(a, b, tab, f, rin, prm, k, raw, R, pxyz, word);
-                    const CompactCell c = unpack_cell(pxyz, word);
-                    fc_ring_store((low ? lo_row : hi_row) + soff, c.x, nx, rho);
+                const Range &r = rng_cur;
+                const int ls = it % kFcLag, hs = it & 1;
+                const P *lp = lag_pairs(ls);
+                const uint32_t *lref = lag_u32(ls, 0), *lword = lag_u32(ls, 1), *lxyz = lag_u32(ls, 2);
+                float2 *own = ring_row(slot, 1);
+                for (int j = tid; j < r.n_own; j += kFcThreads) {
+                    const uint32_t word = lword[j];
+                    const float2 rho = cell_type(word) == kInlet ? make_float2(prm.rho_in[0], prm.rho_in[1])
+                                                                 : fc_density<S>(lp + j, cap, lref[j]);
+                    fc_ring_store(own, (int)(lxyz[j] & 2047u), nx, rho);
+                }
+                const P *hp = hlag_pairs(hs);
+                const uint32_t *href = hlag_u32(hs, 0), *hxyz = hlag_u32(hs, 1);
+                const uint32_t *gw = geo(it & 1, 1);
+                for (int m = 0, h = crank + kFcCluster * tid; h < r.nl + r.nh; ++m, h += kFcCluster * kFcThreads) {
+                    const int e = m * kFcThreads + tid;
+                    const uint32_t word = gw[cap + e], hx = hxyz[e];
+                    const float2 rho = cell_type(word) == kInlet ? make_float2(prm.rho_in[0], prm.rho_in[1])
+                                                                 : fc_density<S>(hp + e, hcap, href[e]);
+                    fc_ring_store(((hx >> 31) ? out_hi : out_lo) + (size_t)slot * slot_elems, (int)(hx & 2047u), nx,
+                                  rho);
                 }
             }
+            // ---------------------------------------------------------------- S3
             cl.sync();
-            // ---------------------------------------------------------------- B
+            // ---------------------------------------------------------------- S4, S5
+            Range rng_next{};
+            if (it + 1 <= Z + 1) {
+                rng_next = ranges(it + 1);
+                issue_pulls(it + 1, rng_next);
+            }
+            if (it + 2 <= Z + 1) stage_geo(it + 2);
+            if (it + 3 <= Z + 2) stage_tab(it + 3);
+            cp_async_commit_group();
+            // ---------------------------------------------------------------- S6
             if (it >= 2) {
-                const size_t off_m = (size_t)((it - 2) & (kFcSlots - 1)) * slot_elems;
-                const size_t off_0 = (size_t)((it - 1) & (kFcSlots - 1)) * slot_elems;
-                const size_t off_p = soff;
-                const P *qp = lag_pairs((it - 1) & 1);
-                const uint32_t *qw = lag_words((it - 1) & 1);
-                for (int j = tid; j < n_prev; j += kFcThreads) {
-                    const uint32_t k = k0_prev + (uint32_t)j;
-                    const uint32_t pxyz = qw[cap + j], word = qw[2 * cap + j];
+                const size_t offs[3] = {(size_t)((it - 2) & (kFcSlots - 1)) * slot_elems,
+                                        (size_t)((it - 1) & (kFcSlots - 1)) * slot_elems, (size_t)slot * slot_elems};
+                const int ls = (it - 1) % kFcLag;
+                const P *qp = lag_pairs(ls);
+                const uint32_t *qref = lag_u32(ls, 0), *qword = lag_u32(ls, 1), *qxyz = lag_u32(ls, 2);
+                const float2 *rows[3] = {row_lo, ring_row(0, 1), row_hi};
+                for (int j = tid; j < rng_prev.n_own; j += kFcThreads) {
+                    const uint32_t k = rng_prev.k0 + (uint32_t)j;
+                    const uint32_t pxyz = qxyz[j], word = qword[j];
                     const CompactCell c = unpack_cell(pxyz, word);
-                    const int r = c.y - yc0;
-                    const float2 *rows[3] = {r > 0 ? ring_row(r - 1) : below0, ring_row(r),
-                                             r < rows_c - 1 ? ring_row(r + 1) : above_last};
-                    const size_t offs[3] = {off_m, off_0, off_p};
-                    // psi pair at x + c_i (i >= 1)
                     auto psi_at = [&](int i) -> float2 {
                         return rows[1 + cy(i)][offs[1 + cz(i)] + (size_t)(c.x + 1 + cx(i))];
                     };
-                    const float2 own_psi = rows[1][off_0 + (size_t)(c.x + 1)];
-                    const long long cell = c.x + (long long)nx * (c.y + (long long)g.ny * c.z);
+                    const float2 own_psi = rows[1][offs[1] + (size_t)(c.x + 1)];
+                    const long long cell = c.x + (long long)nx * (c.y + (long long)ny * c.z);
                     if (cell_type(word) == kInlet) {
                         using PP = typename Pair<S>::P;
                         PP *fo1 = (PP *)fo;
@@ -282,9 +439,10 @@ __global__ void __launch_bounds__(kFcThreads, fc_min_blocks<S>()) k_fused_c(Step
                     float2 v[kQ];
 #pragma unroll
                     for (int i = 0; i < kQ; ++i) v[i] = Pair2<S>::load_shared(qp + (size_t)i * cap + j);
-                    const uint32_t rbits = qw[j];
-                    const Moments2 m =
-                        moments2<Pair2<S>::kScaled>(v, __half22float2(*(const __half2 *)&rbits), Pair2<S>::kUnscale);
+                    const uint32_t rbits = qref[j];
+                    __half2 Rref;
+                    memcpy(&Rref, &rbits, 4);
+                    const Moments2 m = moments2<Pair2<S>::kScaled>(v, __half22float2(Rref), Pair2<S>::kUnscale);
                     const __half2 rho_h = __float22half2_rn(m.rho);
                     ForceSums2 bs;
                     bs.clear();
@@ -320,10 +478,12 @@ __global__ void __launch_bounds__(kFcThreads, fc_min_blocks<S>()) k_fused_c(Step
                     }
                 }
             }
-            k0_prev = k0;
-            n_prev = halo_plane ? 0 : n_own;
+            rng_prev = rng_cur;
+            if (it == 0 || it == Z + 1) rng_prev.n_own = 0;  // halo planes are not collided
+            rng_cur = rng_next;
         }
-        // the next chunk restarts the ring; no CTA may still read it
+        // the next chunk restarts the ring and the stages; no CTA may still read them
+        cp_async_wait_all();
         cl.sync();
     }
 }
@@ -378,14 +538,14 @@ cudaError_t fusedc_plan(lbm_precision prec, int eq_order, const Grid &g, int bat
     e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
     if (e != cudaSuccess) return e;
     if (active < 1) return cudaSuccess;
-    const int bands = (g.ny + kFcBand - 1) / kFcBand;
+    const int bands = (g.ny + kFcCluster - 1) / kFcCluster;
     long long best_nc = 1;
     double best = 1e300;
     for (long long nc = 1; nc <= g.nz; ++nc) {
         const long long units = (long long)batch * bands * nc;
         const long long rounds = (units + active - 1) / active;
         const long long zmax = (g.nz + nc - 1) / nc;
-        const double t = (double)rounds * ((double)zmax + 0.7);
+        const double t = (double)rounds * ((double)zmax + 1.0);
         if (t < best - 1e-9) {
             best = t;
             best_nc = nc;

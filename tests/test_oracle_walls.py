@@ -89,3 +89,44 @@ def test_wall_model2_mass_and_symmetry(oracle_mod):
     (a1, b1, u1), (a2, b2, u2) = outs
     assert np.allclose(a1, b2, atol=1e-13) and np.allclose(b1, a2, atol=1e-13)
     assert np.allclose(u1, u2, atol=1e-13)
+
+
+# ---------------------------------------------------------------- static slug between plates (Sec. 3.3)
+
+def _slug(oracle_mod, rho_s, wall_model=2, steps=2500):
+    from paper_1711_03254_gb300 import wetting as WT
+    t, r1, r2, u = WT.slug_channel()
+    sim = oracle_mod.OracleSim(128, 32, 1, [dict(tau=(1.0, 1.0), G=-2.2, rho_s=rho_s)], wall_model=wall_model)
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    sim.step(steps)
+    a, b, _ = sim.get_fields()
+    sim.close()
+    return WT.contact_angles(a[0, 0], b[0, 0], t[0]), WT.thin_film(b[0, 0], t[0])
+
+
+def test_slug_contact_angle_symmetry(oracle_mod):
+    """Static slug in the 128 x 32 channel of Sec. 3.3: with equal viscosities
+    rho^s = 0 is neutral (90 degrees, by the component-exchange symmetry),
+    rho^s and -rho^s give angles mirrored about 90 degrees, and rho^s > 0
+    makes component 2 wet the walls (rho^s_2 = rho^s, Eq. 11)."""
+    th0, _ = _slug(oracle_mod, 0.0)
+    thp, _ = _slug(oracle_mod, 0.3)
+    thm, _ = _slug(oracle_mod, -0.3)
+    assert all(abs(x - 90.0) < 0.5 for x in th0), th0
+    assert all(x < 75.0 for x in thp), thp
+    assert abs(np.mean(thp) + np.mean(thm) - 180.0) < 0.5, (thp, thm)
+    # both menisci of a slug see the same wall
+    assert abs(thp[0] - thp[1]) < 0.5
+
+
+def test_thin_film_modified_wall_model(oracle_mod):
+    """Thin film (Sec. 3.3): at the same wall potential, which gives contact
+    angles within 2 degrees in both models, the film of component 2 along the
+    walls of the component-1 region is at least five times thinner with the
+    modified wall model (2: the cell's own rho_beta plus rho^s_beta at SOLID
+    neighbours) than with the original one (1: plain rho^s_beta)."""
+    th1, film1 = _slug(oracle_mod, 0.3, wall_model=1)
+    th2, film2 = _slug(oracle_mod, 0.3, wall_model=2)
+    assert abs(np.mean(th1) - np.mean(th2)) < 2.0, (th1, th2)
+    assert film2 * 5.0 < film1, (film1, film2)
