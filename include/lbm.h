@@ -230,6 +230,14 @@ lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *f);
 lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t *bytes);
 lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes);
 
+/* Replace the per-instance parameters (host array [batch], copied; checked as
+ * in lbm_create) for the updates that follow; the state is kept.  The paper
+ * changes the driving force in stages this way to find the critical pressure
+ * of slug displacement (Sec. 3.6).  Synchronises the stream.
+ * Errors: LBM_ERR_ARG (null, tau <= 1/2, non-finite value), LBM_ERR_STATE
+ * (between the parts of a split update), LBM_ERR_CUDA. */
+lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_instance_params *per_instance);
+
 /* Use the given cudaStream_t (cast to void*) for all later work; NULL selects
  * the legacy default stream.  The caller keeps ownership of the stream. */
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);

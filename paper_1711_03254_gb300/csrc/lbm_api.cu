@@ -189,6 +189,19 @@ lbm_status upload_params(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
+// NULL if every instance's parameters are valid, else what is wrong.
+const char *check_params(const lbm_instance_params *per_instance, int batch) {
+    for (int b = 0; b < batch; ++b) {
+        const lbm_instance_params &p = per_instance[b];
+        if (!(p.tau[0] > 0.5) || !(p.tau[1] > 0.5)) return "tau must exceed 1/2";
+        const double vals[] = {p.G, p.rho_s, p.g[0], p.g[1], p.g[2], p.rho_in[0], p.rho_in[1], p.u_in[0], p.u_in[1],
+                               p.u_in[2], p.tau[0], p.tau[1]};
+        for (double v : vals)
+            if (!std::isfinite(v)) return "non-finite parameter";
+    }
+    return nullptr;
+}
+
 // Strategy for an n-update call.  AUTO: the compact two-pass update when the
 // grid fits its packed coordinates, the dense two-pass one otherwise.
 lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
@@ -396,19 +409,9 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
         g_last_error = "lbm_create: precision, eq_order or wall_model out of range";
         return LBM_ERR_ARG;
     }
-    for (int b = 0; b < cfg->batch; ++b) {
-        const lbm_instance_params &p = per_instance[b];
-        if (!(p.tau[0] > 0.5) || !(p.tau[1] > 0.5)) {
-            g_last_error = "lbm_create: tau must exceed 1/2";
-            return LBM_ERR_ARG;
-        }
-        const double vals[] = {p.G, p.rho_s, p.g[0], p.g[1], p.g[2], p.rho_in[0], p.rho_in[1], p.u_in[0], p.u_in[1],
-                               p.u_in[2], p.tau[0], p.tau[1]};
-        for (double v : vals)
-            if (!std::isfinite(v)) {
-                g_last_error = "lbm_create: non-finite parameter";
-                return LBM_ERR_ARG;
-            }
+    if (const char *bad = check_params(per_instance, cfg->batch)) {
+        g_last_error = std::string("lbm_create: ") + bad;
+        return LBM_ERR_ARG;
     }
     lbm_ctx *ctx = new lbm_ctx();
     ctx->cfg = *cfg;
@@ -485,6 +488,24 @@ void lbm_destroy(lbm_ctx *ctx) {
     std::vector<void *> own = ctx->owned;
     for (void *p : own) ctx->dfree(p);
     delete ctx;
+}
+
+lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_instance_params *per_instance) {
+    if (!ctx || !per_instance) return ctx ? ctx->fail(LBM_ERR_ARG, "lbm_set_params: null argument") : LBM_ERR_ARG;
+    if (ctx->half_step) return ctx->fail(LBM_ERR_STATE, "lbm_set_params: finish the split update first");
+    if (const char *bad = check_params(per_instance, ctx->cfg.batch))
+        return ctx->fail(LBM_ERR_ARG, std::string("lbm_set_params: ") + bad);
+    LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    ctx->par.assign(per_instance, per_instance + ctx->cfg.batch);
+    const lbm_status s = upload_params(ctx);
+    if (s != LBM_OK) return s;
+    // the dense layout keeps psi of the SOLID cells, which follows from rho^s
+    if (ctx->has_geometry && ctx->layout == 0) {
+        LBM_CUDA(launch_psi_solid(ctx->link, ctx->psi, ctx->fp64(), ctx->g, ctx->cfg.batch, ctx->dpar, ctx->stream),
+                 "lbm_set_params: solid psi");
+        ctx->launches += 1;
+    }
+    return LBM_OK;
 }
 
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {

@@ -80,11 +80,12 @@ def library() -> ctypes.CDLL:
         L.lbm_destroy.argtypes = [vp]
         L.lbm_destroy.restype = None
         L.lbm_step_part.argtypes = [vp, ctypes.c_int]
+        L.lbm_set_params.argtypes = [vp, ctypes.POINTER(lbm_instance_params)]
         L.lbm_plane_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
         L.lbm_plane_copy.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
         for name in ("lbm_create", "lbm_set_geometry", "lbm_set_fields", "lbm_step", "lbm_get_fields",
                      "lbm_reduce", "lbm_get_distributions", "lbm_set_distributions", "lbm_get_state", "lbm_set_state", "lbm_set_stream", "lbm_set_kernel", "lbm_set_tiling", "lbm_autotune", "lbm_run_to_steady",
-                     "lbm_set_allocator", "lbm_step_part", "lbm_plane_bytes", "lbm_plane_copy"):
+                     "lbm_set_allocator", "lbm_step_part", "lbm_plane_bytes", "lbm_plane_copy", "lbm_set_params"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -151,6 +152,12 @@ def lbm_create(cfg: lbm_config, params) -> ctypes.c_void_p:
     h = ctypes.c_void_p()
     _check(library().lbm_create(ctypes.byref(cfg), params, ctypes.byref(h)))
     return h
+
+
+def lbm_set_params(ctx, params):
+    """Replace the per-instance parameters (list of dicts as for Sim) between updates."""
+    arr = make_params(params)
+    return _check(library().lbm_set_params(ctx, arr), ctx)
 
 
 def lbm_set_geometry(ctx, cell_type: np.ndarray):
@@ -275,6 +282,11 @@ class Sim:
 
     def set_geometry(self, cell_type):
         lbm_set_geometry(self.ctx, np.asarray(cell_type, dtype=np.uint8).reshape(self.shape))
+
+    def set_params(self, params):
+        if len(params) != self.shape[0]:
+            raise ValueError("one parameter set per instance")
+        lbm_set_params(self.ctx, params)
 
     def set_fields(self, rho1, rho2, u):
         lbm_set_fields(self.ctx, np.reshape(rho1, self.shape), np.reshape(rho2, self.shape),

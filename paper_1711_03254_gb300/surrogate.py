@@ -14,8 +14,8 @@ ReLU, loss, Adam); PyTorch only provides device memory.  The network:
     3       S/8       128       pool-conv-conv     (bottom)
   3x3x3 convolutions with ReLU, a 1x1x1 head to 16 channels (5 used).
 
-Input channels (16, 6 used): SOLID mask, wall potential rho^s on SOLID cells,
-log10(viscosity ratio)/3, inclination/45 deg, body force * 1e5, plain initial
+Input channels (16, 6 used): SOLID mask, cos(contact angle) on SOLID cells,
+log10(viscosity ratio)/3, inclination/45 deg, body force * 1e4, plain initial
 droplet indicator.  Output channels: phi = (rho1 - rho2)/rho, rho - 1,
 100 * u_F (3).
 """
@@ -200,16 +200,16 @@ class UNet3D:
 
 # ---------------------------------------------------------------------- problem encoding
 
-def encode_inputs(cell_type, rho_s, nu_ratio, incline_deg, body_force, rho2_init):
+def encode_inputs(cell_type, theta_deg, nu_ratio, incline_deg, body_force, rho2_init):
     """FP32 [S, S, S, CIN] network input of one case (see module docstring)."""
     S = cell_type.shape[0]
     x = np.zeros((S, S, S, CIN), np.float32)
     solid = cell_type == 1
     x[..., 0] = solid
-    x[..., 1] = np.where(solid, rho_s, 0.0)
+    x[..., 1] = np.where(solid, math.cos(math.radians(theta_deg)), 0.0)
     x[..., 2] = math.log10(nu_ratio) / 3.0
     x[..., 3] = incline_deg / 45.0
-    x[..., 4] = body_force * 1e5
+    x[..., 4] = body_force * 1e4
     x[..., 5] = np.where(solid, 0.0, rho2_init)
     return x
 

@@ -4,12 +4,17 @@ solver, training of the U-Net, and the steps-to-steady comparison).
 Problem family: a droplet of component 2 on an inclined flat wall (the
 inclined-channel geometry of Sec. 3.4), parameters drawn from a seeded
 generator:
-  * wettability rho^s ~ U[-0.4, 0.4] (taken directly: the contact-angle
-    calibration of Sec. 3.3 is not part of this library),
-  * inclination ~ U[0 deg, 45 deg],
-  * viscosity ratio ~ logU[1, 100] with nu_high = 1.0 (nu_low >= 0.01), the
-    droplet taking the low or the high viscosity at random,
-  * G = -1.8, no body force (the steady state is static).
+  * contact angle theta ~ U[30 deg, 150 deg], turned into the wall potential
+    rho^s by the contact-angle calibration of Sec. 3.3 (static slugs at this
+    family's coupling, wetting.Calibration; interpolated in log10 of the
+    viscosity ratio between the calibrated pairs);
+  * inclination ~ U[0 deg, 45 deg];
+  * viscosity ratio ~ logU[1, 1000] with nu_high = 1.7 (nu_low >= 0.0017),
+    the droplet taking the low or the high viscosity at random;
+  * a body force of magnitude ~ U[0, 1e-4] along the wall's inward normal
+    (pressing the fluid onto the wall, so the steady state stays static);
+  * G = -1.8 (both components stay stable down to nu = 0.0017 at this
+    coupling; at -2.2 the family diverges at the low viscosities).
 
 The training target is the solver's state once every residual of its batch
 is below the tolerance (or after a cap on the updates), run from the plain
@@ -25,27 +30,69 @@ import time
 
 import numpy as np
 
-from . import lbm, surrogate, workloads as W
+from . import lbm, surrogate, wetting, workloads as W
 
 G_WS = -1.8
-NU_HIGH = 1.0
+NU_HIGH = 1.7
+G_NORMAL_MAX = 1e-4
+# viscosity ratios of the calibration; each with the droplet (component 2)
+# taking the low or the high viscosity
+CAL_RATIOS = (1.0, 10.0, 100.0, 1000.0)
+CAL_GRID = tuple(np.round(np.linspace(-0.6, 0.6, 13), 3))
+_CAL = {}
 
 
-def sample_cases(n: int, seed: int):
+def _pair(ratio: float, drop_low: bool):
+    low = NU_HIGH / ratio
+    return (NU_HIGH, low) if drop_low else (low, NU_HIGH)
+
+
+def family_calibration(steps: int = 30000):
+    """theta(rho^s) of the family's viscosity pairs at its coupling (cached)."""
+    if "cal" not in _CAL:
+        pairs = [_pair(r, dl) for r in CAL_RATIOS for dl in (True, False)]
+        pairs = list(dict.fromkeys(pairs))
+        _CAL["cal"], _CAL["runs"] = wetting.Calibration.measure(pairs, list(CAL_GRID), steps=steps, tol=1e-6,
+                                                                 check_every=500, G=G_WS)
+    return _CAL["cal"]
+
+
+def rho_s_for(theta: float, ratio: float, drop_low: bool) -> float:
+    """Wall potential for contact angle theta at this viscosity ratio: the
+    calibrated inverses at the neighbouring ratios, interpolated in log10."""
+    cal = family_calibration()
+    lr = math.log10(ratio)
+    lg = [math.log10(r) for r in CAL_RATIOS]
+    k = min(max(int(np.searchsorted(lg, lr)) - 1, 0), len(lg) - 2)
+    w = (lr - lg[k]) / (lg[k + 1] - lg[k])
+    a = cal.rho_s(*_pair(CAL_RATIOS[k], drop_low), theta)
+    b = cal.rho_s(*_pair(CAL_RATIOS[k + 1], drop_low), theta)
+    return (1.0 - w) * a + w * b
+
+
+def sample_cases(n: int, seed: int, with_rho_s: bool = True):
     rng = np.random.default_rng(seed)
     cases = []
     for _ in range(n):
-        ratio = 10 ** rng.uniform(0.0, 2.0)
-        low = NU_HIGH / ratio
+        ratio = 10 ** rng.uniform(0.0, 3.0)
         drop_low = bool(rng.random() < 0.5)
-        nu1, nu2 = (NU_HIGH, low) if drop_low else (low, NU_HIGH)
-        cases.append(dict(rho_s=float(rng.uniform(-0.4, 0.4)), incline=float(rng.uniform(0.0, 45.0)),
-                          nu=(nu1, nu2), ratio=float(ratio)))
+        theta = float(rng.uniform(30.0, 150.0))
+        c = dict(theta=theta, incline=float(rng.uniform(0.0, 45.0)), nu=_pair(ratio, drop_low), ratio=float(ratio),
+                 drop_low=drop_low, g_n=float(rng.uniform(0.0, G_NORMAL_MAX)))
+        if with_rho_s:
+            c["rho_s"] = rho_s_for(theta, ratio, drop_low)
+        cases.append(c)
     return cases
 
 
+def _normal(c):
+    th = math.radians(c["incline"])
+    return np.array([-math.sin(th), math.cos(th), 0.0])  # the wall's inward normal (x, y, z)
+
+
 def case_params(c):
-    return dict(tau=(c["nu"][0] * 3 + 0.5, c["nu"][1] * 3 + 0.5), G=G_WS, rho_s=c["rho_s"], g=(0.0, 0.0, 0.0))
+    g = -c["g_n"] * _normal(c)
+    return dict(tau=(c["nu"][0] * 3 + 0.5, c["nu"][1] * 3 + 0.5), G=G_WS, rho_s=c["rho_s"], g=tuple(float(v) for v in g))
 
 
 def case_geometry(c, S: int):
@@ -54,10 +101,10 @@ def case_geometry(c, S: int):
 
 def case_inputs(c, S: int):
     t, r1, r2, u = case_geometry(c, S)
-    return surrogate.encode_inputs(t, c["rho_s"], c["ratio"], c["incline"], 0.0, r2), t, r1, r2, u
+    return surrogate.encode_inputs(t, c["theta"], c["ratio"], c["incline"], c["g_n"], r2), t, r1, r2, u
 
 
-def generate(cases, S: int = 64, max_steps: int = 25000, tol: float = 1e-5, batch: int = 32, precision: str = "fp32",
+def generate(cases, S: int = 64, max_steps: int = 40000, tol: float = 3e-6, batch: int = 32, precision: str = "fp32",
              check_every: int = 500):
     """Run the solver from the plain initial state of every case towards its
     steady state: each batch of instances advances in chunks of check_every
@@ -90,7 +137,7 @@ def generate(cases, S: int = 64, max_steps: int = 25000, tol: float = 1e-5, batc
         for j, c in enumerate(cs):
             if bad[j] or not all(np.isfinite(a[j]).all() for a in (r1, r2, u)):
                 continue
-            X.append(surrogate.encode_inputs(geo[j][0], c["rho_s"], c["ratio"], c["incline"], 0.0, geo[j][2]))
+            X.append(surrogate.encode_inputs(geo[j][0], c["theta"], c["ratio"], c["incline"], c["g_n"], geo[j][2]))
             Y.append(surrogate.encode_targets(r1[j], r2[j], u[j]))
             M.append((geo[j][0] != W.SOLID).astype(np.uint8))
             kept.append(k0 + j)
@@ -171,11 +218,12 @@ def steps_to_steady(c, S, init, tol, check_every=100, max_steps=20000, precision
     return done, dt, float(res[0]), fields
 
 
-def experiment(n_train=320, n_test=8, S_train=64, test_sizes=(64, 128), gen_max_steps=25000, iters=2000, batch=4,
-               lr=1e-3, tol=1e-5, check_every=100, max_steps=60000, seed_train=5, seed_test=6, log=print,
-               variants=(("warm", True), ("warm_rho", False))):
+def experiment(n_train=2000, n_test=32, S_train=64, test_sizes=(64, 128), gen_max_steps=40000, iters=2000, batch=4,
+               lr=1e-3, tol=3e-6, check_every=100, max_steps=60000, seed_train=5, seed_test=6, log=print,
+               variants=(("warm", True), ("warm_rho", False)), n_test_large=8):
     """Generate, train, and compare updates / wall time to steady state from
-    the plain and the learned initial fields.  Returns a summary dict."""
+    the plain and the learned initial fields (n_test cases at the training
+    size, n_test_large at the larger test sizes).  Returns a summary dict."""
     import torch
     t0 = time.perf_counter()
     X, Y, M, kept, gres = generate(sample_cases(n_train, seed_train), S=S_train, max_steps=gen_max_steps, tol=tol)
@@ -195,7 +243,7 @@ def experiment(n_train=320, n_test=8, S_train=64, test_sizes=(64, 128), gen_max_
     tests = []
     for S_test in test_sizes:
         rows = []
-        for c in sample_cases(n_test, seed_test):
+        for c in sample_cases(n_test if S_test == S_train else min(n_test, n_test_large), seed_test):
             x, t, r1, r2, u = case_inputs(c, S_test)
             plain = steps_to_steady(c, S_test, (t, (r1, r2, u)), tol, check_every, max_steps)
             fluid = t != W.SOLID
@@ -226,20 +274,21 @@ if __name__ == "__main__":
     import argparse
     import json
     ap = argparse.ArgumentParser(description="learned warm start: generate, train, compare steps to steady")
-    ap.add_argument("--n-train", type=int, default=320)
-    ap.add_argument("--n-test", type=int, default=8)
+    ap.add_argument("--n-train", type=int, default=2000)
+    ap.add_argument("--n-test", type=int, default=32)
+    ap.add_argument("--n-test-large", type=int, default=8)
     ap.add_argument("--size-train", type=int, default=64)
     ap.add_argument("--test-sizes", default="64,128")
-    ap.add_argument("--gen-max-steps", type=int, default=25000)
+    ap.add_argument("--gen-max-steps", type=int, default=40000)
     ap.add_argument("--iters", type=int, default=2000)
-    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--tol", type=float, default=3e-6)
     ap.add_argument("--max-steps", type=int, default=60000)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     from . import build
     build.build()
     res = experiment(a.n_train, a.n_test, a.size_train, tuple(int(v) for v in a.test_sizes.split(",")),
-                     a.gen_max_steps, a.iters, tol=a.tol, max_steps=a.max_steps)
+                     a.gen_max_steps, a.iters, tol=a.tol, max_steps=a.max_steps, n_test_large=a.n_test_large)
     js = json.dumps(res, default=float)
     if a.out:
         open(a.out, "w").write(js)

@@ -517,3 +517,66 @@ def test_reduced_precision_mass_conservation(lbm, precision, bound):
     sim.step(1000)
     m1 = sim.reduce()[0][:2]
     assert np.all(np.abs(m1 - m0) / m0 < bound), (m0, m1)
+
+
+# ---------------------------------------------------------------- rough channel crop (benchmark's rough channel)
+
+def _rough_crop():
+    import bench
+    t, r1, r2, u = W.rough_channel(64, 32, 32, seed=4, invaded_length=8, ends="periodic")
+    return t, r1, r2, u, [bench.ROUGH_PARAMS]
+
+
+@pytest.mark.parametrize("kernel", ["compact", "two_pass"])
+def test_rough_channel_crop_fp64(lbm, oracle_mod, kernel):
+    """The rough channel's recipe at 64 x 32 x 32 (walls with bumps, an invading
+    slug at nu = 0.0017 against nu = 1.7, wetting walls, body force), FP64,
+    1000 updates: cell by cell against the oracle, and both conserve each
+    component's mass to 1e-12."""
+    t, r1, r2, u, p = _rough_crop()
+    sim, ref, g, o = _pair(lbm, oracle_mod, (64, 32, 32), p, t[None], r1[None], r2[None], u[None], 1000,
+                           wall_model=2, kernel=kernel)
+    assert max(_errs(g, o)) < 1e-11
+    m0 = np.array([r1[t != W.SOLID].sum(), r2[t != W.SOLID].sum()])
+    for red in (sim.reduce()[0], ref.reduce()[0]):
+        assert np.all(np.abs(red[:2] - m0) / m0 < 1e-12)
+
+
+# per storage: densities, u_F, per-component mass drift over the 1000 updates
+ROUGH_BOUNDS = {"fp32": (1e-5, 1e-5, 1e-7), "fp16s": (1e-3, 5e-3, 2e-5), "bf16s": (6e-3, 3e-2, 5e-4)}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16s", "bf16s"])
+def test_rough_channel_crop_storage(lbm, oracle_mod, precision):
+    """The same crop in the FP32-arithmetic storages against the FP64 oracle
+    after 1000 updates: fields within the storage's bounds, mass drift of the
+    storage rounding within its bound (the update itself conserves mass)."""
+    t, r1, r2, u, p = _rough_crop()
+    sim, _, g, o = _pair(lbm, oracle_mod, (64, 32, 32), p, t[None], r1[None], r2[None], u[None], 1000,
+                         precision=precision, wall_model=2)
+    e = _errs(g, o)
+    rb, ub, mb = ROUGH_BOUNDS[precision]
+    assert e[0] < rb and e[1] < rb and e[2] < ub, e
+    m0 = np.array([r1[t != W.SOLID].sum(), r2[t != W.SOLID].sum()])
+    drift = np.abs(sim.reduce()[0][:2] - m0) / m0
+    assert np.all(drift < mb), drift
+
+
+# ---------------------------------------------------------------- Galilean invariance (eq_order 1)
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_shear_wave_on_stream(lbm, oracle_mod, precision, tol):
+    """A shear wave on a uniform stream with the full equilibrium: the GPU
+    matches the oracle, whose wave decays at the rate of the wave at rest and
+    moves with the stream (the oracle pin of Galilean invariance)."""
+    nx = 32
+    x = np.arange(nx) + 0.5
+    k = 2 * np.pi / nx
+    u = np.zeros((1, 1, 1, nx, 3))
+    u[..., 0] = 0.05
+    u[..., 1] = 1e-3 * np.sin(k * x)
+    t = np.zeros((1, 1, 1, nx), np.uint8)
+    r = np.full((1, 1, 1, nx), 0.5)
+    _, _, g, o = _pair(lbm, oracle_mod, (nx, 1, 1), [dict(tau=(0.8, 0.8), G=0.0)], t, r, r, u, 200,
+                       precision=precision, eq_order=1)
+    assert max(_errs(g, o)) < tol

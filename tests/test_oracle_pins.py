@@ -746,3 +746,69 @@ def test_reduce_pin_catches_slips(oracle_mod, old, new):
     with oracle_mod.planted(old, new):
         err = _check_reduce_closed_form(oracle_mod)
     assert err > 1e-6
+
+
+# ---------------------------------------------------------------- Galilean invariance of the full equilibrium
+
+def _shear_wave(oracle_mod, eq_order, U, nx=32, A=1e-3, tau=0.8, steps=200):
+    """Shear wave u_y = A sin(kx) on a uniform stream U along x (one fluid:
+    a 50/50 mixture with equal tau and no coupling), periodic 32 x 1 x 1.
+    Returns (amplitude ratio, exp(-nu k^2 t), displacement of the wave, U t)."""
+    x = np.arange(nx) + 0.5
+    k = 2 * np.pi / nx
+    u = np.zeros((1, 1, 1, nx, 3))
+    u[..., 0] = U
+    u[..., 1] = A * np.sin(k * x)
+    sim = oracle_mod.OracleSim(nx, 1, 1, [dict(tau=(tau, tau), G=0.0)], eq_order=eq_order)
+    sim.set_geometry(np.zeros((1, 1, 1, nx), np.uint8))
+    sim.set_fields(np.full((1, 1, 1, nx), 0.5), np.full((1, 1, 1, nx), 0.5), u)
+    sim.step(steps)
+    _, _, v = sim.get_fields()
+    sim.close()
+    uy = v[0, 0, 0, :, 1]
+    a = 2 * np.sum(uy * np.sin(k * x)) / nx
+    b = 2 * np.sum(uy * np.cos(k * x)) / nx
+    nu = T0 * (tau - 0.5)
+    return np.hypot(a, b) / A, np.exp(-nu * k * k * steps), np.arctan2(-b, a) / k, U * steps
+
+
+def _galilean_errors(oracle_mod):
+    out = {}
+    for U in (0.0, 0.02, 0.05):
+        out[U] = _shear_wave(oracle_mod, 1, U)
+    a0 = out[0.0][0]
+    return dict(decay=max(abs(r[0] - r[1]) / r[1] for r in out.values()),
+                u_dependence=max(abs(r[0] - a0) / a0 for r in out.values()),
+                advection=max(abs(r[2] - r[3]) / max(r[3], 1.0) for r in out.values()))
+
+
+def test_full_equilibrium_galilean_invariance(oracle_mod):
+    """eq_order 1 (the full equilibrium kept beside Eq. 3, f1 of the hot-path
+    table): a shear wave on a uniform stream decays as exp(-nu k^2 t)
+    whatever the stream's speed (within 1e-4 between U = 0 and U = 0.05; 1 %
+    of the continuum rate, the rest being the lattice's O(k^2) dispersion) and
+    is carried with the stream (displacement U t within 0.5 %)."""
+    e = _galilean_errors(oracle_mod)
+    assert e["decay"] < 0.01 and e["u_dependence"] < 1e-4 and e["advection"] < 5e-3, e
+
+
+def test_printed_equilibrium_is_stokes(oracle_mod):
+    """Eq. 3 as printed (eq_order 0) has no rho u u momentum flux, the form the
+    paper gives 'for the Stokes flow': the same wave is not carried by the
+    stream (displacement below 0.01 of U t)."""
+    r = _shear_wave(oracle_mod, 0, 0.05)
+    assert abs(r[2]) < 0.01 * r[3], r
+
+
+@pytest.mark.parametrize("old,new", [
+    ("if (eq_order == 1) e += (cu * cu) / (2.0 * T0 * T0) - uu / (2.0 * T0);",
+     "if (eq_order == 1) e += (cu * cu) / (2.0 * T0 * T0);"),
+    ("if (eq_order == 1) e += (cu * cu) / (2.0 * T0 * T0) - uu / (2.0 * T0);",
+     "if (eq_order == 1) e += (cu * cu) / (3.0 * T0 * T0) - uu / (2.0 * T0);"),
+])
+def test_galilean_pin_catches_equilibrium_slips(oracle_mod, old, new):
+    """The Galilean pin fails with the u^2 term dropped from, or a wrong
+    coefficient planted in, the full equilibrium of the oracle."""
+    with oracle_mod.planted(old, new):
+        e = _galilean_errors(oracle_mod)
+    assert not (e["decay"] < 0.01 and e["u_dependence"] < 1e-4 and e["advection"] < 5e-3), e
