@@ -84,11 +84,15 @@ DENSE_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_kernels.cu"]
 NCU_TRAFFIC = {
     # 128^3 packed spheres (837,994 non-solid cells), dense layout, ncu --set full:
     # 273.1 MB read + 103.1 MB written in one launch
-    "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db", "files": DENSE_SOURCES},
-    # 192^3 packed spheres (2,830,487 non-solid cells; compact f 430 MB per buffer,
-    # larger than L2), ncu --set full: 274.2 MB read + 192.3 MB written in one launch
-    "k_collide_c2/fp16s/spheres": {"bytes_per_fluid_cell": 164.8, "src": "1f62a0de098d92be",
-                                   "files": COMPACT_SOURCES},
+    "k_collide/fp16s/spheres": {"bytes_per_fluid_cell": 449.0, "src": "cad4ff68f880e7db", "files": DENSE_SOURCES,
+                                "how": "ncu --set full, one launch at 128^3, scaled by non-solid cells"},
+    # the benchmark itself (256^3, 6,710,661 non-solid cells), one launch each,
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum:
+    #   k_collide_c2: 649,626,624 B read + 512,179,200 B written = 173.1 B per cell
+    #   k_psi_c:      595,518,208 B read +  50,491,136 B written =  96.3 B per cell
+    "k_collide_c2/fp16s/spheres": {"bytes_per_fluid_cell": 173.13, "src": "f67e4d17e37ff120",
+                                   "files": COMPACT_SOURCES, "step_bytes_per_fluid_cell": 173.13 + 96.27,
+                                   "how": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch at 256^3"},
 }
 # FP64 mode is bound by the FP64 pipe.  Executed FP64 flops per non-solid cell
 # (DADD + DMUL + 2 DFMA from ncu, 128^3 packed spheres, eq_order 0) and the

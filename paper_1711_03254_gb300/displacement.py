@@ -2,11 +2,13 @@
 
 A 2-D periodic channel of height H has a middle section of length Z narrowed
 to height D.  A slug of component 2, which wets the walls (contact angle
-theta < 90 degrees), fills part of the narrow section up to its downstream
-step.  A body force rho_0 g along the channel pushes it towards the wide part;
-its downstream meniscus is pinned at the step until the pressure drop the force
-builds over one period, rho_0 g L, exceeds the capillary pressure difference
-of a meniscus of width D and one of width H (Eq. for the critical pressure):
+theta < 90 degrees), fills the narrow section and reaches into the wide part
+after it, one meniscus in each channel.  Capillarity pulls it into the narrow
+section (its upstream meniscus then rests on the section's entrance); a body
+force rho_0 g along the channel pushes it out.  It leaves once the pressure
+drop the force builds over one period, rho_0 g L, exceeds the capillary
+pressure difference of a meniscus of width D and one of width H (Eq. for the
+critical pressure):
 
     P_crit = 2 sigma cos(theta) (1/D - 1/H),   g_crit = P_crit / (rho_0 L).
 
@@ -29,11 +31,15 @@ T0 = 1.0 / 3.0
 STAGES = (0.7, 0.9, 0.95, 1.0, 1.05, 1.1, 1.3)
 
 
-def constricted_channel(L: int = 160, H: int = 40, D: int = 10, Z: int = 52, slug: int = 24):
+def constricted_channel(L: int = 160, H: int = 40, D: int = 10, Z: int = 52, slug: int = 16):
     """SOLID rows y = 0 and H + 1; x in [x0, x0 + Z) narrowed to the rows
-    [y_lo, y_lo + D) (centred); component 2 in the last `slug` cells of the
-    narrow section, component 1 elsewhere.  Returns (cell_type, rho1, rho2, u)
-    shaped [1, H + 2, L] and the narrow-section mask [H + 2, L]."""
+    [y_lo, y_lo + D) (centred).  Component 2 fills the whole narrow section and
+    the first `slug` columns of the wide channel after it, so that one meniscus
+    sits in each channel (the configuration of the critical pressure; a slug
+    inside the narrow section alone would have to push its meniscus past the
+    step's corner, a higher barrier); component 1 elsewhere.  Returns
+    (cell_type, rho1, rho2, u) shaped [1, H + 2, L] and the narrow-section mask
+    [H + 2, L]."""
     ny = H + 2
     x0 = (L - Z) // 2
     y_lo = 1 + (H - D) // 2
@@ -46,8 +52,8 @@ def constricted_channel(L: int = 160, H: int = 40, D: int = 10, Z: int = 52, slu
     open_rows = (ys >= y_lo) & (ys < y_lo + D)
     t[0][in_narrow_x & ~open_rows] = W.SOLID
     narrow = in_narrow_x & open_rows
-    slug_cells = narrow & (xs >= x0 + Z - slug)
     fluid = t[0] != W.SOLID
+    slug_cells = narrow | (fluid & (xs >= x0 + Z) & (xs < x0 + Z + slug))
     rho2 = np.where(slug_cells, 1.0, 0.0)[None]
     rho1 = np.where(fluid & ~slug_cells, 1.0, 0.0)[None]
     u = np.zeros(t.shape + (3,))
@@ -81,15 +87,20 @@ def surface_tension(G: float = -2.2, radii=(10, 16, 24), steps: int = 8000, prec
     return float(sigma), float(intercept)
 
 
-def critical_factors(cases, G: float = -2.2, L: int = 160, H: int = 40, Z: int = 52, slug: int = 24,
-                     stages=STAGES, steps_per_stage: int = 80000, precision: str = "fp32", leave: float = 0.5):
+def critical_factors(cases, G: float = -2.2, L: int = 160, H: int = 40, Z: int = 52, slug: int = 16,
+                     stages=STAGES, steps_per_stage: int = 80000, settle: float = 0.5, precision: str = "fp32",
+                     drain: float = 0.05, leave: float = 0.5):
     """cases: dicts with nu1, nu2, rho_s, D, g_ref.  All cases run as instances
-    of one context; stage k applies g = stages[k] * g_ref along x for
-    steps_per_stage updates.  A case counts as displaced once less than
-    `leave` of the slug's component 2 remains in the narrow section (or its
-    fields are no longer finite: the carrier then accelerates without bound).
-    Returns, per case, the first stage factor at which it was displaced
-    (None if never) and the remaining fraction after every stage."""
+    of one context.  A settling stage at `settle` * g_ref (half a stage) lets
+    each slug find its pinned position; then stage k applies
+    g = stages[k] * g_ref along x for steps_per_stage updates.  A case counts
+    as displaced at the first stage over which the slug's component 2 in the
+    narrow section falls by more than `drain` (of its initial amount), or to
+    below `leave` of it (a slug held by capillarity stays put at a force below
+    the critical one; the fields turning non-finite counts as displaced: the
+    carrier then accelerates without bound).  Returns, per case, the first
+    displacing stage factor (None if never) and the remaining fraction after
+    the settling stage and after every stage."""
     from . import lbm
     geos = [constricted_channel(L, H, c["D"], Z, slug) for c in cases]
     t = np.stack([g[0] for g in geos])
@@ -103,20 +114,29 @@ def critical_factors(cases, G: float = -2.2, L: int = 160, H: int = 40, Z: int =
         return [dict(tau=(c["nu1"] / T0 + 0.5, c["nu2"] / T0 + 0.5), G=G, rho_s=c["rho_s"],
                      g=(f * c["g_ref"], 0.0, 0.0)) for c in cases]
 
-    sim = lbm.Sim(L, H + 2, 1, params(stages[0]), precision=precision)
+    def remaining(sim):
+        _, b, _ = sim.get_fields()
+        out = []
+        for k in range(len(cases)):
+            bk = b[k, 0]
+            out.append(float(bk[masks[k]].sum()) / m0[k] if np.isfinite(bk).all() else 0.0)
+        return out
+
+    sim = lbm.Sim(L, H + 2, 1, params(settle), precision=precision)
     sim.set_geometry(t)
     sim.set_fields(r1, r2, u)
+    sim.step(steps_per_stage // 2)
+    prev = remaining(sim)
     first = [None] * len(cases)
-    remain = [[] for _ in cases]
+    remain = [[p] for p in prev]
     for f in stages:
         sim.set_params(params(f))
         sim.step(steps_per_stage)
-        _, b, _ = sim.get_fields()
+        now = remaining(sim)
         for k in range(len(cases)):
-            bk = b[k, 0]
-            frac = float(bk[masks[k]].sum()) / m0[k] if np.isfinite(bk).all() else 0.0
-            remain[k].append(frac)
-            if first[k] is None and frac < leave:
+            remain[k].append(now[k])
+            if first[k] is None and (prev[k] - now[k] > drain or now[k] < leave):
                 first[k] = f
+        prev = now
     sim.close()
     return first, remain
