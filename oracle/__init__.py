@@ -45,7 +45,8 @@ def build(force: bool = False) -> str:
 
 class _Config(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-                ("batch", ctypes.c_int), ("eq_order", ctypes.c_int), ("wall_model", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("eq_order", ctypes.c_int), ("wall_model", ctypes.c_int),
+                ("reg_order", ctypes.c_int)]
 
 
 class _Params(ctypes.Structure):
@@ -74,10 +75,11 @@ def _load(path: str):
     L.oracle_feq.argtypes = [ctypes.c_double, dp, ctypes.c_int, dp]
     L.oracle_pi_neq.argtypes = [dp, dp, dp]
     L.oracle_regularize.argtypes = [dp, dp]
+    L.oracle_regularize3.argtypes = [dp, dp, dp]
     L.oracle_forcing.argtypes = [dp, dp, ctypes.c_double, ctypes.c_int, dp]
     L.oracle_tau_mix.argtypes = [ctypes.c_double, ctypes.c_double, dp]
     L.oracle_tau_mix.restype = ctypes.c_double
-    L.oracle_collide_cell.argtypes = [dp, dp, dp, ctypes.c_int, dp, dp, dp, dp]
+    L.oracle_collide_cell.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
     L.oracle_wall_potential.argtypes = [ctypes.c_double, dp]
     return L
 
@@ -157,6 +159,14 @@ def regularize(pi) -> np.ndarray:
     return out
 
 
+def regularize3(pi, u) -> np.ndarray:
+    """f' of Eq. 10 with the third-order Hermite terms (recursive moments)."""
+    out = np.zeros(Q)
+    lib().oracle_regularize3(_dp(np.ascontiguousarray(pi, dtype=np.float64).reshape(9)),
+                             _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(out))
+    return out
+
+
 def forcing(F, u, tau: float, eq_order: int = 0) -> np.ndarray:
     out = np.zeros(Q)
     lib().oracle_forcing(_dp(np.ascontiguousarray(F, dtype=np.float64)),
@@ -168,7 +178,7 @@ def tau_mix(rho1: float, rho2: float, tau) -> float:
     return lib().oracle_tau_mix(float(rho1), float(rho2), _dp(np.ascontiguousarray(tau, dtype=np.float64)))
 
 
-def collide_cell(f, F, tau, eq_order: int = 0):
+def collide_cell(f, F, tau, eq_order: int = 0, reg_order: int = 2):
     """f [2,19] streamed, F [2,3] -> (f_post [2,19], u_F [3], rho [2], tau_mix)."""
     fo = np.zeros(2 * Q)
     uF = np.zeros(3)
@@ -176,7 +186,7 @@ def collide_cell(f, F, tau, eq_order: int = 0):
     tm = np.zeros(1)
     lib().oracle_collide_cell(_dp(np.ascontiguousarray(f, dtype=np.float64).reshape(-1)),
                               _dp(np.ascontiguousarray(F, dtype=np.float64).reshape(-1)),
-                              _dp(np.ascontiguousarray(tau, dtype=np.float64)), int(eq_order),
+                              _dp(np.ascontiguousarray(tau, dtype=np.float64)), int(eq_order), int(reg_order),
                               _dp(fo), _dp(uF), _dp(r), _dp(tm))
     return fo.reshape(2, Q), uF, r, float(tm[0])
 
@@ -199,9 +209,9 @@ class OracleSim:
     [batch, nz, ny, nx] (u: [batch, nz, ny, nx, 3]).
     """
 
-    def __init__(self, nx, ny, nz, params, eq_order=0, wall_model=2):
+    def __init__(self, nx, ny, nz, params, eq_order=0, wall_model=2, reg_order=2):
         self.shape = (len(params), nz, ny, nx)
-        cfg = _Config(nx, ny, nz, len(params), eq_order, wall_model)
+        cfg = _Config(nx, ny, nz, len(params), eq_order, wall_model, reg_order)
         arr = (_Params * len(params))()
         for k, p in enumerate(params):
             arr[k].tau[:] = list(p.get("tau", (1.0, 1.0)))

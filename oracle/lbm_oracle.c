@@ -41,7 +41,13 @@
  *     proportional to u . grad(rho) and the layered Poiseuille profiles of
  *     Sec. 3.2 are missed by tens of percent.
  *   - Regularisation: f'_i = w_i/(2 T0^2) (c_i c_i - T0 I) : Pi^neq with
- *     Pi^neq = sum_i c_i c_i (f_i - feq_i).
+ *     Pi^neq = sum_i c_i c_i (f_i - feq_i) (reg_order 2, the default).
+ *     reg_order 3 adds the third-order Hermite terms of the regularised
+ *     collision the paper cites (Chen/Zhang 2006): the third-order
+ *     non-equilibrium moments follow from Pi^neq and u_F as
+ *     a3_abg = u_a Pi_bg + u_b Pi_ag + u_g Pi_ab, and f' is the function in
+ *     the span of w_i H_k(c_i) (second- and third-order Hermite polynomials)
+ *     whose Hermite moments equal Pi^neq and a3 (see oracle_regularize3).
  *   - rho'_beta of a solid neighbour (Eq. 11).  Wall model 2 (recommended):
  *     rho_beta of the cell itself plus rho^s_beta, so the transition into the
  *     wall is smooth and a uniform fluid next to a wall feels no interaction
@@ -118,6 +124,7 @@ typedef struct {
     int nx, ny, nz, batch;
     int eq_order;   /* 0 = Eq. 3 as printed, 1 = with quadratic terms */
     int wall_model; /* 0 = balanced (A), 1 = plain (B), 2 = own density + rho^s */
+    int reg_order;  /* 0 or 2 = second-order regularisation, 3 = with third-order terms */
 } oracle_config;
 
 typedef struct {
@@ -201,6 +208,90 @@ void oracle_regularize(const double *pi, double *fprime)
     }
 }
 
+/* Hermite polynomials at velocity i: H2_ab = c_a c_b - T0 d_ab and
+ * H3_abg = c_a c_b c_g - T0 (c_a d_bg + c_b d_ag + c_g d_ab). */
+static double hermite2(int i, int a, int b)
+{
+    return C[i][a] * C[i][b] - (a == b ? T0 : 0.0);
+}
+
+static double hermite3(int i, int a, int b, int g)
+{
+    return C[i][a] * C[i][b] * C[i][g]
+         - T0 * (C[i][a] * (b == g) + C[i][b] * (a == g) + C[i][g] * (a == b));
+}
+
+/* Solve M x = r (n x n, row-major, overwritten) by Gaussian elimination with
+ * partial pivoting.  Returns 0, or -1 for a singular matrix. */
+static int solve_dense(int n, double *M, double *r, double *x)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(M[i * n + k]) > fabs(M[p * n + k])) p = i;
+        if (M[p * n + k] == 0.0) return -1;
+        if (p != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = M[k * n + j]; M[k * n + j] = M[p * n + j]; M[p * n + j] = t;
+            }
+            double t = r[k]; r[k] = r[p]; r[p] = t;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            double l = M[i * n + k] / M[k * n + k];
+            for (int j = k; j < n; ++j) M[i * n + j] -= l * M[k * n + j];
+            r[i] -= l * r[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double s = r[k];
+        for (int j = k + 1; j < n; ++j) s -= M[k * n + j] * x[j];
+        x[k] = s / M[k * n + k];
+    }
+    return 0;
+}
+
+/* Eq. 10 with third-order terms.  The target Hermite moments of f' are
+ * a2 = Pi^neq and the recursive third-order moments
+ * a3_abg = u_a Pi_bg + u_b Pi_ag + u_g Pi_ab.  Of the ten third-order
+ * polynomials, H_xxx, H_yyy, H_zzz (c^3 = c on the lattice) and H_xyz (no
+ * D3Q19 velocity has three non-zero components) vanish at every velocity;
+ * the other six (xxy, yzz, xzz, xyy, yyz, xxz) and the six second-order ones
+ * span the basis.  f'_i = w_i sum_k b_k H_k(c_i) with the coefficients b that
+ * make sum_i H_m(c_i) f'_i equal the target of every basis polynomial m:
+ * M b = a with M_mk = sum_i w_i H_m(c_i) H_k(c_i). */
+void oracle_regularize3(const double *pi, const double *u, double *fprime)
+{
+    enum { NB = 12 };
+    static const int I2[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    static const int I3[6][3] = {{0, 0, 1}, {1, 2, 2}, {0, 2, 2}, {0, 1, 1}, {1, 1, 2}, {0, 0, 2}};
+    init_tables();
+    double H[NB][Q], a[NB], M[NB * NB], b[NB];
+    for (int i = 0; i < Q; ++i) {
+        for (int k = 0; k < 6; ++k) H[k][i] = hermite2(i, I2[k][0], I2[k][1]);
+        for (int k = 0; k < 6; ++k) H[6 + k][i] = hermite3(i, I3[k][0], I3[k][1], I3[k][2]);
+    }
+    for (int k = 0; k < 6; ++k) a[k] = pi[3 * I2[k][0] + I2[k][1]];
+    for (int k = 0; k < 6; ++k) {
+        int x = I3[k][0], y = I3[k][1], z = I3[k][2];
+        a[6 + k] = u[x] * pi[3 * y + z] + u[y] * pi[3 * x + z] + u[z] * pi[3 * x + y];
+    }
+    for (int m = 0; m < NB; ++m)
+        for (int k = 0; k < NB; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < Q; ++i) s += weight(i) * H[m][i] * H[k][i];
+            M[m * NB + k] = s;
+        }
+    if (solve_dense(NB, M, a, b) != 0) {
+        for (int i = 0; i < Q; ++i) fprime[i] = NAN;
+        return;
+    }
+    for (int i = 0; i < Q; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < NB; ++k) s += b[k] * H[k][i];
+        fprime[i] = weight(i) * s;
+    }
+}
+
 /* Forcing term of Eq. 1 / Eq. 9 for one component with force F and
  * velocity u (= u_F), see the reading in the file header. */
 void oracle_forcing(const double *F, const double *u, double tau, int eq_order, double *Fi)
@@ -238,7 +329,7 @@ double oracle_tau_mix(double rho1, double rho2, const double *tau)
 /* S2, S5-S7 for one cell.  f: [2][Q] streamed distributions, F: [2][3] total
  * force on each component.  Writes the post-collision distributions fout
  * [2][Q], the velocity u_F [3], the densities rho_out [2] and tau_mix. */
-void oracle_collide_cell(const double *f, const double *F, const double *tau, int eq_order,
+void oracle_collide_cell(const double *f, const double *F, const double *tau, int eq_order, int reg_order,
                          double *fout, double *uF, double *rho_out, double *tau_out)
 {
     double rho_a[2], j[3] = {0.0, 0.0, 0.0};
@@ -264,7 +355,10 @@ void oracle_collide_cell(const double *f, const double *F, const double *tau, in
         double feq[Q], pi[9], fp[Q], Fi[Q];
         oracle_feq(rho_a[al], uF, eq_order, feq);
         oracle_pi_neq(f + al * Q, feq, pi);
-        oracle_regularize(pi, fp);
+        if (reg_order == 3)
+            oracle_regularize3(pi, uF, fp);
+        else
+            oracle_regularize(pi, fp);
         oracle_forcing(F + 3 * al, uF, tau_mix, eq_order, Fi);
         for (int i = 0; i < Q; ++i)
             fout[al * Q + i] = feq[i] + (1.0 - 1.0 / tau_mix) * fp[i] + Fi[i];
@@ -515,7 +609,7 @@ static void step_instance(oracle_ctx *ctx, int b)
                     for (int i = 0; i < Q; ++i) fl[al * Q + i] = ctx->fs[((size_t)al * Q + i) * n + k];
                     for (int a = 0; a < 3; ++a) F[3 * al + a] = force[((size_t)al * n + k) * 3 + a];
                 }
-                oracle_collide_cell(fl, F, p->tau, cfg->eq_order, out, uF, r, &tm);
+                oracle_collide_cell(fl, F, p->tau, cfg->eq_order, cfg->reg_order, out, uF, r, &tm);
                 for (int al = 0; al < 2; ++al) {
                     for (int i = 0; i < Q; ++i) fo[((size_t)al * Q + i) * n + k] = out[al * Q + i];
                     rho_o[(size_t)al * n + k] = r[al];

@@ -812,3 +812,121 @@ def test_galilean_pin_catches_equilibrium_slips(oracle_mod, old, new):
     with oracle_mod.planted(old, new):
         e = _galilean_errors(oracle_mod)
     assert not (e["decay"] < 0.01 and e["u_dependence"] < 1e-4 and e["advection"] < 5e-3), e
+
+
+# ---------------------------------------------------------------- third-order regularisation (Eq. 10, reg_order 3)
+
+_H3_IDX = [(0, 0, 1), (1, 2, 2), (0, 2, 2), (0, 1, 1), (1, 1, 2), (0, 0, 2)]
+
+
+def _hermite_basis(c):
+    """The second-order and the six third-order Hermite polynomials that do not
+    vanish on D3Q19, as rows over the 19 velocities."""
+    c = c.astype(np.float64)
+    rows = []
+    for a, b in [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]:
+        rows.append(c[:, a] * c[:, b] - T0 * delta(a, b))
+    for a, b, g in _H3_IDX:
+        rows.append(c[:, a] * c[:, b] * c[:, g]
+                    - T0 * (c[:, a] * delta(b, g) + c[:, b] * delta(a, g) + c[:, g] * delta(a, b)))
+    return np.array(rows)
+
+
+def _reg3_defects(oracle_mod, seed=21, cases=10):
+    """Largest violation, over random streamed states, of what defines f' with
+    the third-order terms: f' = (f* - feq) / (1 - 1/tau) has no mass or
+    momentum, its momentum flux is Pi^neq of the streamed state, its moments
+    over the six third-order polynomials are u_a Pi_bg + u_b Pi_ag + u_g Pi_ab,
+    and f'_i / w_i is a combination of the twelve Hermite polynomials (nothing
+    in the three directions of the 19 they leave over)."""
+    c, w, _ = oracle_mod.lattice()
+    cf = c.astype(np.float64)
+    H = _hermite_basis(c)
+    # orthonormal basis (in the w-weighted product) of what f'/w may contain
+    B = np.vstack([np.ones(19), cf.T, H])
+    Qm, _ = np.linalg.qr((B * np.sqrt(w)).T)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(cases):
+        u0 = rng.uniform(-0.08, 0.08, 3)
+        f = np.stack([oracle_mod.feq(r, u0, 1) for r in (0.7, 0.3)])
+        f = f * (1 + rng.uniform(-0.05, 0.05, f.shape))
+        tau = [rng.uniform(0.52, 1.5), rng.uniform(0.52, 1.5)]
+        fo, uF, rho, tm = oracle_mod.collide_cell(f, np.zeros((2, 3)), tau, 1, 3)
+        for al in range(2):
+            fe = oracle_mod.feq(rho[al], uF, 1)
+            fp = (fo[al] - fe) / (1 - 1 / tm)
+            pi = np.einsum("i,ia,ib->ab", f[al] - fe, cf, cf)
+            a3 = np.array([uF[a] * pi[b, g] + uF[b] * pi[a, g] + uF[g] * pi[a, b] for a, b, g in _H3_IDX])
+            scale = np.abs(pi).max()
+            d = [abs(fp.sum()), np.abs(cf.T @ fp).max(),
+                 np.abs(np.einsum("i,ia,ib->ab", fp, cf, cf) - pi).max(),
+                 np.abs(H[6:] @ fp - a3).max()]
+            g = fp / np.sqrt(w)
+            d.append(np.abs(g - Qm @ (Qm.T @ g)).max())
+            worst = max(worst, max(d) / scale)
+    return worst
+
+
+def test_third_order_regularisation_moments(oracle_mod):
+    """reg_order 3 reproduces, to rounding, the definition of f' with the
+    third-order Hermite terms (recursive third-order moments from Pi^neq and
+    u_F), checked on the post-collision state of random cells."""
+    assert _reg3_defects(oracle_mod) < 1e-12
+
+
+def test_third_order_regularisation_without_velocity(oracle_mod):
+    """At u_F = 0 the third-order moments vanish and reg_order 3 is the
+    second-order regularisation exactly (up to rounding)."""
+    rng = np.random.default_rng(22)
+    for _ in range(5):
+        P = rng.normal(size=(3, 3))
+        P = P + P.T
+        assert np.allclose(oracle_mod.regularize3(P, np.zeros(3)), oracle_mod.regularize(P), atol=1e-15)
+
+
+def _wave_u_dependence(oracle_mod, reg_order, tau=0.52):
+    amps = []
+    for U in (0.0, 0.05, 0.1):
+        nx, A = 32, 1e-3
+        x = np.arange(nx) + 0.5
+        k = 2 * np.pi / nx
+        u = np.zeros((1, 1, 1, nx, 3))
+        u[..., 0] = U
+        u[..., 1] = A * np.sin(k * x)
+        sim = oracle_mod.OracleSim(nx, 1, 1, [dict(tau=(tau, tau), G=0.0)], eq_order=1, reg_order=reg_order)
+        sim.set_geometry(np.zeros((1, 1, 1, nx), np.uint8))
+        sim.set_fields(np.full((1, 1, 1, nx), 0.5), np.full((1, 1, 1, nx), 0.5), u)
+        sim.step(200)
+        _, _, v = sim.get_fields()
+        sim.close()
+        uy = v[0, 0, 0, :, 1]
+        amps.append(np.hypot(2 * np.sum(uy * np.sin(k * x)) / nx, 2 * np.sum(uy * np.cos(k * x)) / nx) / A)
+    return max(abs(a - amps[0]) / amps[0] for a in amps)
+
+
+def test_third_order_regularisation_galilean(oracle_mod):
+    """Galilean invariance at low viscosity (tau = 0.52): the decay of a shear
+    wave must not depend on the speed of the stream carrying it.  With the
+    second-order regularisation the amplitude after 200 updates moves by more
+    than 1e-4 between U = 0 and U = 0.1; the third-order terms bring that
+    below 2e-5 (measured 2.3e-4 and 5.8e-6)."""
+    assert _wave_u_dependence(oracle_mod, 2) > 1e-4
+    assert _wave_u_dependence(oracle_mod, 3) < 2e-5
+
+
+@pytest.mark.parametrize("old,new", [
+    ("a[6 + k] = u[x] * pi[3 * y + z] + u[y] * pi[3 * x + z] + u[z] * pi[3 * x + y];",
+     "a[6 + k] = u[x] * pi[3 * y + z] + u[y] * pi[3 * x + z];"),
+    ("- T0 * (C[i][a] * (b == g) + C[i][b] * (a == g) + C[i][g] * (a == b));",
+     "- T0 * (C[i][a] * (b == g));"),
+    ("for (int k = 0; k < 6; ++k) H[6 + k][i] = hermite3(i, I3[k][0], I3[k][1], I3[k][2]);",
+     "for (int k = 0; k < 6; ++k) H[6 + k][i] = hermite3(i, I3[k][0], I3[k][1], I3[k][2]) * (k == 0 ? 1.0 : -1.0);"),
+])
+def test_third_order_pins_catch_slips(oracle_mod, old, new):
+    """A dropped term of the recursive moments, a wrong Hermite polynomial or
+    a flipped sign of a basis polynomial's target, planted in the oracle, fails
+    the definition check."""
+    with oracle_mod.planted(old, new):
+        d = _reg3_defects(oracle_mod, cases=3)
+    assert d > 1e-6, d
