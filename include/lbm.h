@@ -95,9 +95,20 @@ typedef struct {
     int batch;               /* independent instances, >= 1 */
     lbm_precision precision;
     int eq_order;            /* 0: Eq. 3 as printed (no quadratic terms); 1: with them */
-    int wall_model;          /* psi of a SOLID neighbour: 0 rho^s_beta with the wall forces balanced
-                                between components, 1 plain rho^s_beta, 2 the cell's own
-                                rho_beta + rho^s_beta (neutral wall at rho^s = 0; recommended) */
+    int wall_model;          /* psi of a SOLID neighbour (Eq. 11): 0 rho^s_beta with the wall forces
+                                balanced between components, 1 plain rho^s_beta, 2 the cell's own
+                                rho_beta + rho^s_beta (neutral wall at rho^s = 0; recommended),
+                                3 the cell's own rho_beta, with the wall potential's force
+                                G rho_alpha sum_solid ws_i c_i rho^s_beta added balanced between
+                                the components (neutral wall, and no net wall force on the
+                                mixture: the permeability of Sec. 3.5) */
+    int reg_order;           /* regularisation of the non-equilibrium part (Eq. 10): 2 (or 0, the
+                                default of a zeroed struct) second-order Hermite projection of
+                                Pi^neq; 3 adds the third-order Hermite terms, built from Pi^neq
+                                and u_F recursively (a3_abg = u_a Pi_bg + u_b Pi_ag + u_g Pi_ab)
+                                and projected onto the six third-order polynomials D3Q19
+                                carries.  reg_order 3 runs in the TWO_PASS and COMPACT
+                                strategies (and AUTO) only */
 } lbm_config;
 
 typedef struct {
@@ -118,7 +129,8 @@ typedef struct {
  * Allocates the device buffers.
  * Errors: LBM_ERR_ARG (null pointers, a dimension < 1, batch < 1 or
  * batch > 32767, more than 226 million cells per instance, tau <= 1/2, a
- * non-finite parameter, precision, eq_order or wall_model out of range),
+ * non-finite parameter, precision, eq_order, wall_model or reg_order out of
+ * range),
  * LBM_ERR_OOM (an allocation through the hook returned NULL), LBM_ERR_CUDA.
  * On failure *out is NULL and nothing stays allocated. */
 lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_instance, lbm_ctx **out);
@@ -244,7 +256,8 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
 
 /* Choose the kernel strategy (default LBM_KERNEL_AUTO).  LBM_ERR_ARG if the
  * strategy cannot run this configuration (e.g. CLUSTER on a large grid,
- * COMPACT beyond its coordinate limits).  The compact strategy keeps the
+ * COMPACT beyond its coordinate limits, FUSED, CLUSTER or FUSED_COMPACT with
+ * reg_order 3).  The compact strategy keeps the
  * distributions in its own layout; the library converts the state between the
  * layouts when a step, an export or an import needs the other one (one
  * gather of f, on the context's stream). */

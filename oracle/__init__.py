@@ -52,7 +52,7 @@ class _Config(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("rho_s", ctypes.c_double),
                 ("g", ctypes.c_double * 3), ("rho_in", ctypes.c_double * 2),
-                ("u_in", ctypes.c_double * 3)]
+                ("u_in", ctypes.c_double * 3), ("slip", ctypes.c_double)]
 
 
 def _load(path: str):
@@ -220,6 +220,7 @@ class OracleSim:
             arr[k].g[:] = list(p.get("g", (0.0, 0.0, 0.0)))
             arr[k].rho_in[:] = list(p.get("rho_in", (0.0, 0.0)))
             arr[k].u_in[:] = list(p.get("u_in", (0.0, 0.0, 0.0)))
+            arr[k].slip = p.get("slip", 0.0)
         h = ctypes.c_void_p()
         rc = lib().oracle_create(ctypes.byref(cfg), arr, ctypes.byref(h))
         if rc != 0:

@@ -54,7 +54,15 @@
  *     force (local momentum conserved).  Wall model 1 ("B", plain):
  *     psi_beta(solid) = rho^s_beta.  Wall model 0 ("A", balanced): B, then the
  *     wall part of the force is projected so that F_w^1 + F_w^2 = 0 in every
- *     cell (forces along walls balanced between components).
+ *     cell (forces along walls balanced between components).  Wall model 3
+ *     (both statements of the paper): the neutral part of model 2 (the solid
+ *     neighbour carries the cell's own rho_beta), and the wall potential's part
+ *     G rho_alpha sum_solid ws_i c_i rho^s_beta projected as in model A, so that
+ *     the wall's forces on the two components cancel in every cell.
+ *   - Surface scattering (the paper defers to another work): a wall returns
+ *     the fraction 1 - slip of the particles by bounce-back and reflects the
+ *     fraction slip specularly about the voxel wall's plane (specular_source);
+ *     slip = 0 (the default) is the no-slip bounce-back.
  *   - rho^s_1 = -rho^s * Theta(-rho^s), rho^s_2 = rho^s * Theta(rho^s).
  *   - INLET cells hold feq(rho_in, u_in) after every step; an OUTLET cell
  *     takes the streamed distributions of its upstream (-x) neighbour.
@@ -112,6 +120,13 @@ static void init_tables(void)
 static double weight(int i) { return W[i]; }
 static int opposite(int i) { return OPP[i]; }
 
+static int direction_of(int cx, int cy, int cz)
+{
+    for (int k = 0; k < Q; ++k)
+        if (C[k][0] == cx && C[k][1] == cy && C[k][2] == cz) return k;
+    return -1;
+}
+
 /* Weights of the interaction-force stencil (Eq. 7, Eq. 11): twice the D3Q19
  * weights, sum_i ws_i c_i c_i = 2 T0 I (1/9 on faces, 1/18 on edges).  With
  * the bare lattice weights the mixture at total density 1 cannot separate for
@@ -123,7 +138,8 @@ static double force_weight(int i) { return 2.0 * W[i]; }
 typedef struct {
     int nx, ny, nz, batch;
     int eq_order;   /* 0 = Eq. 3 as printed, 1 = with quadratic terms */
-    int wall_model; /* 0 = balanced (A), 1 = plain (B), 2 = own density + rho^s */
+    int wall_model; /* 0 = balanced (A), 1 = plain (B), 2 = own density + rho^s,
+                       3 = own density, wall potential's part balanced */
     int reg_order;  /* 0 or 2 = second-order regularisation, 3 = with third-order terms */
 } oracle_config;
 
@@ -134,6 +150,7 @@ typedef struct {
     double g[3];
     double rho_in[2];
     double u_in[3];
+    double slip;    /* fraction of the particles a wall reflects specularly (0 = no-slip) */
 } oracle_params;
 
 typedef struct oracle_ctx {
@@ -397,7 +414,8 @@ int oracle_create(const oracle_config *cfg, const oracle_params *par, oracle_ctx
     if (!cfg || !par || !out) return 1;
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || cfg->batch < 1) return 1;
     for (int b = 0; b < cfg->batch; ++b)
-        if (!(par[b].tau[0] > 0.5) || !(par[b].tau[1] > 0.5)) return 1;
+        if (!(par[b].tau[0] > 0.5) || !(par[b].tau[1] > 0.5) || !(par[b].slip >= 0.0 && par[b].slip <= 1.0))
+            return 1;
     oracle_ctx *ctx = (oracle_ctx *)calloc(1, sizeof(oracle_ctx));
     ctx->cfg = *cfg;
     ctx->n = (size_t)cfg->nx * cfg->ny * cfg->nz;
@@ -469,6 +487,43 @@ int oracle_set_fields(oracle_ctx *ctx, const double *rho1, const double *rho2, c
     return 0;
 }
 
+/* Specular reflection at a voxel wall (the partial-slip reading of the
+ * surface scattering model, Sec. 2).  The value arriving at (x, y, z) in
+ * direction i comes from the SOLID cell x - c_i.  For an edge direction with
+ * non-zero components along axes a and b: if the face neighbour x - c_ia e_a
+ * is not SOLID and x - c_ib e_b is, the wall's normal is e_b and the particle
+ * came from x - c_ia e_a moving with c_i's b-component reversed (and the same
+ * with a and b exchanged).  Writes that cell and direction and returns 1.
+ * Face directions (normal incidence) and corners (both face neighbours SOLID,
+ * or neither) return 0: they bounce back.  The pairing is mutual: the cell
+ * found here reflects the value of direction opp(i) of (x, y, z) the same way,
+ * so a blend of bounce-back and reflection conserves mass. */
+static int specular_source(const oracle_config *cfg, const uint8_t *type, int x, int y, int z, int i,
+                           size_t *s, int *j)
+{
+    int ax[2], na = 0;
+    for (int a = 0; a < 3; ++a)
+        if (C[i][a] != 0) ax[na++] = a;
+    if (na != 2) return 0;
+    int pos[3] = {x, y, z}, dim[3] = {cfg->nx, cfg->ny, cfg->nz};
+    int solid[2];
+    size_t face[2];
+    for (int m = 0; m < 2; ++m) {
+        int q[3] = {pos[0], pos[1], pos[2]};
+        q[ax[m]] = wrap(q[ax[m]] - C[i][ax[m]], dim[ax[m]]);
+        face[m] = cell_index(cfg, q[0], q[1], q[2]);
+        solid[m] = type[face[m]] == CELL_SOLID;
+    }
+    if (solid[0] == solid[1]) return 0;
+    int keep = solid[0] ? 1 : 0; /* the open face: the particle moved along its axis */
+    int flip = 1 - keep;         /* the wall's normal axis */
+    int c[3] = {C[i][0], C[i][1], C[i][2]};
+    c[ax[flip]] = -c[ax[flip]];
+    *s = face[keep];
+    *j = direction_of(c[0], c[1], c[2]);
+    return 1;
+}
+
 /* One update of instance b. */
 static void step_instance(oracle_ctx *ctx, int b)
 {
@@ -482,7 +537,8 @@ static void step_instance(oracle_ctx *ctx, int b)
     double rs[2];
     oracle_wall_potential(p->rho_s, rs);
 
-    /* S1: pull streaming; a link from a solid cell is bounced back. */
+    /* S1: pull streaming; a link from a solid cell is bounced back, or, for
+     * the fraction p->slip, reflected specularly (see specular_source). */
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -494,10 +550,15 @@ static void step_instance(oracle_ctx *ctx, int b)
                         size_t src = cell_index(cfg, wrap(x - C[i][0], nx), wrap(y - C[i][1], ny),
                                                 wrap(z - C[i][2], nz));
                         double v;
-                        if (type[src] == CELL_SOLID)
+                        if (type[src] == CELL_SOLID) {
                             v = f[((size_t)al * Q + opposite(i)) * n + k];
-                        else
+                            size_t s;
+                            int j;
+                            if (p->slip != 0.0 && specular_source(cfg, type, x, y, z, i, &s, &j))
+                                v = (1.0 - p->slip) * v + p->slip * f[((size_t)al * Q + j) * n + s];
+                        } else {
                             v = f[((size_t)al * Q + i) * n + src];
+                        }
                         ctx->fs[((size_t)al * Q + i) * n + k] = v;
                     }
             }
@@ -544,27 +605,33 @@ static void step_instance(oracle_ctx *ctx, int b)
                 if (type[k] == CELL_SOLID || type[k] == CELL_INLET) continue;
                 double rho_a[2] = {ctx->psi[k], ctx->psi[n + k]};
                 double rho = rho_a[0] + rho_a[1];
-                double Fb[2][3], Fw[2][3];
+                double Fb[2][3], Fw[2][3], Fs[2][3];
                 for (int al = 0; al < 2; ++al) {
                     int be = 1 - al;
-                    double sb[3] = {0.0, 0.0, 0.0}, sw[3] = {0.0, 0.0, 0.0};
+                    double sb[3] = {0.0, 0.0, 0.0}, sw[3] = {0.0, 0.0, 0.0}, ss[3] = {0.0, 0.0, 0.0};
                     for (int i = 1; i < Q; ++i) {
                         size_t nb = cell_index(cfg, wrap(x + C[i][0], nx), wrap(y + C[i][1], ny),
                                                wrap(z + C[i][2], nz));
                         double ps = ctx->psi[(size_t)be * n + nb];
                         /* wall model 2: the solid neighbour carries the fluid
-                         * density of this cell plus the wall potential */
+                         * density of this cell plus the wall potential; wall
+                         * model 3: the fluid density here, the wall potential
+                         * in the separate sum ss */
                         if (type[nb] == CELL_SOLID && cfg->wall_model == 2) ps = rho_a[be] + rs[be];
+                        if (type[nb] == CELL_SOLID && cfg->wall_model == 3) ps = rho_a[be];
                         for (int a = 0; a < 3; ++a) {
-                            if (type[nb] == CELL_SOLID)
+                            if (type[nb] == CELL_SOLID) {
                                 sw[a] += force_weight(i) * C[i][a] * ps;
-                            else
+                                ss[a] += force_weight(i) * C[i][a] * rs[be];
+                            } else {
                                 sb[a] += force_weight(i) * C[i][a] * ps;
+                            }
                         }
                     }
                     for (int a = 0; a < 3; ++a) {
                         Fb[al][a] = p->G * rho_a[al] * sb[a];
                         Fw[al][a] = p->G * rho_a[al] * sw[a];
+                        Fs[al][a] = p->G * rho_a[al] * ss[a];
                     }
                 }
                 if (cfg->wall_model == 0) {
@@ -572,6 +639,14 @@ static void step_instance(oracle_ctx *ctx, int b)
                         double net = Fw[0][a] + Fw[1][a];
                         Fw[0][a] -= rho_a[0] / rho * net;
                         Fw[1][a] -= rho_a[1] / rho * net;
+                    }
+                }
+                if (cfg->wall_model == 3) {
+                    /* the wall potential's part, balanced between components */
+                    for (int a = 0; a < 3; ++a) {
+                        double net = Fs[0][a] + Fs[1][a];
+                        Fw[0][a] += Fs[0][a] - rho_a[0] / rho * net;
+                        Fw[1][a] += Fs[1][a] - rho_a[1] / rho * net;
                     }
                 }
                 for (int al = 0; al < 2; ++al)

@@ -344,6 +344,7 @@ StepArgs step_args(lbm_ctx *ctx, int write_macro) {
     StepArgs a{};
     a.precision = ctx->cfg.precision;
     a.eq_order = ctx->cfg.eq_order;
+    a.reg_order = ctx->cfg.reg_order;
     a.wall_model = ctx->cfg.wall_model;
     a.write_macro = write_macro;
     a.batch = ctx->cfg.batch;
@@ -405,8 +406,9 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
         return LBM_ERR_ARG;
     }
     if (cfg->precision < LBM_FP64 || cfg->precision > LBM_FP32_BF16S || cfg->eq_order < 0 || cfg->eq_order > 1 ||
-        cfg->wall_model < 0 || cfg->wall_model > 2) {
-        g_last_error = "lbm_create: precision, eq_order or wall_model out of range";
+        cfg->wall_model < 0 || cfg->wall_model > 3 ||
+        (cfg->reg_order != 0 && cfg->reg_order != 2 && cfg->reg_order != 3)) {
+        g_last_error = "lbm_create: precision, eq_order, wall_model or reg_order out of range";
         return LBM_ERR_ARG;
     }
     if (const char *bad = check_params(per_instance, cfg->batch)) {
@@ -415,6 +417,7 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
     }
     lbm_ctx *ctx = new lbm_ctx();
     ctx->cfg = *cfg;
+    ctx->cfg.reg_order = cfg->reg_order == 3 ? 3 : 2;
     ctx->par.assign(per_instance, per_instance + cfg->batch);
     ctx->g.nx = cfg->nx;
     ctx->g.ny = cfg->ny;
@@ -524,6 +527,9 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: COMPACT needs nx <= 2048, ny <= 2048, nz <= 1024");
     if (kernel == LBM_KERNEL_FUSED_COMPACT && (!ctx->compact_ok || ctx->fp64()))
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: FUSED_COMPACT needs the compact layout and FP32 arithmetic");
+    if (ctx->cfg.reg_order == 3 &&
+        (kernel == LBM_KERNEL_FUSED || kernel == LBM_KERNEL_CLUSTER || kernel == LBM_KERNEL_FUSED_COMPACT))
+        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: reg_order 3 runs in the TWO_PASS and COMPACT strategies");
     ctx->kernel = kernel;
     return LBM_OK;
 }
@@ -672,7 +678,8 @@ lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho1, const double *rho2, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     ctx->dfree(d);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_set_fields");
-    ctx->launches += 1;
+    // the shifted storages first write the reference densities (k_init_ref)
+    ctx->launches += (ctx->cfg.precision == LBM_FP32_F16S || ctx->cfg.precision == LBM_FP32_BF16S) ? 2 : 1;
     ctx->layout = 0;
     ctx->has_fields = true;
     ctx->half_step = false;
@@ -912,7 +919,7 @@ lbm_status lbm_get_state(lbm_ctx *ctx, void *buf, size_t *bytes) {
     const size_t cells = ctx->cells();
     StateHeader h{};
     std::memcpy(h.magic, "LBMSTATE", 8);
-    h.version = 2;
+    h.version = 3;
     h.cfg = ctx->cfg;
     h.layout = (uint32_t)ctx->layout;
     h.step = ctx->step;
@@ -955,9 +962,9 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes) {
     if (bytes < sizeof(h)) return ctx->fail(LBM_ERR_ARG, "lbm_set_state: buffer too small");
     std::memcpy(&h, buf, sizeof(h));
     const lbm_config &c = ctx->cfg;
-    if (std::memcmp(h.magic, "LBMSTATE", 8) != 0 || h.version != 2 || h.cfg.nx != c.nx || h.cfg.ny != c.ny ||
+    if (std::memcmp(h.magic, "LBMSTATE", 8) != 0 || h.version != 3 || h.cfg.nx != c.nx || h.cfg.ny != c.ny ||
         h.cfg.nz != c.nz || h.cfg.batch != c.batch || h.cfg.precision != c.precision ||
-        h.cfg.eq_order != c.eq_order || h.cfg.wall_model != c.wall_model)
+        h.cfg.eq_order != c.eq_order || h.cfg.wall_model != c.wall_model || h.cfg.reg_order != c.reg_order)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_state: configuration mismatch");
     const size_t cells = ctx->cells();
     if (h.f_bytes != ctx->f_bytes() || h.ref_bytes != ctx->ref_bytes() || h.link_bytes != cells * 4 ||
@@ -1001,8 +1008,9 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     cudaDeviceProp prop;
     LBM_CUDA(cudaGetDeviceProperties(&prop, ctx->dev), "cudaGetDeviceProperties");
     char key[512];
-    std::snprintf(key, sizeof key, "%dx%dx%d b%d p%d e%d w%d %s", ctx->cfg.nx, ctx->cfg.ny, ctx->cfg.nz,
-                  ctx->cfg.batch, (int)ctx->cfg.precision, ctx->cfg.eq_order, ctx->cfg.wall_model, prop.name);
+    std::snprintf(key, sizeof key, "%dx%dx%d b%d p%d e%d w%d r%d %s", ctx->cfg.nx, ctx->cfg.ny, ctx->cfg.nz,
+                  ctx->cfg.batch, (int)ctx->cfg.precision, ctx->cfg.eq_order, ctx->cfg.wall_model,
+                  ctx->cfg.reg_order, prop.name);
     for (char *c = key; *c; ++c)
         if (*c == '"' || *c == '\\') *c = '_';
     auto apply = [&](int k, int t, int z) {
@@ -1063,9 +1071,11 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     std::vector<Cand> cands;
     cands.push_back({LBM_KERNEL_TWO_PASS, -1, -1});
     if (ctx->compact_ok) cands.push_back({LBM_KERNEL_COMPACT, -1, -1});
-    if (ctx->fplan.ok) cands.push_back({LBM_KERNEL_FUSED_COMPACT, -1, -1});
-    if (ctx->g.n <= kClusterMaxCells) cands.push_back({LBM_KERNEL_CLUSTER, -1, -1});
-    for (int t = 0; t < fused_tile_count(); ++t) {
+    // the third-order regularisation is built into the two-pass strategies only
+    const bool single_read_ok = ctx->cfg.reg_order != 3;
+    if (ctx->fplan.ok && single_read_ok) cands.push_back({LBM_KERNEL_FUSED_COMPACT, -1, -1});
+    if (ctx->g.n <= kClusterMaxCells && single_read_ok) cands.push_back({LBM_KERNEL_CLUSTER, -1, -1});
+    for (int t = 0; single_read_ok && t < fused_tile_count(); ++t) {
         cands.push_back({LBM_KERNEL_FUSED, t, -1});
         for (int z : {8, 16, 32, 64})
             if (z < ctx->g.nz) cands.push_back({LBM_KERNEL_FUSED, t, z});
@@ -1074,7 +1084,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = 1e30f;
-    Cand pick = {LBM_KERNEL_FUSED, -1, -1};
+    Cand pick = cands.front();
     lbm_status st = LBM_OK;
     for (const Cand &c : cands) {
         if (e != cudaSuccess) break;

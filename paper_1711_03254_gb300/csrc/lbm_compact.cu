@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
         bs.add(i, q);
         Rp[i] = solid ? rho_h : __float22half2_rn(q);
     }
-    const float2 psi_own = (word & 0x7FFFEu) ? __ldg(psi + k) : bc2(0.f);
+    const float2 psi_own = ((word & 0x7FFFEu) && a.wall_model < 2) ? __ldg(psi + k) : bc2(0.f);
     const Forces2 F = forces2(bs, psi_own, word, m.rho, p, a.wall_model);
     const Relax<float> R = relax2(m, F, p);
     const Prep2 cp = prep2<EQ>(m, R, F);
@@ -359,17 +359,13 @@ static cudaError_t launch_compact_t(const StepArgs &a, int parts) {
     // psi pass does, measured 10 % slower here: the update is issue-bound, and
     // the prefetch buffers cost occupancy and registers)
     if (parts & 2) {
-        if constexpr (packed_pairs<S>()) {
-            if (a.eq_order == 0)
-                k_collide_c2<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
+        dispatch_variant(collide_variant(a), [&](auto v) {
+            constexpr int EQ = decltype(v)::value;
+            if constexpr (packed_pairs<S>())
+                k_collide_c2<S, EQ><<<gc, kCollideThreads, 0, a.stream>>>(a);
             else
-                k_collide_c2<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
-        } else {
-            if (a.eq_order == 0)
-                k_collide_c<S, 0><<<gc, kCollideThreads, 0, a.stream>>>(a);
-            else
-                k_collide_c<S, 1><<<gc, kCollideThreads, 0, a.stream>>>(a);
-        }
+                k_collide_c<S, EQ><<<gc, kCollideThreads, 0, a.stream>>>(a);
+        });
     }
     record_event(a, 2);
     return cudaGetLastError();

@@ -264,28 +264,59 @@ __device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restri
     return density_of<T, Storage<S>::shifted>(v, rref);
 }
 
-// Equilibrium of Eq. 3 for direction i (EQ = 1 adds the quadratic terms).
+// Collision variants EQ: bit 0 adds the quadratic terms to the equilibrium of
+// Eq. 3 (eq_order 1); bit 1 adds the third-order Hermite terms to the
+// regularised non-equilibrium part of Eq. 10 (reg_order 3).
+constexpr bool eq_full(int EQ) { return (EQ & 1) != 0; }
+constexpr bool reg_third(int EQ) { return (EQ & 2) != 0; }
+
+// Equilibrium of Eq. 3 for direction i (bit 0 of EQ adds the quadratic terms).
 template <class T, int EQ>
 __device__ __forceinline__ T feq_dir(int i, T rho, T ux, T uy, T uz, T uu) {
     const T cu = T(cx(i)) * ux + T(cy(i)) * uy + T(cz(i)) * uz;
     // 1/T0 = 3, 1/(6 T0^3) = 1/(2 T0^2) = 9/2
     T e = T(1) + cu * (T(3) + T(4.5) * cu * cu - T(4.5) * uu);
-    if (EQ == 1) e += T(4.5) * cu * cu - T(1.5) * uu;
+    if (eq_full(EQ)) e += T(4.5) * cu * cu - T(1.5) * uu;
     return rho * wgt<T>(i) * e;
 }
 
 // S6-S7 for one component: writes f*_i = feq_i + w_i/(2 T0^2) H_i : A + w_i c_i.F/(2 T0)
-// with A = (1 - 1/tau) Pi^neq + (1 - 1/(2 tau)) (u_F F + F u_F).
+// with A = (1 - 1/tau) Pi^neq + (1 - 1/(2 tau)) (u_F F + F u_F), plus, with the
+// third-order regularisation, (1 - 1/tau) w_i times third_order_term.
 // sig(i) is the reference density of the cell value i streams into.
 //
 // Directions come in opposite pairs (i, i+1) with c_{i+1} = -c_i: the parts of
 // f*_i that are even in c (rest term of feq, the quadratic terms of Eq. 3 for
-// EQ = 1, H_i : A) are shared, the odd parts (the c.u terms of feq, the
-// first-order forcing) change sign, so each pair costs one evaluation.
+// eq_full, H_i : A) are shared, the odd parts (the c.u terms of feq, the
+// first-order forcing, the third-order terms) change sign, so each pair costs
+// one evaluation.
 template <class T> struct CollidePrep {
     T rho, ux, uy, uz, Fx, Fy, Fz, uu, odd_k;
     T axx, ayy, azz, axy, axz, ayz, ktr;
+    // relaxed third-order moments (1 - 1/tau) a3 (reg_third only)
+    T bxxy, bxyy, bxxz, bxzz, byyz, byzz;
 };
+
+// Third-order part of the regularised f'_i / w_i for the odd direction i, from
+// the relaxed recursive moments a3_abg = u_a Pi_bg + u_b Pi_ag + u_g Pi_ab
+// (Pi = Pi^neq).  On D3Q19, H_aaa and H_xyz vanish at every velocity and the
+// six other third-order Hermite polynomials alias pairwise (sum_i w_i H_xxy
+// H_yzz = -T0^3); the lattice function whose moments over the six equal a3
+// works out, per velocity class, to
+//   face  c = s e_a:          -9 s (a_abb + a_acc)
+//   edge  c = s e_a + t e_b:   9 (t a_aab + s a_abb)
+// (with 1/T0^3 = 27; the same function as the general projection with the
+// Gram matrix of the six polynomials).
+template <class T, class V>
+__device__ __forceinline__ V third_order_term(int i, V bxxy, V bxyy, V bxxz, V bxzz, V byyz, V byzz) {
+    const int c0 = cx(i), c1 = cy(i), c2 = cz(i);
+    if (c0 && c1) return T(9) * (T(c1) * bxxy + T(c0) * bxyy);
+    if (c0 && c2) return T(9) * (T(c2) * bxxz + T(c0) * bxzz);
+    if (c1 && c2) return T(9) * (T(c2) * byyz + T(c1) * byzz);
+    if (c0) return T(-9 * c0) * (bxyy + bxzz);
+    if (c1) return T(-9 * c1) * (bxxy + byzz);
+    return T(-9 * c2) * (bxxz + byyz);
+}
 
 template <class T, int EQ>
 __device__ __forceinline__ CollidePrep<T> collide_prep(const Moments<T> &m, T ux, T uy, T uz, T Fx, T Fy, T Fz,
@@ -298,9 +329,17 @@ __device__ __forceinline__ CollidePrep<T> collide_prep(const Moments<T> &m, T ux
     // Pi^neq = Pi - Pi^eq with Pi^eq = rho T0 I (+ rho u u for EQ = 1)
     T nxx = m.pxx - m.rd * T0, nyy = m.pyy - m.rd * T0, nzz = m.pzz - m.rd * T0;
     T nxy = m.pxy, nxz = m.pxz, nyz = m.pyz;
-    if (EQ == 1) {
+    if (eq_full(EQ)) {
         nxx -= m.rho * ux * ux; nyy -= m.rho * uy * uy; nzz -= m.rho * uz * uz;
         nxy -= m.rho * ux * uy; nxz -= m.rho * ux * uz; nyz -= m.rho * uy * uz;
+    }
+    if (reg_third(EQ)) {
+        c.bxxy = omega * (T(2) * ux * nxy + uy * nxx);
+        c.bxyy = omega * (T(2) * uy * nxy + ux * nyy);
+        c.bxxz = omega * (T(2) * ux * nxz + uz * nxx);
+        c.bxzz = omega * (T(2) * uz * nxz + ux * nzz);
+        c.byyz = omega * (T(2) * uy * nyz + uz * nyy);
+        c.byzz = omega * (T(2) * uz * nyz + uy * nzz);
     }
     c.axx = omega * nxx + fcoef * (T(2) * ux * Fx);
     c.ayy = omega * nyy + fcoef * (T(2) * uy * Fy);
@@ -319,7 +358,7 @@ __device__ __forceinline__ CollidePrep<T> collide_prep(const Moments<T> &m, T ux
 // two O(w rho) numbers.
 template <class T, int EQ> __device__ __forceinline__ T collide_rest(const CollidePrep<T> &c, T R) {
     T e = c.rho - R;
-    if (EQ == 1) e = (c.rho - R) - T(1.5) * c.rho * c.uu;
+    if (eq_full(EQ)) e = (c.rho - R) - T(1.5) * c.rho * c.uu;
     return wgt<T>(0) * (e + c.ktr);
 }
 
@@ -334,8 +373,9 @@ __device__ __forceinline__ void collide_pair(const CollidePrep<T> &c, int i, T R
     const T cF = c0 * c.Fx + c1 * c.Fy + c2 * c.Fz;
     // w_i x (even part without the rest term, odd part) of f*_i
     T even = T(4.5) * cAc + c.ktr;
-    if (EQ == 1) even += c.rho * (T(4.5) * cu * cu - T(1.5) * c.uu);
-    const T odd = c.rho * cu * (c.odd_k + T(4.5) * cu * cu) + T(1.5) * cF;
+    if (eq_full(EQ)) even += c.rho * (T(4.5) * cu * cu - T(1.5) * c.uu);
+    T odd = c.rho * cu * (c.odd_k + T(4.5) * cu * cu) + T(1.5) * cF;
+    if (reg_third(EQ)) odd += third_order_term<T, T>(i, c.bxxy, c.bxyy, c.bxxz, c.bxzz, c.byyz, c.byzz);
     const T w = wgt<T>(i);
     vi = w * (((c.rho - Ri) + even) + odd);
     vo = w * (((c.rho - Ro) + even) - odd);
@@ -418,8 +458,9 @@ __device__ __forceinline__ Forces<T> sc_forces_finish(const ForceSums<T> &bs, ui
     }
     const uint32_t wl = links & 0x7FFFEu;
     if (wl) {
-        // wall part (Eq. 11): psi_beta(SOLID) = rho^s_beta (models 0, 1), or the
-        // cell's own rho_beta plus rho^s_beta (model 2)
+        // wall part (Eq. 11): psi_beta(SOLID) = rho^s_beta (models 0, 1), the
+        // cell's own rho_beta plus rho^s_beta (model 2), or the cell's own
+        // rho_beta with the wall potential's part added balanced (model 3)
         T d[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
@@ -433,8 +474,8 @@ __device__ __forceinline__ Forces<T> sc_forces_finish(const ForceSums<T> &bs, ui
         T fw[2][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const T w1 = wall_model == 2 ? r[1] + p.rs[1] : p.rs[1];
-            const T w0 = wall_model == 2 ? r[0] + p.rs[0] : p.rs[0];
+            const T w1 = wall_model == 2 ? r[1] + p.rs[1] : wall_model == 3 ? r[1] : p.rs[1];
+            const T w0 = wall_model == 2 ? r[0] + p.rs[0] : wall_model == 3 ? r[0] : p.rs[0];
             fw[0][a] = p.G * r[0] * (w1 * d[a]);
             fw[1][a] = p.G * r[1] * (w0 * d[a]);
         }
@@ -445,6 +486,16 @@ __device__ __forceinline__ Forces<T> sc_forces_finish(const ForceSums<T> &bs, ui
                 const T net = fw[0][a] + fw[1][a];
                 fw[0][a] -= r[0] / rho * net;
                 fw[1][a] -= r[1] / rho * net;
+            }
+        } else if (wall_model == 3) {
+            const T rho = r[0] + r[1];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T fs0 = p.G * r[0] * (p.rs[1] * d[a]);
+                const T fs1 = p.G * r[1] * (p.rs[0] * d[a]);
+                const T net = fs0 + fs1;
+                fw[0][a] += fs0 - r[0] / rho * net;
+                fw[1][a] += fs1 - r[1] / rho * net;
             }
         }
 #pragma unroll

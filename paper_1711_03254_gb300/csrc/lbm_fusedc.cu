@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kFcThreads, fc_min_blocks<S>()) k_fused_c(Step
                         bs.add(i, q);
                         Rp[i] = solid ? rho_h : __float22half2_rn(q);
                     }
-                    const float2 psi_own = (word & 0x7FFFEu) ? own_psi : bc2(0.f);
+                    const float2 psi_own = ((word & 0x7FFFEu) && a.wall_model < 2) ? own_psi : bc2(0.f);
                     const Forces2 F = forces2(bs, psi_own, word, m.rho, prm, a.wall_model);
                     const Relax<float> Rx = relax2(m, F, prm);
                     const Prep2 cp = prep2<EQ>(m, Rx, F);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
@@ -13,6 +14,7 @@ namespace lbm {
 struct StepArgs {
     lbm_precision precision;
     int eq_order, wall_model, write_macro;
+    int reg_order;     // 2 or 3 (0 is taken as 2)
     int batch;
     Grid g;
     const void *f_in;
@@ -38,6 +40,19 @@ struct StepArgs {
     // kernel of the launch (two-pass: 3 events, fused and cluster: 2)
     cudaEvent_t *ev = nullptr;
 };
+
+// Collision variant EQ of the kernels (bit 0: eq_order 1, bit 1: reg_order 3),
+// passed to f as a std::integral_constant.
+inline int collide_variant(const StepArgs &a) { return (a.eq_order ? 1 : 0) | (a.reg_order == 3 ? 2 : 0); }
+
+template <class F> inline void dispatch_variant(int v, F &&f) {
+    switch (v) {
+    case 0: f(std::integral_constant<int, 0>{}); break;
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    default: f(std::integral_constant<int, 3>{}); break;
+    }
+}
 
 inline void record_event(const StepArgs &a, int k) {
     if (a.ev) cudaEventRecord(a.ev[k], a.stream);

@@ -206,11 +206,37 @@ __global__ void __launch_bounds__(256, 2) k_collide(const S *__restrict__ f, S *
     }
 }
 
-// f := feq(rho_alpha, u) from FP64 fields (u interleaved [b][cell][3]); the
-// reference densities are the initial densities.
+// Initial density of every cell as its neighbours see it (0 at SOLID cells,
+// rho_in at INLET cells), rounded to the FP16 reference of the shifted
+// storages: the reference densities of the initial state.
+template <class T>
+__global__ void k_init_ref(const double *__restrict__ r1, const double *__restrict__ r2,
+                           const uint32_t *__restrict__ link, Ref *__restrict__ rout, Grid g,
+                           const InstParam<T> *__restrict__ par) {
+    const int b = blockIdx.y;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const long long gk = (long long)b * g.n + k;
+    const uint32_t t = cell_type(__ldg(link + gk));
+    T a0 = T(0), a1 = T(0);
+    if (t == kInlet) {
+        a0 = par[b].rho_in[0];
+        a1 = par[b].rho_in[1];
+    } else if (t != kSolid) {
+        a0 = (T)r1[gk];
+        a1 = (T)r2[gk];
+    }
+    rout[(long long)b * 2 * g.n + k] = __float2half_rn((float)a0);
+    rout[(long long)b * 2 * g.n + g.n + k] = __float2half_rn((float)a1);
+}
+
+// f := feq(rho_alpha, u) from FP64 fields (u interleaved [b][cell][3]).  The
+// shifted storages store each value against the reference density of the
+// cell it streams into: k_init_ref has written those (ref), and a value that
+// bounces back off a SOLID neighbour takes the cell's own density.
 template <class S, int EQ>
 __global__ void k_init(const double *__restrict__ r1, const double *__restrict__ r2, const double *__restrict__ u,
-                       const uint32_t *__restrict__ link, S *__restrict__ fo, Ref *__restrict__ rout,
+                       const uint32_t *__restrict__ link, S *__restrict__ fo, const Ref *__restrict__ ref,
                        typename Storage<S>::T *__restrict__ macro, typename Storage<S>::T *__restrict__ usnap, Grid g,
                        const InstParam<typename Storage<S>::T> *__restrict__ par) {
     using T = typename Storage<S>::T;
@@ -221,13 +247,6 @@ __global__ void k_init(const double *__restrict__ r1, const double *__restrict__
     const uint32_t word = link[gk];
     const uint32_t t = cell_type(word);
     const InstParam<T> &p = par[b];
-    // initial density of a cell as its neighbours see it
-    auto init_rho = [&](long long cell, int comp) -> T {
-        const uint32_t tc = cell_type(link[(long long)b * g.n + cell]);
-        if (tc == kSolid) return T(0);
-        if (tc == kInlet) return p.rho_in[comp];
-        return (T)(comp == 0 ? r1 : r2)[(long long)b * g.n + cell];
-    };
     T a0, a1, ux, uy, uz;
     if (t == kSolid) {
         a0 = a1 = ux = uy = uz = T(0);
@@ -243,14 +262,14 @@ __global__ void k_init(const double *__restrict__ r1, const double *__restrict__
     Nbr nb;
     nb.init(x, y, z, g);
     const long long fofs = (long long)b * 2 * kQ * g.n;
-    store_equilibrium<S, EQ>(fo + fofs, g.n, (int)k, a0, ux, uy, uz,
-                             [&](int i) -> T { return ref_value(((word >> i) & 1u) ? a0 : init_rho(nb.dst(i), 0)); });
-    store_equilibrium<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, a1, ux, uy, uz,
-                             [&](int i) -> T { return ref_value(((word >> i) & 1u) ? a1 : init_rho(nb.dst(i), 1)); });
-    if constexpr (Storage<S>::shifted) {
-        rout[(long long)b * 2 * g.n + k] = __float2half_rn((float)a0);
-        rout[(long long)b * 2 * g.n + g.n + k] = __float2half_rn((float)a1);
-    }
+    const Ref *ref0 = ref + (long long)b * 2 * g.n, *ref1 = ref0 + g.n;
+    // (only the shifted storages call these)
+    store_equilibrium<S, EQ>(fo + fofs, g.n, (int)k, a0, ux, uy, uz, [&](int i) -> T {
+        return ((word >> i) & 1u) ? ref_value(a0) : (T)__half2float(__ldg(ref0 + nb.dst(i)));
+    });
+    store_equilibrium<S, EQ>(fo + fofs + kQ * g.n, g.n, (int)k, a1, ux, uy, uz, [&](int i) -> T {
+        return ((word >> i) & 1u) ? ref_value(a1) : (T)__half2float(__ldg(ref1 + nb.dst(i)));
+    });
     T *mac = macro + (long long)b * 5 * g.n;
     mac[k] = a0; mac[g.n + k] = a1;
     mac[2 * g.n + k] = ux; mac[3 * g.n + k] = uy; mac[4 * g.n + k] = uz;
@@ -344,14 +363,12 @@ static cudaError_t launch_two_pass_t(const StepArgs &a) {
     k_psi<S><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, a.ref_in, a.link, (T *)a.psi, a.g,
                                          (const InstParam<T> *)a.par, a.list, a.list_count);
     record_event(a, 1);
-    if (a.eq_order == 0)
-        k_collide<S, 0><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
-                                                    (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
-                                                    a.wall_model, a.write_macro, a.list, a.list_count);
-    else
-        k_collide<S, 1><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
-                                                    (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
-                                                    a.wall_model, a.write_macro, a.list, a.list_count);
+    dispatch_variant(collide_variant(a), [&](auto v) {
+        constexpr int EQ = decltype(v)::value;
+        k_collide<S, EQ><<<grid, 256, 0, a.stream>>>((const S *)a.f_in, (S *)a.f_out, a.ref_in, a.ref_out, a.link,
+                                                     (const T *)a.psi, (T *)a.macro, a.g, (const InstParam<T> *)a.par,
+                                                     a.wall_model, a.write_macro, a.list, a.list_count);
+    });
     record_event(a, 2);
     return cudaGetLastError();
 }
@@ -393,6 +410,8 @@ template <class S>
 static cudaError_t launch_init_t(const InitArgs &a) {
     using T = typename Storage<S>::T;
     const dim3 grid = cell_grid(a.g, a.batch, 256);
+    if constexpr (Storage<S>::shifted)
+        k_init_ref<T><<<grid, 256, 0, a.stream>>>(a.r1, a.r2, a.link, a.ref_out, a.g, (const InstParam<T> *)a.par);
     if (a.eq_order == 0)
         k_init<S, 0><<<grid, 256, 0, a.stream>>>(a.r1, a.r2, a.u, a.link, (S *)a.f_out, a.ref_out, (T *)a.macro,
                                                  (T *)a.usnap, a.g, (const InstParam<T> *)a.par);

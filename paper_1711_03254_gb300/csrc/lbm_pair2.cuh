@@ -80,10 +80,12 @@ __device__ __forceinline__ float2 density2(const float2 (&v)[kQ], float2 R, floa
 
 // ---------------------------------------------------------------- forces (S4)
 // Sums sum_i ws_i c_i psi(x + c_i) for both components, over all 18
-// neighbours.  At a SOLID neighbour the caller passes the cell's own psi pair;
-// forces2 removes those terms again (psi_own * sum over the SOLID directions
-// of ws_i c_i), which leaves the bulk sum over the non-SOLID neighbours of
-// Eq. 10 without a select per direction.
+// neighbours.  At a SOLID neighbour the caller passes the cell's own psi pair
+// (its densities: the same sum of the same pulled values).  For wall models 2
+// and 3 those terms are the wall's neutral part (a SOLID neighbour carries
+// the cell's own rho_beta); for models 0 and 1 forces2 removes them again
+// (psi_own * sum over the SOLID directions of ws_i c_i), which leaves the bulk
+// sum over the non-SOLID neighbours of Eq. 10 without a select per direction.
 struct ForceSums2 {
     float2 x, y, z;
     __device__ __forceinline__ void clear() { x = y = z = bc2(0.f); }
@@ -100,8 +102,9 @@ struct Forces2 {
 };
 
 // S4 from the sums: bulk part G rho_alpha sum ws c psi_beta (beta != alpha),
-// the wall part of Eq. 11 at SOLID neighbours (models 0, 1, 2 as
-// sc_forces_finish) and the body force rho_alpha g.
+// the wall part of Eq. 11 at SOLID neighbours (models 0 to 3 as
+// sc_forces_finish) and the body force rho_alpha g.  psi_own is read for
+// models 0 and 1 only.
 __device__ __forceinline__ Forces2 forces2(ForceSums2 s, float2 psi_own, uint32_t links, float2 rho,
                                            const InstParam<float> &p, int wall_model) {
     const float2 grho = mul2(bc2(p.G), rho);
@@ -118,20 +121,22 @@ __device__ __forceinline__ Forces2 forces2(ForceSums2 s, float2 psi_own, uint32_
                 if (cz(i)) d[2] += float(cz(i)) * ws;
             }
         }
-        // the sums ran over the SOLID neighbours with the cell's own psi
-        s.x = fma2(psi_own, bc2(-d[0]), s.x);
-        s.y = fma2(psi_own, bc2(-d[1]), s.y);
-        s.z = fma2(psi_own, bc2(-d[2]), s.z);
+        if (wall_model < 2) {
+            // the sums ran over the SOLID neighbours with the cell's own psi
+            s.x = fma2(psi_own, bc2(-d[0]), s.x);
+            s.y = fma2(psi_own, bc2(-d[1]), s.y);
+            s.z = fma2(psi_own, bc2(-d[2]), s.z);
+        }
         F.x = mul2(grho, swap2(s.x));
         F.y = mul2(grho, swap2(s.y));
         F.z = mul2(grho, swap2(s.z));
-        // psi_beta(SOLID) = rho^s_beta (models 0, 1) or rho_beta + rho^s_beta (model 2)
-        const float2 rs = make_float2(p.rs[0], p.rs[1]);
-        const float2 wp = swap2(wall_model == 2 ? add2(rho, rs) : rs);
-        float2 fw[3] = {mul2(grho, mul2(wp, bc2(d[0]))), mul2(grho, mul2(wp, bc2(d[1]))),
-                        mul2(grho, mul2(wp, bc2(d[2])))};
-        if (wall_model == 0) {
-            // momentum-conserving variant: the net wall force is shared by density
+        // the wall potential's part G rho_alpha rho^s_beta d, balanced between
+        // the components for models 0 and 3 (the net wall force is shared by
+        // density); models 2 and 3 carry the neutral part in the sums already
+        const float2 rsw = swap2(make_float2(p.rs[0], p.rs[1]));
+        float2 fw[3] = {mul2(grho, mul2(rsw, bc2(d[0]))), mul2(grho, mul2(rsw, bc2(d[1]))),
+                        mul2(grho, mul2(rsw, bc2(d[2])))};
+        if (wall_model == 0 || wall_model == 3) {
             const float rt = rho.x + rho.y;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -173,6 +178,7 @@ __device__ __forceinline__ Relax<float> relax2(const Moments2 &m, const Forces2 
 struct Prep2 {
     float2 rho, Fx, Fy, Fz;
     float2 axx, ayy, azz, axy, axz, ayz, ktr;
+    float2 bxxy, bxyy, bxxz, bxzz, byyz, byzz;  // reg_third only (as CollidePrep)
     float ux, uy, uz, uu, odd_k;
 };
 
@@ -189,7 +195,7 @@ __device__ __forceinline__ Prep2 prep2(const Moments2 &m, const Relax<float> &R,
     const float2 mT0 = bc2(-T0);
     float2 nxx = fma2(m.rd, mT0, m.pxx), nyy = fma2(m.rd, mT0, m.pyy), nzz = fma2(m.rd, mT0, m.pzz);
     float2 nxy = m.pxy, nxz = m.pxz, nyz = m.pyz;
-    if (EQ == 1) {
+    if (eq_full(EQ)) {
         const float2 rx = mul2(m.rho, bc2(ux)), ry = mul2(m.rho, bc2(uy)), rz = mul2(m.rho, bc2(uz));
         nxx = fma2(rx, bc2(-ux), nxx);
         nyy = fma2(ry, bc2(-uy), nyy);
@@ -200,6 +206,15 @@ __device__ __forceinline__ Prep2 prep2(const Moments2 &m, const Relax<float> &R,
     }
     // A = omega Pi^neq + fcoef (u_F F + F u_F)
     const float2 om = bc2(R.omega), fc = bc2(R.fcoef);
+    if (reg_third(EQ)) {
+        // omega (2 u_a Pi_ab + u_b Pi_aa) and so on (third_order_term)
+        c.bxxy = mul2(om, fma2(bc2(2.f * ux), nxy, mul2(bc2(uy), nxx)));
+        c.bxyy = mul2(om, fma2(bc2(2.f * uy), nxy, mul2(bc2(ux), nyy)));
+        c.bxxz = mul2(om, fma2(bc2(2.f * ux), nxz, mul2(bc2(uz), nxx)));
+        c.bxzz = mul2(om, fma2(bc2(2.f * uz), nxz, mul2(bc2(ux), nzz)));
+        c.byyz = mul2(om, fma2(bc2(2.f * uy), nyz, mul2(bc2(uz), nyy)));
+        c.byzz = mul2(om, fma2(bc2(2.f * uz), nyz, mul2(bc2(uy), nzz)));
+    }
     c.axx = fma2(om, nxx, mul2(fc, mul2(bc2(2.f * ux), F.x)));
     c.ayy = fma2(om, nyy, mul2(fc, mul2(bc2(2.f * uy), F.y)));
     c.azz = fma2(om, nzz, mul2(fc, mul2(bc2(2.f * uz), F.z)));
@@ -215,8 +230,19 @@ __device__ __forceinline__ Prep2 prep2(const Moments2 &m, const Relax<float> &R,
 // densities of the cell it streams into), times `scale`.
 template <int EQ> __device__ __forceinline__ float2 rest2(const Prep2 &c, float2 R, float scale) {
     float2 e = sub2(c.rho, R);
-    if (EQ == 1) e = fma2(mul2(bc2(-1.5f), c.rho), bc2(c.uu), e);
+    if (eq_full(EQ)) e = fma2(mul2(bc2(-1.5f), c.rho), bc2(c.uu), e);
     return mul2(bc2(wgt<float>(0) * scale), add2(e, c.ktr));
+}
+
+// third_order_term of lbm_device.cuh on pairs
+__device__ __forceinline__ float2 third_order_pair(int i, const Prep2 &c) {
+    const int c0 = cx(i), c1 = cy(i), c2 = cz(i);
+    if (c0 && c1) return fma2(bc2(9.f * c1), c.bxxy, mul2(bc2(9.f * c0), c.bxyy));
+    if (c0 && c2) return fma2(bc2(9.f * c2), c.bxxz, mul2(bc2(9.f * c0), c.bxzz));
+    if (c1 && c2) return fma2(bc2(9.f * c2), c.byyz, mul2(bc2(9.f * c1), c.byzz));
+    if (c0) return mul2(bc2(-9.f * c0), add2(c.bxyy, c.bxzz));
+    if (c1) return mul2(bc2(-9.f * c1), add2(c.bxxy, c.byzz));
+    return mul2(bc2(-9.f * c2), add2(c.bxxz, c.byyz));
 }
 
 // Stored pairs of f*_i and f*_{i+1} (i odd, c_{i+1} = -c_i), times `scale`,
@@ -254,8 +280,9 @@ __device__ __forceinline__ void pair2(const Prep2 &c, int i, float2 Ri, float2 R
         cAc = c.azz;
     }
     float2 even = fma2(bc2(4.5f), cAc, c.ktr);
-    if (EQ == 1) even = fma2(c.rho, bc2(4.5f * cu * cu - 1.5f * c.uu), even);
-    const float2 odd = fma2(c.rho, bc2(cu * (c.odd_k + 4.5f * cu * cu)), mul2(bc2(1.5f), cF));
+    if (eq_full(EQ)) even = fma2(c.rho, bc2(4.5f * cu * cu - 1.5f * c.uu), even);
+    float2 odd = fma2(c.rho, bc2(cu * (c.odd_k + 4.5f * cu * cu)), mul2(bc2(1.5f), cF));
+    if (reg_third(EQ)) odd = add2(odd, third_order_pair(i, c));
     const float2 w = bc2(wgt<float>(i) * scale);
     vi = mul2(w, add2(add2(sub2(c.rho, Ri), even), odd));
     vo = mul2(w, sub2(add2(sub2(c.rho, Ro), even), odd));

@@ -33,7 +33,8 @@ class LbmError(RuntimeError):
 
 class lbm_config(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("batch", ctypes.c_int),
-                ("precision", ctypes.c_int), ("eq_order", ctypes.c_int), ("wall_model", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("eq_order", ctypes.c_int), ("wall_model", ctypes.c_int),
+                ("reg_order", ctypes.c_int)]
 
 
 class lbm_instance_params(ctypes.Structure):
@@ -128,11 +129,11 @@ def use_torch_allocator():
     lbm_set_allocator(alloc, release)
 
 
-def make_config(nx, ny, nz, batch=1, precision="fp64", eq_order=0, wall_model=2):
+def make_config(nx, ny, nz, batch=1, precision="fp64", eq_order=0, wall_model=2, reg_order=2):
     c = lbm_config()
     c.nx, c.ny, c.nz, c.batch = int(nx), int(ny), int(nz), int(batch)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    c.eq_order, c.wall_model = int(eq_order), int(wall_model)
+    c.eq_order, c.wall_model, c.reg_order = int(eq_order), int(wall_model), int(reg_order)
     return c
 
 
@@ -261,9 +262,9 @@ def lbm_destroy(ctx):
 class Sim:
     """Small convenience wrapper holding one context (same calls, same order)."""
 
-    def __init__(self, nx, ny, nz, params, precision="fp64", eq_order=0, wall_model=2, kernel="auto"):
+    def __init__(self, nx, ny, nz, params, precision="fp64", eq_order=0, wall_model=2, kernel="auto", reg_order=2):
         self.shape = (len(params), nz, ny, nx)
-        self.cfg = make_config(nx, ny, nz, len(params), precision, eq_order, wall_model)
+        self.cfg = make_config(nx, ny, nz, len(params), precision, eq_order, wall_model, reg_order)
         self._params = make_params(params)
         self.ctx = lbm_create(self.cfg, self._params)
         if kernel != "auto":

@@ -55,6 +55,10 @@ def test_create_rejects_bad_arguments(lbm):
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(lbm.make_config(4, 4, 4, eq_order=2), lbm.make_params([good]))
     assert e.value.status == 1
+    for bad in (1, 4, -1):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(lbm.make_config(4, 4, 4, reg_order=bad), lbm.make_params([good]))
+        assert e.value.status == 1 and "reg_order" in lbm.lbm_last_error()
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(lbm.make_config(4, 4, 4), lbm.make_params([dict(tau=(1.0, 1.0), G=float("nan"))]))
     assert e.value.status == 1
@@ -68,7 +72,7 @@ def test_allocator_hook_needs_both(lbm):
 
 def test_structs_match_header(lbm):
     import ctypes
-    assert ctypes.sizeof(lbm.lbm_config) == 7 * 4  # 7 ints
+    assert ctypes.sizeof(lbm.lbm_config) == 8 * 4  # 8 ints
     assert ctypes.sizeof(lbm.lbm_instance_params) == 12 * 8
 
 

@@ -61,7 +61,7 @@ def _same(lbm, shape, params, t, r1, r2, u, steps, precision, **kw):
 
 @pytest.mark.parametrize("precision", ["fp16s", "bf16s", "fp32"])
 @pytest.mark.parametrize("shape", [(13, 7, 9), (33, 21, 17), (40, 37, 5), (6, 16, 3), (9, 17, 2)])
-@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 0), (0, 1)])
+@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 0), (0, 1), (0, 3)])
 def test_bitwise_equal_to_compact_two_pass(lbm, precision, shape, eq_order, wall_model):
     """Random walls, wetting wall potential, body force, extreme tau: every
     stored value, the fields and the reductions after 20 updates."""

@@ -1,0 +1,144 @@
+"""The third-order regularisation (reg_order 3, Eq. 10 with the third-order
+Hermite terms) on the GPU against the oracle, through the C ABI.
+
+Parity: the TWO_PASS and COMPACT strategies (the ones that carry it) in FP64
+cell by cell (1e-12 after the run, as the second-order path), FP32 and 16-bit
+storage within the bounds of the second-order path's wall case.  Property: the
+decay of a shear wave at tau = 0.52 does not depend on the speed of the stream
+carrying it (below 2e-5 between U = 0 and 0.1), which the second-order
+regularisation misses by more than 1e-4."""
+import numpy as np
+import pytest
+
+from paper_1711_03254_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+WALL_BOUNDS = {"fp32": (1e-5, 1e-5), "fp16s": (2e-3, 1e-3), "bf16s": (1e-2, 1e-2)}
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_03254_gb300 import build
+    build.build()
+    from paper_1711_03254_gb300 import lbm as mod
+    return mod
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+def _geometry(shape, frac, seed, inlet_outlet=False, lo=0.3, hi=0.7, umax=0.05):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    t = np.where(rng.random((nz, ny, nx)) < frac, W.SOLID, W.FLUID).astype(np.uint8)
+    if inlet_outlet:
+        t[:, :, 0] = np.where(t[:, :, 0] == W.SOLID, W.SOLID, W.INLET)
+        t[:, :, nx - 1] = np.where(t[:, :, nx - 1] == W.SOLID, W.SOLID, W.OUTLET)
+    r1 = np.where(t == W.SOLID, 0.0, rng.uniform(lo, hi, t.shape))
+    r2 = np.where(t == W.SOLID, 0.0, rng.uniform(lo, hi, t.shape))
+    u = rng.uniform(-umax, umax, t.shape + (3,))
+    u[t == W.SOLID] = 0
+    return t, r1, r2, u
+
+
+def _run(lbm, oracle_mod, shape, p, t, r1, r2, u, steps, precision="fp64", eq_order=0, wall_model=2,
+         kernel="auto"):
+    nx, ny, nz = shape
+    sim = lbm.Sim(nx, ny, nz, p, precision=precision, eq_order=eq_order, wall_model=wall_model, kernel=kernel,
+                  reg_order=3)
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    sim.step(steps)
+    g = sim.get_fields()
+    sim.close()
+    ref = oracle_mod.OracleSim(nx, ny, nz, p, eq_order=eq_order, wall_model=wall_model, reg_order=3)
+    ref.set_geometry(t[None])
+    ref.set_fields(r1[None], r2[None], u[None])
+    ref.step(steps)
+    o = ref.get_fields()
+    ref.close()
+    return tuple(_rel(a, b) for a, b in zip(g, o))
+
+
+@pytest.mark.parametrize("kernel", ["two_pass", "compact"])
+@pytest.mark.parametrize("shape", [(6, 5, 7), (33, 3, 2), (70, 19, 23)])
+@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 1), (1, 0), (0, 3)])
+def test_fp64_odd_grids_with_walls(lbm, oracle_mod, shape, eq_order, wall_model, kernel):
+    """Ragged grids, random SOLID cells, wetting walls, a body force and
+    velocities up to 0.05 (the third-order terms grow with u)."""
+    t, r1, r2, u = _geometry(shape, 0.2, 3 + sum(shape))
+    p = [dict(tau=(0.52, 2.5), G=-1.2, rho_s=0.3, g=(1e-4, -2e-5, 3e-5))]
+    e = _run(lbm, oracle_mod, shape, p, t, r1, r2, u, 20, eq_order=eq_order, wall_model=wall_model, kernel=kernel)
+    assert max(e) < 1e-12, e
+
+
+@pytest.mark.parametrize("kernel", ["two_pass", "compact"])
+def test_fp64_inlet_outlet(lbm, oracle_mod, kernel):
+    shape = (12, 6, 5)
+    t, r1, r2, u = _geometry(shape, 0.1, 9, inlet_outlet=True, lo=0.4, hi=0.6)
+    p = [dict(tau=(0.6, 2.0), G=-1.0, rho_s=-0.2, rho_in=(0.1, 0.9), u_in=(0.03, 0.0, 0.0))]
+    e = _run(lbm, oracle_mod, shape, p, t, r1, r2, u, 30, eq_order=1, kernel=kernel)
+    assert max(e) < 1e-12, e
+
+
+@pytest.mark.parametrize("kernel", ["two_pass", "compact"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16s", "bf16s"])
+def test_reduced_precision_walls(lbm, oracle_mod, precision, kernel):
+    shape = (13, 7, 9)
+    t, r1, r2, u = _geometry(shape, 0.2, 31)
+    p = [dict(tau=(0.7, 1.5), G=-1.8, rho_s=0.3, g=(1e-4, 0, 0))]
+    e = _run(lbm, oracle_mod, shape, p, t, r1, r2, u, 20, precision=precision, eq_order=1, kernel=kernel)
+    rb, ub = WALL_BOUNDS[precision]
+    assert e[0] < rb and e[1] < rb and e[2] < ub, e
+
+
+def test_fp64_droplet_auto(lbm, oracle_mod):
+    """32^3 droplet, 500 updates, AUTO strategy (the compact update)."""
+    t, r1, r2, u = W.droplet(32, 32, 32, 8.0)
+    p = [dict(tau=(0.6, 1.0), G=-2.2)]
+    e = _run(lbm, oracle_mod, (32, 32, 32), p, t, r1, r2, u, 500, eq_order=1)
+    assert max(e) < 1e-11, e
+
+
+def test_single_read_strategies_refuse(lbm):
+    sim = lbm.Sim(16, 16, 16, [dict(tau=(1.0, 1.0), G=-2.0)], precision="fp32", reg_order=3)
+    t = np.zeros((1, 16, 16, 16), np.uint8)
+    sim.set_geometry(t)
+    for k in ("fused", "cluster", "fused_compact"):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_kernel(sim.ctx, lbm.KERNELS[k])
+        assert e.value.status == 1 and "reg_order 3" in str(e.value)
+    for k in ("two_pass", "compact", "auto"):
+        lbm.lbm_set_kernel(sim.ctx, lbm.KERNELS[k])
+    sim.close()
+
+
+def _wave_u_dependence(lbm, reg_order, precision, tau=0.52):
+    nx, A = 32, 1e-3
+    x = np.arange(nx) + 0.5
+    k = 2 * np.pi / nx
+    amps = []
+    for U in (0.0, 0.05, 0.1):
+        u = np.zeros((1, 1, 1, nx, 3))
+        u[..., 0] = U
+        u[..., 1] = A * np.sin(k * x)
+        sim = lbm.Sim(nx, 1, 1, [dict(tau=(tau, tau), G=0.0)], precision=precision, eq_order=1, reg_order=reg_order)
+        sim.set_geometry(np.zeros((1, 1, 1, nx), np.uint8))
+        sim.set_fields(np.full((1, 1, 1, nx), 0.5), np.full((1, 1, 1, nx), 0.5), u)
+        sim.step(200)
+        _, _, v = sim.get_fields()
+        sim.close()
+        uy = v[0, 0, 0, :, 1]
+        amps.append(np.hypot(2 * np.sum(uy * np.sin(k * x)) / nx, 2 * np.sum(uy * np.cos(k * x)) / nx) / A)
+    return max(abs(a - amps[0]) / amps[0] for a in amps)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_shear_wave_galilean(lbm, precision):
+    assert _wave_u_dependence(lbm, 2, precision) > 1e-4
+    assert _wave_u_dependence(lbm, 3, precision) < 2e-5

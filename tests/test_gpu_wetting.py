@@ -56,14 +56,28 @@ def test_inverse_reproduces_expected_angles(lbm, calibration):
 
 def test_thin_film_original_against_modified(lbm):
     """At rho^s = 0.3 the component-2 film along the walls of the component-1
-    region is at least five times thinner with the modified wall model (2)
-    than with the original one (1), for equal and for very different
-    viscosities (Sec. 3.3, thin film)."""
+    region is at least five times thinner with the modified wall models (2,
+    and 3 with its balanced wall forces) than with the original one (1), for
+    equal and for very different viscosities (Sec. 3.3, thin film)."""
     cases = [(1 / 6, 1 / 6, 0.3), (0.33, 0.0017, 0.3)]
     f1 = WT.run_slugs(cases, steps=20000, tol=1e-6, wall_model=1)
-    f2 = WT.run_slugs(cases, steps=20000, tol=1e-6, wall_model=2)
-    for a, b in zip(f1, f2):
-        assert b["film"] * 5.0 < a["film"], (a, b)
+    for wm in (2, 3):
+        fm = WT.run_slugs(cases, steps=20000, tol=1e-6, wall_model=wm)
+        for a, b in zip(f1, fm):
+            assert b["film"] * 5.0 < a["film"], (wm, a, b)
+
+
+def test_balanced_walls_narrow_the_angle_range(lbm):
+    """Wall model 3 acts only where both components meet the wall, so its
+    angles stay near 90 degrees: within 65 ... 115 degrees for |rho^s| <= 0.6
+    at equal viscosities (measured 73.2 ... 106.8), where model 2 spans
+    23.6 ... 156.4; and theta(rho^s) is still monotone."""
+    grid = [-0.6, -0.3, 0.0, 0.3, 0.6]
+    out = WT.run_slugs([(1 / 6, 1 / 6, rs) for rs in grid], steps=30000, tol=1e-6, wall_model=3)
+    th = [r["theta"] for r in out]
+    assert all(65.0 < v < 115.0 for v in th), th
+    assert all(a > b for a, b in zip(th, th[1:])), th
+    assert abs(th[2] - 90.0) < 0.5, th
 
 
 def test_slug_matches_oracle(lbm, oracle_mod):

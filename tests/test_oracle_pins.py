@@ -343,7 +343,7 @@ def _run(oracle_mod, t, r1, r2, u, p, eq_order, wall_model, steps=20):
     return a[0], b[0], v[0]
 
 
-@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 1), (0, 0)])
+@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 1), (0, 0), (0, 3)])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_mirror_symmetry(oracle_mod, axis, eq_order, wall_model):
     """Reflecting the geometry, the fields and the body force through a plane
@@ -370,7 +370,7 @@ def test_mirror_symmetry(oracle_mod, axis, eq_order, wall_model):
     assert np.abs(flip_u(u2) - u1).max() < 1e-13
 
 
-@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 0)])
+@pytest.mark.parametrize("eq_order,wall_model", [(0, 2), (1, 0), (1, 3)])
 @pytest.mark.parametrize("axes", [(0, 1), (1, 2), (0, 2)])
 def test_axis_exchange_symmetry(oracle_mod, axes, eq_order, wall_model):
     """Exchanging two axes of the geometry, the fields, the velocities and the

@@ -1,13 +1,17 @@
-"""Pins of the oracle's wall model 2 (Eq. 11 with rho'_beta of a solid
-neighbour = the cell's own rho_beta + rho^s_beta).
+"""Pins of the oracle's wall models 2 (Eq. 11 with rho'_beta of a solid
+neighbour = the cell's own rho_beta + rho^s_beta) and 3 (the cell's own
+rho_beta, and the wall potential's part balanced between the components).
 
 Closed forms: the interaction stencil sums to zero over all 18 neighbours
 (sum_i ws_i c_i = 0), so next to any wall
-  * a uniform fluid feels no interaction force when rho^s = 0, and
-  * with rho^s != 0 the force is exactly G rho_alpha rho^s_beta D, where
-    D = sum over SOLID neighbours of ws_i c_i (ws_i = 2 w_i).
+  * a uniform fluid feels no interaction force when rho^s = 0 (both models),
+  * with rho^s != 0 the force is exactly G rho_alpha rho^s_beta D (model 2),
+    where D = sum over SOLID neighbours of ws_i c_i (ws_i = 2 w_i), and
+  * G rho_1 rho_2 (rho^s_2 - rho^s_1) D / rho on component 1 and its negative
+    on component 2 (model 3): the wall's forces on the components cancel.
 """
 import numpy as np
+import pytest
 
 from paper_1711_03254_gb300 import workloads as W
 
@@ -20,11 +24,11 @@ def _geometry(n=8):
     return t
 
 
-def _one_step_force(oracle_mod, t, rho1, rho2, rho_s, G=-2.0):
+def _one_step_force(oracle_mod, t, rho1, rho2, rho_s, G=-2.0, wall_model=2):
     n = t.shape[0]
     r1 = np.where(t == W.SOLID, 0.0, rho1)
     r2 = np.where(t == W.SOLID, 0.0, rho2)
-    sim = oracle_mod.OracleSim(n, n, n, [dict(tau=(1.0, 1.0), G=G, rho_s=rho_s)], wall_model=2)
+    sim = oracle_mod.OracleSim(n, n, n, [dict(tau=(1.0, 1.0), G=G, rho_s=rho_s)], wall_model=wall_model)
     sim.set_geometry(t[None])
     sim.set_fields(r1[None], r2[None], np.zeros((1, n, n, n, 3)))
     sim.step(1)
@@ -32,11 +36,12 @@ def _one_step_force(oracle_mod, t, rho1, rho2, rho_s, G=-2.0):
     return sim.get_force()[0], a[0], b[0]
 
 
-def test_neutral_wall_exerts_no_force(oracle_mod):
+@pytest.mark.parametrize("wall_model", [2, 3])
+def test_neutral_wall_exerts_no_force(oracle_mod, wall_model):
     """Uniform mixture at rest next to walls, rho^s = 0: every cell's
     interaction force vanishes (the streamed fields stay uniform)."""
     t = _geometry()
-    F, a, b = _one_step_force(oracle_mod, t, 0.4, 0.6, 0.0)
+    F, a, b = _one_step_force(oracle_mod, t, 0.4, 0.6, 0.0, wall_model=wall_model)
     assert np.allclose(a[t != W.SOLID], 0.4, atol=1e-15)
     assert np.abs(F).max() < 1e-15
 
@@ -63,8 +68,51 @@ def test_wall_potential_force_closed_form(oracle_mod):
                 assert np.allclose(F[1, z, y, x], 0.0, atol=1e-15)
 
 
-def test_wall_model2_mass_and_symmetry(oracle_mod):
-    """Walls of model 2 keep each component's mass, and exchanging the
+def _solid_stencil_sum(c, w, t, z, y, x):
+    n = t.shape[0]
+    D = np.zeros(3)
+    for i in range(1, 19):
+        if t[(z + c[i, 2]) % n, (y + c[i, 1]) % n, (x + c[i, 0]) % n] == W.SOLID:
+            D += 2 * w[i] * c[i]
+    return D
+
+
+def _check_model3_closed_form(oracle_mod, rs):
+    c, w, _ = oracle_mod.lattice()
+    t = _geometry()
+    n = t.shape[0]
+    G, r1, r2 = -2.0, 0.4, 0.6
+    F, a, b = _one_step_force(oracle_mod, t, r1, r2, rs, G, wall_model=3)
+    rs1, rs2 = max(-rs, 0.0), max(rs, 0.0)
+    worst = 0.0
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                if t[z, y, x] == W.SOLID:
+                    continue
+                f1 = G * r1 * r2 * (rs2 - rs1) * _solid_stencil_sum(c, w, t, z, y, x) / (r1 + r2)
+                worst = max(worst, np.abs(F[0, z, y, x] - f1).max(), np.abs(F[1, z, y, x] + f1).max())
+    return worst
+
+
+@pytest.mark.parametrize("rs", [0.3, -0.2])
+def test_wall_model3_balanced_closed_form(oracle_mod, rs):
+    """Uniform mixture next to walls of model 3: component 1 feels
+    G rho_1 rho_2 (rho^s_2 - rho^s_1) D / rho and component 2 its negative, in
+    every fluid cell (the wall moves no momentum into the mixture)."""
+    assert _check_model3_closed_form(oracle_mod, rs) < 1e-15
+
+
+def test_wall_model3_pin_catches_missing_balance(oracle_mod):
+    """The closed-form pin fails with the balancing projection dropped from
+    model 3, planted in the oracle."""
+    with oracle_mod.planted("Fw[0][a] += Fs[0][a] - rho_a[0] / rho * net;", "Fw[0][a] += Fs[0][a];"):
+        assert _check_model3_closed_form(oracle_mod, 0.3) > 1e-3
+
+
+@pytest.mark.parametrize("wall_model", [2, 3])
+def test_wall_model2_mass_and_symmetry(oracle_mod, wall_model):
+    """Walls of models 2 and 3 keep each component's mass, and exchanging the
     components together with rho^s -> -rho^s mirrors the evolution."""
     n = 10
     t, r1, r2, u = W.layered_channel(n, n, n, layout="12")
@@ -78,7 +126,7 @@ def test_wall_model2_mass_and_symmetry(oracle_mod):
         if swap:
             p = dict(tau=(1.9, 0.7), G=-2.0, rho_s=-0.25, g=(2e-5, 0, 0))
             a, b = r2, r1
-        sim = oracle_mod.OracleSim(n, n, n, [p], wall_model=2)
+        sim = oracle_mod.OracleSim(n, n, n, [p], wall_model=wall_model)
         sim.set_geometry(t[None])
         sim.set_fields(a[None], b[None], u[None])
         m0 = sim.reduce()[0]
