@@ -79,7 +79,7 @@ def alg_bytes_per_cell(part: str, precision: str) -> int:
 # (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its fluid cells),
 # keyed by kernel/precision/workload, with the hash of the source files the
 # kernel is built from at the time of the capture; any change of them voids it.
-COMPACT_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_pair2.cuh", "lbm_compact.cuh", "lbm_compact.cu"]
+COMPACT_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_pair2.cuh", "lbm_compact.cuh", "lbm_compact_update.cuh"]
 DENSE_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_kernels.cu"]
 NCU_TRAFFIC = {
     # 128^3 packed spheres (837,994 non-solid cells), dense layout, ncu --set full:

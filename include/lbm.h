@@ -118,6 +118,10 @@ typedef struct {
     double g[3];     /* body acceleration applied to both components */
     double rho_in[2];/* INLET densities */
     double u_in[3];  /* INLET velocity */
+    double slip;     /* surface scattering at SOLID walls (Sec. 2): the fraction of the particles a
+                        wall reflects specularly about its voxel face, in [0, 1]; the rest bounce
+                        back.  0 (a zeroed struct) is the no-slip wall.  Non-zero slip runs in the
+                        TWO_PASS and COMPACT strategies (and AUTO) only */
 } lbm_instance_params;
 
 /* Create a context for cfg->batch instances with per-instance parameters

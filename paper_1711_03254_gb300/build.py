@@ -15,8 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
-SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_compact.cu", "lbm_fusedc.cu", "lbm_reduce.cu", "lbm_fused.cu", "lbm_cluster.cu",
-           "lbm_noalloc.cu", "lbm_setup.cu", "ws_conv.cu", "ws_ops.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_compact.cu", "lbm_update_f64.cu", "lbm_update_f32.cu",
+           "lbm_update_f16.cu", "lbm_update_bf16.cu", "lbm_fusedc.cu", "lbm_reduce.cu", "lbm_fused.cu",
+           "lbm_cluster.cu", "lbm_noalloc.cu", "lbm_setup.cu", "ws_conv.cu", "ws_ops.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -106,6 +106,14 @@ struct lbm_ctx {
     }
 
     bool fp64() const { return cfg.precision == LBM_FP64; }
+    bool slip_on() const {
+        for (const lbm_instance_params &p : par)
+            if (p.slip != 0.0) return true;
+        return false;
+    }
+    // the third-order regularisation and wall slip are built into the two-pass
+    // strategies (TWO_PASS, COMPACT) only
+    bool single_read_ok() const { return cfg.reg_order != 3 && !slip_on(); }
     size_t tbytes() const { return fp64() ? 8 : 4; }
     size_t cells() const { return (size_t)cfg.batch * (size_t)g.n; }
     size_t f_bytes() const { return cells() * 2 * 19 * storage_bytes(cfg.precision); }
@@ -169,6 +177,7 @@ template <class T> void fill_params(const lbm_ctx *ctx, std::vector<InstParam<T>
         }
         q.rho_in[0] = (T)p.rho_in[0];
         q.rho_in[1] = (T)p.rho_in[1];
+        q.slip = (T)p.slip;
     }
 }
 
@@ -198,6 +207,7 @@ const char *check_params(const lbm_instance_params *per_instance, int batch) {
                                p.u_in[2], p.tau[0], p.tau[1]};
         for (double v : vals)
             if (!std::isfinite(v)) return "non-finite parameter";
+        if (!(p.slip >= 0.0 && p.slip <= 1.0)) return "slip must lie in [0, 1]";
     }
     return nullptr;
 }
@@ -218,6 +228,12 @@ lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
 }
 
 bool uses_compact_layout(lbm_kernel k) { return k == LBM_KERNEL_COMPACT || k == LBM_KERNEL_FUSED_COMPACT; }
+
+// the strategies whose kernels read f once per update (no slip, no
+// third-order regularisation)
+bool single_read(lbm_kernel k) {
+    return k == LBM_KERNEL_FUSED || k == LBM_KERNEL_CLUSTER || k == LBM_KERNEL_FUSED_COMPACT;
+}
 
 // Fused-kernel tiling when none was set: 32x8 columns (32x4 in FP64, whose
 // ring buffers are twice as large), z chunks sized for about eight CTAs per SM.
@@ -345,6 +361,7 @@ StepArgs step_args(lbm_ctx *ctx, int write_macro) {
     a.precision = ctx->cfg.precision;
     a.eq_order = ctx->cfg.eq_order;
     a.reg_order = ctx->cfg.reg_order;
+    a.slip = ctx->slip_on() ? 1 : 0;
     a.wall_model = ctx->cfg.wall_model;
     a.write_macro = write_macro;
     a.batch = ctx->cfg.batch;
@@ -498,6 +515,10 @@ lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_instance_params *per_instance)
     if (ctx->half_step) return ctx->fail(LBM_ERR_STATE, "lbm_set_params: finish the split update first");
     if (const char *bad = check_params(per_instance, ctx->cfg.batch))
         return ctx->fail(LBM_ERR_ARG, std::string("lbm_set_params: ") + bad);
+    if (single_read(ctx->kernel))
+        for (int b = 0; b < ctx->cfg.batch; ++b)
+            if (per_instance[b].slip != 0.0)
+                return ctx->fail(LBM_ERR_ARG, "lbm_set_params: wall slip needs the TWO_PASS or COMPACT strategy");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
     ctx->par.assign(per_instance, per_instance + ctx->cfg.batch);
     const lbm_status s = upload_params(ctx);
@@ -527,9 +548,9 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: COMPACT needs nx <= 2048, ny <= 2048, nz <= 1024");
     if (kernel == LBM_KERNEL_FUSED_COMPACT && (!ctx->compact_ok || ctx->fp64()))
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: FUSED_COMPACT needs the compact layout and FP32 arithmetic");
-    if (ctx->cfg.reg_order == 3 &&
-        (kernel == LBM_KERNEL_FUSED || kernel == LBM_KERNEL_CLUSTER || kernel == LBM_KERNEL_FUSED_COMPACT))
-        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: reg_order 3 runs in the TWO_PASS and COMPACT strategies");
+    if (!ctx->single_read_ok() && single_read(kernel))
+        return ctx->fail(LBM_ERR_ARG,
+                         "lbm_set_kernel: reg_order 3 and wall slip run in the TWO_PASS and COMPACT strategies");
     ctx->kernel = kernel;
     return LBM_OK;
 }
@@ -1071,8 +1092,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     std::vector<Cand> cands;
     cands.push_back({LBM_KERNEL_TWO_PASS, -1, -1});
     if (ctx->compact_ok) cands.push_back({LBM_KERNEL_COMPACT, -1, -1});
-    // the third-order regularisation is built into the two-pass strategies only
-    const bool single_read_ok = ctx->cfg.reg_order != 3;
+    const bool single_read_ok = ctx->single_read_ok();
     if (ctx->fplan.ok && single_read_ok) cands.push_back({LBM_KERNEL_FUSED_COMPACT, -1, -1});
     if (ctx->g.n <= kClusterMaxCells && single_read_ok) cands.push_back({LBM_KERNEL_CLUSTER, -1, -1});
     for (int t = 0; single_read_ok && t < fused_tile_count(); ++t) {

@@ -18,182 +18,15 @@
 //                      the dense kernels, so both layouts give identical bits).
 //   k_collide_c2       S1-S7 for the FP32-arithmetic storages, both components
 //                      as packed FP32 pairs (lbm_pair2.cuh).
-#include "lbm_compact.cuh"
+#include "lbm_compact_update.cuh"
 
 namespace lbm {
 
-// Occupancy, measured on GB300 (256^3 packed spheres).  The update runs
-// 128-thread blocks, 7 (16-bit storage), 5 (FP32) or 4 (FP64) per SM within the
-// registers; one more block per SM was no faster (16-bit: 0.316 against 0.314
-// ms per update).  The psi pass runs 256-thread blocks, 6 per SM (40
-// registers): 16-bit storage 0.139 ms against 0.159 at 4 and 0.192 at 3 per
-// SM, and 0.163 for a persistent variant that prefetched each thread's next
-// cell with cp.async; FP32 0.186 against 0.218 at 3 per SM.
-constexpr int kPsiThreads = 256, kPsiBlocks = 6, kCollideThreads = 128;
-template <class S> constexpr int collide_min_blocks() { return sizeof(S) == 2 ? 7 : (sizeof(S) == 4 ? 5 : 4); }
-
-template <class S>
-__global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {
-    using T = typename Storage<S>::T;
-    using V = typename Vec2<T>::V;
-    const int b = blockIdx.y;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
-    const CompactCell c = compact_cell(a, b, k);
-    const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
-    V *psi = (V *)a.psi + (size_t)b * a.kmax;
-    T p0, p1;
-    if (cell_type(c.word) == kInlet) {
-        p0 = p.rho_in[0];
-        p1 = p.rho_in[1];
-    } else {
-        const typename Pair<S>::P *f = (const typename Pair<S>::P *)a.f_in + (size_t)b * kQ * a.kmax;
-        auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-            if constexpr (packed_pairs<S>()) {
-                float2 v[kQ];
-                pull_pairs2<S>(f, a.kmax, sk, nb, sw, v);
-                const float2 d = density2<Pair2<S>::kScaled>(v, ref_pair2(a, b, sk), Pair2<S>::kUnscale);
-                p0 = d.x;
-                p1 = d.y;
-            } else {
-                T v0[kQ], v1[kQ], r0, r1;
-                pull_pairs<S>(f, a.kmax, sk, nb, sw, v0, v1);
-                ref_pair<S>(a, b, sk, r0, r1);
-                p0 = density_of<T, Storage<S>::shifted>(v0, r0);
-                p1 = density_of<T, Storage<S>::shifted>(v1, r1);
-            }
-        };
-        CNbr own;
-        own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
-        int xu;
-        uint32_t ku, wu;
-        if (outlet_source(a, b, c, own, xu, ku, wu)) {
-            CNbr up;
-            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
-            pull(up, ku, wu);
-        } else {
-            pull(own, k, c.word);
-        }
-    }
-    V out;
-    out.x = p0;
-    out.y = p1;
-    psi[k] = out;
-}
-
-template <class S, int EQ>
-__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
-    using T = typename Storage<S>::T;
-    using V = typename Vec2<T>::V;
-    using P = typename Pair<S>::P;
-    const int b = blockIdx.y;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
-    const CompactCell c = compact_cell(a, b, k);
-    const uint32_t word = c.word;
-    const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
-    const uint32_t n = a.kmax;
-    P *fo = (P *)a.f_out + (size_t)b * kQ * n;
-    const V *psi = (const V *)a.psi + (size_t)b * n;
-    __half2 *rout = (__half2 *)a.ref_out + (size_t)b * n;
-    const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
-    T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
-    CNbr own;
-    own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
-    // psi of both components at the 18 neighbours (own cell where SOLID: masked
-    // by the force and never used as a reference there)
-    T q0[kQ], q1[kQ];
-    auto load_psi = [&]() {
-#pragma unroll
-        for (int i = 1; i < kQ; ++i) {
-            const uint32_t j = ((word >> i) & 1u) ? k : own.dst(i);
-            const V q = __ldg(psi + j);
-            q0[i] = q.x;
-            q1[i] = q.y;
-        }
-    };
-    if (cell_type(word) == kInlet) {
-        load_psi();
-        const T uu = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            const bool self_ref = i == 0 || ((word >> i) & 1u);
-            const T s0 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[0] : q0[i]) : T(0);
-            const T s1 = Storage<S>::shifted ? wgt<T>(i) * ref_value(self_ref ? p.rho_in[1] : q1[i]) : T(0);
-            Pair<S>::store(fo + (size_t)i * n + k, feq_dir<T, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
-                           feq_dir<T, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu), s0, s1);
-        }
-        if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)p.rho_in[0], (float)p.rho_in[1]);
-        if (a.write_macro) {
-            mac[cell] = p.rho_in[0];
-            mac[a.g.n + cell] = p.rho_in[1];
-            mac[2 * a.g.n + cell] = p.u_in[0];
-            mac[3 * a.g.n + cell] = p.u_in[1];
-            mac[4 * a.g.n + cell] = p.u_in[2];
-        }
-        return;
-    }
-    const P *f = (const P *)a.f_in + (size_t)b * kQ * n;
-    Moments<T> m0, m1;
-    auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-        T v0[kQ], v1[kQ], r0, r1;
-        pull_pairs<S>(f, n, sk, nb, sw, v0, v1);
-        ref_pair<S>(a, b, sk, r0, r1);
-        m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
-        m1 = moments_of<T, Storage<S>::shifted>(v1, r1);
-    };
-    {
-        int xu;
-        uint32_t ku, wu;
-        if (outlet_source(a, b, c, own, xu, ku, wu)) {
-            CNbr up;
-            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
-            pull(up, ku, wu);
-        } else {
-            pull(own, k, word);
-        }
-    }
-    // psi of both components at the 18 neighbours, streamed into the force sums;
-    // what the stores need of it is kept as FP16 reference pairs (the reference
-    // density of the cell each value streams into; own cell where SOLID)
-    ForceSums<T> bs;
-    bs.clear();
-    __half2 Rp[kQ];
-    Rp[0] = __floats2half2_rn((float)m0.rho, (float)m1.rho);
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-        const bool solid = (word >> i) & 1u;
-        const V q = __ldg(psi + (solid ? k : own.dst(i)));
-        bs.add(i, solid, q.x, q.y);
-        if constexpr (Storage<S>::shifted)
-            Rp[i] = __floats2half2_rn((float)(solid ? m0.rho : q.x), (float)(solid ? m1.rho : q.y));
-    }
-    const Forces<T> F = sc_forces_finish<T>(bs, word, m0.rho, m1.rho, p, a.wall_model);
-    const Relax<T> R = relax<T>(m0, m1, F, p);
-    const CollidePrep<T> c0 =
-        collide_prep<T, EQ>(m0, R.ux, R.uy, R.uz, F.F[0][0], F.F[0][1], F.F[0][2], R.omega, R.fcoef);
-    const CollidePrep<T> c1 =
-        collide_prep<T, EQ>(m1, R.ux, R.uy, R.uz, F.F[1][0], F.F[1][1], F.F[1][2], R.omega, R.fcoef);
-    auto ref0 = [&](int i) -> T { return Storage<S>::shifted ? (T)__low2float(Rp[i]) : T(0); };
-    auto ref1 = [&](int i) -> T { return Storage<S>::shifted ? (T)__high2float(Rp[i]) : T(0); };
-    Pair<S>::store_d(fo + k, collide_rest<T, EQ>(c0, ref0(0)), collide_rest<T, EQ>(c1, ref1(0)));
-#pragma unroll
-    for (int i = 1; i < kQ; i += 2) {
-        T a_i, a_o, b_i, b_o;
-        collide_pair<T, EQ>(c0, i, ref0(i), ref0(i + 1), a_i, a_o);
-        collide_pair<T, EQ>(c1, i, ref1(i), ref1(i + 1), b_i, b_o);
-        Pair<S>::store_d(fo + (size_t)i * n + k, a_i, b_i);
-        Pair<S>::store_d(fo + (size_t)(i + 1) * n + k, a_o, b_o);
-    }
-    if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)m0.rho, (float)m1.rho);
-    if (a.write_macro) {
-        mac[cell] = m0.rho;
-        mac[a.g.n + cell] = m1.rho;
-        mac[2 * a.g.n + cell] = R.ux;
-        mac[3 * a.g.n + cell] = R.uy;
-        mac[4 * a.g.n + cell] = R.uz;
-    }
-}
+// instantiated in lbm_update_*.cu
+extern template cudaError_t launch_compact_t<double>(const StepArgs &, int);
+extern template cudaError_t launch_compact_t<float>(const StepArgs &, int);
+extern template cudaError_t launch_compact_t<__half>(const StepArgs &, int);
+extern template cudaError_t launch_compact_t<__nv_bfloat16>(const StepArgs &, int);
 
 __global__ void k_compact_links(const uint32_t *__restrict__ list, const int *__restrict__ count,
                                 const uint32_t *__restrict__ link, uint32_t *__restrict__ clink, long long n,
@@ -232,144 +65,6 @@ __global__ void k_layout(bool to_compact, const S *__restrict__ fin, S *__restri
     }
 }
 
-// k_collide_c2: the update of k_collide_c with both components as packed FP32
-// pairs (lbm_pair2.cuh), for the FP32 and 16-bit storages.  Same steps and
-// memory accesses; the neighbour psi pairs enter the force sums unselected
-// (the cell's own pair at SOLID neighbours, removed in forces2), and the
-// storage scale of FP16 is folded into the moment sums and the weights.
-template <class S, int EQ>
-__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c2(StepArgs a) {
-    using P = typename Pair2<S>::P;
-    const int b = blockIdx.y;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
-    const CompactCell c = compact_cell(a, b, k);
-    const uint32_t word = c.word;
-    const InstParam<float> &p = ((const InstParam<float> *)a.par)[b];
-    const uint32_t n = a.kmax;
-    const float2 *psi = (const float2 *)a.psi + (size_t)b * n;
-    __half2 *rout = (__half2 *)a.ref_out + (size_t)b * n;
-    const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
-    float *mac = (float *)a.macro + (long long)b * 5 * a.g.n;
-    CNbr own;
-    own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
-    if (cell_type(word) == kInlet) {
-        // equilibrium at (rho_in, u_in) as deviations from the reference pairs
-        typename Pair<S>::P *fo = (typename Pair<S>::P *)a.f_out + (size_t)b * kQ * n;
-        const float uu = p.u_in[0] * p.u_in[0] + p.u_in[1] * p.u_in[1] + p.u_in[2] * p.u_in[2];
-#pragma unroll
-        for (int i = 0; i < kQ; ++i) {
-            const bool self_ref = i == 0 || ((word >> i) & 1u);
-            const float2 q = self_ref ? make_float2(p.rho_in[0], p.rho_in[1]) : __ldg(psi + own.dst(i));
-            Pair<S>::store(fo + (size_t)i * n + k, feq_dir<float, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
-                           feq_dir<float, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu),
-                           wgt<float>(i) * ref_value(q.x), wgt<float>(i) * ref_value(q.y));
-        }
-        rout[k] = __floats2half2_rn(p.rho_in[0], p.rho_in[1]);
-        if (a.write_macro) {
-            mac[cell] = p.rho_in[0];
-            mac[a.g.n + cell] = p.rho_in[1];
-            mac[2 * a.g.n + cell] = p.u_in[0];
-            mac[3 * a.g.n + cell] = p.u_in[1];
-            mac[4 * a.g.n + cell] = p.u_in[2];
-        }
-        return;
-    }
-    // the psi pairs of the 18 neighbours (the cell's own at SOLID ones) start
-    // on their way into this thread's shared-memory slots now, so that their
-    // latency overlaps the pull of f; no other thread reads the slots
-    __shared__ float2 qs[kQ - 1][kCollideThreads];
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-        const bool solid = (word >> i) & 1u;
-        cp_async_ca<8>(&qs[i - 1][tid], psi + (solid ? k : own.dst(i)));
-    }
-    cp_async_commit_group();
-    const P *f = (const P *)a.f_in + (size_t)b * kQ * n;
-    P *fo = (P *)a.f_out + (size_t)b * kQ * n;
-    Moments2 m;
-    auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
-        float2 v[kQ];
-        pull_pairs2<S>(f, n, sk, nb, sw, v);
-        m = moments2<Pair2<S>::kScaled>(v, ref_pair2(a, b, sk), Pair2<S>::kUnscale);
-    };
-    {
-        int xu;
-        uint32_t ku, wu;
-        if (outlet_source(a, b, c, own, xu, ku, wu)) {
-            CNbr up;
-            up.init(xu, c.y, c.z, ku, instance_tab(a, b), a.words, a.g);
-            pull(up, ku, wu);
-        } else {
-            pull(own, k, word);
-        }
-    }
-    // psi pairs of the 18 neighbours into the force sums; the stores keep the
-    // FP16 reference pair of each direction (the density of the cell the
-    // value streams into; the cell's own at SOLID neighbours)
-    const __half2 rho_h = __float22half2_rn(m.rho);
-    ForceSums2 bs;
-    bs.clear();
-    __half2 Rp[kQ];
-    Rp[0] = rho_h;
-    cp_async_wait_all();
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-        const bool solid = (word >> i) & 1u;
-        const float2 q = qs[i - 1][tid];
-        bs.add(i, q);
-        Rp[i] = solid ? rho_h : __float22half2_rn(q);
-    }
-    const float2 psi_own = ((word & 0x7FFFEu) && a.wall_model < 2) ? __ldg(psi + k) : bc2(0.f);
-    const Forces2 F = forces2(bs, psi_own, word, m.rho, p, a.wall_model);
-    const Relax<float> R = relax2(m, F, p);
-    const Prep2 cp = prep2<EQ>(m, R, F);
-    constexpr float sc = Pair2<S>::kScale;
-    Pair2<S>::store(fo + k, rest2<EQ>(cp, __half22float2(Rp[0]), sc));
-#pragma unroll
-    for (int i = 1; i < kQ; i += 2) {
-        float2 vi, vo;
-        pair2<EQ>(cp, i, __half22float2(Rp[i]), __half22float2(Rp[i + 1]), sc, vi, vo);
-        Pair2<S>::store(fo + (size_t)i * n + k, vi);
-        Pair2<S>::store(fo + (size_t)(i + 1) * n + k, vo);
-    }
-    rout[k] = rho_h;
-    if (a.write_macro) {
-        mac[cell] = m.rho.x;
-        mac[a.g.n + cell] = m.rho.y;
-        mac[2 * a.g.n + cell] = R.ux;
-        mac[3 * a.g.n + cell] = R.uy;
-        mac[4 * a.g.n + cell] = R.uz;
-    }
-}
-
-// parts: bit 0 the density pass, bit 1 the collision pass (both: one update;
-// one at a time: the split update of a domain decomposition, with the ghost
-// planes exchanged in between)
-template <class S>
-static cudaError_t launch_compact_t(const StepArgs &a, int parts) {
-    const long long m = a.list_max > 0 ? a.list_max : 1;
-    const dim3 gp((unsigned)((m + kPsiThreads - 1) / kPsiThreads), (unsigned)a.batch, 1);
-    const dim3 gc((unsigned)((m + kCollideThreads - 1) / kCollideThreads), (unsigned)a.batch, 1);
-    record_event(a, 0);
-    if (parts & 1) k_psi_c<S><<<gp, kPsiThreads, 0, a.stream>>>(a);
-    record_event(a, 1);
-    // (a persistent variant that prefetches the next cell with cp.async, as the
-    // psi pass does, measured 10 % slower here: the update is issue-bound, and
-    // the prefetch buffers cost occupancy and registers)
-    if (parts & 2) {
-        dispatch_variant(collide_variant(a), [&](auto v) {
-            constexpr int EQ = decltype(v)::value;
-            if constexpr (packed_pairs<S>())
-                k_collide_c2<S, EQ><<<gc, kCollideThreads, 0, a.stream>>>(a);
-            else
-                k_collide_c<S, EQ><<<gc, kCollideThreads, 0, a.stream>>>(a);
-        });
-    }
-    record_event(a, 2);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_compact(const StepArgs &a, int parts) {
     switch (a.precision) {

@@ -197,6 +197,49 @@ __device__ __forceinline__ float2 ref_pair2(const StepArgs &a, int b, uint32_t s
     return __half22float2(__ldg((const __half2 *)a.ref_in + (size_t)b * a.kmax + sk));
 }
 
+// Wall slip of the pulled pairs v of cell sk (the compact form of
+// slip_values): each edge direction whose source is SOLID gets (1 - s) times
+// the bounced-back pair plus s times the specular reflection, in storage
+// units.  The reflected pair is stored against its source cell's reference
+// pair; it is moved to this cell's with both entries of the instance's
+// reference table `ref` (FP32 and 16-bit storages all hold deviations).
+template <class S>
+__device__ __forceinline__ void slip_pairs2(const typename Pair2<S>::P *__restrict__ f, uint32_t n, uint32_t sk,
+                                            const CNbr &nb, uint32_t sw, float s, const __half2 *__restrict__ ref,
+                                            float2 (&v)[kQ]) {
+    if (s == 0.f) return;
+    const float2 rown = __half22float2(__ldg(ref + sk));
+    const float2 sv = bc2(s), kv = bc2(1.f - s);
+#pragma unroll
+    for (int i = 7; i < kQ; ++i) {
+        int via, j;
+        if (!((sw >> opp(i)) & 1u) || !specular_source(i, sw, via, j)) continue;
+        const uint32_t src = nb.dst(via);
+        float2 r = Pair2<S>::load(f + ((size_t)j * n + src));
+        r = fma2(sub2(__half22float2(__ldg(ref + src)), rown), bc2(wgt<float>(i) * Pair2<S>::kScale), r);
+        v[i] = fma2(sv, r, mul2(kv, v[i]));
+    }
+}
+
+// slip_pairs2 for the FP64 pairs (no reference densities).
+template <class S>
+__device__ __forceinline__ void slip_pairs(const typename Pair<S>::P *__restrict__ f, uint32_t n, const CNbr &nb,
+                                           uint32_t sw, typename Storage<S>::T s, typename Storage<S>::T (&v0)[kQ],
+                                           typename Storage<S>::T (&v1)[kQ]) {
+    using T = typename Storage<S>::T;
+    static_assert(!Storage<S>::shifted, "slip_pairs serves the unshifted FP64 storage");
+    if (s == T(0)) return;
+#pragma unroll
+    for (int i = 7; i < kQ; ++i) {
+        int via, j;
+        if (!((sw >> opp(i)) & 1u) || !specular_source(i, sw, via, j)) continue;
+        T r0, r1;
+        Pair<S>::load(f + ((size_t)j * n + nb.dst(via)), r0, r1);
+        v0[i] = (T(1) - s) * v0[i] + s * r0;
+        v1[i] = (T(1) - s) * v1[i] + s * r1;
+    }
+}
+
 // ---------------------------------------------------------------- cp.async helpers
 template <int BYTES> __device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);

@@ -35,6 +35,47 @@ __host__ __device__ constexpr int w36(int i) { return i == 0 ? 12 : (i <= 6 ? 2 
 
 template <class T> __device__ __forceinline__ constexpr T wgt(int i) { return T(w36(i)) / T(36); }
 
+// Specular reflection at a voxel wall (partial slip, the surface scattering
+// of Sec. 2).  For an edge direction i with non-zero components on axes a < b
+// whose source x - c_i is SOLID: if the face neighbour x - c_ia e_a is open
+// and x - c_ib e_b SOLID, the wall's normal is e_b and the particle came from
+// x - c_ia e_a in the direction of c_i with its b component reversed (and
+// likewise with a and b exchanged); at corners (both face neighbours SOLID, or
+// neither) it bounces back.  The partner cell reflects this cell's value the
+// same way, so blending the two conserves mass.
+__host__ __device__ constexpr int dir_of(int x, int y, int z) {
+    for (int k = 0; k < kQ; ++k)
+        if (cx(k) == x && cy(k) == y && cz(k) == z) return k;
+    return -1;
+}
+__host__ __device__ constexpr int comp(int i, int a) { return a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i)); }
+// the m-th (0, 1) axis on which the edge direction i is non-zero
+__host__ __device__ constexpr int edge_axis(int i, int m) {
+    return m == 0 ? (cx(i) != 0 ? 0 : 1) : (cz(i) != 0 ? 2 : 1);
+}
+// direction from x to its face neighbour x - c_ia e_a (a = edge_axis(i, m))
+__host__ __device__ constexpr int face_back(int i, int m) {
+    return dir_of(edge_axis(i, m) == 0 ? -cx(i) : 0, edge_axis(i, m) == 1 ? -cy(i) : 0,
+                  edge_axis(i, m) == 2 ? -cz(i) : 0);
+}
+// c_i with its component on edge_axis(i, m) reversed
+__host__ __device__ constexpr int mirrored(int i, int m) {
+    return dir_of(edge_axis(i, m) == 0 ? -cx(i) : cx(i), edge_axis(i, m) == 1 ? -cy(i) : cy(i),
+                  edge_axis(i, m) == 2 ? -cz(i) : cz(i));
+}
+// For the edge direction i of a cell with SOLID-neighbour bits `links` and
+// x - c_i SOLID: the direction from the cell to the reflection's source cell
+// (`via`) and the direction of the reflected value there (`j`); false at
+// corners.
+__device__ __forceinline__ bool specular_source(int i, uint32_t links, int &via, int &j) {
+    const bool sa = (links >> face_back(i, 0)) & 1u, sb = (links >> face_back(i, 1)) & 1u;
+    if (sa == sb) return false;
+    via = sa ? face_back(i, 1) : face_back(i, 0);
+    j = sa ? mirrored(i, 0) : mirrored(i, 1);
+    return true;
+}
+constexpr bool has_slip(int EQ) { return (EQ & 4) != 0; }
+
 // Cell-type encoding of the per-cell geometry word: bits 0..18 flag the
 // directions i whose neighbour x + c_i is SOLID, bits 24..25 hold the type.
 constexpr uint32_t kFluid = 0, kSolid = 1, kInlet = 2, kOutlet = 3;
@@ -229,10 +270,40 @@ template <class T, bool SHIFTED> __device__ __forceinline__ T density_of(const T
     return SHIFTED ? rref + r : r;
 }
 
-template <class S, bool RO = true, class NB = Nbr>
+// Wall slip of one component's pulled values v (dense layout): every edge
+// direction whose source is SOLID gets (1 - s) times the bounced-back value
+// plus s times the specular reflection (specular_source).  In the shifted
+// formats the reflected value is stored against its source cell's reference
+// density, and is moved to this cell's (rref) with the source's entry of the
+// component's reference plane rcomp.
+template <class S, class NB>
+__device__ __forceinline__ void slip_values(const S *__restrict__ fcomp, long long n, const NB &nb, uint32_t links,
+                                            typename Storage<S>::T s, const Ref *__restrict__ rcomp,
+                                            typename Storage<S>::T rref, typename Storage<S>::T (&v)[kQ]) {
+    using T = typename Storage<S>::T;
+    if (s == T(0)) return;
+#pragma unroll
+    for (int i = 7; i < kQ; ++i) {
+        int via, j;
+        if (!((links >> opp(i)) & 1u) || !specular_source(i, links, via, j)) continue;
+        const uint32_t src = (uint32_t)nb.dst(via);
+        T r = Storage<S>::load(fcomp + ((uint32_t)j * (uint32_t)n + src), T(0));
+        if constexpr (Storage<S>::shifted) r += wgt<T>(i) * ((T)__half2float(__ldg(rcomp + src)) - rref);
+        v[i] = (T(1) - s) * v[i] + s * r;
+    }
+}
+
+// Optional wall slip of a pull: the instance's slip fraction and the pulled
+// component's reference plane (shifted formats).
+template <class T> struct SlipArgs {
+    T s = T(0);
+    const Ref *rcomp = nullptr;
+};
+
+template <class S, bool RO = true, class NB = Nbr, bool SLIP = false>
 __device__ __forceinline__ Moments<typename Storage<S>::T>
 pull_moments(const S *__restrict__ fcomp, long long n, int self, const NB &nb, uint32_t links,
-             typename Storage<S>::T rref) {
+             typename Storage<S>::T rref, SlipArgs<typename Storage<S>::T> sl = {}) {
     using T = typename Storage<S>::T;
     T v[kQ];  // stored values: deviations d_i in the shifted formats, f_i otherwise
 #pragma unroll
@@ -243,14 +314,16 @@ pull_moments(const S *__restrict__ fcomp, long long n, int self, const NB &nb, u
                                 : (uint32_t)i * (uint32_t)n + (uint32_t)nb.src(i);
         v[i] = RO ? Storage<S>::load(fcomp + idx, T(0)) : Storage<S>::load_rw(fcomp + idx, T(0));
     }
+    if constexpr (SLIP) slip_values<S>(fcomp, n, nb, links, sl.s, sl.rcomp, rref, v);
     return moments_of<T, Storage<S>::shifted>(v, rref);
 }
 
 // Density only (for the pseudo-potential pass), same summation order.
-template <class S, bool RO = true, class NB = Nbr>
+template <class S, bool RO = true, class NB = Nbr, bool SLIP = false>
 __device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restrict__ fcomp, long long n, int self,
                                                               const NB &nb, uint32_t links,
-                                                              typename Storage<S>::T rref) {
+                                                              typename Storage<S>::T rref,
+                                                              SlipArgs<typename Storage<S>::T> sl = {}) {
     using T = typename Storage<S>::T;
     T v[kQ];
 #pragma unroll
@@ -261,6 +334,7 @@ __device__ __forceinline__ typename Storage<S>::T pull_density(const S *__restri
                                 : (uint32_t)i * (uint32_t)n + (uint32_t)nb.src(i);
         v[i] = RO ? Storage<S>::load(fcomp + idx, T(0)) : Storage<S>::load_rw(fcomp + idx, T(0));
     }
+    if constexpr (SLIP) slip_values<S>(fcomp, n, nb, links, sl.s, sl.rcomp, rref, v);
     return density_of<T, Storage<S>::shifted>(v, rref);
 }
 

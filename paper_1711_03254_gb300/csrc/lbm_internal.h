@@ -15,6 +15,7 @@ struct StepArgs {
     lbm_precision precision;
     int eq_order, wall_model, write_macro;
     int reg_order;     // 2 or 3 (0 is taken as 2)
+    int slip;          // 1: some instance has wall slip (the pulls blend in specular reflection)
     int batch;
     Grid g;
     const void *f_in;
@@ -41,16 +42,22 @@ struct StepArgs {
     cudaEvent_t *ev = nullptr;
 };
 
-// Collision variant EQ of the kernels (bit 0: eq_order 1, bit 1: reg_order 3),
-// passed to f as a std::integral_constant.
-inline int collide_variant(const StepArgs &a) { return (a.eq_order ? 1 : 0) | (a.reg_order == 3 ? 2 : 0); }
+// Variant EQ of the two-pass kernels (bit 0: eq_order 1, bit 1: reg_order 3,
+// bit 2: wall slip), passed to f as a std::integral_constant.
+inline int collide_variant(const StepArgs &a) {
+    return (a.eq_order ? 1 : 0) | (a.reg_order == 3 ? 2 : 0) | (a.slip ? 4 : 0);
+}
 
 template <class F> inline void dispatch_variant(int v, F &&f) {
     switch (v) {
     case 0: f(std::integral_constant<int, 0>{}); break;
     case 1: f(std::integral_constant<int, 1>{}); break;
     case 2: f(std::integral_constant<int, 2>{}); break;
-    default: f(std::integral_constant<int, 3>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    default: f(std::integral_constant<int, 7>{}); break;
     }
 }
 

@@ -17,6 +17,7 @@ template <class T> struct InstParam {
     T g[3];      // body acceleration
     T rho_in[2]; // INLET densities
     T u_in[3];   // INLET velocity
+    T slip;      // fraction of the wall's particles reflected specularly
 };
 
 struct Grid {

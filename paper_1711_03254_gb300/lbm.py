@@ -39,7 +39,8 @@ class lbm_config(ctypes.Structure):
 
 class lbm_instance_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("rho_s", ctypes.c_double),
-                ("g", ctypes.c_double * 3), ("rho_in", ctypes.c_double * 2), ("u_in", ctypes.c_double * 3)]
+                ("g", ctypes.c_double * 3), ("rho_in", ctypes.c_double * 2), ("u_in", ctypes.c_double * 3),
+                ("slip", ctypes.c_double)]
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -146,6 +147,7 @@ def make_params(params):
         arr[k].g[:] = [float(v) for v in p.get("g", (0.0, 0.0, 0.0))]
         arr[k].rho_in[:] = [float(v) for v in p.get("rho_in", (0.0, 0.0))]
         arr[k].u_in[:] = [float(v) for v in p.get("u_in", (0.0, 0.0, 0.0))]
+        arr[k].slip = float(p.get("slip", 0.0))
     return arr
 
 

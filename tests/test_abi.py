@@ -62,6 +62,10 @@ def test_create_rejects_bad_arguments(lbm):
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create(lbm.make_config(4, 4, 4), lbm.make_params([dict(tau=(1.0, 1.0), G=float("nan"))]))
     assert e.value.status == 1
+    for bad in (-0.1, 1.5, float("nan")):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(lbm.make_config(4, 4, 4), lbm.make_params([dict(tau=(1.0, 1.0), slip=bad)]))
+        assert e.value.status == 1
 
 
 def test_allocator_hook_needs_both(lbm):
@@ -73,7 +77,7 @@ def test_allocator_hook_needs_both(lbm):
 def test_structs_match_header(lbm):
     import ctypes
     assert ctypes.sizeof(lbm.lbm_config) == 8 * 4  # 8 ints
-    assert ctypes.sizeof(lbm.lbm_instance_params) == 12 * 8
+    assert ctypes.sizeof(lbm.lbm_instance_params) == 13 * 8
 
 
 def test_create_rejects_grids_beyond_32_bit_plane_offsets(lbm):
