@@ -80,7 +80,7 @@ def alg_bytes_per_cell(part: str, precision: str) -> int:
 # keyed by kernel/precision/workload, with the hash of the source files the
 # kernel is built from at the time of the capture; any change of them voids it.
 COMPACT_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_pair2.cuh", "lbm_compact.cuh", "lbm_compact_update.cuh"]
-DENSE_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_kernels.cu"]
+DENSE_SOURCES = ["lbm_types.h", "lbm_device.cuh", "lbm_twopass.cuh"]
 NCU_TRAFFIC = {
     # 128^3 packed spheres (837,994 non-solid cells), dense layout, ncu --set full:
     # 273.1 MB read + 103.1 MB written in one launch

@@ -8,15 +8,17 @@
 
 namespace lbm {
 
-// Occupancy, measured on GB300 (256^3 packed spheres).  The update runs
-// 128-thread blocks, 7 (16-bit storage), 5 (FP32) or 4 (FP64) per SM within the
-// registers; one more block per SM was no faster (16-bit: 0.316 against 0.314
-// ms per update).  The psi pass runs 256-thread blocks, 6 per SM (40
-// registers): 16-bit storage 0.139 ms against 0.159 at 4 and 0.192 at 3 per
-// SM, and 0.163 for a persistent variant that prefetched each thread's next
-// cell with cp.async; FP32 0.186 against 0.218 at 3 per SM.
+// Occupancy, measured on GB300 (256^3 packed spheres, ms per update).  The
+// update runs 128-thread blocks, 6 per SM for the FP32 and 16-bit storages
+// (80 registers, no spills) and 4 for FP64: FP16 0.297 against 0.317 at 5 and
+// 0.310 at 7 (72 registers, spilling), 256-thread blocks 3 per SM 0.322; FP32
+// 0.380 against 0.401 at 5, 0.415 at 7 and 0.441 at 4; FP64 the same at 3 to 5.
+// The psi pass runs 256-thread blocks, 6 per SM (40 registers): 16-bit
+// storage 0.139 ms against 0.159 at 4 and 0.192 at 3 per SM (5 and 8: 0.139),
+// and 0.163 for a persistent variant that prefetched each thread's next cell
+// with cp.async; FP32 0.186 against 0.218 at 3 per SM.
 constexpr int kPsiThreads = 256, kPsiBlocks = 6, kCollideThreads = 128;
-template <class S> constexpr int collide_min_blocks() { return sizeof(S) == 2 ? 7 : (sizeof(S) == 4 ? 5 : 4); }
+template <class S> constexpr int collide_min_blocks() { return sizeof(S) == 2 ? 6 : (sizeof(S) == 4 ? 6 : 4); }
 
 template <class S, bool SLIP>
 __global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {

@@ -155,7 +155,7 @@ def test_fp64_batched_instances(lbm, oracle_mod, kernel):
 # 2.4e-5 with the packed-pair arithmetic of the compact layout).  The wall case
 # has no such neutral mode and holds FP32 to 1e-5 and FP16 to 1e-3 on u_F.
 DROPLET_BOUNDS = {"fp32": (1e-5, 5e-5), "fp16s": (1e-3, 1e-2), "bf16s": (6e-3, 6e-2)}
-WALL_BOUNDS = {"fp32": (1e-5, 1e-5), "fp16s": (2e-3, 1e-3), "bf16s": (1e-2, 1e-2)}
+WALL_BOUNDS = {"fp32": (1e-5, 1e-5), "fp16s": (1e-3, 1e-3), "bf16s": (1e-2, 1e-2)}
 
 
 @pytest.mark.parametrize("kernel", KERNELS)

@@ -16,7 +16,7 @@ from paper_1711_03254_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-WALL_BOUNDS = {"fp32": (1e-5, 1e-5), "fp16s": (2e-3, 1e-3), "bf16s": (1e-2, 1e-2)}
+WALL_BOUNDS = {"fp32": (1e-5, 1e-5), "fp16s": (1e-3, 1e-3), "bf16s": (1e-2, 1e-2)}
 
 
 @pytest.fixture(scope="module")
