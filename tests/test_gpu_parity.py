@@ -228,6 +228,35 @@ def test_reductions_match_oracle(lbm, oracle_mod):
     assert abs(a[5] - b[5]) <= 1e-9 * abs(b[5])
 
 
+def test_fp32_reductions_against_fp64_sums(lbm):
+    """With FP32 fields the reduction forms each cell's terms in FP32 and
+    sums groups of eight cells in FP32 before FP64: masses, momentum,
+    max |u_F| and the residual against FP64 sums of the exported fields."""
+    shape = (40, 30, 20)
+    t, r1, r2, u = _random_geometry(shape, 0.2, 43, lo=0.3, hi=0.7)
+    sim = lbm.Sim(*shape, [dict(tau=(0.8, 1.3), G=-2.0, rho_s=0.2, g=(1e-4, 0, 0))], precision="fp32")
+    sim.set_geometry(t[None])
+    sim.set_fields(r1[None], r2[None], u[None])
+    sim.step(10)
+    sim.reduce()
+    _, _, u0 = sim.get_fields()
+    sim.step(7)
+    red = sim.reduce()[0]
+    a, b, v = sim.get_fields()
+    fl = (t != W.SOLID)[None]
+    rho = a + b
+    assert abs(red[0] - a[fl].sum()) < 1e-6 * a[fl].sum() and abs(red[1] - b[fl].sum()) < 1e-6 * b[fl].sum()
+    P = (rho[..., None] * v)[fl].sum(axis=0)
+    scale = np.abs(rho[..., None] * v)[fl].sum()
+    assert np.all(np.abs(red[2:5] - P) < 1e-6 * scale), (red[2:5], P)
+    d2 = ((v - u0) ** 2)[fl].sum()
+    u2 = (v ** 2)[fl].sum()
+    res = np.sqrt(d2) / (7 * np.sqrt(u2))
+    assert abs(red[5] - res) < 1e-4 * res, (red[5], res)
+    umax = np.sqrt((v ** 2).sum(-1))[fl].max()
+    assert abs(red[6] - umax) < 1e-6 * umax, (red[6], umax)
+
+
 def test_reductions_are_deterministic(lbm):
     t, r1, r2, u = W.droplet(24, 24, 24, 6.0)
     outs = []
