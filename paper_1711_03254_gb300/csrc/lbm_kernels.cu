@@ -47,9 +47,13 @@ __global__ void k_init_ref(const double *__restrict__ r1, const double *__restri
 // f := feq(rho_alpha, u) from FP64 fields (u interleaved [b][cell][3]).  The
 // shifted storages store each value against the reference density of the
 // cell it streams into: k_init_ref has written those (ref), and a value that
-// bounces back off a SOLID neighbour takes the cell's own density.
+// bounces back off a SOLID neighbour takes the cell's own density.  Four
+// blocks per SM (64 registers, some spilled): at the 86 registers the compiler
+// chose unbounded, two blocks left the kernel waiting on memory latency (22 %
+// of the warps active, 0.57 ms at 192^3); lbm_set_fields at 256^3 went from
+// 5.17 to 4.68 ms with its copies (3 blocks: 4.79).
 template <class S, int EQ>
-__global__ void k_init(const double *__restrict__ r1, const double *__restrict__ r2, const double *__restrict__ u,
+__global__ void __launch_bounds__(256, 4) k_init(const double *__restrict__ r1, const double *__restrict__ r2, const double *__restrict__ u,
                        const uint32_t *__restrict__ link, S *__restrict__ fo, const Ref *__restrict__ ref,
                        typename Storage<S>::T *__restrict__ macro, typename Storage<S>::T *__restrict__ usnap, Grid g,
                        const InstParam<typename Storage<S>::T> *__restrict__ par) {
