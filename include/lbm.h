@@ -56,7 +56,8 @@ typedef enum {
     LBM_ERR_CUDA = 2,     /* a CUDA runtime call failed (message in lbm_last_error) */
     LBM_ERR_OOM = 3,      /* device allocation failed */
     LBM_ERR_DIVERGED = 4, /* non-finite value, or |u_F| above the sound speed 1/sqrt(3), found by lbm_reduce */
-    LBM_ERR_TIMEOUT = 5,  /* lbm_run_to_steady used up its update budget before the tolerance */
+    LBM_ERR_TIMEOUT = 5,  /* lbm_run_to_steady used up its update budget before the tolerance, or a
+                             grid-wide barrier of the persistent update gave up waiting */
     LBM_ERR_STATE = 6     /* call out of order (e.g. step before set_fields) */
 } lbm_status;
 
@@ -76,18 +77,27 @@ typedef enum {
 
 /* Kernel strategy for lbm_step. */
 typedef enum {
-    LBM_KERNEL_AUTO = 0,     /* compact when the grid fits its coordinate limits, else two-pass */
+    LBM_KERNEL_AUTO = 0,     /* compact when the grid fits its coordinate limits, else two-pass;
+                                for n >= 8 updates of at most 65,536 non-solid cells in all
+                                (FP32 arithmetic, no wall slip) the persistent update, except
+                                inside lbm_run_to_steady's graphs */
     LBM_KERNEL_TWO_PASS = 1, /* density pre-pass, then stream+collide, over the non-solid cells */
     LBM_KERNEL_FUSED = 2,    /* single read of f: z-marching tiles with a recomputed density halo */
     LBM_KERNEL_CLUSTER = 3,  /* persistent: one thread-block cluster per instance, n updates per launch */
     LBM_KERNEL_COMPACT = 4,  /* two-pass on a compact layout that stores only the non-solid cells
                                 (in cell order; neighbours found from per-row occupancy words);
                                 needs nx <= 2048, ny <= 2048, nz <= 1024 */
-    LBM_KERNEL_FUSED_COMPACT = 5 /* single read of f on the compact layout: thread-block clusters
+    LBM_KERNEL_FUSED_COMPACT = 5, /* single read of f on the compact layout: thread-block clusters
                                 march bands of rows along z, densities kept in shared memory;
                                 FP32 arithmetic only; where a plane's rows do not fit in shared
                                 memory the compact two-pass update runs instead (see
                                 lbm_resolved_kernel) */
+    LBM_KERNEL_PERSISTENT = 6  /* the compact two-pass update, n updates in one cooperative launch
+                                with grid-wide barriers between the passes (for small instances
+                                and batches of them); FP32 arithmetic, no wall slip; a barrier
+                                that waits about two seconds gives up, and the next
+                                lbm_reduce, lbm_get_fields or lbm_run_to_steady returns
+                                LBM_ERR_TIMEOUT */
 } lbm_kernel;
 
 typedef struct {
@@ -254,6 +264,15 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *buf, size_t bytes);
  * (between the parts of a split update), LBM_ERR_CUDA. */
 lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_instance_params *per_instance);
 
+/* Failure test of the persistent update (LBM_KERNEL_PERSISTENT): its
+ * grid-wide barriers wait at most wait_cycles SM clock cycles (default 4e9,
+ * about two seconds) and, with missing > 0, wait for that many arrivals more
+ * than the launch has, so that every barrier gives up after the bound; the
+ * launch then ends early and the next lbm_reduce, lbm_get_fields or
+ * lbm_run_to_steady returns LBM_ERR_TIMEOUT.  missing = 0 restores normal
+ * barriers.  Errors: LBM_ERR_ARG (null, wait_cycles < 1000). */
+lbm_status lbm_set_barrier_test(lbm_ctx *ctx, long long wait_cycles, unsigned missing);
+
 /* Use the given cudaStream_t (cast to void*) for all later work; NULL selects
  * the legacy default stream.  The caller keeps ownership of the stream. */
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
@@ -327,7 +346,7 @@ typedef enum {
     LBM_PART_PSI = 0,     /* two-pass: density and psi of every fluid cell */
     LBM_PART_COLLIDE = 1, /* two-pass: pull, forces, collision, store */
     LBM_PART_FUSED = 2,   /* single-read fused update */
-    LBM_PART_CLUSTER = 3, /* persistent cluster launch (several updates each) */
+    LBM_PART_CLUSTER = 3, /* persistent launch (several updates each): CLUSTER, PERSISTENT */
     LBM_PART_COUNT = 4
 } lbm_part;
 

@@ -23,6 +23,9 @@ thread_local std::string g_last_error;
 constexpr double kMaxSpeed = 0.57735026918962576;
 // the persistent cluster kernel loops each thread over cells of its instance
 constexpr long long kClusterMaxCells = 65536;
+// AUTO steps problems of at most this many non-solid cells (summed over the
+// batch) with the persistent update
+constexpr long long kPersistAutoItems = 65536;
 constexpr int kMaxBatch = 32767;
 
 size_t storage_bytes(lbm_precision p) {
@@ -58,6 +61,11 @@ struct lbm_ctx {
     uint32_t *cxyz = nullptr, *clink = nullptr;
     uint2 *rowtab = nullptr;
     int words = 0;
+    bool in_graph = false;     // lbm_run_to_steady is resolving and capturing its updates
+    unsigned *bar = nullptr;   // persistent update: barrier counter, give-up flag
+    bool persist_used = false; // a persistent launch ran since the flag was last read
+    long long bar_cycles = 4000000000LL;  // bound on a barrier wait (about 2 s of SM clock)
+    unsigned bar_missing = 0;  // failure test: arrivals the barriers wait for that never come
     FcPlan fplan{};  // single-read fused update on the compact layout (ok when it fits)
     std::vector<uint32_t> plane_start;  // compact index of each plane's first cell (instance 0), nz + 1
     bool half_step = false;             // the density pass of a split update has run
@@ -215,11 +223,18 @@ const char *check_params(const lbm_instance_params *per_instance, int batch) {
 // Strategy for an n-update call.  AUTO: the compact two-pass update when the
 // grid fits its packed coordinates, the dense two-pass one otherwise.
 lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
-    (void)n;
     // the fused compact update needs its rows and lag buffer to fit in shared
     // memory; where they do not, its layout's two-pass update runs
     if (ctx->kernel == LBM_KERNEL_FUSED_COMPACT) return ctx->fplan.ok ? LBM_KERNEL_FUSED_COMPACT : LBM_KERNEL_COMPACT;
     if (ctx->kernel != LBM_KERNEL_AUTO) return ctx->kernel;
+    // small problems stepped from the host: one cooperative launch for the n
+    // updates beats two launches per update (GB300, FP32, us per update: 16^3
+    // 7.5 against 12.3, 16 x 16^3 11.4 against 14.4; even at 32^3 x 4 and
+    // slower beyond).  Inside the steady loop's CUDA graphs the two-launch
+    // update is the faster one at every size (16^3: 7.1 against 7.9).
+    if (ctx->compact_ok && !ctx->fp64() && !ctx->slip_on() && !ctx->in_graph && n >= 8 &&
+        (long long)ctx->cfg.batch * ctx->list_max <= kPersistAutoItems)
+        return LBM_KERNEL_PERSISTENT;
     // measured on GB300: the two-pass update on the compact layout beats the
     // dense two-pass one on porous (1.5x) and all-fluid (1.1x) grids, the fused
     // one (2-4x), and the persistent cluster kernel on every small case tried
@@ -227,7 +242,9 @@ lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
     return ctx->compact_ok ? LBM_KERNEL_COMPACT : LBM_KERNEL_TWO_PASS;
 }
 
-bool uses_compact_layout(lbm_kernel k) { return k == LBM_KERNEL_COMPACT || k == LBM_KERNEL_FUSED_COMPACT; }
+bool uses_compact_layout(lbm_kernel k) {
+    return k == LBM_KERNEL_COMPACT || k == LBM_KERNEL_FUSED_COMPACT || k == LBM_KERNEL_PERSISTENT;
+}
 
 // the strategies whose kernels read f once per update (no slip, no
 // third-order regularisation)
@@ -383,7 +400,22 @@ StepArgs step_args(lbm_ctx *ctx, int write_macro) {
     a.words = ctx->words;
     a.kmax = (uint32_t)ctx->list_max;
     a.stream = ctx->stream;
+    a.bar = ctx->bar;
+    a.bar_cycles = ctx->bar_cycles;
+    a.bar_missing = ctx->bar_missing;
     return a;
+}
+
+// After persistent launches: LBM_ERR_TIMEOUT if a grid-wide barrier gave up
+// (its blocks then left the launch early and the state is not an update).
+lbm_status check_barrier(lbm_ctx *ctx) {
+    if (!ctx->persist_used) return LBM_OK;
+    unsigned h[2] = {0, 0};
+    LBM_CUDA(cudaMemcpyAsync(h, ctx->bar, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "barrier flag");
+    LBM_CUDA(cudaStreamSynchronize(ctx->stream), "barrier flag");
+    ctx->persist_used = false;
+    if (h[1]) return ctx->fail(LBM_ERR_TIMEOUT, "persistent update: a grid-wide barrier gave up waiting");
+    return LBM_OK;
 }
 
 }  // namespace
@@ -486,8 +518,9 @@ lbm_status lbm_create(const lbm_config *cfg, const lbm_instance_params *per_inst
     ctx->dpar = ctx->dalloc((size_t)cfg->batch * sizeof(InstParam<double>));
     ctx->partial = (double *)ctx->dalloc((size_t)cfg->batch * ctx->nblk * 9 * sizeof(double));
     ctx->red_out = (double *)ctx->dalloc((size_t)cfg->batch * 9 * sizeof(double));
+    ctx->bar = (unsigned *)ctx->dalloc(4 * sizeof(unsigned));
     if (!ctx->f[0] || !ctx->f[1] || (!ctx->fp64() && (!ctx->ref[0] || !ctx->ref[1])) || !ctx->link || !ctx->psi || !ctx->macro || !ctx->usnap || !ctx->dpar ||
-        !ctx->partial || !ctx->red_out) {
+        !ctx->partial || !ctx->red_out || !ctx->bar) {
         g_last_error = "lbm_create: device allocation failed";
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
@@ -515,7 +548,7 @@ lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_instance_params *per_instance)
     if (ctx->half_step) return ctx->fail(LBM_ERR_STATE, "lbm_set_params: finish the split update first");
     if (const char *bad = check_params(per_instance, ctx->cfg.batch))
         return ctx->fail(LBM_ERR_ARG, std::string("lbm_set_params: ") + bad);
-    if (single_read(ctx->kernel))
+    if (single_read(ctx->kernel) || ctx->kernel == LBM_KERNEL_PERSISTENT)
         for (int b = 0; b < ctx->cfg.batch; ++b)
             if (per_instance[b].slip != 0.0)
                 return ctx->fail(LBM_ERR_ARG, "lbm_set_params: wall slip needs the TWO_PASS or COMPACT strategy");
@@ -532,6 +565,14 @@ lbm_status lbm_set_params(lbm_ctx *ctx, const lbm_instance_params *per_instance)
     return LBM_OK;
 }
 
+lbm_status lbm_set_barrier_test(lbm_ctx *ctx, long long wait_cycles, unsigned missing) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (wait_cycles < 1000) return ctx->fail(LBM_ERR_ARG, "lbm_set_barrier_test: wait_cycles below 1000");
+    ctx->bar_cycles = wait_cycles;
+    ctx->bar_missing = missing;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
     if (!ctx) return LBM_ERR_ARG;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -540,7 +581,7 @@ lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream) {
 
 lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
     if (!ctx) return LBM_ERR_ARG;
-    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_FUSED_COMPACT)
+    if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_PERSISTENT)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: unknown strategy");
     if (kernel == LBM_KERNEL_CLUSTER && ctx->g.n > kClusterMaxCells)
         return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: CLUSTER needs at most 65536 cells per instance");
@@ -551,6 +592,9 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
     if (!ctx->single_read_ok() && single_read(kernel))
         return ctx->fail(LBM_ERR_ARG,
                          "lbm_set_kernel: reg_order 3 and wall slip run in the TWO_PASS and COMPACT strategies");
+    if (kernel == LBM_KERNEL_PERSISTENT && (!ctx->compact_ok || ctx->fp64() || ctx->slip_on()))
+        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: PERSISTENT needs the compact layout, FP32 arithmetic and no "
+                                      "wall slip");
     ctx->kernel = kernel;
     return LBM_OK;
 }
@@ -719,12 +763,13 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
         const lbm_status ls = ensure_layout(ctx, uses_compact_layout(k) ? 1 : 0);
         if (ls != LBM_OK) return ls;
     }
-    if (k == LBM_KERNEL_CLUSTER) {
+    if (k == LBM_KERNEL_CLUSTER || k == LBM_KERNEL_PERSISTENT) {
         if (n > 0) {
             StepArgs a = step_args(ctx, 1);
-            a.ev = ctx->events_for(LBM_KERNEL_CLUSTER);
-            cudaError_t e = launch_cluster(a, n);
-            if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_step cluster launch");
+            a.ev = ctx->events_for(k);
+            cudaError_t e = k == LBM_KERNEL_CLUSTER ? launch_cluster(a, n) : launch_persist(a, n);
+            if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_step persistent launch");
+            if (k == LBM_KERNEL_PERSISTENT) ctx->persist_used = true;
             ctx->launches += 1;
             ctx->cur ^= (n & 1);
         }
@@ -846,13 +891,17 @@ lbm_status lbm_get_fields(lbm_ctx *ctx, double *rho1, double *rho2, double *u) {
     ctx->dfree(d);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_get_fields");
     ctx->launches += 1;
-    return LBM_OK;
+    return check_barrier(ctx);
 }
 
 lbm_status lbm_reduce(lbm_ctx *ctx, double *out) {
     if (!ctx || !out) return ctx ? ctx->fail(LBM_ERR_ARG, "lbm_reduce: null argument") : LBM_ERR_ARG;
     if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_reduce: no fields yet");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    {
+        const lbm_status bs = check_barrier(ctx);
+        if (bs != LBM_OK) return bs;
+    }
     ReduceArgs a{};
     a.fp64 = ctx->fp64();
     a.batch = ctx->cfg.batch;
@@ -1095,6 +1144,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     const bool single_read_ok = ctx->single_read_ok();
     if (ctx->fplan.ok && single_read_ok) cands.push_back({LBM_KERNEL_FUSED_COMPACT, -1, -1});
     if (ctx->g.n <= kClusterMaxCells && single_read_ok) cands.push_back({LBM_KERNEL_CLUSTER, -1, -1});
+    if (ctx->compact_ok && !ctx->fp64() && !ctx->slip_on()) cands.push_back({LBM_KERNEL_PERSISTENT, -1, -1});
     for (int t = 0; single_read_ok && t < fused_tile_count(); ++t) {
         cands.push_back({LBM_KERNEL_FUSED, t, -1});
         for (int z : {8, 16, 32, 64})
@@ -1171,6 +1221,12 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
     if (check_every < 1 || max_steps < 0) return ctx->fail(LBM_ERR_ARG, "lbm_run_to_steady: bad counts");
     if (!ctx->has_fields) return ctx->fail(LBM_ERR_STATE, "lbm_run_to_steady: call lbm_set_fields first");
     LBM_CUDA(cudaSetDevice(ctx->dev), "cudaSetDevice");
+    // AUTO resolves for graph replay while this call runs
+    struct InGraph {
+        lbm_ctx *c;
+        explicit InGraph(lbm_ctx *c_) : c(c_) { c->in_graph = true; }
+        ~InGraph() { c->in_graph = false; }
+    } in_graph(ctx);
     const int B = ctx->cfg.batch;
     {
         // convert the layout now: a conversion must not be captured into the graphs
@@ -1231,7 +1287,7 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
     bool diverged = false, conv = false;
     const lbm_kernel kres = resolve_kernel(ctx, check_every);
     const long long launches_per_replay =
-        (kres == LBM_KERNEL_CLUSTER ? 1
+        ((kres == LBM_KERNEL_CLUSTER || kres == LBM_KERNEL_PERSISTENT) ? 1
          : (kres == LBM_KERNEL_FUSED || kres == LBM_KERNEL_FUSED_COMPACT) ? check_every
                                                                          : 2LL * check_every) + 2;
     ctx->since_snap = 0;  // the first replay measures against the current snapshot
@@ -1264,6 +1320,11 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int check_every, double tol, int max_
     if (hres) cudaFreeHost(hres);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "lbm_run_to_steady");
+    if (kres == LBM_KERNEL_PERSISTENT) {
+        ctx->persist_used = true;
+        const lbm_status bs = check_barrier(ctx);
+        if (bs != LBM_OK) return bs;
+    }
     if (diverged)
         return ctx->fail(LBM_ERR_DIVERGED, "lbm_run_to_steady: non-finite value or |u_F| above the lattice sound speed");
     if (!conv) return ctx->fail(LBM_ERR_TIMEOUT, "lbm_run_to_steady: max_steps used up before the tolerance");

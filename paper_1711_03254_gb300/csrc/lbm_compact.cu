@@ -27,6 +27,10 @@ extern template cudaError_t launch_compact_t<double>(const StepArgs &, int);
 extern template cudaError_t launch_compact_t<float>(const StepArgs &, int);
 extern template cudaError_t launch_compact_t<__half>(const StepArgs &, int);
 extern template cudaError_t launch_compact_t<__nv_bfloat16>(const StepArgs &, int);
+extern template cudaError_t launch_persist_t<double>(const StepArgs &, int);
+extern template cudaError_t launch_persist_t<float>(const StepArgs &, int);
+extern template cudaError_t launch_persist_t<__half>(const StepArgs &, int);
+extern template cudaError_t launch_persist_t<__nv_bfloat16>(const StepArgs &, int);
 
 __global__ void k_compact_links(const uint32_t *__restrict__ list, const int *__restrict__ count,
                                 const uint32_t *__restrict__ link, uint32_t *__restrict__ clink, long long n,
@@ -72,6 +76,16 @@ cudaError_t launch_compact(const StepArgs &a, int parts) {
     case LBM_FP32: return launch_compact_t<float>(a, parts);
     case LBM_FP32_F16S: return launch_compact_t<__half>(a, parts);
     case LBM_FP32_BF16S: return launch_compact_t<__nv_bfloat16>(a, parts);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_persist(const StepArgs &a, int nsteps) {
+    switch (a.precision) {
+    case LBM_FP64: return launch_persist_t<double>(a, nsteps);
+    case LBM_FP32: return launch_persist_t<float>(a, nsteps);
+    case LBM_FP32_F16S: return launch_persist_t<__half>(a, nsteps);
+    case LBM_FP32_BF16S: return launch_persist_t<__nv_bfloat16>(a, nsteps);
     }
     return cudaErrorInvalidValue;
 }

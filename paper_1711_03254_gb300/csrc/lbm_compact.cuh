@@ -98,6 +98,7 @@ template <> struct Pair2<float> {
     static constexpr bool kScaled = false;
     static constexpr float kUnscale = 1.f, kScale = 1.f;
     __device__ static __forceinline__ float2 load(const P *p) { return __ldg(p); }
+    __device__ static __forceinline__ float2 load_cg(const P *p) { return __ldcg(p); }
     __device__ static __forceinline__ float2 load_shared(const P *p) { return *p; }
     __device__ static __forceinline__ void store(P *p, float2 v) { *p = v; }
 };
@@ -106,6 +107,7 @@ template <> struct Pair2<__half> {
     static constexpr bool kScaled = true;
     static constexpr float kUnscale = kF16Unscale, kScale = kF16Scale;
     __device__ static __forceinline__ float2 load(const P *p) { return __half22float2(__ldg(p)); }
+    __device__ static __forceinline__ float2 load_cg(const P *p) { return __half22float2(__ldcg(p)); }
     __device__ static __forceinline__ float2 load_shared(const P *p) { return __half22float2(*p); }
     __device__ static __forceinline__ void store(P *p, float2 v) { *p = __float22half2_rn(v); }
 };
@@ -114,6 +116,7 @@ template <> struct Pair2<__nv_bfloat16> {
     static constexpr bool kScaled = false;
     static constexpr float kUnscale = 1.f, kScale = 1.f;
     __device__ static __forceinline__ float2 load(const P *p) { return __bfloat1622float2(__ldg(p)); }
+    __device__ static __forceinline__ float2 load_cg(const P *p) { return __bfloat1622float2(__ldcg(p)); }
     __device__ static __forceinline__ float2 load_shared(const P *p) { return __bfloat1622float2(*p); }
     __device__ static __forceinline__ void store(P *p, float2 v) { *p = __float22bfloat162_rn(v); }
 };
@@ -181,20 +184,25 @@ __device__ __forceinline__ void ref_pair(const StepArgs &a, int b, uint32_t sk, 
     }
 }
 
+// Loads of data written earlier in the same launch (the persistent update)
+// go through L2 (COH = true): the read-only L1 path could still hold the
+// lines of two updates before.
+template <bool COH, class T> __device__ __forceinline__ T ld_data(const T *p) { return COH ? __ldcg(p) : __ldg(p); }
+
 // pull_pairs for the packed-pair path: the 19 stored pairs in storage units.
-template <class S>
+template <class S, bool COH = false>
 __device__ __forceinline__ void pull_pairs2(const typename Pair2<S>::P *__restrict__ f, uint32_t n, uint32_t sk,
                                             const CNbr &nb, uint32_t sw, float2 (&v)[kQ]) {
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const bool bb = (sw >> opp(i)) & 1u;
         const uint32_t idx = bb ? (uint32_t)opp(i) * n + sk : (uint32_t)i * n + nb.src(i);
-        v[i] = Pair2<S>::load(f + idx);
+        v[i] = COH ? Pair2<S>::load_cg(f + idx) : Pair2<S>::load(f + idx);
     }
 }
 
-__device__ __forceinline__ float2 ref_pair2(const StepArgs &a, int b, uint32_t sk) {
-    return __half22float2(__ldg((const __half2 *)a.ref_in + (size_t)b * a.kmax + sk));
+template <bool COH = false> __device__ __forceinline__ float2 ref_pair2(const StepArgs &a, int b, uint32_t sk) {
+    return __half22float2(ld_data<COH>((const __half2 *)a.ref_in + (size_t)b * a.kmax + sk));
 }
 
 // Wall slip of the pulled pairs v of cell sk (the compact form of
@@ -203,20 +211,20 @@ __device__ __forceinline__ float2 ref_pair2(const StepArgs &a, int b, uint32_t s
 // units.  The reflected pair is stored against its source cell's reference
 // pair; it is moved to this cell's with both entries of the instance's
 // reference table `ref` (FP32 and 16-bit storages all hold deviations).
-template <class S>
+template <class S, bool COH = false>
 __device__ __forceinline__ void slip_pairs2(const typename Pair2<S>::P *__restrict__ f, uint32_t n, uint32_t sk,
                                             const CNbr &nb, uint32_t sw, float s, const __half2 *__restrict__ ref,
                                             float2 (&v)[kQ]) {
     if (s == 0.f) return;
-    const float2 rown = __half22float2(__ldg(ref + sk));
+    const float2 rown = __half22float2(ld_data<COH>(ref + sk));
     const float2 sv = bc2(s), kv = bc2(1.f - s);
 #pragma unroll
     for (int i = 7; i < kQ; ++i) {
         int via, j;
         if (!((sw >> opp(i)) & 1u) || !specular_source(i, sw, via, j)) continue;
         const uint32_t src = nb.dst(via);
-        float2 r = Pair2<S>::load(f + ((size_t)j * n + src));
-        r = fma2(sub2(__half22float2(__ldg(ref + src)), rown), bc2(wgt<float>(i) * Pair2<S>::kScale), r);
+        float2 r = COH ? Pair2<S>::load_cg(f + ((size_t)j * n + src)) : Pair2<S>::load(f + ((size_t)j * n + src));
+        r = fma2(sub2(__half22float2(ld_data<COH>(ref + src)), rown), bc2(wgt<float>(i) * Pair2<S>::kScale), r);
         v[i] = fma2(sv, r, mul2(kv, v[i]));
     }
 }

@@ -20,13 +20,13 @@ namespace lbm {
 constexpr int kPsiThreads = 256, kPsiBlocks = 6, kCollideThreads = 128;
 template <class S> constexpr int collide_min_blocks() { return sizeof(S) == 2 ? 6 : (sizeof(S) == 4 ? 6 : 4); }
 
-template <class S, bool SLIP>
-__global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {
+// S1-S3 for the non-solid cell k of instance b: pull, sum to rho_alpha, store
+// the psi pair.  COH: f and the reference densities were written earlier in
+// the same launch (the persistent update), so they are read through L2.
+template <class S, bool SLIP, bool COH>
+__device__ __forceinline__ void psi_cell(const StepArgs &a, int b, uint32_t k) {
     using T = typename Storage<S>::T;
     using V = typename Vec2<T>::V;
-    const int b = blockIdx.y;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
     const CompactCell c = compact_cell(a, b, k);
     const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
     V *psi = (V *)a.psi + (size_t)b * a.kmax;
@@ -39,13 +39,15 @@ __global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {
         auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
             if constexpr (packed_pairs<S>()) {
                 float2 v[kQ];
-                pull_pairs2<S>(f, a.kmax, sk, nb, sw, v);
+                pull_pairs2<S, COH>(f, a.kmax, sk, nb, sw, v);
                 if constexpr (SLIP)
-                    slip_pairs2<S>(f, a.kmax, sk, nb, sw, p.slip, (const __half2 *)a.ref_in + (size_t)b * a.kmax, v);
-                const float2 d = density2<Pair2<S>::kScaled>(v, ref_pair2(a, b, sk), Pair2<S>::kUnscale);
+                    slip_pairs2<S, COH>(f, a.kmax, sk, nb, sw, p.slip,
+                                        (const __half2 *)a.ref_in + (size_t)b * a.kmax, v);
+                const float2 d = density2<Pair2<S>::kScaled>(v, ref_pair2<COH>(a, b, sk), Pair2<S>::kUnscale);
                 p0 = d.x;
                 p1 = d.y;
             } else {
+                static_assert(!COH, "the persistent update serves the FP32-arithmetic storages");
                 T v0[kQ], v1[kQ], r0, r1;
                 pull_pairs<S>(f, a.kmax, sk, nb, sw, v0, v1);
                 if constexpr (SLIP) slip_pairs<S>(f, a.kmax, nb, sw, p.slip, v0, v1);
@@ -70,6 +72,14 @@ __global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {
     out.x = p0;
     out.y = p1;
     psi[k] = out;
+}
+
+template <class S, bool SLIP>
+__global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {
+    const int b = blockIdx.y;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
+    psi_cell<S, SLIP, false>(a, b, k);
 }
 
 template <class S, int EQ>
@@ -192,12 +202,14 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
 // memory accesses; the neighbour psi pairs enter the force sums unselected
 // (the cell's own pair at SOLID neighbours, removed in forces2), and the
 // storage scale of FP16 is folded into the moment sums and the weights.
-template <class S, int EQ>
-__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c2(StepArgs a) {
+// The body of k_collide_c2 for the non-solid cell k of instance b; qs is the
+// block's shared-memory slots of the neighbour psi pairs (one column per
+// thread).  COH: psi, f and the reference densities were written earlier in
+// the same launch (the persistent update) and are read through L2.
+template <class S, int EQ, bool COH>
+__device__ __forceinline__ void collide_cell2(const StepArgs &a, int b, uint32_t k, int write_macro,
+                                              float2 (&qs)[kQ - 1][kCollideThreads]) {
     using P = typename Pair2<S>::P;
-    const int b = blockIdx.y;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
     const CompactCell c = compact_cell(a, b, k);
     const uint32_t word = c.word;
     const InstParam<float> &p = ((const InstParam<float> *)a.par)[b];
@@ -215,13 +227,13 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             const bool self_ref = i == 0 || ((word >> i) & 1u);
-            const float2 q = self_ref ? make_float2(p.rho_in[0], p.rho_in[1]) : __ldg(psi + own.dst(i));
+            const float2 q = self_ref ? make_float2(p.rho_in[0], p.rho_in[1]) : ld_data<COH>(psi + own.dst(i));
             Pair<S>::store(fo + (size_t)i * n + k, feq_dir<float, EQ>(i, p.rho_in[0], p.u_in[0], p.u_in[1], p.u_in[2], uu),
                            feq_dir<float, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu),
                            wgt<float>(i) * ref_value(q.x), wgt<float>(i) * ref_value(q.y));
         }
         rout[k] = __floats2half2_rn(p.rho_in[0], p.rho_in[1]);
-        if (a.write_macro) {
+        if (write_macro) {
             mac[cell] = p.rho_in[0];
             mac[a.g.n + cell] = p.rho_in[1];
             mac[2 * a.g.n + cell] = p.u_in[0];
@@ -232,24 +244,27 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
     }
     // the psi pairs of the 18 neighbours (the cell's own at SOLID ones) start
     // on their way into this thread's shared-memory slots now, so that their
-    // latency overlaps the pull of f; no other thread reads the slots
-    __shared__ float2 qs[kQ - 1][kCollideThreads];
+    // latency overlaps the pull of f; no other thread reads the slots (the
+    // persistent update loads them through L2 into the same slots)
     const int tid = threadIdx.x;
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
         const bool solid = (word >> i) & 1u;
-        cp_async_ca<8>(&qs[i - 1][tid], psi + (solid ? k : own.dst(i)));
+        if constexpr (COH)
+            qs[i - 1][tid] = __ldcg(psi + (solid ? k : own.dst(i)));
+        else
+            cp_async_ca<8>(&qs[i - 1][tid], psi + (solid ? k : own.dst(i)));
     }
-    cp_async_commit_group();
+    if constexpr (!COH) cp_async_commit_group();
     const P *f = (const P *)a.f_in + (size_t)b * kQ * n;
     P *fo = (P *)a.f_out + (size_t)b * kQ * n;
     Moments2 m;
     auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
         float2 v[kQ];
-        pull_pairs2<S>(f, n, sk, nb, sw, v);
+        pull_pairs2<S, COH>(f, n, sk, nb, sw, v);
         if constexpr (has_slip(EQ))
-            slip_pairs2<S>(f, n, sk, nb, sw, p.slip, (const __half2 *)a.ref_in + (size_t)b * n, v);
-        m = moments2<Pair2<S>::kScaled>(v, ref_pair2(a, b, sk), Pair2<S>::kUnscale);
+            slip_pairs2<S, COH>(f, n, sk, nb, sw, p.slip, (const __half2 *)a.ref_in + (size_t)b * n, v);
+        m = moments2<Pair2<S>::kScaled>(v, ref_pair2<COH>(a, b, sk), Pair2<S>::kUnscale);
     };
     {
         int xu;
@@ -270,7 +285,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
     bs.clear();
     __half2 Rp[kQ];
     Rp[0] = rho_h;
-    cp_async_wait_all();
+    if constexpr (!COH) cp_async_wait_all();
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
         const bool solid = (word >> i) & 1u;
@@ -278,7 +293,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
         bs.add(i, q);
         Rp[i] = solid ? rho_h : __float22half2_rn(q);
     }
-    const float2 psi_own = ((word & 0x7FFFEu) && a.wall_model < 2) ? __ldg(psi + k) : bc2(0.f);
+    const float2 psi_own = ((word & 0x7FFFEu) && a.wall_model < 2) ? ld_data<COH>(psi + k) : bc2(0.f);
     const Forces2 F = forces2(bs, psi_own, word, m.rho, p, a.wall_model);
     const Relax<float> R = relax2(m, F, p);
     const Prep2 cp = prep2<EQ>(m, R, F);
@@ -292,12 +307,164 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
         Pair2<S>::store(fo + (size_t)(i + 1) * n + k, vo);
     }
     rout[k] = rho_h;
-    if (a.write_macro) {
+    if (write_macro) {
         mac[cell] = m.rho.x;
         mac[a.g.n + cell] = m.rho.y;
         mac[2 * a.g.n + cell] = R.ux;
         mac[3 * a.g.n + cell] = R.uy;
         mac[4 * a.g.n + cell] = R.uz;
+    }
+}
+
+template <class S, int EQ>
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c2(StepArgs a) {
+    __shared__ float2 qs[kQ - 1][kCollideThreads];
+    const int b = blockIdx.y;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
+    collide_cell2<S, EQ, false>(a, b, k, a.write_macro, qs);
+}
+
+// ---------------------------------------------------------------- persistent update
+// LBM_KERNEL_PERSISTENT: one cooperative launch runs n updates of the compact
+// two-pass update.  Every block strides over all (instance, cell) items of the
+// batch: the density pass, a grid-wide barrier, the collision pass, a barrier,
+// and so on; the ping-pong buffers swap every update.  Data written earlier in
+// the launch (f, psi, the reference densities) is read through L2.  It serves
+// small instances and batches of them, where two launches per update cost more
+// than the work.
+constexpr int kPersistThreads = kCollideThreads;
+constexpr int kPersistMaxUpdates = 1 << 20;      // per launch: the barrier counter stays below 2^32
+constexpr long long kBarrierCycles = 4000000000LL;  // about 2 s of SM clock
+
+// Grid-wide barrier of a cooperative launch, with a bound on the wait.  Thread
+// 0 of every block arrives on bar[0] and waits until all blocks of this phase
+// have arrived (and `missing` more, which the failure test sets), until
+// another block has given up (bar[1] set), or for `cycles` of its SM clock,
+// after which it sets bar[1] itself.  Returns false when the launch must end
+// (the host then reports LBM_ERR_TIMEOUT).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned phase, long long cycles, unsigned missing) {
+    __shared__ int go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned target = phase * gridDim.x + missing;
+        const long long t0 = clock64();
+        int ok = 1;
+        while (*(volatile unsigned *)bar < target) {
+            if (*(volatile unsigned *)(bar + 1)) {
+                ok = 0;
+                break;
+            }
+            if (clock64() - t0 > cycles) {
+                atomicExch(bar + 1, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        go = ok;
+    }
+    __syncthreads();
+    return go != 0;
+}
+
+// a0: the buffers of the first update (f_in -> f_out), a1: swapped
+template <class S, int EQ>
+__global__ void __launch_bounds__(kPersistThreads) k_persist_c(StepArgs a0, StepArgs a1, int n, int write_macro,
+                                                               unsigned *bar) {
+    __shared__ float2 qs[kQ - 1][kPersistThreads];
+    // both argument sets in shared memory, read by every thread
+    __shared__ __align__(16) unsigned char sa_raw[2 * sizeof(StepArgs)];
+    StepArgs *sa = reinterpret_cast<StepArgs *>(sa_raw);
+    if (threadIdx.x == 0) {
+        memcpy(&sa[0], &a0, sizeof(StepArgs));
+        memcpy(&sa[1], &a1, sizeof(StepArgs));
+    }
+    __syncthreads();
+    const long long items = (long long)a0.batch * a0.kmax;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned phase = 0;
+    for (int u = 0; u < n; ++u) {
+        const StepArgs &a = sa[u & 1];
+        for (long long j = first; j < items; j += stride) {
+            const int b = (int)(j / a.kmax);
+            const uint32_t k = (uint32_t)(j - (long long)b * a.kmax);
+            if (k < (uint32_t)__ldg(a.list_count + b)) psi_cell<S, false, true>(a, b, k);
+        }
+        if (!grid_barrier(bar, ++phase, a.bar_cycles, a.bar_missing)) return;
+        const int wm = (write_macro && u == n - 1) ? 1 : 0;
+        for (long long j = first; j < items; j += stride) {
+            const int b = (int)(j / a.kmax);
+            const uint32_t k = (uint32_t)(j - (long long)b * a.kmax);
+            if (k < (uint32_t)__ldg(a.list_count + b)) collide_cell2<S, EQ, true>(a, b, k, wm, qs);
+        }
+        if (!grid_barrier(bar, ++phase, a.bar_cycles, a.bar_missing)) return;
+    }
+}
+
+// n updates in cooperative launches of at most kPersistMaxUpdates each, as
+// many blocks as fit on the GPU at once (none idle waiting for a slot, which
+// the barriers need) but no more than the items.  Variants: eq_order and
+// reg_order (wall slip is refused on the host).
+template <class S>
+cudaError_t launch_persist_t(const StepArgs &a, int n) {
+    if constexpr (!packed_pairs<S>()) {
+        return cudaErrorNotSupported;
+    } else {
+        cudaError_t e = cudaSuccess;
+        auto run = [&](auto v) {
+            constexpr int EQ = decltype(v)::value;
+            const void *kern = (const void *)k_persist_c<S, EQ>;
+            int dev = 0, sms = 0, per_sm = 0;
+            e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, 0);
+            if (e != cudaSuccess) return;
+            if (per_sm < 1) {
+                e = cudaErrorLaunchOutOfResources;
+                return;
+            }
+            const long long items = (long long)a.batch * a.kmax;
+            long long want = (items + kPersistThreads - 1) / kPersistThreads;
+            if (want > (long long)per_sm * sms) want = (long long)per_sm * sms;
+            if (want < 1) want = 1;
+            StepArgs sw = a;
+            sw.f_in = a.f_out;
+            sw.f_out = const_cast<void *>(a.f_in);
+            sw.ref_in = a.ref_out;
+            sw.ref_out = const_cast<Ref *>(a.ref_in);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)want, 1, 1);
+            cfg.blockDim = dim3(kPersistThreads, 1, 1);
+            cfg.stream = a.stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            record_event(a, 0);
+            for (int done = 0; done < n && e == cudaSuccess;) {
+                const int chunk = n - done < kPersistMaxUpdates ? n - done : kPersistMaxUpdates;
+                const int wm = done + chunk == n ? a.write_macro : 0;
+                e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), a.stream);
+                if (e == cudaSuccess)
+                    e = cudaLaunchKernelEx(&cfg, k_persist_c<S, EQ>, (done & 1) ? sw : a, (done & 1) ? a : sw, chunk,
+                                           wm, a.bar);
+                done += chunk;
+            }
+            record_event(a, 1);
+        };
+        switch (collide_variant(a) & 3) {
+        case 0: run(std::integral_constant<int, 0>{}); break;
+        case 1: run(std::integral_constant<int, 1>{}); break;
+        case 2: run(std::integral_constant<int, 2>{}); break;
+        default: run(std::integral_constant<int, 3>{}); break;
+        }
+        return e;
     }
 }
 

@@ -16,6 +16,9 @@ struct StepArgs {
     int eq_order, wall_model, write_macro;
     int reg_order;     // 2 or 3 (0 is taken as 2)
     int slip;          // 1: some instance has wall slip (the pulls blend in specular reflection)
+    unsigned *bar = nullptr;  // persistent update: barrier counter and give-up flag (2 words)
+    long long bar_cycles = 0; // its barriers' bound on a wait, in SM clock cycles
+    unsigned bar_missing = 0; // arrivals its barriers wait for beyond the grid (failure test: > 0)
     int batch;
     Grid g;
     const void *f_in;
@@ -100,6 +103,7 @@ cudaError_t launch_fused(const StepArgs &a, int tile, int zchunk);
 int fused_tile_count();
 // nsteps updates in one persistent launch, one thread-block cluster per instance
 cudaError_t launch_cluster(const StepArgs &a, int nsteps);
+cudaError_t launch_persist(const StepArgs &a, int nsteps);
 int cluster_size_for(long long n);
 cudaError_t launch_init(const InitArgs &a);
 cudaError_t launch_links(const uint8_t *type, uint32_t *link, const Grid &g, int batch, cudaStream_t s);

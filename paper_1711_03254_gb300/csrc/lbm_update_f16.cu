@@ -6,5 +6,6 @@ namespace lbm {
 
 template cudaError_t launch_two_pass_t<__half>(const StepArgs &);
 template cudaError_t launch_compact_t<__half>(const StepArgs &, int);
+template cudaError_t launch_persist_t<__half>(const StepArgs &, int);
 
 }  // namespace lbm

@@ -6,5 +6,6 @@ namespace lbm {
 
 template cudaError_t launch_two_pass_t<float>(const StepArgs &);
 template cudaError_t launch_compact_t<float>(const StepArgs &, int);
+template cudaError_t launch_persist_t<float>(const StepArgs &, int);
 
 }  // namespace lbm

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
 LBM_FP64, LBM_FP32, LBM_FP32_F16S, LBM_FP32_BF16S = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP32_F16S, "bf16s": LBM_FP32_BF16S}
 LBM_KERNEL_AUTO, LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED, LBM_KERNEL_CLUSTER = 0, 1, 2, 3
-KERNELS = {"auto": 0, "two_pass": 1, "fused": 2, "cluster": 3, "compact": 4, "fused_compact": 5}
+KERNELS = {"auto": 0, "two_pass": 1, "fused": 2, "cluster": 3, "compact": 4, "fused_compact": 5, "persistent": 6}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM", 4: "LBM_ERR_DIVERGED",
           5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 
@@ -85,9 +85,11 @@ def library() -> ctypes.CDLL:
         L.lbm_set_params.argtypes = [vp, ctypes.POINTER(lbm_instance_params)]
         L.lbm_plane_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
         L.lbm_plane_copy.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
+        L.lbm_set_barrier_test.argtypes = [vp, ctypes.c_longlong, ctypes.c_uint]
         for name in ("lbm_create", "lbm_set_geometry", "lbm_set_fields", "lbm_step", "lbm_get_fields",
                      "lbm_reduce", "lbm_get_distributions", "lbm_set_distributions", "lbm_get_state", "lbm_set_state", "lbm_set_stream", "lbm_set_kernel", "lbm_set_tiling", "lbm_autotune", "lbm_run_to_steady",
-                     "lbm_set_allocator", "lbm_step_part", "lbm_plane_bytes", "lbm_plane_copy", "lbm_set_params"):
+                     "lbm_set_allocator", "lbm_step_part", "lbm_plane_bytes", "lbm_plane_copy", "lbm_set_params",
+                     "lbm_set_barrier_test"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -215,6 +217,10 @@ def lbm_set_state(ctx, state: bytes):
 
 def lbm_set_stream(ctx, stream_handle: int):
     return _check(library().lbm_set_stream(ctx, ctypes.c_void_p(int(stream_handle)) if stream_handle else None), ctx)
+
+
+def lbm_set_barrier_test(ctx, wait_cycles: int, missing: int):
+    return _check(library().lbm_set_barrier_test(ctx, int(wait_cycles), int(missing)), ctx)
 
 
 def lbm_set_kernel(ctx, kernel):

@@ -553,8 +553,12 @@ def test_compact_limits_fall_back(lbm):
     assert e.value.status == 1
     small = lbm.Sim(64, 64, 16, [dict(tau=(1.0, 1.0), G=-1.8)], precision="fp32")
     small.set_geometry(np.zeros((1, 16, 64, 64), np.uint8))
-    assert lbm.lbm_resolved_kernel(small.ctx, 10) == "compact"
+    # up to 65,536 non-solid cells AUTO steps n >= 8 updates in one persistent launch
+    assert lbm.lbm_resolved_kernel(small.ctx, 10) == "persistent"
     assert lbm.lbm_resolved_kernel(small.ctx, 1) == "compact"
+    larger = lbm.Sim(64, 64, 17, [dict(tau=(1.0, 1.0), G=-1.8)], precision="fp32")
+    larger.set_geometry(np.zeros((1, 17, 64, 64), np.uint8))
+    assert lbm.lbm_resolved_kernel(larger.ctx, 10) == "compact"
 
 
 @pytest.mark.parametrize("precision,bound", [("fp32", 1e-6), ("fp16s", 5e-5), ("bf16s", 5e-3)])
