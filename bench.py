@@ -74,6 +74,9 @@ def alg_bytes_per_cell(part: str, precision: str) -> int:
         # f once each way, reference pairs, packed coordinates and geometry word;
         # psi stays on chip
         return 76 * s + 4 + 4 + 2 * ref
+    if part == "persistent":
+        # each update of the persistent launch: both passes of the compact update
+        return alg_bytes_per_cell("psi", precision) + alg_bytes_per_cell("collide", precision)
     return 76 * s + 4 + 2 * ref  # fused, and each update of a cluster launch
 # DRAM traffic of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its fluid cells),
@@ -139,6 +142,36 @@ def workload(n=N, kind="spheres"):
     except OSError:
         pass
     return t, r1, r2, u
+
+
+# the layered-channel viscosity sweep: 16 instances of 4 x 128 x 4, two layers
+# split at mid-channel, body force 1e-6, viscosity ratios log-spaced from 1 to
+# 1000 with nu_high = 1.7 (so the minimum nu is 0.0017), half with the
+# low-viscosity layer below, half above
+SWEEP_RATIOS = [10 ** (3.0 * k / 7) for k in range(8)]
+
+
+def sweep_case(k):
+    ratio = SWEEP_RATIOS[k % 8]
+    low_first = k < 8
+    nu1, nu2 = (1.7 / ratio, 1.7) if low_first else (1.7, 1.7 / ratio)
+    return dict(tau=(nu1 * 3 + 0.5, nu2 * 3 + 0.5), G=G, g=(1e-6, 0.0, 0.0)), (nu1, nu2)
+
+
+def batch_workload(n, kind):
+    """(cell types, rho1, rho2, u with a leading instance axis, the instances'
+    parameters) of a bench workload; every workload but the sweep is one
+    instance."""
+    if kind == "sweep":
+        from paper_1711_03254_gb300 import workloads as W
+        ts, a, b, v, ps = [], [], [], [], []
+        for k in range(16):
+            p, (nu1, nu2) = sweep_case(k)
+            t, r1, r2, u = W.layered_channel(4, 128, 4, layout="12", wall_comp_nu=nu1, core_comp_nu=nu2, g=1e-6)
+            ts.append(t), a.append(r1), b.append(r2), v.append(u), ps.append(p)
+        return np.stack(ts), np.stack(a), np.stack(b), np.stack(v), ps
+    t, r1, r2, u = workload(n, kind)
+    return t[None], r1[None], r2[None], u[None], [WORKLOAD_PARAMS[kind]]
 
 
 def peaks():
@@ -238,6 +271,29 @@ def cpu_baseline(t, r1, r2, u, target_s=15.0, crop=64, params=None, name="256^3 
             "sample": f"{crop}^3 corner of the {name}, {steps} updates, FP64"}
 
 
+def cpu_baseline_batch(t, r1, r2, u, params, name, target_s=15.0):
+    """The FP64 oracle over all instances of a small batched workload, for
+    as many updates as fit ~target_s."""
+    import oracle
+    oracle.build()
+    B, nz, ny, nx = t.shape
+    sim = oracle.OracleSim(nx, ny, nz, params)
+    sim.set_geometry(t)
+    sim.set_fields(r1, r2, u)
+    sim.step(1)
+    t0 = time.perf_counter()
+    sim.step(2)
+    per = (time.perf_counter() - t0) / 2
+    steps = max(1, int(target_s / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    fluid = int((t != 1).sum())
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": fluid * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"the {name}, all instances, {steps} updates, FP64"}
+
+
 def run_reference(args):
     # rank 0 alone times the oracle; the other ranks leave without work (no
     # process group is needed for that)
@@ -296,7 +352,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=N)
-    ap.add_argument("--workload", default="spheres", choices=["spheres", "droplet", "rough"])
+    ap.add_argument("--workload", default="spheres", choices=["spheres", "droplet", "rough", "sweep"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -308,16 +364,15 @@ def main():
     build.build()
     lbm.use_torch_allocator()
     n = args.size
-    t, r1, r2, u = workload(n, args.workload)
-    nz, ny, nx = t.shape
-    fluid = int((t != 1).sum())
+    t, r1, r2, u, params = batch_workload(n, args.workload)
+    nz, ny, nx = t.shape[1:]
+    fluid = int((t != 1).sum())  # non-solid cells of all instances
     stream = torch.cuda.current_stream()
 
-    par = WORKLOAD_PARAMS[args.workload]
-    sim = lbm.Sim(nx, ny, nz, [par], precision=args.precision, kernel=args.kernel)
+    sim = lbm.Sim(nx, ny, nz, params, precision=args.precision, kernel=args.kernel)
     lbm.lbm_set_stream(sim.ctx, stream.cuda_stream)
-    sim.set_geometry(t[None])
-    sim.set_fields(r1[None], r2[None], u[None])
+    sim.set_geometry(t)
+    sim.set_fields(r1, r2, u)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     red0 = sim.reduce(allow_diverged=True)
@@ -339,7 +394,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     ms_max = max_over_ranks(ms, ws)
     red1 = sim.reduce(allow_diverged=True)
-    mass_drift = float(np.max(np.abs(red1[0, :2] - red0[0, :2]) / red0[0, :2]))
+    mass_drift = float(np.max(np.abs(red1[:, :2] - red0[:, :2]) / red0[:, :2]))
 
     mlups = fluid * args.steps * ws / (ms_max / 1e3) / 1e6
     hbm, peak_kind = peaks()
@@ -348,6 +403,8 @@ def main():
     part_ms, part_launches = timing[part]
     strategy = lbm.lbm_resolved_kernel(sim.ctx, args.steps)
     kernel_name = {"psi": "k_psi", "collide": "k_collide", "fused": "k_fused", "cluster": "k_cluster"}[part]
+    if strategy == "persistent":
+        kernel_name = "k_persist_c"
     if strategy == "compact":
         # compact layout: packed-pair update for the FP32-arithmetic storages
         kernel_name += {"psi": "_c", "collide": "_c" if args.precision == "fp64" else "_c2"}[part]
@@ -357,7 +414,8 @@ def main():
     # the roofline's algorithmic figure for the dominant kernel and the step
     method_bytes = 2 * 38 * F_BYTES[args.precision] + 1
     # what this kernel moves at least
-    impl_bytes = alg_bytes_per_cell("fused_compact" if strategy == "fused_compact" else part, args.precision)
+    impl_bytes = alg_bytes_per_cell("fused_compact" if strategy == "fused_compact" else
+                                    ("persistent" if strategy == "persistent" else part), args.precision)
     updates_per_launch = args.steps if part == "cluster" else 1
     avg_s = part_ms / part_launches / 1e3
     achieved = method_bytes * fluid * updates_per_launch / avg_s / 1e9
@@ -407,12 +465,12 @@ def main():
             # page-locked host array (the copies then run as DMA from/to it)
             dt_ = {np.dtype(np.float64): torch.float64, np.dtype(np.uint8): torch.uint8}[a.dtype]
             return torch.empty(a.shape, dtype=dt_, pin_memory=True).numpy()
-        th, r1h, r2h, uh = pinned(t[None]), pinned(r1[None]), pinned(r2[None]), pinned(u[None])
-        th[...], r1h[...], r2h[...], uh[...] = t[None], r1[None], r2[None], u[None]
-        r1b, r2b, ub = pinned(r1[None]), pinned(r2[None]), pinned(u[None])
+        th, r1h, r2h, uh = pinned(t), pinned(r1), pinned(r2), pinned(u)
+        th[...], r1h[...], r2h[...], uh[...] = t, r1, r2, u
+        r1b, r2b, ub = pinned(r1), pinned(r2), pinned(u)
         rates = []
         for _ in range(E2E_SAMPLES):
-            sim2 = lbm.Sim(nx, ny, nz, [par], precision=args.precision, kernel=args.kernel)
+            sim2 = lbm.Sim(nx, ny, nz, params, precision=args.precision, kernel=args.kernel)
             lbm.lbm_set_stream(sim2.ctx, stream.cuda_stream)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -431,9 +489,13 @@ def main():
 
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(t, r1, r2, u, params=par,
-                          name={"spheres": f"{n}^3 packed-sphere workload", "droplet": f"{n}^3 droplet workload",
-                                "rough": f"{2 * n}x{n}x{n} rough channel"}[args.workload])
+        if args.workload == "sweep":
+            cb = cpu_baseline_batch(t, r1, r2, u, params, "16-instance layered-channel sweep 4x128x4")
+        else:
+            cb = cpu_baseline(t[0], r1[0], r2[0], u[0], params=params[0],
+                              name={"spheres": f"{n}^3 packed-sphere workload",
+                                    "droplet": f"{n}^3 droplet workload",
+                                    "rough": f"{2 * n}x{n}x{n} rough channel"}[args.workload])
 
     if rank == 0:
         line = {"metric": "MLUPS (fluid-cell updates per second, 2-comp D3Q19)", "value": round(mlups, 1),
@@ -446,7 +508,10 @@ def main():
                     "droplet": f"periodic droplet {n}^3, R={n // 8}, tau 1/1, G={G}, no walls",
                     "rough": (f"rough channel {2 * n}x{n}x{n}, walls on y and z with seeded bumps <= 4, "
                               f"periodic ends, invading slug nu 0.0017 vs defending nu 1.7 (ratio 1000), "
-                              f"G={G}, rho^s 0.2, g=1e-5 along x, wall model 2")}[args.workload],
+                              f"G={G}, rho^s 0.2, g=1e-5 along x, wall model 2"),
+                    "sweep": (f"viscosity sweep: 16 instances of the two-layer channel 4x128x4 (walls at y, "
+                              f"layers split at mid-channel), ratios 1..1000 log-spaced with nu_high 1.7 "
+                              f"(min nu 0.0017), G={G}, g=1e-6, batched in one context")}[args.workload],
                            "storage": args.precision, "kernel": args.kernel, "strategy": strategy,
                            "fluid_cells": fluid,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},

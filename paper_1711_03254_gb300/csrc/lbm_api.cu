@@ -23,9 +23,10 @@ thread_local std::string g_last_error;
 constexpr double kMaxSpeed = 0.57735026918962576;
 // the persistent cluster kernel loops each thread over cells of its instance
 constexpr long long kClusterMaxCells = 65536;
-// AUTO steps problems of at most this many non-solid cells (summed over the
-// batch) with the persistent update
-constexpr long long kPersistAutoItems = 65536;
+// AUTO runs problems of at most this many non-solid cells (summed over the
+// batch) with the persistent update: stepped from the host, and inside the
+// steady loop's CUDA graphs
+constexpr long long kPersistAutoItems = 65536, kPersistGraphItems = 32768;
 constexpr int kMaxBatch = 32767;
 
 size_t storage_bytes(lbm_precision p) {
@@ -227,13 +228,15 @@ lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
     // memory; where they do not, its layout's two-pass update runs
     if (ctx->kernel == LBM_KERNEL_FUSED_COMPACT) return ctx->fplan.ok ? LBM_KERNEL_FUSED_COMPACT : LBM_KERNEL_COMPACT;
     if (ctx->kernel != LBM_KERNEL_AUTO) return ctx->kernel;
-    // small problems stepped from the host: one cooperative launch for the n
-    // updates beats two launches per update (GB300, FP32, us per update: 16^3
-    // 7.5 against 12.3, 16 x 16^3 11.4 against 14.4; even at 32^3 x 4 and
-    // slower beyond).  Inside the steady loop's CUDA graphs the two-launch
-    // update is the faster one at every size (16^3: 7.1 against 7.9).
-    if (ctx->compact_ok && !ctx->fp64() && !ctx->slip_on() && !ctx->in_graph && n >= 8 &&
-        (long long)ctx->cfg.batch * ctx->list_max <= kPersistAutoItems)
+    // small problems: one cooperative launch for the n updates, each thread
+    // keeping its cell, beats two launches per update (GB300, FP32, us per
+    // update, stepped from the host: 16^3 5.6 against 12.3, 16 x 16^3 9.3
+    // against 14.4, even at 4 x 32^3; in the steady loop's CUDA graphs, where
+    // launches are cheap: 16^3 6.2 against 7.0, 8 x 16^3 7.3 against 8.0, even
+    // at 16 x 16^3)
+    const long long items = (long long)ctx->cfg.batch * ctx->list_max;
+    if (ctx->compact_ok && !ctx->fp64() && !ctx->slip_on() && n >= 8 &&
+        items <= (ctx->in_graph ? kPersistGraphItems : kPersistAutoItems))
         return LBM_KERNEL_PERSISTENT;
     // measured on GB300: the two-pass update on the compact layout beats the
     // dense two-pass one on porous (1.5x) and all-fluid (1.1x) grids, the fused
