@@ -17,7 +17,13 @@ timed region (lbm_timing_begin / lbm_timing_end).  `step_frac` puts the same
 bytes over the whole step, and `kernel_impl_frac` puts the bytes the dominant
 kernel itself must move in this design over its launch time.
 
+Other workloads (--workload): "droplet" (all-fluid periodic box), "rough"
+(the rough channel 2n x n x n with an invading slug), "sweep" (16 instances of
+the two-layer channel 4 x 128 x 4, viscosity ratios to 1000, batched in one
+context: AUTO steps them in one persistent launch).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16s|bf16s]
+                  [--workload spheres|droplet|rough|sweep] [--kernel auto|compact|...]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
 """
 from __future__ import annotations
@@ -144,18 +150,23 @@ def workload(n=N, kind="spheres"):
     return t, r1, r2, u
 
 
-# the layered-channel viscosity sweep: 16 instances of 4 x 128 x 4, two layers
-# split at mid-channel, body force 1e-6, viscosity ratios log-spaced from 1 to
-# 1000 with nu_high = 1.7 (so the minimum nu is 0.0017), half with the
-# low-viscosity layer below, half above
-SWEEP_RATIOS = [10 ** (3.0 * k / 7) for k in range(8)]
+# the layered-channel viscosity sweep: 16 instances of 4 x 128 x 4 (walls at
+# y), viscosity ratio {1, 10, 100, 1000} with the minimum nu 0.0017, the
+# low-viscosity component along the walls or in the core, layouts 1|2|1 and
+# 1|2.  G = -1.8: with both components at nu 0.0017 the layers are unstable at
+# -2.2 (in the oracle too).  Body force 4e-8: at 1e-6 the nu = 0.0017 layers
+# would flow at about the lattice sound speed.
+SWEEP_G, SWEEP_FORCE = -1.8, 4e-8
 
 
-def sweep_case(k):
-    ratio = SWEEP_RATIOS[k % 8]
-    low_first = k < 8
-    nu1, nu2 = (1.7 / ratio, 1.7) if low_first else (1.7, 1.7 / ratio)
-    return dict(tau=(nu1 * 3 + 0.5, nu2 * 3 + 0.5), G=G, g=(1e-6, 0.0, 0.0)), (nu1, nu2)
+def sweep_cases():
+    cases = []
+    for ratio in (1, 10, 100, 1000):
+        for low_at_wall in (True, False):
+            for layout in ("121", "12"):
+                lo, hi = 0.0017, 0.0017 * ratio
+                cases.append((layout,) + ((lo, hi) if low_at_wall else (hi, lo)))
+    return cases
 
 
 def batch_workload(n, kind):
@@ -165,10 +176,11 @@ def batch_workload(n, kind):
     if kind == "sweep":
         from paper_1711_03254_gb300 import workloads as W
         ts, a, b, v, ps = [], [], [], [], []
-        for k in range(16):
-            p, (nu1, nu2) = sweep_case(k)
-            t, r1, r2, u = W.layered_channel(4, 128, 4, layout="12", wall_comp_nu=nu1, core_comp_nu=nu2, g=1e-6)
-            ts.append(t), a.append(r1), b.append(r2), v.append(u), ps.append(p)
+        for layout, nu1, nu2 in sweep_cases():
+            t, r1, r2, u = W.layered_channel(4, 128, 4, layout=layout, wall_comp_nu=nu1, core_comp_nu=nu2,
+                                             g=SWEEP_FORCE)
+            ts.append(t), a.append(r1), b.append(r2), v.append(u)
+            ps.append(dict(tau=(nu1 * 3 + 0.5, nu2 * 3 + 0.5), G=SWEEP_G, g=(SWEEP_FORCE, 0.0, 0.0)))
         return np.stack(ts), np.stack(a), np.stack(b), np.stack(v), ps
     t, r1, r2, u = workload(n, kind)
     return t[None], r1[None], r2[None], u[None], [WORKLOAD_PARAMS[kind]]
@@ -509,9 +521,10 @@ def main():
                     "rough": (f"rough channel {2 * n}x{n}x{n}, walls on y and z with seeded bumps <= 4, "
                               f"periodic ends, invading slug nu 0.0017 vs defending nu 1.7 (ratio 1000), "
                               f"G={G}, rho^s 0.2, g=1e-5 along x, wall model 2"),
-                    "sweep": (f"viscosity sweep: 16 instances of the two-layer channel 4x128x4 (walls at y, "
-                              f"layers split at mid-channel), ratios 1..1000 log-spaced with nu_high 1.7 "
-                              f"(min nu 0.0017), G={G}, g=1e-6, batched in one context")}[args.workload],
+                    "sweep": (f"viscosity sweep: 16 instances of the two-layer channel 4x128x4 (walls at y), "
+                              f"ratio 1/10/100/1000 with min nu 0.0017, low viscosity at the walls or in the "
+                              f"core, layouts 1|2|1 and 1|2, G={SWEEP_G}, g={SWEEP_FORCE}, "
+                              f"batched in one context")}[args.workload],
                            "storage": args.precision, "kernel": args.kernel, "strategy": strategy,
                            "fluid_cells": fluid,
                            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
