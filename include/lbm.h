@@ -79,8 +79,8 @@ typedef enum {
 typedef enum {
     LBM_KERNEL_AUTO = 0,     /* compact when the grid fits its coordinate limits, else two-pass;
                                 for n >= 8 updates of at most 65,536 non-solid cells in all
-                                (32,768 inside lbm_run_to_steady's graphs; FP32 arithmetic, no
-                                wall slip) the persistent update */
+                                (32,768 inside lbm_run_to_steady's graphs; no wall slip) the
+                                persistent update */
     LBM_KERNEL_TWO_PASS = 1, /* density pre-pass, then stream+collide, over the non-solid cells */
     LBM_KERNEL_FUSED = 2,    /* single read of f: z-marching tiles with a recomputed density halo */
     LBM_KERNEL_CLUSTER = 3,  /* persistent: one thread-block cluster per instance, n updates per launch */
@@ -94,7 +94,7 @@ typedef enum {
                                 lbm_resolved_kernel) */
     LBM_KERNEL_PERSISTENT = 6  /* the compact two-pass update, n updates in one cooperative launch
                                 with grid-wide barriers between the passes (for small instances
-                                and batches of them); FP32 arithmetic, no wall slip; a barrier
+                                and batches of them); no wall slip; a barrier
                                 that waits about two seconds gives up, and the next
                                 lbm_reduce, lbm_get_fields or lbm_run_to_steady returns
                                 LBM_ERR_TIMEOUT */

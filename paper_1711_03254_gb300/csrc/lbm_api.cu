@@ -233,9 +233,10 @@ lbm_kernel resolve_kernel(const lbm_ctx *ctx, int n) {
     // update, stepped from the host: 16^3 5.6 against 12.3, 16 x 16^3 9.3
     // against 14.4, even at 4 x 32^3; in the steady loop's CUDA graphs, where
     // launches are cheap: 16^3 6.2 against 7.0, 8 x 16^3 7.3 against 8.0, even
-    // at 16 x 16^3)
+    // at 16 x 16^3; FP64, stepped: 16^3 28.1 against 34.8, the 16-instance
+    // channel sweep 53.2 against 57.4)
     const long long items = (long long)ctx->cfg.batch * ctx->list_max;
-    if (ctx->compact_ok && !ctx->fp64() && !ctx->slip_on() && n >= 8 &&
+    if (ctx->compact_ok && !ctx->slip_on() && n >= 8 &&
         items <= (ctx->in_graph ? kPersistGraphItems : kPersistAutoItems))
         return LBM_KERNEL_PERSISTENT;
     // measured on GB300: the two-pass update on the compact layout beats the
@@ -595,9 +596,8 @@ lbm_status lbm_set_kernel(lbm_ctx *ctx, lbm_kernel kernel) {
     if (!ctx->single_read_ok() && single_read(kernel))
         return ctx->fail(LBM_ERR_ARG,
                          "lbm_set_kernel: reg_order 3 and wall slip run in the TWO_PASS and COMPACT strategies");
-    if (kernel == LBM_KERNEL_PERSISTENT && (!ctx->compact_ok || ctx->fp64() || ctx->slip_on()))
-        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: PERSISTENT needs the compact layout, FP32 arithmetic and no "
-                                      "wall slip");
+    if (kernel == LBM_KERNEL_PERSISTENT && (!ctx->compact_ok || ctx->slip_on()))
+        return ctx->fail(LBM_ERR_ARG, "lbm_set_kernel: PERSISTENT needs the compact layout and no wall slip");
     ctx->kernel = kernel;
     return LBM_OK;
 }
@@ -1147,7 +1147,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps_per_trial, const char *cache_pat
     const bool single_read_ok = ctx->single_read_ok();
     if (ctx->fplan.ok && single_read_ok) cands.push_back({LBM_KERNEL_FUSED_COMPACT, -1, -1});
     if (ctx->g.n <= kClusterMaxCells && single_read_ok) cands.push_back({LBM_KERNEL_CLUSTER, -1, -1});
-    if (ctx->compact_ok && !ctx->fp64() && !ctx->slip_on()) cands.push_back({LBM_KERNEL_PERSISTENT, -1, -1});
+    if (ctx->compact_ok && !ctx->slip_on()) cands.push_back({LBM_KERNEL_PERSISTENT, -1, -1});
     for (int t = 0; single_read_ok && t < fused_tile_count(); ++t) {
         cands.push_back({LBM_KERNEL_FUSED, t, -1});
         for (int z : {8, 16, 32, 64})

@@ -22,6 +22,11 @@ template <> struct Pair<double> {
         a = v.x;
         b = v.y;
     }
+    __device__ static __forceinline__ void load_cg(const P *p, double &a, double &b) {
+        const P v = __ldcg(p);
+        a = v.x;
+        b = v.y;
+    }
     __device__ static __forceinline__ void store(P *p, double a, double b, double, double) { *p = make_double2(a, b); }
     __device__ static __forceinline__ void store_d(P *p, double a, double b) { *p = make_double2(a, b); }
     __device__ static __forceinline__ void load_shared(const P *p, double &a, double &b) {
@@ -161,7 +166,7 @@ __device__ __forceinline__ bool outlet_source(const StepArgs &a, int b, const Co
 
 // Pull the 19 stored pairs of the cell with compact index sk (neighbours nb,
 // geometry word sw) into v0, v1 (bounce-back from SOLID neighbours).
-template <class S>
+template <class S, bool COH = false>
 __device__ __forceinline__ void pull_pairs(const typename Pair<S>::P *__restrict__ f, uint32_t n, uint32_t sk,
                                            const CNbr &nb, uint32_t sw, typename Storage<S>::T (&v0)[kQ],
                                            typename Storage<S>::T (&v1)[kQ]) {
@@ -169,7 +174,10 @@ __device__ __forceinline__ void pull_pairs(const typename Pair<S>::P *__restrict
     for (int i = 0; i < kQ; ++i) {
         const bool bb = (sw >> opp(i)) & 1u;
         const uint32_t idx = bb ? (uint32_t)opp(i) * n + sk : (uint32_t)i * n + nb.src(i);
-        Pair<S>::load(f + idx, v0[i], v1[i]);
+        if constexpr (COH)
+            Pair<S>::load_cg(f + idx, v0[i], v1[i]);
+        else
+            Pair<S>::load(f + idx, v0[i], v1[i]);
     }
 }
 

@@ -51,9 +51,8 @@ __device__ __forceinline__ void psi_cell(const StepArgs &a, int b, uint32_t k, c
                 p0 = d.x;
                 p1 = d.y;
             } else {
-                static_assert(!COH, "the persistent update serves the FP32-arithmetic storages");
                 T v0[kQ], v1[kQ], r0, r1;
-                pull_pairs<S>(f, a.kmax, sk, nb, sw, v0, v1);
+                pull_pairs<S, COH>(f, a.kmax, sk, nb, sw, v0, v1);
                 if constexpr (SLIP) slip_pairs<S>(f, a.kmax, nb, sw, p.slip, v0, v1);
                 ref_pair<S>(a, b, sk, r0, r1);
                 p0 = density_of<T, Storage<S>::shifted>(v0, r0);
@@ -87,15 +86,15 @@ __global__ void __launch_bounds__(kPsiThreads, kPsiBlocks) k_psi_c(StepArgs a) {
     psi_cell<S, SLIP, false>(a, b, k);
 }
 
-template <class S, int EQ>
-__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
+// The body of k_collide_c for the non-solid cell k of instance b (COH and
+// PRE as for collide_cell2).
+template <class S, int EQ, bool COH, bool PRE = false>
+__device__ __forceinline__ void collide_cell(const StepArgs &a, int b, uint32_t k, int write_macro,
+                                             const CompactCell *cell_pre = nullptr, const CNbr *nbr_pre = nullptr) {
     using T = typename Storage<S>::T;
     using V = typename Vec2<T>::V;
     using P = typename Pair<S>::P;
-    const int b = blockIdx.y;
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
-    const CompactCell c = compact_cell(a, b, k);
+    const CompactCell c = PRE ? *cell_pre : compact_cell(a, b, k);
     const uint32_t word = c.word;
     const InstParam<T> &p = ((const InstParam<T> *)a.par)[b];
     const uint32_t n = a.kmax;
@@ -104,8 +103,9 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
     __half2 *rout = (__half2 *)a.ref_out + (size_t)b * n;
     const long long cell = c.x + (long long)a.g.nx * (c.y + (long long)a.g.ny * c.z);
     T *mac = (T *)a.macro + (long long)b * 5 * a.g.n;
-    CNbr own;
-    own.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
+    CNbr own_l;
+    if constexpr (!PRE) own_l.init(c.x, c.y, c.z, k, instance_tab(a, b), a.words, a.g);
+    const CNbr &own = PRE ? *nbr_pre : own_l;
     // psi of both components at the 18 neighbours (own cell where SOLID: masked
     // by the force and never used as a reference there)
     T q0[kQ], q1[kQ];
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
             const uint32_t j = ((word >> i) & 1u) ? k : own.dst(i);
-            const V q = __ldg(psi + j);
+            const V q = ld_data<COH>(psi + j);
             q0[i] = q.x;
             q1[i] = q.y;
         }
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
                            feq_dir<T, EQ>(i, p.rho_in[1], p.u_in[0], p.u_in[1], p.u_in[2], uu), s0, s1);
         }
         if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)p.rho_in[0], (float)p.rho_in[1]);
-        if (a.write_macro) {
+        if (write_macro) {
             mac[cell] = p.rho_in[0];
             mac[a.g.n + cell] = p.rho_in[1];
             mac[2 * a.g.n + cell] = p.u_in[0];
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
     Moments<T> m0, m1;
     auto pull = [&](const CNbr &nb, uint32_t sk, uint32_t sw) {
         T v0[kQ], v1[kQ], r0, r1;
-        pull_pairs<S>(f, n, sk, nb, sw, v0, v1);
+        pull_pairs<S, COH>(f, n, sk, nb, sw, v0, v1);
         if constexpr (has_slip(EQ)) slip_pairs<S>(f, n, nb, sw, p.slip, v0, v1);
         ref_pair<S>(a, b, sk, r0, r1);
         m0 = moments_of<T, Storage<S>::shifted>(v0, r0);
@@ -193,13 +193,21 @@ __global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_co
         Pair<S>::store_d(fo + (size_t)(i + 1) * n + k, a_o, b_o);
     }
     if constexpr (Storage<S>::shifted) rout[k] = __floats2half2_rn((float)m0.rho, (float)m1.rho);
-    if (a.write_macro) {
+    if (write_macro) {
         mac[cell] = m0.rho;
         mac[a.g.n + cell] = m1.rho;
         mac[2 * a.g.n + cell] = R.ux;
         mac[3 * a.g.n + cell] = R.uy;
         mac[4 * a.g.n + cell] = R.uz;
     }
+}
+
+template <class S, int EQ>
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<S>()) k_collide_c(StepArgs a) {
+    const int b = blockIdx.y;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (uint32_t)__ldg(a.list_count + b)) return;
+    collide_cell<S, EQ, false>(a, b, k, a.write_macro);
 }
 
 // k_collide_c2: the update of k_collide_c with both components as packed FP32
@@ -384,7 +392,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned phase, long
 // on one chain of loads, f and psi, instead of three); 4 blocks per SM at 128
 // registers (16^3: 5.6 us per update against 7.5 looking the indices up).
 template <class S, int EQ, bool OWNED>
-__global__ void __launch_bounds__(kPersistThreads, OWNED ? 4 : 1)
+__global__ void __launch_bounds__(kPersistThreads, OWNED ? (sizeof(S) == 8 ? 3 : 4) : 1)
     k_persist_c(StepArgs a0, StepArgs a1, int n, int write_macro, unsigned *bar) {
     __shared__ float2 qs[kQ - 1][kPersistThreads];
     // both argument sets in shared memory, read by every thread
@@ -419,7 +427,12 @@ __global__ void __launch_bounds__(kPersistThreads, OWNED ? 4 : 1)
             if (has) psi_cell<S, false, true, true>(a, b, k, &c, &own);
             if (!grid_barrier(bar, ++phase, a.bar_cycles, a.bar_missing)) return;
             const int wm = (write_macro && u == n - 1) ? 1 : 0;
-            if (has) collide_cell2<S, EQ, true, true>(a, b, k, wm, qs, &c, &own);
+            if (has) {
+                if constexpr (packed_pairs<S>())
+                    collide_cell2<S, EQ, true, true>(a, b, k, wm, qs, &c, &own);
+                else
+                    collide_cell<S, EQ, true, true>(a, b, k, wm, &c, &own);
+            }
             if (!grid_barrier(bar, ++phase, a.bar_cycles, a.bar_missing)) return;
         }
         return;
@@ -436,7 +449,12 @@ __global__ void __launch_bounds__(kPersistThreads, OWNED ? 4 : 1)
         for (long long j = first; j < items; j += stride) {
             const int b = (int)(j / a.kmax);
             const uint32_t k = (uint32_t)(j - (long long)b * a.kmax);
-            if (k < (uint32_t)__ldg(a.list_count + b)) collide_cell2<S, EQ, true>(a, b, k, wm, qs);
+            if (k < (uint32_t)__ldg(a.list_count + b)) {
+                if constexpr (packed_pairs<S>())
+                    collide_cell2<S, EQ, true>(a, b, k, wm, qs);
+                else
+                    collide_cell<S, EQ, true>(a, b, k, wm);
+            }
         }
         if (!grid_barrier(bar, ++phase, a.bar_cycles, a.bar_missing)) return;
     }
@@ -448,9 +466,7 @@ __global__ void __launch_bounds__(kPersistThreads, OWNED ? 4 : 1)
 // reg_order (wall slip is refused on the host).
 template <class S>
 cudaError_t launch_persist_t(const StepArgs &a, int n) {
-    if constexpr (!packed_pairs<S>()) {
-        return cudaErrorNotSupported;
-    } else {
+    {
         cudaError_t e = cudaSuccess;
         auto run = [&](auto v) {
             constexpr int EQ = decltype(v)::value;
