@@ -97,10 +97,10 @@ NCU_TRAFFIC = {
                                 "how": "ncu --set full, one launch at 128^3, scaled by non-solid cells"},
     # the benchmark itself (256^3, 6,710,661 non-solid cells), one launch each,
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum:
-    #   k_collide_c2: 649,627,136 B read + 497,705,728 B written = 171.0 B per cell
-    #   k_psi_c:      595,574,528 B read +  50,471,936 B written =  96.3 B per cell
-    "k_collide_c2/fp16s/spheres": {"bytes_per_fluid_cell": 170.97, "src": "542ef5c29e6be80f",
-                                   "files": COMPACT_SOURCES, "step_bytes_per_fluid_cell": 170.97 + 96.27,
+    #   k_collide_c2: 649,660,672 B read + 497,568,000 B written = 171.0 B per cell
+    #   k_psi_c:      595,477,504 B read +  50,510,080 B written =  96.3 B per cell
+    "k_collide_c2/fp16s/spheres": {"bytes_per_fluid_cell": 170.96, "src": "856ecc299163ec5a",
+                                   "files": COMPACT_SOURCES, "step_bytes_per_fluid_cell": 170.96 + 96.26,
                                    "how": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch at 256^3"},
 }
 # FP64 mode is bound by the FP64 pipe.  Executed FP64 flops per non-solid cell
