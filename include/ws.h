@@ -30,12 +30,25 @@ extern "C" {
 
 /* y = act(conv(x, w) + bias); y is BF16 (y_f32 = 0) or FP32 (y_f32 = 1) with
  * row stride ldy; relu != 0 applies max(., 0); bias may be NULL.  Runs as an
- * implicit GEMM on the tcgen05 tensor cores: 128 positions x all Co output
- * channels per thread block, accumulated in tensor memory.  Additional
- * argument rules: Co <= 256, y 16-byte aligned, ldy a multiple of 8 (BF16)
- * or 4 (FP32). */
+ * implicit GEMM on the tcgen05 tensor cores (M = output positions, N = Co,
+ * K = taps x Ci), accumulated in tensor memory.  Two kernels:
+ *  - resident tiles (k = 3, W <= 254): a thread block owns a run of output
+ *    lines of one plane; TMA loads its input one padded plane at a time and
+ *    the 9 taps of the plane are shifted views of that tile;
+ *  - gathered tiles (k = 1, and k = 3 where no resident plan fits): 128
+ *    positions per block, each tap's rows gathered with 16-byte copies.
+ * Additional argument rules: Co <= 256, y 16-byte aligned, ldy a multiple of
+ * 8 (BF16) or 4 (FP32).  Errors: 1 bad argument (also when the resident
+ * kernel is forced and no plan fits), 2 launch failure or no TMA encoder in
+ * the driver. */
 int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void *y, int ldy, int y_f32, int N,
                   int D, int H, int W, int Ci, int Co, int k, int relu, void *stream);
+
+/* Selects the forward kernel of later ws_conv3d_fwd calls (process-wide):
+ * 0 automatic (resident tiles where a plan fits, else gathered), 1 gathered
+ * tiles always, 2 resident tiles always for k = 3.  Returns the previous
+ * choice, or -1 for an unknown value (nothing changes). */
+int ws_conv3d_fwd_algo(int algo);
 
 /* wf[ci][t][co] = w[co][k^3-1-t][ci]: weights for the data gradient, which is
  * then ws_conv3d_fwd(dy, wf) with Ci and Co exchanged. */

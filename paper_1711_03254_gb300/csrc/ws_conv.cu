@@ -17,6 +17,7 @@
 // Activations are channels-last with a row stride (ld) and a channel offset,
 // so concatenations are views of one buffer.  Channel counts are multiples of
 // 16 (the host checks).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -248,6 +249,217 @@ __global__ void __launch_bounds__(TTHREADS) k_conv_fwd_tc(const bf16 *__restrict
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols));
+    }
+}
+
+// ------------------------------------------------------------------ forward, resident tiles (3x3x3)
+// k_conv3_fwd_res: the same convolution for k = 3 with the input tile held in
+// shared memory instead of gathered per tap.  A block owns the outputs of
+// `by` consecutive lines of one plane.  Its input is loaded plane by plane by
+// TMA: for the K-step (16-channel chunk c, plane offset dz) one box of
+// (by + 2) lines x (W + 2) columns x 8 channels per K half, halo included
+// (outside the volume the tensor map fills zeros), lands as rows of 16 bytes
+// in the order (line, column).  In that layout an output row q = l (W + 2) + x
+// and its input at tap (dy, dx) are a fixed distance apart, dy (W + 2) + dx
+// rows, so the A operand of a tap is the same shared-memory tile seen through
+// a descriptor that starts 16 (dy (W + 2) + dx) bytes further: the 9 taps of a
+// plane cost one load.  The rows between two lines (the x halo) are computed
+// and discarded.  The no-swizzle K-major layout has rows 16 bytes apart
+// within a core matrix and, with a stride byte offset of 128, across core
+// matrices, so any 16-byte start is a valid tile; the two K halves of a chunk
+// are separate boxes one leading byte offset apart.  The weights of the 9 taps
+// of (c, dz) arrive by TMA as [tap][K half][Co rows] tiles.
+//
+// Roles: thread 0 issues the TMA loads into a ring of stages, thread 32
+// issues the MMAs (M = 128 rows per tile, N = Co, K = 16) into one
+// accumulator per 128-row tile in tensor memory and releases each stage with
+// tcgen05.commit; all four warps run the epilogue.  Every wait is bounded; a
+// thread that gives up records it in g_tc_timeout, the MMA thread still
+// commits what it issued and the TMA thread waits for its loads in flight,
+// and the block writes nothing.
+constexpr int RTHREADS = 128;
+
+struct ResPlan {
+    int by, nyt, pitch, ntiles, stages, cols;
+    uint32_t a_half, stage_bytes, tx_bytes;
+};
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
+
+template <bool OUT_F32>
+__global__ void __launch_bounds__(RTHREADS) k_conv3_fwd_res(const __grid_constant__ CUtensorMap xmap,
+                                                           const __grid_constant__ CUtensorMap wmap,
+                                                           const float *__restrict__ bias, void *__restrict__ Y,
+                                                           int ldy, Act a, int Ci, int Co, int relu, ResPlan pl) {
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NS = pl.stages;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + (size_t)NS * pl.stage_bytes);
+    uint64_t *empty = full + NS;
+    uint64_t *done = empty + NS;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+
+    // the tile: lines y0 .. y0 + lt - 1 of plane z of sample n
+    const int yt = blockIdx.x % pl.nyt, zn = blockIdx.x / pl.nyt;
+    const int z = zn % a.D, n = zn / a.D;
+    const int y0 = yt * pl.by, lt = min(pl.by, a.H - y0);
+    const int nt = ((lt - 1) * pl.pitch + a.W + 127) / 128;
+    // K-steps (chunk, dz) over the planes inside the volume
+    const int dz_lo = z == 0 ? 1 : 0, dz_hi = z == a.D - 1 ? 1 : 2, ndz = dz_hi - dz_lo + 1;
+    const int nsteps = (Ci / 16) * ndz;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(pl.cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2 * NS + 1; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])));
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = *tslot;
+    const uint32_t base = smem_u32(sm);
+
+    if (tid == 0) {
+        // TMA producer
+        int issued = 0;
+        for (int s = 0; s < nsteps; ++s) {
+            const int st = s % NS;
+            if (s >= NS && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((s / NS) - 1) & 1))) {
+                atomicExch(abort_flag, 1);
+                break;
+            }
+            const int c = s / ndz, dz = dz_lo + s % ndz;
+            const uint32_t fb = smem_u32(&full[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(pl.tx_bytes)
+                         : "memory");
+            const uint32_t sa = base + (uint32_t)st * pl.stage_bytes, sb = sa + 2 * pl.a_half;
+            tma_load_5d(sa, &xmap, c * 16, -1, y0 - 1, z + dz - 1, n, fb);
+            tma_load_5d(sa + pl.a_half, &xmap, c * 16 + 8, -1, y0 - 1, z + dz - 1, n, fb);
+            for (int t9 = 0; t9 < 9; ++t9)
+                for (int h = 0; h < 2; ++h)
+                    tma_load_3d(sb + (uint32_t)(t9 * 2 + h) * (uint32_t)Co * 16u, &wmap, c * 16 + 8 * h, dz * 9 + t9,
+                                0, fb);
+            issued = s + 1;
+        }
+        // wait for the loads still in flight (the last phase issued on each stage)
+        for (int st = 0; st < NS && st < issued; ++st) {
+            const int last = st + ((issued - 1 - st) / NS) * NS;
+            mbar_wait(smem_u32(&full[st]), (uint32_t)((last / NS) & 1));
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        const uint32_t idesc = umma_idesc_bf16(128, Co);
+        for (int s = 0; s < nsteps; ++s) {
+            const int st = s % NS;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((s / NS) & 1))) {
+                atomicExch(abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t sa = base + (uint32_t)st * pl.stage_bytes, sb = sa + 2 * pl.a_half;
+            for (int j = 0; j < nt; ++j)
+                for (int t9 = 0; t9 < 9; ++t9) {
+                    const int dy = t9 / 3, dx = t9 - 3 * dy;
+                    const uint64_t ad = umma_desc(sa + (uint32_t)(128 * j + dy * pl.pitch + dx) * 16u, pl.a_half, 128);
+                    const uint64_t bd = umma_desc(sb + (uint32_t)(t9 * 2) * (uint32_t)Co * 16u, (uint32_t)Co * 16u, 128);
+                    const uint32_t acc = (s > 0 || t9 > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(j * Co)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&empty[st])));
+        }
+        // arrives once every MMA issued above has finished
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(done)));
+    }
+    __syncwarp();
+    const bool okw = mbar_wait(smem_u32(done), 0u);
+    const bool ok_run = __syncthreads_and(okw) && *(volatile int *)abort_flag == 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+    if (ok_run) {
+        // epilogue: warp w owns accumulator rows (TMEM lanes) 32 w .. 32 w + 31 of every tile
+        for (int j = 0; j < nt; ++j) {
+            const int q = 128 * j + 32 * warp + lane;
+            const int line = q / pl.pitch, x = q - line * pl.pitch;
+            const bool valid = x < a.W && line < lt;
+            const long long row = (((long long)n * a.D + z) * a.H + y0 + line) * a.W + x;
+            for (int c0 = 0; c0 < Co; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * Co + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+                if (valid) {
+                    float o[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        float xv = __uint_as_float(v[e]);
+                        if (bias) xv += bias[c0 + e];
+                        if (relu) xv = fmaxf(xv, 0.f);
+                        o[e] = xv;
+                    }
+                    if (OUT_F32) {
+                        float4 *dst = reinterpret_cast<float4 *>((float *)Y + row * ldy + c0);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            dst[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
+                    } else {
+                        uint4 *dst = reinterpret_cast<uint4 *>((bf16 *)Y + row * ldy + c0);
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            uint4 u;
+                            __nv_bfloat162 h0 = __floats2bfloat162_rn(o[8 * e], o[8 * e + 1]);
+                            __nv_bfloat162 h1 = __floats2bfloat162_rn(o[8 * e + 2], o[8 * e + 3]);
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(o[8 * e + 4], o[8 * e + 5]);
+                            __nv_bfloat162 h3 = __floats2bfloat162_rn(o[8 * e + 6], o[8 * e + 7]);
+                            u.x = *reinterpret_cast<uint32_t *>(&h0);
+                            u.y = *reinterpret_cast<uint32_t *>(&h1);
+                            u.z = *reinterpret_cast<uint32_t *>(&h2);
+                            u.w = *reinterpret_cast<uint32_t *>(&h3);
+                            dst[e] = u;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(pl.cols));
     }
 }
 
@@ -486,6 +698,136 @@ using namespace ws;
 
 static bool bad_channels(int c) { return c < 16 || (c % 16) != 0; }
 
+// forward kernel choice: 0 automatic, 1 gathered tiles (k_conv_fwd_tc), 2 resident tiles (k_conv3_fwd_res)
+static int g_fwd_algo = 0;
+
+// cuTensorMapEncodeTiled from the driver, fetched through the runtime (no libcuda link)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 128-row tiles that cover lt output lines of pitch W + 2
+static int res_tiles(int lt, int pitch, int W) { return ((lt - 1) * pitch + W + 127) / 128; }
+
+// Tile plan of k_conv3_fwd_res: the line count `by` with the fewest computed
+// rows per output (discarded halo columns and ragged tiles), among those whose
+// accumulators fit the tensor memory (tiles x Co <= 512 columns) and whose
+// ring of at least two stages fits shared memory, at the most blocks per SM
+// that the tensor memory allows and the ring leaves room for (a block alone on
+// its SM counts 15 % slower for its unhidden epilogue).  Returns false if none
+// fits.
+static constexpr int kSmemPerSM = 233472, kSmemPerBlockMax = 232448, kSmemReserved = 1024;
+static size_t res_smem(const ResPlan &p) { return (size_t)p.stages * p.stage_bytes + 1024 + 8 * (2 * p.stages + 2) + 16; }
+static bool res_plan(int W, int H, int Co, ResPlan &best) {
+    const int pitch = W + 2;
+    if (pitch > 256 || Co > 256) return false;
+    double best_eff = -1.0;
+    for (int by = 1; by <= H && by <= 254; ++by) {
+        const int nt = res_tiles(by, pitch, W);
+        if (nt * Co > 512) break;
+        int cols = 32;
+        while (cols < nt * Co) cols *= 2;
+        int per_sm = 512 / cols;
+        int R = 128 * nt + 2 * pitch + 2;
+        if (R < (by + 2) * pitch) R = (by + 2) * pitch;
+        R = (R + 7) / 8 * 8;
+        ResPlan p;
+        p.by = by;
+        p.nyt = (H + by - 1) / by;
+        p.pitch = pitch;
+        p.ntiles = nt;
+        p.cols = cols;
+        p.a_half = (uint32_t)R * 16u;
+        p.stage_bytes = 2 * p.a_half + 18u * (uint32_t)Co * 16u;
+        p.tx_bytes = 2u * (uint32_t)((by + 2) * pitch) * 16u + 18u * (uint32_t)Co * 16u;
+        // the most stages (2 .. 6) at the most blocks per SM that still fit two
+        int ns = 1;
+        for (; per_sm >= 1; --per_sm) {
+            long long budget = (long long)kSmemPerSM / per_sm - kSmemReserved;
+            if (budget > kSmemPerBlockMax) budget = kSmemPerBlockMax;
+            for (ns = 6; ns >= 2; --ns) {
+                p.stages = ns;
+                if ((long long)res_smem(p) <= budget) break;
+            }
+            if (ns >= 2) break;
+        }
+        if (ns < 2) continue;
+        long long rows = 0;
+        for (int y = 0; y < H; y += by) rows += 128LL * res_tiles(by < H - y ? by : H - y, pitch, W);
+        const double eff = (double)H * W / (double)rows * (per_sm >= 2 ? 1.0 : 0.85);
+        if (eff >= best_eff) {
+            best_eff = eff;
+            best = p;
+        }
+    }
+    return best_eff > 0.0;
+}
+
+// shared memory to request so that no more blocks share an SM than its tensor memory holds
+static size_t res_smem_request(const ResPlan &p) {
+    size_t s = res_smem(p);
+    const int per_sm = 512 / p.cols;
+    const size_t floor_bytes = (size_t)kSmemPerSM / (size_t)(per_sm + 1) - kSmemReserved + 16;
+    if (s < floor_bytes) s = floor_bytes;
+    if (s > (size_t)kSmemPerBlockMax) s = kSmemPerBlockMax;
+    return s;
+}
+
+static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bias, void *y, int ldy, int y_f32,
+                         const Act &a, int Ci, int Co, int relu, cudaStream_t s, const ResPlan &pl) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return 2;
+    CUtensorMap xmap, wmap;
+    const cuuint64_t xdim[5] = {(cuuint64_t)Ci, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D, (cuuint64_t)a.N};
+    const cuuint64_t row = (cuuint64_t)ldx * 2;
+    const cuuint64_t xstr[4] = {row, row * a.W, row * a.W * a.H, row * a.W * a.H * a.D};
+    const cuuint32_t xbox[5] = {8, (cuuint32_t)pl.pitch, (cuuint32_t)(pl.by + 2), 1, 1};
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), xdim, xstr, xbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 2;
+    const cuuint64_t wdim[3] = {(cuuint64_t)Ci, 27, (cuuint64_t)Co};
+    const cuuint64_t wstr[2] = {(cuuint64_t)Ci * 2, (cuuint64_t)Ci * 2 * 27};
+    const cuuint32_t wbox[3] = {8, 1, (cuuint32_t)Co};
+    if (enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(w), wdim, wstr, wbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 2;
+    const size_t smem = res_smem_request(pl);
+    static size_t attr[2] = {0, 0};
+    const int which = y_f32 ? 1 : 0;
+    if (attr[which] < smem) {
+        const cudaError_t e = y_f32 ? cudaFuncSetAttribute(k_conv3_fwd_res<true>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                                    : cudaFuncSetAttribute(k_conv3_fwd_res<false>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return 2;
+        attr[which] = smem;
+    }
+    const long long blocks = (long long)a.N * a.D * pl.nyt;
+    if (blocks > 0x7FFFFFFFLL) return 1;
+    if (y_f32)
+        k_conv3_fwd_res<true><<<(unsigned)blocks, RTHREADS, smem, s>>>(xmap, wmap, bias, y, ldy, a, Ci, Co, relu, pl);
+    else
+        k_conv3_fwd_res<false><<<(unsigned)blocks, RTHREADS, smem, s>>>(xmap, wmap, bias, y, ldy, a, Ci, Co, relu, pl);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
 // byte offsets of the weight gradient's MN-major operand descriptors: between
 // the two core matrices of a K chunk (leading) and between 8-row groups (stride)
 constexpr uint32_t kWgradLbo = 128, kWgradSbo = 256;
@@ -503,6 +845,11 @@ int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void
     Act a{N, D, H, W};
     const long long P = (long long)N * D * H * W;
     cudaStream_t s = (cudaStream_t)stream;
+    if (k == 3 && g_fwd_algo != 1) {
+        ResPlan pl;
+        if (res_plan(W, H, Co, pl)) return conv3_fwd_res(x, ldx, w, bias, y, ldy, y_f32, a, Ci, Co, relu, s, pl);
+        if (g_fwd_algo == 2) return 1;
+    }
     const int cols = Co <= 32 ? 32 : (Co <= 64 ? 64 : (Co <= 128 ? 128 : 256));
     const size_t smem = 2 * (size_t)TKC * (TBM * 32 + (size_t)Co * 32) + 2 * sizeof(uint64_t) + 16;
     static bool attr[2] = {false, false};
@@ -522,6 +869,13 @@ int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void
         k_conv_fwd_tc<false><<<grid, TTHREADS, smem, s>>>((const bf16 *)x, ldx, (const bf16 *)w, bias, y, ldy, a,
                                                           Ci, Co, k, relu, cols);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+int ws_conv3d_fwd_algo(int algo) {
+    if (algo < 0 || algo > 2) return -1;
+    const int prev = g_fwd_algo;
+    g_fwd_algo = algo;
+    return prev;
 }
 
 int ws_conv3d_flip_weights(const void *w, void *wf, int Co, int Ci, int k, void *stream) {

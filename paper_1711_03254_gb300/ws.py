@@ -20,6 +20,7 @@ def _lib():
     if not _sig_done:
         vp, i, ll, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_float
         L.ws_conv3d_fwd.argtypes = [vp, i, vp, vp, vp, i, i, i, i, i, i, i, i, i, i, vp]
+        L.ws_conv3d_fwd_algo.argtypes = [i]
         L.ws_conv3d_flip_weights.argtypes = [vp, vp, i, i, i, vp]
         L.ws_conv3d_bwd_weight.argtypes = [vp, i, vp, i, vp, vp, i, i, i, i, i, i, i, vp]
         L.ws_avgpool2.argtypes = [vp, i, vp, i, i, i, i, i, i, vp]
@@ -31,8 +32,8 @@ def _lib():
         L.ws_adam.argtypes = [vp, vp, vp, vp, vp, ll, f, f, f, f, f, vp]
         L.ws_to_bf16.argtypes = [vp, i, vp, i, ll, i, vp]
         L.ws_tc_status.argtypes = [vp]
-        for name in ("ws_conv3d_fwd", "ws_conv3d_flip_weights", "ws_conv3d_bwd_weight", "ws_avgpool2",
-                     "ws_avgpool2_bwd", "ws_upsample2", "ws_upsample2_bwd", "ws_relu_bwd", "ws_mse_loss", "ws_adam",
+        for name in ("ws_conv3d_fwd", "ws_conv3d_fwd_algo", "ws_conv3d_flip_weights", "ws_conv3d_bwd_weight",
+                     "ws_avgpool2", "ws_avgpool2_bwd", "ws_upsample2", "ws_upsample2_bwd", "ws_relu_bwd", "ws_mse_loss", "ws_adam",
                      "ws_to_bf16", "ws_tc_status"):
             getattr(L, name).restype = ctypes.c_int
         _sig_done = True
@@ -72,6 +73,16 @@ def ws_conv3d_fwd(x, w, bias, y, relu: bool):
                               y.data_ptr(), _ld(y), int(y.dtype == torch.float32), N, D, H, W, Ci, Co, k, int(relu),
                               _stream())
     _ok(rc, "ws_conv3d_fwd")
+
+
+def ws_conv3d_fwd_algo(algo: str) -> str:
+    """Forward kernel of later ws_conv3d_fwd calls: "auto", "gather" or
+    "resident"; returns the previous choice."""
+    names = ("auto", "gather", "resident")
+    prev = _lib().ws_conv3d_fwd_algo(names.index(algo))
+    if prev < 0:
+        raise WsError(f"ws_conv3d_fwd_algo rejected {algo}")
+    return names[prev]
 
 
 def ws_conv3d_flip_weights(w, wf):

@@ -125,3 +125,17 @@ def test_surrogate_rejects_bad_arguments_before_launch(lbm):
     p = 1 << 12  # any non-null, 16-byte aligned value: argument checks come first
     assert L.ws_conv3d_fwd(p, 24, p, None, p, 24, 0, 1, 2, 2, 2, 24, 16, 3, 0, None) == 1
     assert L.ws_conv3d_fwd(p, 16, p, None, p, 512, 0, 1, 2, 2, 2, 16, 512, 3, 0, None) == 1
+
+
+def test_surrogate_forward_kernel_switch(lbm):
+    # process-wide choice of the forward kernel; unknown values change nothing
+    from paper_1711_03254_gb300 import ws
+    L = ws._lib()
+    prev = L.ws_conv3d_fwd_algo(2)
+    assert prev in (0, 1, 2)
+    assert L.ws_conv3d_fwd_algo(3) == -1 and L.ws_conv3d_fwd_algo(-1) == -1
+    assert L.ws_conv3d_fwd_algo(1) == 2
+    assert ws.ws_conv3d_fwd_algo("auto") == "gather"
+    with pytest.raises(ValueError):
+        ws.ws_conv3d_fwd_algo("fastest")
+    L.ws_conv3d_fwd_algo(prev)

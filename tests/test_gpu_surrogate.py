@@ -33,10 +33,21 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
+@pytest.fixture(params=["resident", "gather"])
+def algo(request, env):
+    """Runs a test once with each forward kernel (the data gradient is the
+    forward kernel on flipped weights, so it follows the choice too)."""
+    _, ws, _ = env
+    prev = ws.ws_conv3d_fwd_algo(request.param)
+    yield request.param
+    ws.ws_conv3d_fwd_algo(prev)
+
+
 @pytest.mark.parametrize("shape,Ci,Co,k", [((2, 6, 5, 7), 32, 48, 3), ((1, 9, 4, 3), 16, 16, 3),
                                            ((1, 8, 8, 8), 96, 64, 3), ((2, 5, 6, 7), 48, 32, 1),
-                                           ((1, 8, 8, 12), 64, 224, 3)])
-def test_conv_forward_and_gradients(env, shape, Ci, Co, k):
+                                           ((1, 8, 8, 12), 64, 224, 3), ((1, 3, 21, 64), 32, 32, 3),
+                                           ((2, 3, 13, 64), 16, 96, 3), ((1, 4, 20, 32), 64, 64, 3)])
+def test_conv_forward_and_gradients(env, algo, shape, Ci, Co, k):
     torch, ws, conv = env
     rng = np.random.default_rng(sum(shape) + Ci + Co + k)
     N, D, H, W = shape
@@ -81,6 +92,30 @@ def test_conv_forward_and_gradients(env, shape, Ci, Co, k):
     ws.ws_conv3d_bwd_weight(xv, dyt, dw2, db2, k)
     assert _rel(dw2.cpu().numpy(), 2 * rdw) < 2e-5 and _rel(db2.cpu().numpy(), 2 * rdb) < 2e-5
     assert ws.ws_tc_status() == 0  # no tensor-core wait gave up
+
+
+def test_resident_kernel_refuses_wide_lines(env):
+    """The resident-tile kernel holds a line plus its two halo columns in one
+    TMA box (at most 256 columns): wider lines take the gathered kernel, and
+    forcing the resident one is refused as a bad argument."""
+    torch, ws, conv = env
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(5)
+    x = _bf16_round(torch, rng.standard_normal((1, 2, 2, 300, 16)))
+    w = _bf16_round(torch, rng.standard_normal((16, 3, 3, 3, 16)) * 0.1)
+    xt = torch.from_numpy(x).to(dev).to(torch.bfloat16)
+    wt = torch.from_numpy(w).to(dev).to(torch.bfloat16)
+    y = torch.zeros((1, 2, 2, 300, 16), dtype=torch.float32, device=dev)
+    ws.ws_conv3d_fwd(xt, wt, None, y, relu=False)  # automatic: the gathered kernel
+    assert _rel(y.cpu().numpy(), conv.conv3d_fwd(x, w)) < 2e-5
+    prev = ws.ws_conv3d_fwd_algo("resident")
+    try:
+        with pytest.raises(ws.WsError):
+            ws.ws_conv3d_fwd(xt, wt, None, y, relu=False)
+    finally:
+        ws.ws_conv3d_fwd_algo(prev)
+    assert ws._lib().ws_conv3d_fwd_algo(3) == -1
+    assert ws.ws_tc_status() == 0
 
 
 def test_pool_upsample_relu(env):
