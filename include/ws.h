@@ -56,16 +56,29 @@ int ws_conv3d_flip_weights(const void *w, void *wf, int Co, int Ci, int k, void 
 
 /* dw[co][t][ci] += sum_p dy[p][co] x[p + t - k/2][ci] and db[co] += sum_p dy[p][co]
  * (db may be NULL).  Accumulates: clear dw and db first.  Runs on the tcgen05
- * tensor cores with rows (tap, ci) in tiles of 128 and N = Co <= 256; x and dy
- * 16-byte aligned.  Each chunk of 4096 positions writes its partial sums into a
- * workspace the library holds (grown on demand with cudaMalloc, after draining
- * the stream); the chunks are then added into dw in chunk order, so repeated
- * calls give identical bits.  The workspace is one per process: calls that
+ * tensor cores with N = Co <= 256; x and dy 16-byte aligned.  Two kernels:
+ *  - resident tiles (k = 3, W <= 254, Co <= 160): K = the positions of runs of
+ *    whole lines, M = 128 rows of (tap pair (dz, dy), channel) loaded by TMA
+ *    as line boxes, the three dx taps as shifted views of the same boxes;
+ *  - gathered rows (k = 1, and k = 3 where no resident plan fits): rows
+ *    (tap, ci) in tiles of 128, K = chunks of 4096 positions gathered with
+ *    16-byte copies.
+ * Each block writes its partial sums into a workspace the library holds
+ * (grown on demand with cudaMalloc, after draining the stream); the partials
+ * are then added into dw in a fixed order, so repeated calls give identical
+ * bits.  The workspace is one per process: calls that
  * could overlap on the GPU (other streams, other host threads) race on it, so
  * issue them on one stream.  Errors: 1 bad argument, 2 allocation or launch
  * failure. */
 int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float *dw, float *db, int N, int D, int H,
                          int W, int Ci, int Co, int k, void *stream);
+
+/* Selects the weight-gradient kernel of later ws_conv3d_bwd_weight calls
+ * (process-wide): 0 automatic (resident tiles where a plan fits, else
+ * gathered rows), 1 gathered rows always, 2 resident tiles always for k = 3
+ * (a call that no plan fits then returns 1).  Returns the previous choice, or
+ * -1 for an unknown value (nothing changes). */
+int ws_conv3d_bwd_weight_algo(int algo);
 
 /* 2x2x2 average pooling (D, H, W even) and its adjoint; nearest-neighbour 2x
  * upsampling and its adjoint (sum of the 8 children).  BF16 in and out.  The

@@ -7,8 +7,8 @@ given resolution and batch) this times, with CUDA events on the current stream
 after warm-up, the forward convolution with each forward kernel (resident
 tiles, gathered tiles), the data gradient (the forward kernel on flipped
 weights, Ci and Co exchanged; the first layer has none) and the weight
-gradient, and prints one JSON line per layer and a summary line.  TFLOP/s
-counts 2 Ci Co 27 multiply-adds per output position; `frac` divides by the
+gradient with each of its kernels, and prints one JSON line per layer and a
+summary line.  TFLOP/s counts 2 Ci Co 27 multiply-adds per output position; `frac` divides by the
 measured BF16 tensor peak of MEASURED_PEAKS.json when that file is present.
 Inputs are random BF16 values; the layers are compute-bound, so launches are
 timed back to back without flushing L2.
@@ -18,8 +18,6 @@ from __future__ import annotations
 import argparse
 import json
 import os
-
-import numpy as np
 
 
 def _peak():
@@ -74,7 +72,8 @@ def main(argv=None):
     g = torch.Generator(device=dev)
     g.manual_seed(1)
     peak = _peak()
-    tot = {"fwd_resident": 0.0, "fwd_gather": 0.0, "bwd_data": 0.0, "bwd_weight": 0.0}
+    tot = {"fwd_resident": 0.0, "fwd_gather": 0.0, "bwd_data": 0.0, "bwd_weight_resident": 0.0,
+           "bwd_weight_gather": 0.0}
     flops_tot = {"fwd": 0.0, "bwd_data": 0.0, "bwd_weight": 0.0}
     for name, ci, co, s in layers(args.size):
         N = args.batch
@@ -91,6 +90,7 @@ def main(argv=None):
         flops = 2.0 * N * s ** 3 * 27 * ci * co
         row = dict(layer=name, size=s, batch=N, Ci=ci, Co=co, gflop=round(flops / 1e9, 2))
         prev = ws.ws_conv3d_fwd_algo("auto")
+        prev_w = ws.ws_conv3d_bwd_weight_algo("auto")
         try:
             for algo in ("resident", "gather"):
                 ws.ws_conv3d_fwd_algo(algo)
@@ -105,12 +105,15 @@ def main(argv=None):
                 row["bwd_data_tflops"] = round(flops / ms / 1e9, 1)
                 tot["bwd_data"] += ms
                 flops_tot["bwd_data"] += flops
-            ms = _time(torch, lambda: ws.ws_conv3d_bwd_weight(x, dy, gw, gb, 3), args.reps)
-            row["bwd_weight_ms"] = round(ms, 4)
-            row["bwd_weight_tflops"] = round(flops / ms / 1e9, 1)
-            tot["bwd_weight"] += ms
+            for algo in ("resident", "gather"):
+                ws.ws_conv3d_bwd_weight_algo(algo)
+                ms = _time(torch, lambda: ws.ws_conv3d_bwd_weight(x, dy, gw, gb, 3), args.reps)
+                row[f"bwd_weight_{algo}_ms"] = round(ms, 4)
+                row[f"bwd_weight_{algo}_tflops"] = round(flops / ms / 1e9, 1)
+                tot[f"bwd_weight_{algo}"] += ms
         finally:
             ws.ws_conv3d_fwd_algo(prev)
+            ws.ws_conv3d_bwd_weight_algo(prev_w)
         flops_tot["fwd"] += flops
         flops_tot["bwd_weight"] += flops
         if peak:
@@ -120,7 +123,8 @@ def main(argv=None):
         raise RuntimeError("a tensor-core convolution gave up on a bounded wait")
     summ = dict(summary=True, size=args.size, batch=args.batch, peak_bf16_tflops=peak)
     for key, ms in tot.items():
-        fl = flops_tot["fwd"] if key.startswith("fwd") else flops_tot[key]
+        kind = "fwd" if key.startswith("fwd") else ("bwd_weight" if key.startswith("bwd_weight") else key)
+        fl = flops_tot[kind]
         summ[f"{key}_ms"] = round(ms, 3)
         summ[f"{key}_tflops"] = round(fl / ms / 1e9, 1)
         if peak:

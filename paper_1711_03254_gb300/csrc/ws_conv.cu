@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "../../include/ws.h"
@@ -634,6 +635,174 @@ __global__ void __launch_bounds__(WTTHREADS) k_conv_wgrad_tc(const bf16 *__restr
     }
 }
 
+// ------------------------------------------------------------------ backward weight, resident tiles (3x3x3)
+// k_conv3_wgrad_res: dW[co][t][ci] = sum_p dY[p][co] X[p + t - 1][ci] with the
+// positions of a run of `by` lines as K, M = 128 rows of (tap pair (dz, dy),
+// ci) and N = Co.  Per K-block (by lines y0.. of plane z of sample n) TMA
+// loads, for each (dz, dy) of the block's tile and each 8-channel group, the
+// box of X at lines y0 + dy - 1 .., plane z + dz - 1, columns -1 .. W (one
+// region of 16-byte rows in the order (line, column)), and the box of dY at
+// lines y0 .., columns 0 .. W + 1 (zeros beyond W, so the two columns that
+// pad each line add nothing).  In that order the input of tap dx for the
+// position in row q sits in row q + dx of the X region: the three dx taps are
+// the same regions seen through descriptors 16 dx bytes apart.  Both operands
+// are MN-major (8 channels of one position form a 16-byte row; K pairs 128 B
+// apart, 8-channel groups one region apart).  M holds 128 / ci_blk tap pairs
+// of ci_blk channels; a block owns one such tile of one channel block and a
+// range of K-blocks, accumulates [dx][M][Co] in tensor memory and writes its
+// partial rows part[pb][t * Ci + ci][co]; k_wgrad_sum adds the partials in
+// order.  Rows that TMA never writes (each region's tail, the regions of tap
+// pairs past the ninth) are zeroed once, so they add exact zeros.  Roles,
+// barriers and bounded waits as in k_conv3_fwd_res.
+struct WgPlan {
+    int by, nyb, pitch, ksteps, J, ci_blk, ntile, npb, kpb, stages, cols;
+    uint32_t region, stage_bytes;
+};
+
+__global__ void __launch_bounds__(RTHREADS) k_conv3_wgrad_res(const __grid_constant__ CUtensorMap xmap,
+                                                             const __grid_constant__ CUtensorMap dymap,
+                                                             float *__restrict__ part, Act a, int Ci, int Co,
+                                                             WgPlan pl) {
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NS = pl.stages, G = pl.ci_blk / 8, NB = Co / 8;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + (size_t)NS * pl.stage_bytes);
+    uint64_t *empty = full + NS;
+    uint64_t *done = empty + NS;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+
+    const int pb = blockIdx.x, cb = blockIdx.y / pl.ntile, ti = blockIdx.y % pl.ntile;
+    const int nkb = a.N * a.D * pl.nyb;
+    const int kb0 = pb * pl.kpb, kb1 = min(kb0 + pl.kpb, nkb);
+    const int nsteps = kb1 > kb0 ? kb1 - kb0 : 0;
+    const int nreal = min(pl.J, 9 - ti * pl.J);  // tap pairs of this tile (>= 1)
+    const uint32_t tx = (uint32_t)(nreal * G + NB) * (uint32_t)(pl.by * pl.pitch) * 16u;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(pl.cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2 * NS + 1; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])));
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    {
+        uint4 *z4 = reinterpret_cast<uint4 *>(sm);
+        const uint32_t n16 = (uint32_t)NS * pl.stage_bytes / 16u;
+        for (uint32_t i = tid; i < n16; i += RTHREADS) z4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // the zeros are read by the tensor cores (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = *tslot;
+    const uint32_t base = smem_u32(sm);
+
+    if (tid == 0) {
+        int issued = 0;
+        for (int s = 0; s < nsteps; ++s) {
+            const int st = s % NS;
+            if (s >= NS && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((s / NS) - 1) & 1))) {
+                atomicExch(abort_flag, 1);
+                break;
+            }
+            const int kb = kb0 + s;
+            const int yb = kb % pl.nyb, z = (kb / pl.nyb) % a.D, n = kb / (pl.nyb * a.D);
+            const int y0 = yb * pl.by;
+            const uint32_t fb = smem_u32(&full[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(tx) : "memory");
+            const uint32_t sa = base + (uint32_t)st * pl.stage_bytes;
+            for (int j = 0; j < nreal; ++j) {
+                const int m = ti * pl.J + j, dz = m / 3, dy = m - 3 * dz;
+                for (int g = 0; g < G; ++g)
+                    tma_load_5d(sa + (uint32_t)(j * G + g) * pl.region, &xmap, cb * pl.ci_blk + 8 * g, -1,
+                                y0 + dy - 1, z + dz - 1, n, fb);
+            }
+            for (int g = 0; g < NB; ++g)
+                tma_load_5d(sa + (uint32_t)(16 + g) * pl.region, &dymap, 8 * g, 0, y0, z, n, fb);
+            issued = s + 1;
+        }
+        for (int st = 0; st < NS && st < issued; ++st) {
+            const int last = st + ((issued - 1 - st) / NS) * NS;
+            mbar_wait(smem_u32(&full[st]), (uint32_t)((last / NS) & 1));
+        }
+    } else if (tid == 32) {
+        // MN-major A and B (bits 15, 16), FP32 accumulator, BF16 operands
+        const uint32_t idesc = umma_idesc_bf16(128, Co) | (1u << 15) | (1u << 16);
+        for (int s = 0; s < nsteps; ++s) {
+            const int st = s % NS;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((s / NS) & 1))) {
+                atomicExch(abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t sa = base + (uint32_t)st * pl.stage_bytes, sb = sa + 16u * pl.region;
+            for (int ks = 0; ks < pl.ksteps; ++ks) {
+                const uint64_t bd = umma_desc(sb + (uint32_t)ks * 256u, 128, pl.region);
+                for (int dx = 0; dx < 3; ++dx) {
+                    const uint64_t ad = umma_desc(sa + (uint32_t)(ks * 16 + dx) * 16u, 128, pl.region);
+                    const uint32_t acc = (s > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(dx * Co)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&empty[st])));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(done)));
+    }
+    __syncwarp();
+    const bool okw = mbar_wait(smem_u32(done), 0u);
+    const bool ok_run = __syncthreads_and(okw) && *(volatile int *)abort_flag == 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+    // this thread's accumulator row: tap pair m = ti J + j, channel cb ci_blk + cl
+    const int r = 32 * warp + lane, j = r / pl.ci_blk, cl = r - j * pl.ci_blk, m = ti * pl.J + j;
+    const bool real = m < 9;
+    for (int dx = 0; dx < 3; ++dx) {
+        const int t = (real ? m : 0) * 3 + dx;
+        float *prow = part + ((size_t)pb * 27 * Ci + (size_t)t * Ci + (size_t)(cb * pl.ci_blk + cl)) * Co;
+        for (int c0 = 0; c0 < Co; c0 += 16) {
+            if (ok_run && nsteps > 0) {
+                uint32_t v[16];
+                const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dx * Co + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+                if (real)
+#pragma unroll
+                    for (int e = 0; e < 16; e += 4)
+                        *reinterpret_cast<float4 *>(prow + c0 + e) =
+                            make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
+                                        __uint_as_float(v[e + 3]));
+            } else if (real) {
+                // no K-block here, or a wait gave up (the status flag reports it): zero partials
+                for (int e = 0; e < 16; e += 4) *reinterpret_cast<float4 *>(prow + c0 + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(pl.cols));
+    }
+}
+
 // dW[co][t][ci] += sum over the nk chunks of part[chunk][t * Ci + ci][co], in chunk order
 __global__ void k_wgrad_sum(const float *__restrict__ part, int nk, int rows_pad, int rows, int Co, int KV, int Ci,
                             float *__restrict__ dW) {
@@ -787,20 +956,25 @@ static size_t res_smem_request(const ResPlan &p) {
     return s;
 }
 
+static bool act_map(CUtensorMap *map, const void *t, int ld, const Act &a, int C, int box_x, int box_y) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t dim[5] = {(cuuint64_t)C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D, (cuuint64_t)a.N};
+    const cuuint64_t row = (cuuint64_t)ld * 2;
+    const cuuint64_t str[4] = {row, row * a.W, row * a.W * a.H, row * a.W * a.H * a.D};
+    const cuuint32_t box[5] = {8, (cuuint32_t)box_x, (cuuint32_t)box_y, 1, 1};
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(t), dim, str, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bias, void *y, int ldy, int y_f32,
                          const Act &a, int Ci, int Co, int relu, cudaStream_t s, const ResPlan &pl) {
     EncodeTiledFn enc = encode_tiled();
-    if (!enc) return 2;
     CUtensorMap xmap, wmap;
-    const cuuint64_t xdim[5] = {(cuuint64_t)Ci, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D, (cuuint64_t)a.N};
-    const cuuint64_t row = (cuuint64_t)ldx * 2;
-    const cuuint64_t xstr[4] = {row, row * a.W, row * a.W * a.H, row * a.W * a.H * a.D};
-    const cuuint32_t xbox[5] = {8, (cuuint32_t)pl.pitch, (cuuint32_t)(pl.by + 2), 1, 1};
-    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
-    if (enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), xdim, xstr, xbox, ones,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return 2;
+    if (!enc || !act_map(&xmap, x, ldx, a, Ci, pl.pitch, pl.by + 2)) return 2;
+    const cuuint32_t ones[3] = {1, 1, 1};
     const cuuint64_t wdim[3] = {(cuuint64_t)Ci, 27, (cuuint64_t)Co};
     const cuuint64_t wstr[2] = {(cuuint64_t)Ci * 2, (cuuint64_t)Ci * 2 * 27};
     const cuuint32_t wbox[3] = {8, 1, (cuuint32_t)Co};
@@ -825,6 +999,100 @@ static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bia
         k_conv3_fwd_res<true><<<(unsigned)blocks, RTHREADS, smem, s>>>(xmap, wmap, bias, y, ldy, a, Ci, Co, relu, pl);
     else
         k_conv3_fwd_res<false><<<(unsigned)blocks, RTHREADS, smem, s>>>(xmap, wmap, bias, y, ldy, a, Ci, Co, relu, pl);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+// weight-gradient kernel choice: 0 automatic, 1 gathered rows (k_conv_wgrad_tc), 2 resident tiles (k_conv3_wgrad_res)
+static int g_wgrad_algo = 0;
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            n = 0;
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+static size_t wg_smem(const WgPlan &p) { return (size_t)p.stages * p.stage_bytes + 1024 + 8 * (2 * p.stages + 2) + 16; }
+
+// Plan of k_conv3_wgrad_res: the widest channel block (128, 64, 32 or 16
+// channels dividing Ci; M = 128 rows hold 128 / ci_blk tap pairs), K-blocks
+// of about 256 rows (whole lines of W + 2 columns), the most stages (2 .. 4)
+// at the most blocks per SM that the tensor memory (3 Co columns) allows, and
+// about four blocks per SM in all.  Returns false where no plan fits (W > 254,
+// Co > 160, or not even two stages).
+static bool wg_plan(const Act &a, int Ci, int Co, WgPlan &p) {
+    const int pitch = a.W + 2;
+    if (pitch > 256 || 3 * Co > 512) return false;
+    int cb = 128;
+    while (cb > 16 && Ci % cb) cb /= 2;
+    if (Ci % cb) return false;
+    p.ci_blk = cb;
+    p.J = 128 / cb;
+    p.ntile = (9 + p.J - 1) / p.J;
+    p.pitch = pitch;
+    p.cols = 32;
+    while (p.cols < 3 * Co) p.cols *= 2;
+    bool found = false;
+    for (int by = std::max(1, std::min(a.H, 256 / pitch)); by >= 1 && !found; --by) {
+        p.by = by;
+        p.ksteps = (by * pitch + 15) / 16;
+        const int rb = (p.ksteps * 16 + 2 + 7) / 8 * 8;
+        p.region = (uint32_t)rb * 16u;
+        p.stage_bytes = (uint32_t)(16 + Co / 8) * p.region;
+        for (int per_sm = 512 / p.cols; per_sm >= 1 && !found; --per_sm) {
+            long long budget = (long long)kSmemPerSM / per_sm - kSmemReserved;
+            if (budget > kSmemPerBlockMax) budget = kSmemPerBlockMax;
+            for (int ns = 4; ns >= 2; --ns) {
+                p.stages = ns;
+                if ((long long)wg_smem(p) <= budget) {
+                    found = true;
+                    break;
+                }
+            }
+        }
+    }
+    if (!found) return false;
+    p.nyb = (a.H + p.by - 1) / p.by;
+    const long long nkb = (long long)a.N * a.D * p.nyb;
+    if (nkb > 0x7FFFFFFFLL) return false;
+    const int by_blocks = (Ci / cb) * p.ntile;
+    long long npb = (4LL * sm_count() + by_blocks - 1) / by_blocks;
+    if (npb < 1) npb = 1;
+    if (npb > nkb) npb = nkb;
+    p.kpb = (int)((nkb + npb - 1) / npb);
+    p.npb = (int)((nkb + p.kpb - 1) / p.kpb);
+    return by_blocks <= 65535;
+}
+
+static size_t wg_smem_request(const WgPlan &p) {
+    size_t s = wg_smem(p);
+    const int per_sm = 512 / p.cols;
+    const size_t floor_bytes = (size_t)kSmemPerSM / (size_t)(per_sm + 1) - kSmemReserved + 16;
+    if (s < floor_bytes) s = floor_bytes;
+    if (s > (size_t)kSmemPerBlockMax) s = kSmemPerBlockMax;
+    return s;
+}
+
+// the weight-gradient partials of k_conv3_wgrad_res into part [npb][27 Ci][Co]
+static int conv3_wgrad_res(const void *x, int ldx, const void *dy, int ldy, float *part, const Act &a, int Ci, int Co,
+                           cudaStream_t s, const WgPlan &pl) {
+    CUtensorMap xmap, dymap;
+    if (!act_map(&xmap, x, ldx, a, Ci, pl.pitch, pl.by) || !act_map(&dymap, dy, ldy, a, Co, pl.pitch, pl.by)) return 2;
+    const size_t smem = wg_smem_request(pl);
+    static size_t attr = 0;
+    if (attr < smem) {
+        if (cudaFuncSetAttribute(k_conv3_wgrad_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 2;
+        attr = smem;
+    }
+    const dim3 grid((unsigned)pl.npb, (unsigned)((Ci / pl.ci_blk) * pl.ntile), 1);
+    k_conv3_wgrad_res<<<grid, RTHREADS, smem, s>>>(xmap, dymap, part, a, Ci, Co, pl);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -878,6 +1146,13 @@ int ws_conv3d_fwd_algo(int algo) {
     return prev;
 }
 
+int ws_conv3d_bwd_weight_algo(int algo) {
+    if (algo < 0 || algo > 2) return -1;
+    const int prev = g_wgrad_algo;
+    g_wgrad_algo = algo;
+    return prev;
+}
+
 int ws_conv3d_flip_weights(const void *w, void *wf, int Co, int Ci, int k, void *stream) {
     if (!w || !wf || Co < 1 || Ci < 1 || (k != 1 && k != 3)) return 1;
     const int KV = k * k * k;
@@ -909,9 +1184,30 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
         attr = true;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const int rows = KV * Ci, tiles = (rows + 127) / 128;
     const long long bias_blocks = (P + 8 * 64 - 1) / (8 * 64);
     const int nbb = (int)(bias_blocks < 1024 ? bias_blocks : 1024);
+    if (k == 3 && g_wgrad_algo != 1) {
+        WgPlan pl;
+        if (wg_plan(a, Ci, Co, pl)) {
+            const size_t wpart = (size_t)pl.npb * 27 * Ci * Co;
+            float *ws_buf = grad_workspace((wpart + (size_t)nbb * Co) * sizeof(float), s);
+            if (!ws_buf) return 2;
+            const int rc = conv3_wgrad_res(x, ldx, dy, ldy, ws_buf, a, Ci, Co, s, pl);
+            if (rc) return rc;
+            const long long elems = 27LL * Ci * Co;
+            k_wgrad_sum<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(ws_buf, pl.npb, 27 * Ci, 27 * Ci, Co, 27, Ci,
+                                                                        dw);
+            if (db) {
+                float *bpart = ws_buf + wpart;
+                const dim3 g2((unsigned)nbb, (unsigned)((Co + 31) / 32), 1);
+                k_bias_grad<<<g2, 256, 0, s>>>((const bf16 *)dy, ldy, bpart, P, Co);
+                k_bias_sum<<<(Co + 255) / 256, 256, 0, s>>>(bpart, nbb, Co, db);
+            }
+            return cudaGetLastError() == cudaSuccess ? 0 : 2;
+        }
+        if (g_wgrad_algo == 2) return 1;
+    }
+    const int rows = KV * Ci, tiles = (rows + 127) / 128;
     // partial tiles [nk][tiles * 128][Co], then the bias partials [nbb][Co]
     const size_t wpart = (size_t)nk * tiles * 128 * Co;
     float *ws_buf = grad_workspace((wpart + (size_t)nbb * Co) * sizeof(float), s);

@@ -21,6 +21,7 @@ def _lib():
         vp, i, ll, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_float
         L.ws_conv3d_fwd.argtypes = [vp, i, vp, vp, vp, i, i, i, i, i, i, i, i, i, i, vp]
         L.ws_conv3d_fwd_algo.argtypes = [i]
+        L.ws_conv3d_bwd_weight_algo.argtypes = [i]
         L.ws_conv3d_flip_weights.argtypes = [vp, vp, i, i, i, vp]
         L.ws_conv3d_bwd_weight.argtypes = [vp, i, vp, i, vp, vp, i, i, i, i, i, i, i, vp]
         L.ws_avgpool2.argtypes = [vp, i, vp, i, i, i, i, i, i, vp]
@@ -33,7 +34,7 @@ def _lib():
         L.ws_to_bf16.argtypes = [vp, i, vp, i, ll, i, vp]
         L.ws_tc_status.argtypes = [vp]
         for name in ("ws_conv3d_fwd", "ws_conv3d_fwd_algo", "ws_conv3d_flip_weights", "ws_conv3d_bwd_weight",
-                     "ws_avgpool2", "ws_avgpool2_bwd", "ws_upsample2", "ws_upsample2_bwd", "ws_relu_bwd", "ws_mse_loss", "ws_adam",
+                     "ws_conv3d_bwd_weight_algo", "ws_avgpool2", "ws_avgpool2_bwd", "ws_upsample2", "ws_upsample2_bwd", "ws_relu_bwd", "ws_mse_loss", "ws_adam",
                      "ws_to_bf16", "ws_tc_status"):
             getattr(L, name).restype = ctypes.c_int
         _sig_done = True
@@ -82,6 +83,16 @@ def ws_conv3d_fwd_algo(algo: str) -> str:
     prev = _lib().ws_conv3d_fwd_algo(names.index(algo))
     if prev < 0:
         raise WsError(f"ws_conv3d_fwd_algo rejected {algo}")
+    return names[prev]
+
+
+def ws_conv3d_bwd_weight_algo(algo: str) -> str:
+    """Weight-gradient kernel of later ws_conv3d_bwd_weight calls: "auto",
+    "gather" or "resident"; returns the previous choice."""
+    names = ("auto", "gather", "resident")
+    prev = _lib().ws_conv3d_bwd_weight_algo(names.index(algo))
+    if prev < 0:
+        raise WsError(f"ws_conv3d_bwd_weight_algo rejected {algo}")
     return names[prev]
 
 

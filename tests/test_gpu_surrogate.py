@@ -35,12 +35,14 @@ def _rel(a, b):
 
 @pytest.fixture(params=["resident", "gather"])
 def algo(request, env):
-    """Runs a test once with each forward kernel (the data gradient is the
-    forward kernel on flipped weights, so it follows the choice too)."""
+    """Runs a test once with each kernel family, for the forward convolution
+    (the data gradient is the forward kernel on flipped weights, so it follows
+    the choice too) and the weight gradient."""
     _, ws, _ = env
-    prev = ws.ws_conv3d_fwd_algo(request.param)
+    prev = ws.ws_conv3d_fwd_algo(request.param), ws.ws_conv3d_bwd_weight_algo(request.param)
     yield request.param
-    ws.ws_conv3d_fwd_algo(prev)
+    ws.ws_conv3d_fwd_algo(prev[0])
+    ws.ws_conv3d_bwd_weight_algo(prev[1])
 
 
 @pytest.mark.parametrize("shape,Ci,Co,k", [((2, 6, 5, 7), 32, 48, 3), ((1, 9, 4, 3), 16, 16, 3),
@@ -77,7 +79,10 @@ def test_conv_forward_and_gradients(env, algo, shape, Ci, Co, k):
     dx = torch.zeros((N, D, H, W, Ci), dtype=torch.float32, device=dev)
     ws.ws_conv3d_fwd(dyt, wf, None, dx, relu=False)
     assert _rel(dx.cpu().numpy(), conv.conv3d_bwd_data(dy, w)) < 2e-5
-    # weight and bias gradients
+    # weight and bias gradients (the resident weight-gradient kernel holds 3 Co
+    # accumulator columns, so Co > 160 takes the gathered one)
+    if algo == "resident" and Co > 160:
+        ws.ws_conv3d_bwd_weight_algo("auto")
     dw = torch.zeros((Co, k, k, k, Ci), dtype=torch.float32, device=dev)
     db = torch.zeros(Co, dtype=torch.float32, device=dev)
     ws.ws_conv3d_bwd_weight(xv, dyt, dw, db, k)
@@ -95,9 +100,9 @@ def test_conv_forward_and_gradients(env, algo, shape, Ci, Co, k):
 
 
 def test_resident_kernel_refuses_wide_lines(env):
-    """The resident-tile kernel holds a line plus its two halo columns in one
-    TMA box (at most 256 columns): wider lines take the gathered kernel, and
-    forcing the resident one is refused as a bad argument."""
+    """The resident-tile kernels hold a line plus its two halo columns in one
+    TMA box (at most 256 columns): wider lines take the gathered kernels, and
+    forcing the resident ones is refused as a bad argument."""
     torch, ws, conv = env
     dev = torch.device("cuda:0")
     rng = np.random.default_rng(5)
@@ -108,13 +113,19 @@ def test_resident_kernel_refuses_wide_lines(env):
     y = torch.zeros((1, 2, 2, 300, 16), dtype=torch.float32, device=dev)
     ws.ws_conv3d_fwd(xt, wt, None, y, relu=False)  # automatic: the gathered kernel
     assert _rel(y.cpu().numpy(), conv.conv3d_fwd(x, w)) < 2e-5
-    prev = ws.ws_conv3d_fwd_algo("resident")
+    dw = torch.zeros((16, 3, 3, 3, 16), dtype=torch.float32, device=dev)
+    ws.ws_conv3d_bwd_weight(xt, xt, dw, None, 3)  # automatic: the gathered kernel
+    assert _rel(dw.cpu().numpy(), conv.conv3d_bwd_weight(x, x, 3)[0]) < 2e-5
+    prev = ws.ws_conv3d_fwd_algo("resident"), ws.ws_conv3d_bwd_weight_algo("resident")
     try:
         with pytest.raises(ws.WsError):
             ws.ws_conv3d_fwd(xt, wt, None, y, relu=False)
+        with pytest.raises(ws.WsError):
+            ws.ws_conv3d_bwd_weight(xt, xt, dw, None, 3)
     finally:
-        ws.ws_conv3d_fwd_algo(prev)
-    assert ws._lib().ws_conv3d_fwd_algo(3) == -1
+        ws.ws_conv3d_fwd_algo(prev[0])
+        ws.ws_conv3d_bwd_weight_algo(prev[1])
+    assert ws._lib().ws_conv3d_fwd_algo(3) == -1 and ws._lib().ws_conv3d_bwd_weight_algo(3) == -1
     assert ws.ws_tc_status() == 0
 
 
