@@ -651,7 +651,9 @@ __global__ void __launch_bounds__(WTTHREADS) k_conv_wgrad_tc(const bf16 *__restr
 // of ci_blk channels; a block owns one such tile of one channel block and a
 // range of K-blocks, accumulates [dx][M][Co] in tensor memory and writes its
 // partial rows part[pb][t * Ci + ci][co]; k_wgrad_sum adds the partials in
-// order.  Rows that TMA never writes (each region's tail, the regions of tap
+// order.  With bpart given, one unused tap-pair slot of the last tile holds
+// ones instead of X, which makes its rows the bias-gradient partial
+// sum_p dY[p][co] (bpart[pb][co]).  Rows that TMA never writes (each region's tail, the regions of tap
 // pairs past the ninth) are zeroed once, so they add exact zeros.  Roles,
 // barriers and bounded waits as in k_conv3_fwd_res.
 struct WgPlan {
@@ -661,8 +663,8 @@ struct WgPlan {
 
 __global__ void __launch_bounds__(RTHREADS) k_conv3_wgrad_res(const __grid_constant__ CUtensorMap xmap,
                                                              const __grid_constant__ CUtensorMap dymap,
-                                                             float *__restrict__ part, Act a, int Ci, int Co,
-                                                             WgPlan pl) {
+                                                             float *__restrict__ part, float *__restrict__ bpart,
+                                                             Act a, int Ci, int Co, WgPlan pl) {
     extern __shared__ __align__(128) unsigned char sm_raw[];
     unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -691,10 +693,17 @@ __global__ void __launch_bounds__(RTHREADS) k_conv3_wgrad_res(const __grid_const
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
     }
+    // the bias gradient rides in the first unused tap-pair slot of the last
+    // tile of channel block 0: a region of ones gives rows sum_p dY[p][co]
+    const int jb = (bpart && cb == 0 && ti == pl.ntile - 1 && nreal < pl.J) ? nreal : -1;
     {
         uint4 *z4 = reinterpret_cast<uint4 *>(sm);
-        const uint32_t n16 = (uint32_t)NS * pl.stage_bytes / 16u;
-        for (uint32_t i = tid; i < n16; i += RTHREADS) z4[i] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t n16 = (uint32_t)NS * pl.stage_bytes / 16u, per_region = pl.region / 16u;
+        const uint32_t per_stage = pl.stage_bytes / 16u, ones = 0x3F803F80u;  // BF16 1.0 twice
+        for (uint32_t i = tid; i < n16; i += RTHREADS) {
+            const bool one = jb >= 0 && (i % per_stage) / per_region == (uint32_t)(jb * G);
+            z4[i] = one ? make_uint4(ones, ones, ones, ones) : make_uint4(0u, 0u, 0u, 0u);
+        }
     }
     // the zeros are read by the tensor cores (async proxy)
     asm volatile("fence.proxy.async.shared::cta;\n" ::);
@@ -766,8 +775,9 @@ __global__ void __launch_bounds__(RTHREADS) k_conv3_wgrad_res(const __grid_const
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
 
     // this thread's accumulator row: tap pair m = ti J + j, channel cb ci_blk + cl
+    // (the bias row is the first row of slot jb)
     const int r = 32 * warp + lane, j = r / pl.ci_blk, cl = r - j * pl.ci_blk, m = ti * pl.J + j;
-    const bool real = m < 9;
+    const bool real = m < 9, brow = jb >= 0 && j == jb && cl == 0;
     for (int dx = 0; dx < 3; ++dx) {
         const int t = (real ? m : 0) * 3 + dx;
         float *prow = part + ((size_t)pb * 27 * Ci + (size_t)t * Ci + (size_t)(cb * pl.ci_blk + cl)) * Co;
@@ -789,9 +799,16 @@ __global__ void __launch_bounds__(RTHREADS) k_conv3_wgrad_res(const __grid_const
                         *reinterpret_cast<float4 *>(prow + c0 + e) =
                             make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
                                         __uint_as_float(v[e + 3]));
-            } else if (real) {
+                if (brow && dx == 0)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) bpart[(size_t)pb * Co + c0 + e] = __uint_as_float(v[e]);
+            } else {
                 // no K-block here, or a wait gave up (the status flag reports it): zero partials
-                for (int e = 0; e < 16; e += 4) *reinterpret_cast<float4 *>(prow + c0 + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (real)
+                    for (int e = 0; e < 16; e += 4)
+                        *reinterpret_cast<float4 *>(prow + c0 + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (brow && dx == 0)
+                    for (int e = 0; e < 16; ++e) bpart[(size_t)pb * Co + c0 + e] = 0.f;
             }
         }
     }
@@ -1021,9 +1038,10 @@ static size_t wg_smem(const WgPlan &p) { return (size_t)p.stages * p.stage_bytes
 
 // Plan of k_conv3_wgrad_res: the widest channel block (128, 64, 32 or 16
 // channels dividing Ci; M = 128 rows hold 128 / ci_blk tap pairs), K-blocks
-// of about 256 rows (whole lines of W + 2 columns), the most stages (2 .. 4)
-// at the most blocks per SM that the tensor memory (3 Co columns) allows, and
-// about four blocks per SM in all.  Returns false where no plan fits (W > 254,
+// of at most 132 rows (whole lines of W + 2 columns; the best of 2 .. 12 lines
+// measured on the U-Net's 64^3, 32^3 and 16^3 layers within 5 %), the most
+// stages (2 .. 4) at the most blocks per SM that the tensor memory (3 Co
+// columns) allows, and about four blocks per SM in all.  Returns false where no plan fits (W > 254,
 // Co > 160, or not even two stages).
 static bool wg_plan(const Act &a, int Ci, int Co, WgPlan &p) {
     const int pitch = a.W + 2;
@@ -1038,7 +1056,7 @@ static bool wg_plan(const Act &a, int Ci, int Co, WgPlan &p) {
     p.cols = 32;
     while (p.cols < 3 * Co) p.cols *= 2;
     bool found = false;
-    for (int by = std::max(1, std::min(a.H, 256 / pitch)); by >= 1 && !found; --by) {
+    for (int by = std::max(1, std::min(a.H, 132 / pitch)); by >= 1 && !found; --by) {
         p.by = by;
         p.ksteps = (by * pitch + 15) / 16;
         const int rb = (p.ksteps * 16 + 2 + 7) / 8 * 8;
@@ -1079,8 +1097,8 @@ static size_t wg_smem_request(const WgPlan &p) {
 }
 
 // the weight-gradient partials of k_conv3_wgrad_res into part [npb][27 Ci][Co]
-static int conv3_wgrad_res(const void *x, int ldx, const void *dy, int ldy, float *part, const Act &a, int Ci, int Co,
-                           cudaStream_t s, const WgPlan &pl) {
+static int conv3_wgrad_res(const void *x, int ldx, const void *dy, int ldy, float *part, float *bpart, const Act &a,
+                           int Ci, int Co, cudaStream_t s, const WgPlan &pl) {
     CUtensorMap xmap, dymap;
     if (!act_map(&xmap, x, ldx, a, Ci, pl.pitch, pl.by) || !act_map(&dymap, dy, ldy, a, Co, pl.pitch, pl.by)) return 2;
     const size_t smem = wg_smem_request(pl);
@@ -1092,7 +1110,7 @@ static int conv3_wgrad_res(const void *x, int ldx, const void *dy, int ldy, floa
         attr = smem;
     }
     const dim3 grid((unsigned)pl.npb, (unsigned)((Ci / pl.ci_blk) * pl.ntile), 1);
-    k_conv3_wgrad_res<<<grid, RTHREADS, smem, s>>>(xmap, dymap, part, a, Ci, Co, pl);
+    k_conv3_wgrad_res<<<grid, RTHREADS, smem, s>>>(xmap, dymap, part, bpart, a, Ci, Co, pl);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -1189,19 +1207,24 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
     if (k == 3 && g_wgrad_algo != 1) {
         WgPlan pl;
         if (wg_plan(a, Ci, Co, pl)) {
+            // the kernel sums the bias gradient too when its last tile has a free tap-pair slot
+            const bool fold = db && pl.J * pl.ntile > 9;
             const size_t wpart = (size_t)pl.npb * 27 * Ci * Co;
-            float *ws_buf = grad_workspace((wpart + (size_t)nbb * Co) * sizeof(float), s);
+            const size_t bparts = fold ? (size_t)pl.npb : (size_t)nbb;
+            float *ws_buf = grad_workspace((wpart + bparts * Co) * sizeof(float), s);
             if (!ws_buf) return 2;
-            const int rc = conv3_wgrad_res(x, ldx, dy, ldy, ws_buf, a, Ci, Co, s, pl);
+            float *bpart = ws_buf + wpart;
+            const int rc = conv3_wgrad_res(x, ldx, dy, ldy, ws_buf, fold ? bpart : nullptr, a, Ci, Co, s, pl);
             if (rc) return rc;
             const long long elems = 27LL * Ci * Co;
             k_wgrad_sum<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(ws_buf, pl.npb, 27 * Ci, 27 * Ci, Co, 27, Ci,
                                                                         dw);
             if (db) {
-                float *bpart = ws_buf + wpart;
-                const dim3 g2((unsigned)nbb, (unsigned)((Co + 31) / 32), 1);
-                k_bias_grad<<<g2, 256, 0, s>>>((const bf16 *)dy, ldy, bpart, P, Co);
-                k_bias_sum<<<(Co + 255) / 256, 256, 0, s>>>(bpart, nbb, Co, db);
+                if (!fold) {
+                    const dim3 g2((unsigned)nbb, (unsigned)((Co + 31) / 32), 1);
+                    k_bias_grad<<<g2, 256, 0, s>>>((const bf16 *)dy, ldy, bpart, P, Co);
+                }
+                k_bias_sum<<<(Co + 255) / 256, 256, 0, s>>>(bpart, (int)bparts, Co, db);
             }
             return cudaGetLastError() == cudaSuccess ? 0 : 2;
         }
