@@ -59,7 +59,9 @@ int ws_conv3d_flip_weights(const void *w, void *wf, int Co, int Ci, int k, void 
  * tensor cores with N = Co <= 256; x and dy 16-byte aligned.  Two kernels:
  *  - resident tiles (k = 3, W <= 254, Co <= 160): K = the positions of runs of
  *    whole lines, M = 128 rows of (tap pair (dz, dy), channel) loaded by TMA
- *    as line boxes, the three dx taps as shifted views of the same boxes;
+ *    as line boxes, the three dx taps as shifted views of the same boxes; for
+ *    Ci a multiple of 32 and Co <= 48, M = (dz, channel) rows of boxes with
+ *    halo lines instead, and all nine (dy, dx) taps are shifted views;
  *  - gathered rows (k = 1, and k = 3 where no resident plan fits): rows
  *    (tap, ci) in tiles of 128, K = chunks of 4096 positions gathered with
  *    16-byte copies.
@@ -76,8 +78,9 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
 /* Selects the weight-gradient kernel of later ws_conv3d_bwd_weight calls
  * (process-wide): 0 automatic (resident tiles where a plan fits, else
  * gathered rows), 1 gathered rows always, 2 resident tiles always for k = 3
- * (a call that no plan fits then returns 1).  Returns the previous choice, or
- * -1 for an unknown value (nothing changes). */
+ * (a call that no plan fits then returns 1), 3 as 2 but with tap-pair rows
+ * only (never the (dz, channel) rows).  Returns the previous choice, or -1
+ * for an unknown value (nothing changes). */
 int ws_conv3d_bwd_weight_algo(int algo);
 
 /* 2x2x2 average pooling (D, H, W even) and its adjoint; nearest-neighbour 2x

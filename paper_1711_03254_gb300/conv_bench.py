@@ -7,11 +7,12 @@ given resolution and batch) this times, with CUDA events on the current stream
 after warm-up, the forward convolution with each forward kernel (resident
 tiles, gathered tiles), the data gradient (the forward kernel on flipped
 weights, Ci and Co exchanged; the first layer has none) and the weight
-gradient with each of its kernels, and prints one JSON line per layer and a
-summary line.  TFLOP/s counts 2 Ci Co 27 multiply-adds per output position; `frac` divides by the
-measured BF16 tensor peak of MEASURED_PEAKS.json when that file is present.
-Inputs are random BF16 values; the layers are compute-bound, so launches are
-timed back to back without flushing L2.
+gradient with each of its kernels ("resident": the automatic resident choice,
+"pairs": tap-pair rows only, "gather"), and prints one JSON line per layer and
+a summary line.  TFLOP/s counts 2 Ci Co 27 multiply-adds per output position;
+`frac` divides by the measured BF16 tensor peak of MEASURED_PEAKS.json when
+that file is present.  Inputs are random BF16 values; the layers are
+compute-bound, so launches are timed back to back without flushing L2.
 """
 from __future__ import annotations
 
@@ -73,7 +74,7 @@ def main(argv=None):
     g.manual_seed(1)
     peak = _peak()
     tot = {"fwd_resident": 0.0, "fwd_gather": 0.0, "bwd_data": 0.0, "bwd_weight_resident": 0.0,
-           "bwd_weight_gather": 0.0}
+           "bwd_weight_pairs": 0.0, "bwd_weight_gather": 0.0}
     flops_tot = {"fwd": 0.0, "bwd_data": 0.0, "bwd_weight": 0.0}
     for name, ci, co, s in layers(args.size):
         N = args.batch
@@ -105,7 +106,7 @@ def main(argv=None):
                 row["bwd_data_tflops"] = round(flops / ms / 1e9, 1)
                 tot["bwd_data"] += ms
                 flops_tot["bwd_data"] += flops
-            for algo in ("resident", "gather"):
+            for algo in ("resident", "pairs", "gather"):
                 ws.ws_conv3d_bwd_weight_algo(algo)
                 ms = _time(torch, lambda: ws.ws_conv3d_bwd_weight(x, dy, gw, gb, 3), args.reps)
                 row[f"bwd_weight_{algo}_ms"] = round(ms, 4)

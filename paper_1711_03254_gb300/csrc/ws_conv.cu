@@ -820,16 +820,197 @@ __global__ void __launch_bounds__(RTHREADS) k_conv3_wgrad_res(const __grid_const
     }
 }
 
-// dW[co][t][ci] += sum over the nk chunks of part[chunk][t * Ci + ci][co], in chunk order
-__global__ void k_wgrad_sum(const float *__restrict__ part, int nk, int rows_pad, int rows, int Co, int KV, int Ci,
-                            float *__restrict__ dW) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)rows * Co) return;
-    const int row = (int)(e / Co), co = (int)(e - (long long)row * Co);
+// k_conv3_wgrad_dz: the weight gradient for Co <= 48 with all nine in-plane
+// taps as descriptor shifts.  M = 128 rows = 4 slots of 32 channels: slot dz
+// (0, 1, 2) holds, per 8-channel group, the box of X at plane z + dz - 1, lines
+// y0 - 1 .. y0 + by, columns -1 .. W, so that the input of tap (dy, dx) for the
+// position in row q of the dY box sits in row q + dy (W + 2) + dx; slot 3 holds
+// ones in its first group (the bias gradient, channel block 0 only) and reads
+// whatever follows in its other groups (rows that are dropped).  Per K-step
+// nine MMAs, one per (dy, dx), into accumulators [dy][dx][M][Co] (9 Co tensor
+// memory columns).  Each X line is loaded three times (once per dz) instead of
+// nine.  Region order per stage: 12 X regions (slot, group), the ones region,
+// then the dY regions, padded with zero regions up to 16; all regions have
+// the same size, so the 16 M groups are one stride byte offset apart.
+// Partials, bounded waits and roles as in k_conv3_wgrad_res.
+__global__ void __launch_bounds__(RTHREADS) k_conv3_wgrad_dz(const __grid_constant__ CUtensorMap xmap,
+                                                            const __grid_constant__ CUtensorMap dymap,
+                                                            float *__restrict__ part, float *__restrict__ bpart,
+                                                            Act a, int Ci, int Co, WgPlan pl) {
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NS = pl.stages, NB = Co / 8;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + (size_t)NS * pl.stage_bytes);
+    uint64_t *empty = full + NS;
+    uint64_t *done = empty + NS;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
+
+    const int pb = blockIdx.x, cb = blockIdx.y;
+    const int nkb = a.N * a.D * pl.nyb;
+    const int kb0 = pb * pl.kpb, kb1 = min(kb0 + pl.kpb, nkb);
+    const int nsteps = kb1 > kb0 ? kb1 - kb0 : 0;
+    const uint32_t rows_x = (uint32_t)((pl.by + 2) * pl.pitch), rows_y = (uint32_t)(pl.by * pl.pitch);
+    const uint32_t tx = (12u * rows_x + (uint32_t)NB * rows_y) * 16u;
+    const bool fold = bpart && cb == 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(pl.cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2 * NS + 1; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])));
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    {
+        // zeros everywhere (region tails, padding regions), ones in region 12 when folding the bias
+        uint4 *z4 = reinterpret_cast<uint4 *>(sm);
+        const uint32_t n16 = (uint32_t)NS * pl.stage_bytes / 16u, per_region = pl.region / 16u;
+        const uint32_t per_stage = pl.stage_bytes / 16u, ones = 0x3F803F80u;  // BF16 1.0 twice
+        for (uint32_t i = tid; i < n16; i += RTHREADS) {
+            const bool one = fold && (i % per_stage) / per_region == 12u;
+            z4[i] = one ? make_uint4(ones, ones, ones, ones) : make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = *tslot;
+    const uint32_t base = smem_u32(sm);
+
+    if (tid == 0) {
+        int issued = 0;
+        for (int s = 0; s < nsteps; ++s) {
+            const int st = s % NS;
+            if (s >= NS && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((s / NS) - 1) & 1))) {
+                atomicExch(abort_flag, 1);
+                break;
+            }
+            const int kb = kb0 + s;
+            const int yb = kb % pl.nyb, z = (kb / pl.nyb) % a.D, n = kb / (pl.nyb * a.D);
+            const int y0 = yb * pl.by;
+            const uint32_t fb = smem_u32(&full[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(tx) : "memory");
+            const uint32_t sa = base + (uint32_t)st * pl.stage_bytes;
+            for (int dz = 0; dz < 3; ++dz)
+                for (int g = 0; g < 4; ++g)
+                    tma_load_5d(sa + (uint32_t)(dz * 4 + g) * pl.region, &xmap, cb * 32 + 8 * g, -1, y0 - 1,
+                                z + dz - 1, n, fb);
+            for (int g = 0; g < NB; ++g)
+                tma_load_5d(sa + (uint32_t)(13 + g) * pl.region, &dymap, 8 * g, 0, y0, z, n, fb);
+            issued = s + 1;
+        }
+        for (int st = 0; st < NS && st < issued; ++st) {
+            const int last = st + ((issued - 1 - st) / NS) * NS;
+            mbar_wait(smem_u32(&full[st]), (uint32_t)((last / NS) & 1));
+        }
+    } else if (tid == 32) {
+        // MN-major A and B (bits 15, 16), FP32 accumulator, BF16 operands
+        const uint32_t idesc = umma_idesc_bf16(128, Co) | (1u << 15) | (1u << 16);
+        for (int s = 0; s < nsteps; ++s) {
+            const int st = s % NS;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((s / NS) & 1))) {
+                atomicExch(abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t sa = base + (uint32_t)st * pl.stage_bytes, sb = sa + 13u * pl.region;
+            for (int ks = 0; ks < pl.ksteps; ++ks) {
+                const uint64_t bd = umma_desc(sb + (uint32_t)ks * 256u, 128, pl.region);
+                for (int t9 = 0; t9 < 9; ++t9) {
+                    const int dy = t9 / 3, dx = t9 - 3 * dy;
+                    const uint64_t ad =
+                        umma_desc(sa + (uint32_t)(ks * 16 + dy * pl.pitch + dx) * 16u, 128, pl.region);
+                    const uint32_t acc = (s > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(t9 * Co)),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&empty[st])));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(done)));
+    }
+    __syncwarp();
+    const bool okw = mbar_wait(smem_u32(done), 0u);
+    const bool ok_run = __syncthreads_and(okw) && *(volatile int *)abort_flag == 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+    // this thread's accumulator row: slot dz = r / 32, channel cb 32 + r % 32 (the bias row is row 96)
+    const int r = 32 * warp + lane, slot = r >> 5, cl = r & 31;
+    const bool real = slot < 3, brow = fold && r == 96;
+    for (int t9 = 0; t9 < 9; ++t9) {
+        const int t = (real ? slot : 0) * 9 + t9;
+        float *prow = part + ((size_t)pb * 27 * Ci + (size_t)t * Ci + (size_t)(cb * 32 + cl)) * Co;
+        for (int c0 = 0; c0 < Co; c0 += 16) {
+            if (ok_run && nsteps > 0) {
+                uint32_t v[16];
+                const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t9 * Co + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+                if (real)
+#pragma unroll
+                    for (int e = 0; e < 16; e += 4)
+                        *reinterpret_cast<float4 *>(prow + c0 + e) =
+                            make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
+                                        __uint_as_float(v[e + 3]));
+                if (brow && t9 == 0)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) bpart[(size_t)pb * Co + c0 + e] = __uint_as_float(v[e]);
+            } else {
+                if (real)
+                    for (int e = 0; e < 16; e += 4)
+                        *reinterpret_cast<float4 *>(prow + c0 + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (brow && t9 == 0)
+                    for (int e = 0; e < 16; ++e) bpart[(size_t)pb * Co + c0 + e] = 0.f;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(pl.cols));
+    }
+}
+
+// dW[co][t][ci] += sum over the nk chunks of part[chunk][t * Ci + ci][co] in a
+// fixed order: 32 elements per block (threadIdx.x), thread row j = threadIdx.y
+// adds the chunks c = j, j + 8, j + 16, ... in turn, and the eight row sums are
+// then added in row order, so the result does not depend on scheduling.
+constexpr int kSumLanes = 8;
+__global__ void __launch_bounds__(32 * kSumLanes) k_wgrad_sum(const float *__restrict__ part, int nk, int rows_pad,
+                                                              int rows, int Co, int KV, int Ci,
+                                                              float *__restrict__ dW) {
+    __shared__ float sh[kSumLanes][32];
+    const long long e = (long long)blockIdx.x * 32 + threadIdx.x;
+    const bool in = e < (long long)rows * Co;
+    const int row = in ? (int)(e / Co) : 0, co = in ? (int)(e - (long long)row * Co) : 0;
     float s = 0.f;
-    for (int c = 0; c < nk; ++c) s += part[((size_t)c * rows_pad + row) * Co + co];
-    const int t = row / Ci, ci = row - t * Ci;
-    dW[((long long)co * KV + t) * Ci + ci] += s;
+    if (in)
+        for (int c = threadIdx.y; c < nk; c += kSumLanes) s += part[((size_t)c * rows_pad + row) * Co + co];
+    sh[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && in) {
+        float t = 0.f;
+        for (int j = 0; j < kSumLanes; ++j) t += sh[j][threadIdx.x];
+        const int tap = row / Ci, ci = row - tap * Ci;
+        dW[((long long)co * KV + tap) * Ci + ci] += t;
+    }
 }
 
 // bpart[block][co] = this block's sum of dY[p][co]; k_bias_sum adds the blocks in order
@@ -1019,7 +1200,9 @@ static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bia
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
-// weight-gradient kernel choice: 0 automatic, 1 gathered rows (k_conv_wgrad_tc), 2 resident tiles (k_conv3_wgrad_res)
+// weight-gradient kernel choice: 0 automatic, 1 gathered rows (k_conv_wgrad_tc), 2 resident tiles
+// (k_conv3_wgrad_dz where it applies, else k_conv3_wgrad_res), 3 resident tiles without the dz slots
+// (k_conv3_wgrad_res only)
 static int g_wgrad_algo = 0;
 
 static int sm_count() {
@@ -1034,6 +1217,12 @@ static int sm_count() {
     return n;
 }
 
+// blocks of a weight-gradient launch: at most this many full waves (resident
+// blocks x SMs).  One wave measured best on the U-Net's layers (64^3 32->32:
+// 314 TFLOP/s against 262 with two waves and 196 with four): fewer partials to
+// add and no block waiting for a second wave.
+constexpr int kWgWaves = 1;
+
 static size_t wg_smem(const WgPlan &p) { return (size_t)p.stages * p.stage_bytes + 1024 + 8 * (2 * p.stages + 2) + 16; }
 
 // Plan of k_conv3_wgrad_res: the widest channel block (128, 64, 32 or 16
@@ -1041,8 +1230,8 @@ static size_t wg_smem(const WgPlan &p) { return (size_t)p.stages * p.stage_bytes
 // of at most 132 rows (whole lines of W + 2 columns; the best of 2 .. 12 lines
 // measured on the U-Net's 64^3, 32^3 and 16^3 layers within 5 %), the most
 // stages (2 .. 4) at the most blocks per SM that the tensor memory (3 Co
-// columns) allows, and about four blocks per SM in all.  Returns false where no plan fits (W > 254,
-// Co > 160, or not even two stages).
+// columns) allows, and kWgWaves full waves of blocks in all.  Returns false
+// where no plan fits (W > 254, Co > 160, or not even two stages).
 static bool wg_plan(const Act &a, int Ci, int Co, WgPlan &p) {
     const int pitch = a.W + 2;
     if (pitch > 256 || 3 * Co > 512) return false;
@@ -1056,6 +1245,7 @@ static bool wg_plan(const Act &a, int Ci, int Co, WgPlan &p) {
     p.cols = 32;
     while (p.cols < 3 * Co) p.cols *= 2;
     bool found = false;
+    int resident = 1;
     for (int by = std::max(1, std::min(a.H, 132 / pitch)); by >= 1 && !found; --by) {
         p.by = by;
         p.ksteps = (by * pitch + 15) / 16;
@@ -1069,6 +1259,7 @@ static bool wg_plan(const Act &a, int Ci, int Co, WgPlan &p) {
                 p.stages = ns;
                 if ((long long)wg_smem(p) <= budget) {
                     found = true;
+                    resident = per_sm;
                     break;
                 }
             }
@@ -1079,7 +1270,57 @@ static bool wg_plan(const Act &a, int Ci, int Co, WgPlan &p) {
     const long long nkb = (long long)a.N * a.D * p.nyb;
     if (nkb > 0x7FFFFFFFLL) return false;
     const int by_blocks = (Ci / cb) * p.ntile;
-    long long npb = (4LL * sm_count() + by_blocks - 1) / by_blocks;
+    long long npb = (long long)kWgWaves * resident * sm_count() / by_blocks;  // no partial last wave
+    if (npb < 1) npb = 1;
+    if (npb > nkb) npb = nkb;
+    p.kpb = (int)((nkb + npb - 1) / npb);
+    p.npb = (int)((nkb + p.kpb - 1) / p.kpb);
+    return by_blocks <= 65535;
+}
+
+// Plan of k_conv3_wgrad_dz (Ci a multiple of 32, Co <= 48): K-blocks of at
+// most 132 rows as for k_conv3_wgrad_res, regions holding the X box with its
+// two halo lines and the rows the dy, dx shifts reach past the last K-step,
+// the most stages (2 .. 4) that fit at the blocks per SM the tensor memory
+// (9 Co columns) allows, kWgWaves full waves of blocks in all.
+static bool wg_dz_plan(const Act &a, int Ci, int Co, WgPlan &p) {
+    const int pitch = a.W + 2;
+    if (pitch > 256 || Ci % 32 || Co > 48) return false;
+    p.ci_blk = 32;
+    p.J = 4;
+    p.ntile = 1;
+    p.pitch = pitch;
+    p.cols = 32;
+    while (p.cols < 9 * Co) p.cols *= 2;
+    const int nreg = std::max(16, 13 + Co / 8);
+    bool found = false;
+    int resident = 1;
+    for (int by = std::max(1, std::min(a.H, 132 / pitch)); by >= 1 && !found; --by) {
+        if (by + 2 > 256) continue;
+        p.by = by;
+        p.ksteps = (by * pitch + 15) / 16;
+        const int rb = (std::max((by + 2) * pitch, p.ksteps * 16 + 2 * pitch + 2) + 7) / 8 * 8;
+        p.region = (uint32_t)rb * 16u;
+        p.stage_bytes = (uint32_t)nreg * p.region;
+        for (int per_sm = 512 / p.cols; per_sm >= 1 && !found; --per_sm) {
+            long long budget = (long long)kSmemPerSM / per_sm - kSmemReserved;
+            if (budget > kSmemPerBlockMax) budget = kSmemPerBlockMax;
+            for (int ns = 4; ns >= 2; --ns) {
+                p.stages = ns;
+                if ((long long)wg_smem(p) <= budget) {
+                    found = true;
+                    resident = per_sm;
+                    break;
+                }
+            }
+        }
+    }
+    if (!found) return false;
+    p.nyb = (a.H + p.by - 1) / p.by;
+    const long long nkb = (long long)a.N * a.D * p.nyb;
+    if (nkb > 0x7FFFFFFFLL) return false;
+    const int by_blocks = Ci / 32;
+    long long npb = (long long)kWgWaves * resident * sm_count() / by_blocks;  // no partial last wave
     if (npb < 1) npb = 1;
     if (npb > nkb) npb = nkb;
     p.kpb = (int)((nkb + npb - 1) / npb);
@@ -1098,19 +1339,24 @@ static size_t wg_smem_request(const WgPlan &p) {
 
 // the weight-gradient partials of k_conv3_wgrad_res into part [npb][27 Ci][Co]
 static int conv3_wgrad_res(const void *x, int ldx, const void *dy, int ldy, float *part, float *bpart, const Act &a,
-                           int Ci, int Co, cudaStream_t s, const WgPlan &pl) {
+                           int Ci, int Co, cudaStream_t s, const WgPlan &pl, bool dz_slots) {
     CUtensorMap xmap, dymap;
-    if (!act_map(&xmap, x, ldx, a, Ci, pl.pitch, pl.by) || !act_map(&dymap, dy, ldy, a, Co, pl.pitch, pl.by)) return 2;
+    if (!act_map(&xmap, x, ldx, a, Ci, pl.pitch, dz_slots ? pl.by + 2 : pl.by) ||
+        !act_map(&dymap, dy, ldy, a, Co, pl.pitch, pl.by))
+        return 2;
     const size_t smem = wg_smem_request(pl);
-    static size_t attr = 0;
-    if (attr < smem) {
-        if (cudaFuncSetAttribute(k_conv3_wgrad_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
+    static size_t attr[2] = {0, 0};
+    if (attr[dz_slots] < smem) {
+        if (cudaFuncSetAttribute(dz_slots ? k_conv3_wgrad_dz : k_conv3_wgrad_res,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return 2;
-        attr = smem;
+        attr[dz_slots] = smem;
     }
     const dim3 grid((unsigned)pl.npb, (unsigned)((Ci / pl.ci_blk) * pl.ntile), 1);
-    k_conv3_wgrad_res<<<grid, RTHREADS, smem, s>>>(xmap, dymap, part, bpart, a, Ci, Co, pl);
+    if (dz_slots)
+        k_conv3_wgrad_dz<<<grid, RTHREADS, smem, s>>>(xmap, dymap, part, bpart, a, Ci, Co, pl);
+    else
+        k_conv3_wgrad_res<<<grid, RTHREADS, smem, s>>>(xmap, dymap, part, bpart, a, Ci, Co, pl);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -1165,7 +1411,7 @@ int ws_conv3d_fwd_algo(int algo) {
 }
 
 int ws_conv3d_bwd_weight_algo(int algo) {
-    if (algo < 0 || algo > 2) return -1;
+    if (algo < 0 || algo > 3) return -1;
     const int prev = g_wgrad_algo;
     g_wgrad_algo = algo;
     return prev;
@@ -1206,19 +1452,21 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
     const int nbb = (int)(bias_blocks < 1024 ? bias_blocks : 1024);
     if (k == 3 && g_wgrad_algo != 1) {
         WgPlan pl;
-        if (wg_plan(a, Ci, Co, pl)) {
-            // the kernel sums the bias gradient too when its last tile has a free tap-pair slot
-            const bool fold = db && pl.J * pl.ntile > 9;
+        // Ci a multiple of 32 and Co <= 48: the dz-slot kernel (each X line loaded 3 times, not 9)
+        const bool dz_slots = g_wgrad_algo != 3 && wg_dz_plan(a, Ci, Co, pl);
+        if (dz_slots || wg_plan(a, Ci, Co, pl)) {
+            // the kernel sums the bias gradient too when it has a free slot for a row of ones
+            const bool fold = db && (dz_slots || pl.J * pl.ntile > 9);
             const size_t wpart = (size_t)pl.npb * 27 * Ci * Co;
             const size_t bparts = fold ? (size_t)pl.npb : (size_t)nbb;
             float *ws_buf = grad_workspace((wpart + bparts * Co) * sizeof(float), s);
             if (!ws_buf) return 2;
             float *bpart = ws_buf + wpart;
-            const int rc = conv3_wgrad_res(x, ldx, dy, ldy, ws_buf, fold ? bpart : nullptr, a, Ci, Co, s, pl);
+            const int rc = conv3_wgrad_res(x, ldx, dy, ldy, ws_buf, fold ? bpart : nullptr, a, Ci, Co, s, pl, dz_slots);
             if (rc) return rc;
             const long long elems = 27LL * Ci * Co;
-            k_wgrad_sum<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(ws_buf, pl.npb, 27 * Ci, 27 * Ci, Co, 27, Ci,
-                                                                        dw);
+            k_wgrad_sum<<<(unsigned)((elems + 31) / 32), dim3(32, kSumLanes), 0, s>>>(ws_buf, pl.npb, 27 * Ci,
+                                                                                      27 * Ci, Co, 27, Ci, dw);
             if (db) {
                 if (!fold) {
                     const dim3 g2((unsigned)nbb, (unsigned)((Co + 31) / 32), 1);
@@ -1228,7 +1476,7 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
             }
             return cudaGetLastError() == cudaSuccess ? 0 : 2;
         }
-        if (g_wgrad_algo == 2) return 1;
+        if (g_wgrad_algo >= 2) return 1;
     }
     const int rows = KV * Ci, tiles = (rows + 127) / 128;
     // partial tiles [nk][tiles * 128][Co], then the bias partials [nbb][Co]
@@ -1239,7 +1487,8 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
     k_conv_wgrad_tc<<<grid, WTTHREADS, smem, s>>>((const bf16 *)x, ldx, (const bf16 *)dy, ldy, ws_buf, a, Ci, Co, k,
                                                   chunk, cols, kWgradLbo, kWgradSbo);
     const long long elems = (long long)rows * Co;
-    k_wgrad_sum<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(ws_buf, (int)nk, tiles * 128, rows, Co, KV, Ci, dw);
+    k_wgrad_sum<<<(unsigned)((elems + 31) / 32), dim3(32, kSumLanes), 0, s>>>(ws_buf, (int)nk, tiles * 128, rows, Co,
+                                                                              KV, Ci, dw);
     if (db) {
         float *bpart = ws_buf + wpart;
         const dim3 g2((unsigned)nbb, (unsigned)((Co + 31) / 32), 1);

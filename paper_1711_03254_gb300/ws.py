@@ -88,8 +88,9 @@ def ws_conv3d_fwd_algo(algo: str) -> str:
 
 def ws_conv3d_bwd_weight_algo(algo: str) -> str:
     """Weight-gradient kernel of later ws_conv3d_bwd_weight calls: "auto",
-    "gather" or "resident"; returns the previous choice."""
-    names = ("auto", "gather", "resident")
+    "gather", "resident" or "pairs" (resident, tap-pair rows only); returns
+    the previous choice."""
+    names = ("auto", "gather", "resident", "pairs")
     prev = _lib().ws_conv3d_bwd_weight_algo(names.index(algo))
     if prev < 0:
         raise WsError(f"ws_conv3d_bwd_weight_algo rejected {algo}")

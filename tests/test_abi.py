@@ -140,6 +140,7 @@ def test_surrogate_forward_kernel_switch(lbm):
         ws.ws_conv3d_fwd_algo("fastest")
     L.ws_conv3d_fwd_algo(prev)
     prev = L.ws_conv3d_bwd_weight_algo(2)
-    assert L.ws_conv3d_bwd_weight_algo(7) == -1 and L.ws_conv3d_bwd_weight_algo(1) == 2
+    assert L.ws_conv3d_bwd_weight_algo(7) == -1 and L.ws_conv3d_bwd_weight_algo(3) == 2
+    assert L.ws_conv3d_bwd_weight_algo(1) == 3
     assert ws.ws_conv3d_bwd_weight_algo("auto") == "gather"
     L.ws_conv3d_bwd_weight_algo(prev)

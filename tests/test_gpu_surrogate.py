@@ -33,13 +33,15 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
-@pytest.fixture(params=["resident", "gather"])
+@pytest.fixture(params=["resident", "pairs", "gather"])
 def algo(request, env):
     """Runs a test once with each kernel family, for the forward convolution
     (the data gradient is the forward kernel on flipped weights, so it follows
-    the choice too) and the weight gradient."""
+    the choice too) and the weight gradient ("pairs": the resident forward
+    kernel and the resident weight gradient with tap-pair rows only)."""
     _, ws, _ = env
-    prev = ws.ws_conv3d_fwd_algo(request.param), ws.ws_conv3d_bwd_weight_algo(request.param)
+    fwd = "resident" if request.param == "pairs" else request.param
+    prev = ws.ws_conv3d_fwd_algo(fwd), ws.ws_conv3d_bwd_weight_algo(request.param)
     yield request.param
     ws.ws_conv3d_fwd_algo(prev[0])
     ws.ws_conv3d_bwd_weight_algo(prev[1])
@@ -48,7 +50,8 @@ def algo(request, env):
 @pytest.mark.parametrize("shape,Ci,Co,k", [((2, 6, 5, 7), 32, 48, 3), ((1, 9, 4, 3), 16, 16, 3),
                                            ((1, 8, 8, 8), 96, 64, 3), ((2, 5, 6, 7), 48, 32, 1),
                                            ((1, 8, 8, 12), 64, 224, 3), ((1, 3, 21, 64), 32, 32, 3),
-                                           ((2, 3, 13, 64), 16, 96, 3), ((1, 4, 20, 32), 64, 64, 3)])
+                                           ((2, 3, 13, 64), 16, 96, 3), ((1, 4, 20, 32), 64, 64, 3),
+                                           ((1, 4, 9, 12), 96, 32, 3)])
 def test_conv_forward_and_gradients(env, algo, shape, Ci, Co, k):
     torch, ws, conv = env
     rng = np.random.default_rng(sum(shape) + Ci + Co + k)
@@ -81,7 +84,7 @@ def test_conv_forward_and_gradients(env, algo, shape, Ci, Co, k):
     assert _rel(dx.cpu().numpy(), conv.conv3d_bwd_data(dy, w)) < 2e-5
     # weight and bias gradients (the resident weight-gradient kernel holds 3 Co
     # accumulator columns, so Co > 160 takes the gathered one)
-    if algo == "resident" and Co > 160:
+    if algo in ("resident", "pairs") and Co > 160:
         ws.ws_conv3d_bwd_weight_algo("auto")
     dw = torch.zeros((Co, k, k, k, Ci), dtype=torch.float32, device=dev)
     db = torch.zeros(Co, dtype=torch.float32, device=dev)
@@ -125,7 +128,7 @@ def test_resident_kernel_refuses_wide_lines(env):
     finally:
         ws.ws_conv3d_fwd_algo(prev[0])
         ws.ws_conv3d_bwd_weight_algo(prev[1])
-    assert ws._lib().ws_conv3d_fwd_algo(3) == -1 and ws._lib().ws_conv3d_bwd_weight_algo(3) == -1
+    assert ws._lib().ws_conv3d_fwd_algo(3) == -1 and ws._lib().ws_conv3d_bwd_weight_algo(4) == -1
     assert ws.ws_tc_status() == 0
 
 
