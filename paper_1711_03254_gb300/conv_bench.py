@@ -12,7 +12,8 @@ gradient with each of its kernels ("resident": the automatic resident choice,
 a summary line.  TFLOP/s counts 2 Ci Co 27 multiply-adds per output position;
 `frac` divides by the measured BF16 tensor peak of MEASURED_PEAKS.json when
 that file is present.  Inputs are random BF16 values; the layers are
-compute-bound, so launches are timed back to back without flushing L2.
+compute-bound, so launches are timed back to back without flushing L2.  A
+last line times whole training iterations (--train-iters).
 """
 from __future__ import annotations
 
@@ -64,6 +65,8 @@ def main(argv=None):
     ap.add_argument("--size", type=int, default=64)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--train-iters", type=int, default=50,
+                    help="also time this many whole training iterations (0: skip)")
     args = ap.parse_args(argv)
     import torch
     from . import build
@@ -131,6 +134,49 @@ def main(argv=None):
         if peak:
             summ[f"{key}_frac"] = round(fl / ms / 1e9 / peak, 3)
     print(json.dumps(summ), flush=True)
+    if args.train_iters > 0:
+        print(json.dumps(train_step(torch, args.size, args.batch, args.train_iters, peak)), flush=True)
+
+
+def train_step(torch, size, batch, iters, peak):
+    """Whole training iterations of the U-Net (BF16 cast, forward, masked loss,
+    backward, Adam) on random inputs, as the warm-start training runs them, with
+    the automatic kernel choice and with the gathered kernels; TFLOP/s counts
+    the convolutions' 3 x forward multiply-adds."""
+    from . import surrogate
+    dev = torch.device("cuda:0")
+    g = torch.Generator(device=dev)
+    g.manual_seed(2)
+    net = surrogate.UNet3D(batch, size, seed=0)
+    shape = (batch, size, size, size)
+    x = torch.randn(shape + (surrogate.CIN,), generator=g, device=dev)
+    y = torch.randn(shape + (surrogate.NOUT,), generator=g, device=dev)
+    m = torch.ones(shape, dtype=torch.uint8, device=dev)
+    wch = torch.ones(surrogate.NOUT, dtype=torch.float32, device=dev)
+
+    def it():
+        net.forward(x)
+        net.loss_and_grad(y, m, wch)
+        net.backward()
+        net.adam_step(lr=1e-4)
+
+    from . import ws
+    fl = 3.0 * net.flops_per_sample() * batch
+    out = dict(train=True, size=size, batch=batch, iters=iters)
+    prev = ws.ws_conv3d_fwd_algo("auto"), ws.ws_conv3d_bwd_weight_algo("auto")
+    try:
+        for algo in ("auto", "gather"):
+            ws.ws_conv3d_fwd_algo(algo)
+            ws.ws_conv3d_bwd_weight_algo(algo)
+            ms = _time(torch, it, iters)
+            out[f"{algo}_ms_per_iter"] = round(ms, 3)
+            out[f"{algo}_tflops"] = round(fl / ms / 1e9, 1)
+            if peak:
+                out[f"{algo}_frac"] = round(fl / ms / 1e9 / peak, 3)
+    finally:
+        ws.ws_conv3d_fwd_algo(prev[0])
+        ws.ws_conv3d_bwd_weight_algo(prev[1])
+    return out
 
 
 if __name__ == "__main__":
