@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(TTHREADS) k_conv_fwd_tc(const bf16 *__restrict
 constexpr int RTHREADS = 128;
 
 struct ResPlan {
-    int by, nyt, pitch, ntiles, stages, cols;
+    int by, nyt, pitch, ntiles, stages, cols, per_sm;
     uint32_t a_half, stage_bytes, tx_bytes;
 };
 
@@ -1093,15 +1093,22 @@ static int res_tiles(int lt, int pitch, int W) { return ((lt - 1) * pitch + W + 
 // Tile plan of k_conv3_fwd_res: the line count `by` with the fewest computed
 // rows per output (discarded halo columns and ragged tiles), among those whose
 // accumulators fit the tensor memory (tiles x Co <= 512 columns) and whose
-// ring of at least two stages fits shared memory, at the most blocks per SM
-// that the tensor memory allows and the ring leaves room for (a block alone on
-// its SM counts 15 % slower for its unhidden epilogue).  Returns false if none
-// fits.
+// ring of at least two stages fits shared memory (a plan that leaves one block
+// per SM counts 15 % slower).  Then blocks per SM and stages as measured best
+// on the U-Net's layers (batch 4): for Co >= 64 one block per SM with up to 4
+// stages (32^3 64->64: 521 TFLOP/s against 418 with two blocks of 3 stages;
+// 160->64: 625 against 466), for narrower outputs two blocks per SM with 2
+// stages each (64^3 96->32: 628 against 572 with 3 stages; 32->32: 484
+// against 470), and ties broken toward fewer lines.  That choice is made for
+// lines of 32 columns or more, where it was measured; at 16^3 it left a
+// nearly empty second wave (96->96: 164 against 243 TFLOP/s), so narrower lines
+// keep the search's stages and blocks per SM.  Returns false if none fits.
 static constexpr int kSmemPerSM = 233472, kSmemPerBlockMax = 232448, kSmemReserved = 1024;
 static size_t res_smem(const ResPlan &p) { return (size_t)p.stages * p.stage_bytes + 1024 + 8 * (2 * p.stages + 2) + 16; }
 static bool res_plan(int W, int H, int Co, ResPlan &best) {
     const int pitch = W + 2;
     if (pitch > 256 || Co > 256) return false;
+    const bool tuned = W >= 32;  // the measured choice below; narrower lines keep the search's own
     double best_eff = -1.0;
     for (int by = 1; by <= H && by <= 254; ++by) {
         const int nt = res_tiles(by, pitch, W);
@@ -1136,18 +1143,44 @@ static bool res_plan(int W, int H, int Co, ResPlan &best) {
         long long rows = 0;
         for (int y = 0; y < H; y += by) rows += 128LL * res_tiles(by < H - y ? by : H - y, pitch, W);
         const double eff = (double)H * W / (double)rows * (per_sm >= 2 ? 1.0 : 0.85);
-        if (eff >= best_eff) {
+        if (tuned ? eff > best_eff + 1e-9 : eff >= best_eff) {  // ties: the fewer lines where tuned
             best_eff = eff;
             best = p;
         }
     }
-    return best_eff > 0.0;
+    if (best_eff <= 0.0) return false;
+    if (!tuned) {
+        best.per_sm = 512 / best.cols;
+        while (best.per_sm > 1 &&
+               (long long)res_smem(best) > (long long)kSmemPerSM / best.per_sm - kSmemReserved)
+            --best.per_sm;
+        return true;
+    }
+    // blocks per SM and stages of the chosen tiles: one block with up to 4
+    // stages for Co >= 64, else up to two blocks with 2 stages each (two
+    // stages fit one block per SM whenever the search above found a plan)
+    const int ns_max = Co >= 64 ? 4 : 2;
+    best.stages = 0;
+    for (int per_sm = Co >= 64 ? 1 : std::min(512 / best.cols, 2); per_sm >= 1 && !best.stages; --per_sm) {
+        long long budget = (long long)kSmemPerSM / per_sm - kSmemReserved;
+        if (budget > kSmemPerBlockMax) budget = kSmemPerBlockMax;
+        for (int ns = ns_max; ns >= 2; --ns) {
+            best.stages = ns;
+            if ((long long)res_smem(best) <= budget) {
+                best.per_sm = per_sm;
+                break;
+            }
+            best.stages = 0;
+        }
+    }
+    return best.stages >= 2;
 }
 
-// shared memory to request so that no more blocks share an SM than its tensor memory holds
+// shared memory to request so that no more blocks share an SM than the plan's
+// blocks per SM (which the tensor memory holds)
 static size_t res_smem_request(const ResPlan &p) {
     size_t s = res_smem(p);
-    const int per_sm = 512 / p.cols;
+    const int per_sm = p.per_sm;
     const size_t floor_bytes = (size_t)kSmemPerSM / (size_t)(per_sm + 1) - kSmemReserved + 16;
     if (s < floor_bytes) s = floor_bytes;
     if (s > (size_t)kSmemPerBlockMax) s = kSmemPerBlockMax;
