@@ -32,9 +32,13 @@ extern "C" {
  * row stride ldy; relu != 0 applies max(., 0); bias may be NULL.  Runs as an
  * implicit GEMM on the tcgen05 tensor cores (M = output positions, N = Co,
  * K = taps x Ci), accumulated in tensor memory.  Two kernels:
- *  - resident tiles (k = 3, W <= 254): a thread block owns a run of output
- *    lines of one plane; TMA loads its input one padded plane at a time and
- *    the 9 taps of the plane are shifted views of that tile;
+ *  - resident tiles (k = 3, W <= 254): a run of output lines of one plane is
+ *    one tile; TMA loads its input one padded plane at a time and the 9 taps
+ *    of the plane are shifted views of that tile.  For Co >= 64 or Ci = 16,
+ *    where two accumulator buffers fit the tensor memory, one persistent
+ *    block per SM strides over the tiles (the epilogue of a tile overlapping
+ *    the next tile's MMAs); otherwise each block computes one tile.  Both give
+ *    the same bits;
  *  - gathered tiles (k = 1, and k = 3 where no resident plan fits): 128
  *    positions per block, each tap's rows gathered with 16-byte copies.
  * Additional argument rules: Co <= 256, y 16-byte aligned, ldy a multiple of
@@ -46,8 +50,10 @@ int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void
 
 /* Selects the forward kernel of later ws_conv3d_fwd calls (process-wide):
  * 0 automatic (resident tiles where a plan fits, else gathered), 1 gathered
- * tiles always, 2 resident tiles always for k = 3.  Returns the previous
- * choice, or -1 for an unknown value (nothing changes). */
+ * tiles always, 2 resident tiles always for k = 3, 3 as 2 but one block per
+ * tile (never the persistent kernel), 4 as 2 but persistent wherever its
+ * buffers fit.  Returns the previous choice, or -1 for an unknown value
+ * (nothing changes). */
 int ws_conv3d_fwd_algo(int algo);
 
 /* wf[ci][t][co] = w[co][k^3-1-t][ci]: weights for the data gradient, which is

@@ -4,16 +4,20 @@
 
 For every 3x3x3 layer of the U-Net (surrogate.Surrogate's layer table at the
 given resolution and batch) this times, with CUDA events on the current stream
-after warm-up, the forward convolution with each forward kernel (resident
-tiles, gathered tiles), the data gradient (the forward kernel on flipped
-weights, Ci and Co exchanged; the first layer has none) and the weight
-gradient with each of its kernels ("resident": the automatic resident choice,
-"pairs": tap-pair rows only, "gather"), and prints one JSON line per layer and
-a summary line.  TFLOP/s counts 2 Ci Co 27 multiply-adds per output position;
-`frac` divides by the measured BF16 tensor peak of MEASURED_PEAKS.json when
-that file is present.  Inputs are random BF16 values; the layers are
-compute-bound, so launches are timed back to back without flushing L2.  A
-last line times whole training iterations (--train-iters).
+after warm-up:
+  - the forward convolution with each forward kernel ("resident": the
+    automatic resident choice, "pertile": one block per tile, "persistent":
+    persistent wherever it fits, "gather": the gathered kernel);
+  - the data gradient (the forward kernel on flipped weights, Ci and Co
+    exchanged; the first layer has none);
+  - the weight gradient with each of its kernels ("resident": the automatic
+    resident choice, "pairs": tap-pair rows only, "gather").
+It prints one JSON line per layer and a summary line.  TFLOP/s counts
+2 Ci Co 27 multiply-adds per output position; `frac` divides by the measured
+BF16 tensor peak of MEASURED_PEAKS.json when that file is present.  Inputs are
+random BF16 values; the layers are compute-bound, so launches are timed back
+to back without flushing L2.  A last line times whole training iterations
+(--train-iters).
 """
 from __future__ import annotations
 
@@ -76,8 +80,8 @@ def main(argv=None):
     g = torch.Generator(device=dev)
     g.manual_seed(1)
     peak = _peak()
-    tot = {"fwd_resident": 0.0, "fwd_gather": 0.0, "bwd_data": 0.0, "bwd_weight_resident": 0.0,
-           "bwd_weight_pairs": 0.0, "bwd_weight_gather": 0.0}
+    tot = {"fwd_resident": 0.0, "fwd_pertile": 0.0, "fwd_persistent": 0.0, "fwd_gather": 0.0,
+           "bwd_data": 0.0, "bwd_weight_resident": 0.0, "bwd_weight_pairs": 0.0, "bwd_weight_gather": 0.0}
     flops_tot = {"fwd": 0.0, "bwd_data": 0.0, "bwd_weight": 0.0}
     for name, ci, co, s in layers(args.size):
         N = args.batch
@@ -96,7 +100,7 @@ def main(argv=None):
         prev = ws.ws_conv3d_fwd_algo("auto")
         prev_w = ws.ws_conv3d_bwd_weight_algo("auto")
         try:
-            for algo in ("resident", "gather"):
+            for algo in ("resident", "pertile", "persistent", "gather"):
                 ws.ws_conv3d_fwd_algo(algo)
                 ms = _time(torch, lambda: ws.ws_conv3d_fwd(x, w, b, y, True), args.reps)
                 row[f"fwd_{algo}_ms"] = round(ms, 4)

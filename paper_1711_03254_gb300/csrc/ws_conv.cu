@@ -381,17 +381,25 @@ __global__ void __launch_bounds__(RTHREADS) k_conv3_fwd_res(const __grid_constan
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
             const uint32_t sa = base + (uint32_t)st * pl.stage_bytes, sb = sa + 2 * pl.a_half;
-            for (int j = 0; j < nt; ++j)
+            // descriptors of the taps: a base descriptor's start-address field (16-byte
+            // units) plus the tap's offset (all addresses stay below 256 KB)
+            const uint64_t ad0 = umma_desc(sa, pl.a_half, 128), bd0 = umma_desc(sb, (uint32_t)Co * 16u, 128);
+            const uint32_t pitch = (uint32_t)pl.pitch, bstep = 2u * (uint32_t)Co;
+            for (int j = 0; j < nt; ++j) {
+                const uint64_t aj = ad0 + (uint64_t)(128 * j);
+                const uint32_t dj = tmem + (uint32_t)(j * Co);
+#pragma unroll
                 for (int t9 = 0; t9 < 9; ++t9) {
-                    const int dy = t9 / 3, dx = t9 - 3 * dy;
-                    const uint64_t ad = umma_desc(sa + (uint32_t)(128 * j + dy * pl.pitch + dx) * 16u, pl.a_half, 128);
-                    const uint64_t bd = umma_desc(sb + (uint32_t)(t9 * 2) * (uint32_t)Co * 16u, (uint32_t)Co * 16u, 128);
+                    const uint32_t dy = (uint32_t)(t9 / 3), dx = (uint32_t)(t9 % 3);
+                    const uint64_t ad = aj + (uint64_t)(dy * pitch + dx);
+                    const uint64_t bd = bd0 + (uint64_t)((uint32_t)t9 * bstep);
                     const uint32_t acc = (s > 0 || t9 > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(j * Co)),
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dj),
                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                 }
+            }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_u32(&empty[st])));
         }
@@ -462,6 +470,242 @@ __global__ void __launch_bounds__(RTHREADS) k_conv3_fwd_res(const __grid_constan
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(pl.cols));
     }
+}
+
+// ------------------------------------------------------------------ forward, persistent resident tiles
+// k_conv3_fwd_pers: the tiles of k_conv3_fwd_res (same loads, descriptors and
+// accumulation order, so the same bits) computed by one persistent block per
+// SM that strides over the tiles, with two accumulator buffers in tensor
+// memory so that the epilogue of one tile overlaps the MMAs of the next.
+// Warp 0 (one thread) issues TMA into the ring of stages across tiles, warp 1
+// (one thread) issues the MMAs, warps 2-5 run the epilogue (warp w reads the
+// TMEM lanes 32 (w mod 4) ..).  Barriers: full / empty per stage, tfull per
+// buffer (tcgen05.commit after a tile's last K-step), tempty per buffer (one
+// arrival per epilogue warp once it has read the tile).  Every wait is bounded;
+// a role that gives up sets a shared flag, the others stop at their next wait,
+// the MMA thread waits for its MMAs and the TMA thread for its loads before
+// the block releases its tensor memory.
+constexpr int PTHREADS = 192;
+
+struct ResTile {
+    int n, z, y0, lt, nt, dz_lo, ndz, nsteps;
+};
+
+__device__ __forceinline__ ResTile res_tile(int t, const Act &a, const ResPlan &pl, int Ci) {
+    ResTile r;
+    const int yt = t % pl.nyt, zn = t / pl.nyt;
+    r.z = zn % a.D;
+    r.n = zn / a.D;
+    r.y0 = yt * pl.by;
+    r.lt = min(pl.by, a.H - r.y0);
+    r.nt = ((r.lt - 1) * pl.pitch + a.W + 127) / 128;
+    r.dz_lo = r.z == 0 ? 1 : 0;
+    r.ndz = (r.z == a.D - 1 ? 1 : 2) - r.dz_lo + 1;
+    r.nsteps = (Ci / 16) * r.ndz;
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+template <bool OUT_F32>
+__global__ void __launch_bounds__(PTHREADS, 1) k_conv3_fwd_pers(const __grid_constant__ CUtensorMap xmap,
+                                                               const __grid_constant__ CUtensorMap wmap,
+                                                               const float *__restrict__ bias, void *__restrict__ Y,
+                                                               int ldy, Act a, int Ci, int Co, int relu, ResPlan pl,
+                                                               int ntile_total, uint32_t buf_cols) {
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NS = pl.stages;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + (size_t)NS * pl.stage_bytes);
+    uint64_t *empty = full + NS;
+    uint64_t *tfull = empty + NS;  // [2]
+    uint64_t *tempty = tfull + 2;  // [2]
+    uint64_t *done = tempty + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(pl.cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2 * NS + 2; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[s])));
+        for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(smem_u32(&tempty[b])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(done)));
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = *tslot;
+    const uint32_t base = smem_u32(sm);
+
+    if (tid == 0) {
+        // TMA producer: K-steps of this block's tiles in turn, through the ring
+        int g = 0, issued = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntile_total && ok; t += gridDim.x) {
+            const ResTile r = res_tile(t, a, pl, Ci);
+            for (int s = 0; s < r.nsteps; ++s, ++g) {
+                const int st = g % NS;
+                if ((g >= NS && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((g / NS) - 1) & 1))) || *abort_flag) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                const int c = s / r.ndz, dz = r.dz_lo + s % r.ndz;
+                const uint32_t fb = smem_u32(&full[st]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(pl.tx_bytes)
+                             : "memory");
+                const uint32_t sa = base + (uint32_t)st * pl.stage_bytes, sb = sa + 2 * pl.a_half;
+                tma_load_5d(sa, &xmap, c * 16, -1, r.y0 - 1, r.z + dz - 1, r.n, fb);
+                tma_load_5d(sa + pl.a_half, &xmap, c * 16 + 8, -1, r.y0 - 1, r.z + dz - 1, r.n, fb);
+                for (int t9 = 0; t9 < 9; ++t9)
+                    for (int h = 0; h < 2; ++h)
+                        tma_load_3d(sb + (uint32_t)(t9 * 2 + h) * (uint32_t)Co * 16u, &wmap, c * 16 + 8 * h,
+                                    dz * 9 + t9, 0, fb);
+                issued = g + 1;
+            }
+        }
+        // wait for the loads still in flight (the last phase issued on each stage)
+        for (int st = 0; st < NS && st < issued; ++st) {
+            const int last = st + ((issued - 1 - st) / NS) * NS;
+            mbar_wait(smem_u32(&full[st]), (uint32_t)((last / NS) & 1));
+        }
+    } else if (tid == 32) {
+        // MMA issuer: tile i accumulates into buffer i & 1
+        const uint32_t idesc = umma_idesc_bf16(128, Co);
+        int g = 0, i = 0;
+        for (int t = blockIdx.x; t < ntile_total; t += gridDim.x, ++i) {
+            const ResTile r = res_tile(t, a, pl, Ci);
+            const int buf = i & 1;
+            if ((i >= 2 && !mbar_wait(smem_u32(&tempty[buf]), (uint32_t)(((i / 2) - 1) & 1))) || *abort_flag) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t dbase = tmem + (uint32_t)buf * buf_cols;
+            bool ok = true;
+            for (int s = 0; s < r.nsteps; ++s, ++g) {
+                const int st = g % NS;
+                if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((g / NS) & 1)) || *abort_flag) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+                const uint32_t sa = base + (uint32_t)st * pl.stage_bytes, sb = sa + 2 * pl.a_half;
+                // descriptors of the taps: the start-address field (16-byte units) of a base
+                // descriptor plus the tap's offset (all addresses stay below 256 KB)
+                const uint64_t ad0 = umma_desc(sa, pl.a_half, 128), bd0 = umma_desc(sb, (uint32_t)Co * 16u, 128);
+                const uint32_t pitch = (uint32_t)pl.pitch, bstep = 2u * (uint32_t)Co;
+                for (int j = 0; j < r.nt; ++j) {
+                    const uint64_t aj = ad0 + (uint64_t)(128 * j);
+                    const uint32_t dj = dbase + (uint32_t)(j * Co);
+#pragma unroll
+                    for (int t9 = 0; t9 < 9; ++t9) {
+                        const uint32_t dy = (uint32_t)(t9 / 3), dx = (uint32_t)(t9 % 3);
+                        const uint64_t ad = aj + (uint64_t)(dy * pitch + dx);
+                        const uint64_t bd = bd0 + (uint64_t)((uint32_t)t9 * bstep);
+                        const uint32_t acc = (s > 0 || t9 > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dj),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&empty[st])));
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&tfull[buf])));
+        }
+        // arrives once every MMA issued above has finished
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(done)));
+        mbar_wait(smem_u32(done), 0u);
+    } else if (warp >= 2) {
+        // epilogue: warp w reads the accumulator rows (TMEM lanes) 32 (w mod 4) .. of every tile
+        const int q4 = warp & 3;
+        int i = 0;
+        for (int t = blockIdx.x; t < ntile_total; t += gridDim.x, ++i) {
+            const int buf = i & 1;
+            const bool okw = mbar_wait(smem_u32(&tfull[buf]), (uint32_t)((i / 2) & 1));
+            if (!__all_sync(0xFFFFFFFFu, okw) || *abort_flag) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const ResTile r = res_tile(t, a, pl, Ci);
+            for (int j = 0; j < r.nt; ++j) {
+                const int q = 128 * j + 32 * q4 + lane;
+                const int line = q / pl.pitch, x = q - line * pl.pitch;
+                const bool valid = x < a.W && line < r.lt;
+                const long long row = (((long long)r.n * a.D + r.z) * a.H + r.y0 + line) * a.W + x;
+                for (int c0 = 0; c0 < Co; c0 += 16) {
+                    uint32_t v[16];
+                    const uint32_t addr =
+                        tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)buf * buf_cols + (uint32_t)(j * Co + c0);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];\n"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(addr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+                    if (valid) {
+                        float o[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            float xv = __uint_as_float(v[e]);
+                            if (bias) xv += bias[c0 + e];
+                            if (relu) xv = fmaxf(xv, 0.f);
+                            o[e] = xv;
+                        }
+                        if (OUT_F32) {
+                            float4 *dst = reinterpret_cast<float4 *>((float *)Y + row * ldy + c0);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                dst[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
+                        } else {
+                            uint4 *dst = reinterpret_cast<uint4 *>((bf16 *)Y + row * ldy + c0);
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                __nv_bfloat162 h[4];
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(o[8 * e + 2 * k], o[8 * e + 2 * k + 1]);
+                                uint4 u;
+                                u.x = *reinterpret_cast<uint32_t *>(&h[0]);
+                                u.y = *reinterpret_cast<uint32_t *>(&h[1]);
+                                u.z = *reinterpret_cast<uint32_t *>(&h[2]);
+                                u.w = *reinterpret_cast<uint32_t *>(&h[3]);
+                                dst[e] = u;
+                            }
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(pl.cols));
+    }
+    if (tid == 0 && *abort_flag) atomicExch(&g_tc_timeout, 1);
 }
 
 // W' [Ci][KV][Co] = W [Co][KV-1-t][Ci]: backward-data weights
@@ -1065,7 +1309,21 @@ using namespace ws;
 
 static bool bad_channels(int c) { return c < 16 || (c % 16) != 0; }
 
-// forward kernel choice: 0 automatic, 1 gathered tiles (k_conv_fwd_tc), 2 resident tiles (k_conv3_fwd_res)
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            n = 0;
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// forward kernel choice: 0 automatic, 1 gathered tiles (k_conv_fwd_tc), 2 resident tiles
+// (k_conv3_fwd_pers or k_conv3_fwd_res, as measured faster), 3 resident tiles, one block per tile
+// (k_conv3_fwd_res only), 4 resident tiles, persistent wherever its buffers fit
 static int g_fwd_algo = 0;
 
 // cuTensorMapEncodeTiled from the driver, fetched through the runtime (no libcuda link)
@@ -1200,6 +1458,24 @@ static bool act_map(CUtensorMap *map, const void *t, int ld, const Act &a, int C
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Persistent variant of a resident-tile plan: the same tiles with two
+// accumulator buffers (each a power of two of at least tiles x Co columns, the
+// pair within the 512 columns), one block per SM, the most stages (2 ..
+// kPersStages) that fit.  False where the buffers do not fit.
+constexpr int kPersStages = 4;
+static size_t pers_smem(const ResPlan &p) { return (size_t)p.stages * p.stage_bytes + 1024 + 8 * (2 * p.stages + 5) + 16; }
+static bool pers_plan(const ResPlan &res, int Co, ResPlan &p, uint32_t &buf_cols) {
+    p = res;
+    buf_cols = 32;
+    while (buf_cols < (uint32_t)(p.ntiles * Co)) buf_cols *= 2;
+    if (2 * buf_cols > 512) return false;
+    p.cols = (int)(2 * buf_cols);
+    p.per_sm = 1;
+    for (p.stages = kPersStages; p.stages >= 2; --p.stages)
+        if (pers_smem(p) <= (size_t)kSmemPerBlockMax) return true;
+    return false;
+}
+
 static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bias, void *y, int ldy, int y_f32,
                          const Act &a, int Ci, int Co, int relu, cudaStream_t s, const ResPlan &pl) {
     EncodeTiledFn enc = encode_tiled();
@@ -1226,6 +1502,34 @@ static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bia
     }
     const long long blocks = (long long)a.N * a.D * pl.nyt;
     if (blocks > 0x7FFFFFFFLL) return 1;
+    ResPlan pp;
+    uint32_t buf_cols = 0;
+    // persistent where it measured faster (U-Net layers at 64^3, 32^3, 16^3, batch 4): Co >= 64
+    // (32^3 64->64: 517 against 466 TFLOP/s) and 16-channel inputs (3 K-steps a tile; 64^3 16->32:
+    // 381 against 321); one block per tile for narrower outputs of wider inputs (64^3 96->32: 617
+    // against 478, 32->32: 440 against 433)
+    const bool want_pers = g_fwd_algo == 4 || (g_fwd_algo != 3 && (Co >= 64 || Ci <= 16));
+    if (want_pers && pers_plan(pl, Co, pp, buf_cols)) {
+        // one persistent block per SM (at most one per tile)
+        const size_t psmem = std::max(pers_smem(pp), (size_t)kSmemPerSM / 2 - kSmemReserved + 16);
+        static size_t pattr[2] = {0, 0};
+        if (pattr[which] < psmem) {
+            const cudaError_t e = y_f32 ? cudaFuncSetAttribute(k_conv3_fwd_pers<true>,
+                                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem)
+                                        : cudaFuncSetAttribute(k_conv3_fwd_pers<false>,
+                                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+            if (e != cudaSuccess) return 2;
+            pattr[which] = psmem;
+        }
+        const unsigned grid = (unsigned)std::min<long long>(blocks, sm_count());
+        if (y_f32)
+            k_conv3_fwd_pers<true><<<grid, PTHREADS, psmem, s>>>(xmap, wmap, bias, y, ldy, a, Ci, Co, relu, pp,
+                                                                 (int)blocks, buf_cols);
+        else
+            k_conv3_fwd_pers<false><<<grid, PTHREADS, psmem, s>>>(xmap, wmap, bias, y, ldy, a, Ci, Co, relu, pp,
+                                                                  (int)blocks, buf_cols);
+        return cudaGetLastError() == cudaSuccess ? 0 : 2;
+    }
     if (y_f32)
         k_conv3_fwd_res<true><<<(unsigned)blocks, RTHREADS, smem, s>>>(xmap, wmap, bias, y, ldy, a, Ci, Co, relu, pl);
     else
@@ -1238,17 +1542,6 @@ static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bia
 // (k_conv3_wgrad_res only)
 static int g_wgrad_algo = 0;
 
-static int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
-                                                      cudaSuccess)
-            n = 0;
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
 
 // blocks of a weight-gradient launch: at most this many full waves (resident
 // blocks x SMs).  One wave measured best on the U-Net's layers (64^3 32->32:
@@ -1413,7 +1706,7 @@ int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void
     if (k == 3 && g_fwd_algo != 1) {
         ResPlan pl;
         if (res_plan(W, H, Co, pl)) return conv3_fwd_res(x, ldx, w, bias, y, ldy, y_f32, a, Ci, Co, relu, s, pl);
-        if (g_fwd_algo == 2) return 1;
+        if (g_fwd_algo >= 2) return 1;
     }
     const int cols = Co <= 32 ? 32 : (Co <= 64 ? 64 : (Co <= 128 ? 128 : 256));
     const size_t smem = 2 * (size_t)TKC * (TBM * 32 + (size_t)Co * 32) + 2 * sizeof(uint64_t) + 16;
@@ -1437,7 +1730,7 @@ int ws_conv3d_fwd(const void *x, int ldx, const void *w, const float *bias, void
 }
 
 int ws_conv3d_fwd_algo(int algo) {
-    if (algo < 0 || algo > 2) return -1;
+    if (algo < 0 || algo > 4) return -1;
     const int prev = g_fwd_algo;
     g_fwd_algo = algo;
     return prev;

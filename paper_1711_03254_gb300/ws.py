@@ -34,7 +34,8 @@ def _lib():
         L.ws_to_bf16.argtypes = [vp, i, vp, i, ll, i, vp]
         L.ws_tc_status.argtypes = [vp]
         for name in ("ws_conv3d_fwd", "ws_conv3d_fwd_algo", "ws_conv3d_flip_weights", "ws_conv3d_bwd_weight",
-                     "ws_conv3d_bwd_weight_algo", "ws_avgpool2", "ws_avgpool2_bwd", "ws_upsample2", "ws_upsample2_bwd", "ws_relu_bwd", "ws_mse_loss", "ws_adam",
+                     "ws_conv3d_bwd_weight_algo", "ws_avgpool2", "ws_avgpool2_bwd", "ws_upsample2",
+                     "ws_upsample2_bwd", "ws_relu_bwd", "ws_mse_loss", "ws_adam",
                      "ws_to_bf16", "ws_tc_status"):
             getattr(L, name).restype = ctypes.c_int
         _sig_done = True
@@ -77,9 +78,11 @@ def ws_conv3d_fwd(x, w, bias, y, relu: bool):
 
 
 def ws_conv3d_fwd_algo(algo: str) -> str:
-    """Forward kernel of later ws_conv3d_fwd calls: "auto", "gather" or
-    "resident"; returns the previous choice."""
-    names = ("auto", "gather", "resident")
+    """Forward kernel of later ws_conv3d_fwd calls: "auto", "gather",
+    "resident", "pertile" (resident, one block per tile, never persistent) or
+    "persistent" (resident, persistent wherever its buffers fit); returns the
+    previous choice."""
+    names = ("auto", "gather", "resident", "pertile", "persistent")
     prev = _lib().ws_conv3d_fwd_algo(names.index(algo))
     if prev < 0:
         raise WsError(f"ws_conv3d_fwd_algo rejected {algo}")

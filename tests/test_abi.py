@@ -133,8 +133,9 @@ def test_surrogate_forward_kernel_switch(lbm):
     L = ws._lib()
     prev = L.ws_conv3d_fwd_algo(2)
     assert prev in (0, 1, 2)
-    assert L.ws_conv3d_fwd_algo(3) == -1 and L.ws_conv3d_fwd_algo(-1) == -1
-    assert L.ws_conv3d_fwd_algo(1) == 2
+    assert L.ws_conv3d_fwd_algo(5) == -1 and L.ws_conv3d_fwd_algo(-1) == -1
+    assert L.ws_conv3d_fwd_algo(4) == 2 and L.ws_conv3d_fwd_algo(3) == 4
+    assert L.ws_conv3d_fwd_algo(1) == 3
     assert ws.ws_conv3d_fwd_algo("auto") == "gather"
     with pytest.raises(ValueError):
         ws.ws_conv3d_fwd_algo("fastest")

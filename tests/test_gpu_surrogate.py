@@ -33,15 +33,18 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
-@pytest.fixture(params=["resident", "pairs", "gather"])
+@pytest.fixture(params=["resident", "pairs", "persistent", "gather"])
 def algo(request, env):
     """Runs a test once with each kernel family, for the forward convolution
     (the data gradient is the forward kernel on flipped weights, so it follows
-    the choice too) and the weight gradient ("pairs": the resident forward
-    kernel and the resident weight gradient with tap-pair rows only)."""
+    the choice too) and the weight gradient ("resident": the automatic resident
+    choices; "pairs": the resident forward kernel with one block per tile and
+    the weight gradient with tap-pair rows only; "persistent": the persistent
+    forward kernel wherever its buffers fit)."""
     _, ws, _ = env
-    fwd = "resident" if request.param == "pairs" else request.param
-    prev = ws.ws_conv3d_fwd_algo(fwd), ws.ws_conv3d_bwd_weight_algo(request.param)
+    fwd = {"pairs": "pertile"}.get(request.param, request.param)
+    wgrad = {"persistent": "resident"}.get(request.param, request.param)
+    prev = ws.ws_conv3d_fwd_algo(fwd), ws.ws_conv3d_bwd_weight_algo(wgrad)
     yield request.param
     ws.ws_conv3d_fwd_algo(prev[0])
     ws.ws_conv3d_bwd_weight_algo(prev[1])
@@ -84,7 +87,7 @@ def test_conv_forward_and_gradients(env, algo, shape, Ci, Co, k):
     assert _rel(dx.cpu().numpy(), conv.conv3d_bwd_data(dy, w)) < 2e-5
     # weight and bias gradients (the resident weight-gradient kernel holds 3 Co
     # accumulator columns, so Co > 160 takes the gathered one)
-    if algo in ("resident", "pairs") and Co > 160:
+    if algo in ("resident", "pairs", "persistent") and Co > 160:
         ws.ws_conv3d_bwd_weight_algo("auto")
     dw = torch.zeros((Co, k, k, k, Ci), dtype=torch.float32, device=dev)
     db = torch.zeros(Co, dtype=torch.float32, device=dev)
@@ -128,7 +131,7 @@ def test_resident_kernel_refuses_wide_lines(env):
     finally:
         ws.ws_conv3d_fwd_algo(prev[0])
         ws.ws_conv3d_bwd_weight_algo(prev[1])
-    assert ws._lib().ws_conv3d_fwd_algo(3) == -1 and ws._lib().ws_conv3d_bwd_weight_algo(4) == -1
+    assert ws._lib().ws_conv3d_fwd_algo(5) == -1 and ws._lib().ws_conv3d_bwd_weight_algo(4) == -1
     assert ws.ws_tc_status() == 0
 
 
