@@ -10,9 +10,16 @@
 //                        (M = taps x Ci, N = Co, K = positions), split over position chunks.
 //
 // All three products run on the tcgen05 tensor cores with the accumulator in
-// tensor memory: k_conv_fwd_tc (forward, and the data gradient through the
-// flipped weights) and k_conv_wgrad_tc (weight gradient), fed by cp.async
-// double-buffered shared-memory stages.
+// tensor memory.  Kernels:
+//   k_conv3_fwd_res, k_conv3_fwd_pers   forward (and data gradient) for 3x3x3, the
+//                                       input tile resident in shared memory (TMA),
+//                                       the taps as shifted descriptors; one block
+//                                       per tile or one persistent block per SM
+//   k_conv3_wgrad_res, k_conv3_wgrad_dz weight gradient for 3x3x3 from TMA line boxes,
+//                                       tap pairs or dz slots as M rows
+//   k_conv_fwd_tc, k_conv_wgrad_tc      the gathered kernels (cp.async, two stages):
+//                                       1x1x1 and the shapes no resident plan fits
+// The host picks among them (ws_conv3d_fwd_algo, ws_conv3d_bwd_weight_algo).
 //
 // Activations are channels-last with a row stride (ld) and a channel offset,
 // so concatenations are views of one buffer.  Channel counts are multiples of
