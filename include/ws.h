@@ -89,6 +89,25 @@ int ws_conv3d_bwd_weight(const void *x, int ldx, const void *dy, int ldy, float 
  * for an unknown value (nothing changes). */
 int ws_conv3d_bwd_weight_algo(int algo);
 
+/* The tiling the resident-tile kernels would use for a 3x3x3 convolution of
+ * this shape under the current kernel choice (host only: no GPU work, no
+ * allocation).  which = 0: forward (also the data gradient with Ci and Co
+ * exchanged); out[0..13] = persistent kernel (0/1), lines per tile, tiles per
+ * plane, line pitch (W + 2), 128-row M tiles per tile, stages, tensor-memory
+ * columns, blocks per SM, bytes of one K half of a stage's input, stage bytes,
+ * TMA bytes per stage, dynamic shared memory requested, blocks in the grid,
+ * columns per accumulator buffer (persistent kernel, else 0).  which = 1:
+ * weight gradient; out[0..15] = dz-slot kernel (0/1), lines per K-block,
+ * K-blocks per plane, line pitch, K-steps per K-block, tap slots per M tile,
+ * channels per M group, M tiles per channel block, position blocks, K-blocks
+ * per position block, stages, tensor-memory columns, region bytes, stage
+ * bytes, dynamic shared memory requested, blocks per position block (grid y).
+ * The block counts follow the SM count of the current device (1 where no
+ * device is visible).  Writes min(nout, count) values and returns the count;
+ * -1 when the gathered kernel would run (no resident plan fits, or it is
+ * selected), -2 for invalid arguments. */
+int ws_conv3d_plan(int which, int N, int D, int H, int W, int Ci, int Co, long long *out, int nout);
+
 /* 2x2x2 average pooling (D, H, W even) and its adjoint; nearest-neighbour 2x
  * upsampling and its adjoint (sum of the 8 children).  BF16 in and out.  The
  * adjoints of pool/upsample accumulate into dx when accumulate != 0.  D, H, W

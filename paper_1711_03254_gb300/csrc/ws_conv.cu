@@ -1483,6 +1483,15 @@ static bool pers_plan(const ResPlan &res, int Co, ResPlan &p, uint32_t &buf_cols
     return false;
 }
 
+// The persistent forward kernel where it measured faster (U-Net layers at 64^3,
+// 32^3, 16^3, batch 4): Co >= 64 (32^3 64->64: 517 against 466 TFLOP/s) and
+// 16-channel inputs (3 K-steps a tile; 64^3 16->32: 381 against 321); one
+// block per tile for narrower outputs of wider inputs (64^3 96->32: 617
+// against 478, 32->32: 440 against 433).
+static bool want_persistent(int Ci, int Co) {
+    return g_fwd_algo == 4 || (g_fwd_algo != 3 && (Co >= 64 || Ci <= 16));
+}
+
 static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bias, void *y, int ldy, int y_f32,
                          const Act &a, int Ci, int Co, int relu, cudaStream_t s, const ResPlan &pl) {
     EncodeTiledFn enc = encode_tiled();
@@ -1511,12 +1520,7 @@ static int conv3_fwd_res(const void *x, int ldx, const void *w, const float *bia
     if (blocks > 0x7FFFFFFFLL) return 1;
     ResPlan pp;
     uint32_t buf_cols = 0;
-    // persistent where it measured faster (U-Net layers at 64^3, 32^3, 16^3, batch 4): Co >= 64
-    // (32^3 64->64: 517 against 466 TFLOP/s) and 16-channel inputs (3 K-steps a tile; 64^3 16->32:
-    // 381 against 321); one block per tile for narrower outputs of wider inputs (64^3 96->32: 617
-    // against 478, 32->32: 440 against 433)
-    const bool want_pers = g_fwd_algo == 4 || (g_fwd_algo != 3 && (Co >= 64 || Ci <= 16));
-    if (want_pers && pers_plan(pl, Co, pp, buf_cols)) {
+    if (want_persistent(Ci, Co) && pers_plan(pl, Co, pp, buf_cols)) {
         // one persistent block per SM (at most one per tile)
         const size_t psmem = std::max(pers_smem(pp), (size_t)kSmemPerSM / 2 - kSmemReserved + 16);
         static size_t pattr[2] = {0, 0};
@@ -1741,6 +1745,41 @@ int ws_conv3d_fwd_algo(int algo) {
     const int prev = g_fwd_algo;
     g_fwd_algo = algo;
     return prev;
+}
+
+int ws_conv3d_plan(int which, int N, int D, int H, int W, int Ci, int Co, long long *out, int nout) {
+    if (!out || nout < 0 || N < 1 || D < 1 || H < 1 || W < 1 || bad_channels(Ci) || bad_channels(Co) || Co > 256 ||
+        (which != 0 && which != 1))
+        return -2;
+    long long v[16] = {0};
+    int n = 0;
+    const Act a{N, D, H, W};
+    if (which == 0) {
+        ResPlan pl, pp;
+        uint32_t buf_cols = 0;
+        if (g_fwd_algo == 1 || !res_plan(W, H, Co, pl)) return -1;
+        const long long tiles = (long long)N * D * pl.nyt;
+        const bool pers = want_persistent(Ci, Co) && pers_plan(pl, Co, pp, buf_cols);
+        const ResPlan &q = pers ? pp : pl;
+        const size_t smem = pers ? std::max(pers_smem(pp), (size_t)kSmemPerSM / 2 - kSmemReserved + 16)
+                                 : res_smem_request(pl);
+        const long long f[14] = {pers ? 1 : 0, q.by, q.nyt, q.pitch, q.ntiles, q.stages, q.cols, q.per_sm,
+                                 q.a_half, q.stage_bytes, q.tx_bytes, (long long)smem,
+                                 pers ? std::min<long long>(tiles, sm_count()) : tiles,
+                                 pers ? (long long)buf_cols : 0};
+        for (; n < 14; ++n) v[n] = f[n];
+    } else {
+        WgPlan pl;
+        if (g_wgrad_algo == 1) return -1;
+        const bool dz = g_wgrad_algo != 3 && wg_dz_plan(a, Ci, Co, pl);
+        if (!dz && !wg_plan(a, Ci, Co, pl)) return -1;
+        const long long f[16] = {dz ? 1 : 0, pl.by, pl.nyb, pl.pitch, pl.ksteps, pl.J, pl.ci_blk, pl.ntile,
+                                 pl.npb, pl.kpb, pl.stages, pl.cols, pl.region, pl.stage_bytes,
+                                 (long long)wg_smem_request(pl), (long long)(Ci / pl.ci_blk) * pl.ntile};
+        for (; n < 16; ++n) v[n] = f[n];
+    }
+    for (int i = 0; i < n && i < nout; ++i) out[i] = v[i];
+    return n;
 }
 
 int ws_conv3d_bwd_weight_algo(int algo) {

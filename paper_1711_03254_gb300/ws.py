@@ -22,6 +22,7 @@ def _lib():
         L.ws_conv3d_fwd.argtypes = [vp, i, vp, vp, vp, i, i, i, i, i, i, i, i, i, i, vp]
         L.ws_conv3d_fwd_algo.argtypes = [i]
         L.ws_conv3d_bwd_weight_algo.argtypes = [i]
+        L.ws_conv3d_plan.argtypes = [i, i, i, i, i, i, i, ctypes.POINTER(ll), i]
         L.ws_conv3d_flip_weights.argtypes = [vp, vp, i, i, i, vp]
         L.ws_conv3d_bwd_weight.argtypes = [vp, i, vp, i, vp, vp, i, i, i, i, i, i, i, vp]
         L.ws_avgpool2.argtypes = [vp, i, vp, i, i, i, i, i, i, vp]
@@ -36,7 +37,7 @@ def _lib():
         for name in ("ws_conv3d_fwd", "ws_conv3d_fwd_algo", "ws_conv3d_flip_weights", "ws_conv3d_bwd_weight",
                      "ws_conv3d_bwd_weight_algo", "ws_avgpool2", "ws_avgpool2_bwd", "ws_upsample2",
                      "ws_upsample2_bwd", "ws_relu_bwd", "ws_mse_loss", "ws_adam",
-                     "ws_to_bf16", "ws_tc_status"):
+                     "ws_to_bf16", "ws_tc_status", "ws_conv3d_plan"):
             getattr(L, name).restype = ctypes.c_int
         _sig_done = True
     return L
@@ -98,6 +99,26 @@ def ws_conv3d_bwd_weight_algo(algo: str) -> str:
     if prev < 0:
         raise WsError(f"ws_conv3d_bwd_weight_algo rejected {algo}")
     return names[prev]
+
+
+_FWD_PLAN = ("persistent", "by", "nyt", "pitch", "ntiles", "stages", "cols", "per_sm", "a_half", "stage_bytes",
+             "tx_bytes", "smem", "grid", "buf_cols")
+_WGRAD_PLAN = ("dz", "by", "nyb", "pitch", "ksteps", "J", "ci_blk", "ntile", "npb", "kpb", "stages", "cols",
+               "region", "stage_bytes", "smem", "grid_y")
+
+
+def ws_conv3d_plan(which: str, N: int, D: int, H: int, W: int, Ci: int, Co: int):
+    """Tiling of the resident-tile kernels for a 3x3x3 convolution ("fwd" or
+    "wgrad") under the current kernel choice, as a dict; None where the
+    gathered kernel would run.  Host only."""
+    names = _FWD_PLAN if which == "fwd" else _WGRAD_PLAN
+    out = (ctypes.c_longlong * 16)()
+    n = _lib().ws_conv3d_plan(0 if which == "fwd" else 1, N, D, H, W, Ci, Co, out, 16)
+    if n == -1:
+        return None
+    if n < 0:
+        raise WsError(f"ws_conv3d_plan rejected {which} {(N, D, H, W, Ci, Co)}")
+    return dict(zip(names, out[:n]))
 
 
 def ws_conv3d_flip_weights(w, wf):
