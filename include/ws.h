@@ -6,7 +6,9 @@
  * the paper has no counterpart (it is a systems layer on top of the method).
  *
  * Conventions
- *  - All pointers are DEVICE pointers owned by the caller; nothing allocates.
+ *  - Tensor pointers are DEVICE pointers owned by the caller.  The library
+ *    allocates only the weight gradient's workspace (ws_conv3d_bwd_weight);
+ *    ws_conv3d_plan writes a HOST array.
  *  - Activations are channels-last BF16: element (n, z, y, x, c) of a tensor
  *    with row stride ld (>= channels) is at ((((n*D + z)*H + y)*W + x)*ld + c);
  *    a channel offset is applied by passing a pointer into the row.  Channel
@@ -16,7 +18,8 @@
  *    padding, stride 1); biases and weight gradients are FP32.
  *  - Work is queued on `stream` (cudaStream_t, NULL = legacy default) without
  *    synchronisation.  Return value: 0 ok, 1 invalid argument (nothing
- *    launched), 2 CUDA launch error.
+ *    launched), 2 CUDA launch error; the kernel-choice and plan queries
+ *    document their own.
  */
 #ifndef WS_H
 #define WS_H
